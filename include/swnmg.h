@@ -1,0 +1,167 @@
+/*
+ * swnmg.h -- C ABI of the GB300 Newton multigrid library for steady shallow
+ * water flow with topography and wet/dry areas (Wu & Tang, arXiv:1608.06721).
+ *
+ * The problem (Section 2.2): given a uniform 1D or 2D Cartesian mesh, the bed
+ * z at cell centres, boundary data and an initial state, find the cell
+ * averages U with R(U) = 0, where R is the well-balanced finite-volume
+ * residual of eq. Res (eq. DSeqs with eq. totalFlux).
+ *
+ * Conventions for every entry point:
+ *   - cell index i = ix + nx*iy (x fastest); 1D problems have ny = 1;
+ *   - states and vectors are SoA device arrays of ncomp*n doubles, component c
+ *     of cell i at [c*n + i]; 1D: (h, hu), 2D: (h, hu, hv);
+ *   - device pointers are owned by the caller and must stay valid for the
+ *     call; the context owns its workspace (allocated in swnmg_create, freed
+ *     in swnmg_destroy);
+ *   - all work is issued on the stream given to swnmg_create; a call returns
+ *     after its results are complete on that stream unless stated otherwise;
+ *   - functions never abort or trap: failures return a status code and
+ *     swnmg_last_error() describes the last failure of that context;
+ *   - there is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns SWNMG_ERR_CUDA.
+ */
+#ifndef SWNMG_H
+#define SWNMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+#define SWNMG_API extern "C" __attribute__((visibility("default")))
+#else
+#define SWNMG_API __attribute__((visibility("default")))
+#endif
+
+typedef enum {
+  SWNMG_OK = 0,
+  SWNMG_ERR_ARG = 1,            /* invalid argument or unsupported size */
+  SWNMG_ERR_CUDA = 2,           /* CUDA runtime error (text in swnmg_last_error) */
+  SWNMG_ERR_NOT_CONVERGED = 3,  /* max_newton reached */
+  SWNMG_ERR_NONFINITE = 4,      /* NaN/Inf in the state or residual */
+  SWNMG_ERR_DIVERGED = 5,       /* sum ||R_i||_1 grew 1e6x above its minimum */
+  SWNMG_ERR_TIMEOUT = 6,        /* a device-side wait ran out of its bound */
+  SWNMG_ERR_OOM = 7             /* device allocation failed */
+} swnmg_status;
+
+/* boundary kinds, Remark 2.3 */
+enum {
+  SWNMG_BC_WALL_REFLECT = 0,     /* h_g = h_I, u_n,g = -u_n,I, u_tau,g = u_tau,I */
+  SWNMG_BC_WALL_SLIP = 1,        /* h_g = h_I, u_n,g = 0, u_tau,g = u_tau,I */
+  SWNMG_BC_INFLOW_DISCHARGE = 2, /* subcritical inflow: discharge q and u_tau prescribed */
+  SWNMG_BC_OUTFLOW_DEPTH = 3,    /* subcritical outflow: depth h prescribed */
+  SWNMG_BC_SUPER_INFLOW = 4,     /* supercritical inflow: h, q, u_tau prescribed */
+  SWNMG_BC_SUPER_OUTFLOW = 5     /* supercritical outflow: ghost = interior */
+};
+
+/* numerical fluxes, Remark 2.2 */
+enum { SWNMG_FLUX_HLL = 0, SWNMG_FLUX_HLLC = 1, SWNMG_FLUX_LLF = 2 };
+enum { SWNMG_INIT_CASCADE = 0, SWNMG_INIT_NONE = 1 };   /* Algorithm 1 Step 1, or warm start */
+enum { SWNMG_PREC_FP64 = 0, SWNMG_PREC_MIXED = 1 };     /* MIXED: FP32 multigrid inner solve */
+
+/* Boundary data of one side.  q is the discharge along the +axis direction
+ * (hu on the W/E sides, hv on S/N), so an inflow through the west side has
+ * q > 0; ut is the prescribed tangential velocity. */
+typedef struct { int32_t kind; double h, q, ut; } swnmg_bc;
+
+/* Uniform mesh on [x0,x1] x [y0,y1] (1D: [x0,x1], ny = 1), gravity g,
+ * boundary sides ordered W, E, S, N.  nx (and ny) must be divisible by
+ * 2^n_levels (the coarse meshes aggregate 2 or 2x2 cells, Section 2.3). */
+typedef struct {
+  int32_t dim, nx, ny;
+  double x0, x1, y0, y1, g;
+  swnmg_bc bc[4];
+} swnmg_problem;
+
+/* Solver parameters; swnmg_default_params gives the paper's values
+ * (Section 3 preamble): alpha = 3, fd_eps = 1e-8, tau = 1, h_eps = 1e-6,
+ * eps_r = 0.03, eps_p = 0.2, N_mg = 2 (1D) / 3 (2D), N_L = 3, V-cycle.
+ *   llf_wetdry    1: add eps_r sqrt(g max h) to the LLF speed on every edge
+ *   tol           stop when sum_i ||R_i||_1 < tol (Step 3)
+ *   nu1, nu2      symmetric block-SGS sweeps before/after the coarse correction
+ *   gamma         1: V-cycle, 2: W-cycle (Algorithm 0)
+ *   coarse_sweeps 2D coarsest level: this many symmetric SGS sweeps
+ *                 (1D coarsest levels are solved exactly)
+ *   max_blusgs    cap of BLU-SGS sweeps per level in Step 1 */
+typedef struct {
+  int32_t flux, llf_wetdry;
+  double alpha, fd_eps, tau, h_eps, eps_r, eps_p, tol;
+  int32_t n_levels, n_mg, nu1, nu2, gamma, coarse_sweeps, max_newton, max_blusgs,
+      init_mode, precision;
+} swnmg_params;
+
+#define SWNMG_HIST 512
+typedef struct {
+  int32_t status, n_newton, n_vcycles;
+  int32_t blusgs_sweeps[16];     /* Step 1 sweeps per level */
+  double init_res, final_res;    /* sum ||R_i||_1 before Step 2 and at exit */
+  double res_hist[SWNMG_HIST];   /* sum ||R_i||_1 after Newton step k+1 */
+  double ms_step1, ms_newton;    /* wall time of Step 1 and of Steps 2-3 */
+} swnmg_stats;
+
+typedef struct swnmg_ctx swnmg_ctx;
+
+/* Fills *out with the paper's parameters for dim (1 or 2). */
+SWNMG_API swnmg_status swnmg_default_params(int32_t dim, swnmg_params* out);
+
+/* Creates a solver context for one problem: validates sizes, allocates the
+ * operator hierarchy and workspace on the current device, copies z_dev
+ * (n doubles) and builds the coarse beds by averaging (Algorithm 1, Step 1).
+ * stream: a cudaStream_t (NULL = legacy default stream). */
+SWNMG_API swnmg_status swnmg_create(const swnmg_problem* prob, const swnmg_params* prm,
+                                    const double* z_dev, void* stream, swnmg_ctx** out);
+
+SWNMG_API swnmg_status swnmg_destroy(swnmg_ctx* ctx);
+
+/* Text of the last failure of ctx (static storage when ctx is NULL). */
+SWNMG_API const char* swnmg_last_error(const swnmg_ctx* ctx);
+
+/* Replaces the parameters; n_levels, precision and dim-dependent sizes must
+ * not change (SWNMG_ERR_ARG otherwise). */
+SWNMG_API swnmg_status swnmg_set_params(swnmg_ctx* ctx, const swnmg_params* prm);
+
+/* eq. Res on the finest mesh: R_dev (ncomp*n) = R(U_dev); rnorm_dev (n,
+ * nullable) = ||R_i||_1; l1_host (nullable) = sum_i ||R_i||_1 (this one
+ * synchronises the stream). */
+SWNMG_API swnmg_status swnmg_residual(swnmg_ctx* ctx, const double* U_dev, double* R_dev,
+                                      double* rnorm_dev, double* l1_host);
+
+/* eq. NewtonREG assembled at U_dev: finite-difference blocks (eq. NumerDiff,
+ * boundary edges with the ghost recomputed, epsilon = fd_eps) plus
+ * alpha ||R_i||_1 on the diagonal, the Galerkin hierarchy of eq. ProjectAR and
+ * the block LU factors, all kept in ctx for swnmg_vcycle / swnmg_sgs_sweep. */
+SWNMG_API swnmg_status swnmg_jacobian(swnmg_ctx* ctx, const double* U_dev);
+
+/* Copies the level-l operator to host memory in the layout
+ * out[((i*5 + b)*nc + s)*nc + k], b = 0 diagonal (with the regularisation),
+ * 1 W, 2 E, 3 S, 4 N (zero on the boundary); FP32 blocks are widened. */
+SWNMG_API swnmg_status swnmg_get_blocks(swnmg_ctx* ctx, int32_t level, double* host_out);
+
+/* Runs ncycles of Algorithm 0 (gamma-cycle, block SGS smoothing, restriction
+ * and Galerkin operators of eq. ProjectAR, correction of eq. correction) on
+ * A dU = rhs with the operators of the last swnmg_jacobian; dU_dev is the
+ * initial guess and the result (ncomp*n doubles; FP32 internally in MIXED). */
+SWNMG_API swnmg_status swnmg_vcycle(swnmg_ctx* ctx, const double* rhs_dev, double* dU_dev,
+                                    int32_t ncycles);
+
+/* One block Gauss-Seidel sweep (forward = lexicographic, 0 = reverse) of
+ * the level-l operator on x_dev (ncomp*n_l doubles) for right-hand side
+ * rhs_dev; the smoother of Section 2.3, exposed for testing. */
+SWNMG_API swnmg_status swnmg_sgs_sweep(swnmg_ctx* ctx, int32_t level, const double* rhs_dev,
+                                       double* x_dev, int32_t forward);
+
+/* nsweeps symmetric BLU-SGS sweeps (Algorithm 1, Steps 1 and 2.1) on U_dev
+ * at level l (ncomp*n_l doubles, bed = the averaged level-l bed):
+ * U_i <- U_i - (alpha||R_i||_1 I + dR_i/dU_i)^{-1} R_i in lexicographic order
+ * then reverse, each followed by the dry reset of Remark 2.5. */
+SWNMG_API swnmg_status swnmg_blusgs(swnmg_ctx* ctx, double* U_dev, int32_t level,
+                                    int32_t nsweeps);
+
+/* Algorithm 1 (NMGM): U_dev holds the initial data on entry and the steady
+ * state on return; st (nullable) receives the counters and residual history.
+ * Returns SWNMG_OK on convergence (sum ||R_i||_1 < tol). */
+SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* ctx, double* U_dev, swnmg_stats* st);
+
+/* Number of cells of level l (0 if l is out of range). */
+SWNMG_API int64_t swnmg_level_cells(const swnmg_ctx* ctx, int32_t level);
+
+#endif /* SWNMG_H */

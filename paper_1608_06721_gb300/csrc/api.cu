@@ -1,0 +1,535 @@
+// api.cu -- the C ABI (include/swnmg.h): context, operator hierarchy and the
+// host side of Algorithm 1 (NMGM) and Algorithm 0 (gamma-cycle).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+#include "../../include/swnmg.h"
+
+using namespace swnmg;
+
+namespace {
+
+struct Level {
+  int nx = 0, ny = 0, n = 0;
+  double ex = 0, ey = 0;
+  double* z = nullptr;      // bed at cell centres
+  double* U = nullptr;      // Step 1 state (levels >= 1)
+  void* blk = nullptr;      // 5 blocks (raw diagonal first), working precision
+  void* lu = nullptr;       // LU of the diagonal
+  int8_t* piv = nullptr;
+  void* b = nullptr;        // right-hand side of A x = b
+  void* x = nullptr;        // iterate
+};
+
+const char* status_text(swnmg_status s) {
+  switch (s) {
+    case SWNMG_OK: return "ok";
+    case SWNMG_ERR_ARG: return "invalid argument";
+    case SWNMG_ERR_CUDA: return "CUDA error";
+    case SWNMG_ERR_NOT_CONVERGED: return "not converged";
+    case SWNMG_ERR_NONFINITE: return "non-finite state or residual";
+    case SWNMG_ERR_DIVERGED: return "diverged";
+    case SWNMG_ERR_TIMEOUT: return "device wait timed out";
+    case SWNMG_ERR_OOM: return "out of device memory";
+  }
+  return "unknown";
+}
+
+char g_err[512] = "";
+
+}  // namespace
+
+struct swnmg_ctx {
+  swnmg_problem prob;
+  swnmg_params prm;
+  int nc = 0, nl = 0, fp32 = 0;
+  size_t wsz = 8;           // bytes per working-precision value
+  cudaStream_t st = nullptr;
+  Level lv[13];
+  double* R = nullptr;      // residual scratch (level-0 size)
+  double* rn = nullptr;     // ||R_i||_1
+  double* eb = nullptr;     // per-edge Jacobian pieces (level-0 size)
+  double* red = nullptr;    // reduction partials (1024) + result
+  double* band = nullptr;   // exact coarse-solve scratch
+  int* derr = nullptr;
+  double* hbuf = nullptr;   // pinned host scalar
+  bool coarse_exact = false;
+  std::string err;
+};
+
+namespace {
+
+swnmg_status fail(swnmg_ctx* c, swnmg_status s, const std::string& msg) {
+  std::string m = std::string(status_text(s)) + ": " + msg;
+  if (c) c->err = m;
+  snprintf(g_err, sizeof g_err, "%s", m.c_str());
+  return s;
+}
+
+#define CUDA_TRY(ctx, expr)                                                          \
+  do {                                                                               \
+    cudaError_t e_ = (expr);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? SWNMG_ERR_OOM : SWNMG_ERR_CUDA, \
+                  std::string(#expr) + " -> " + cudaGetErrorString(e_));              \
+  } while (0)
+
+#define LAUNCH_CHECK(ctx) CUDA_TRY(ctx, cudaGetLastError())
+
+DevLevel dev_level(const swnmg_ctx* c, int l) {
+  DevLevel L;
+  L.dim = c->prob.dim;
+  L.nc = c->nc;
+  L.nx = c->lv[l].nx;
+  L.ny = c->lv[l].ny;
+  L.n = c->lv[l].n;
+  L.ex = c->lv[l].ex;
+  L.ey = c->lv[l].ey;
+  L.flux = c->prm.flux;
+  L.llf_wetdry = c->prm.llf_wetdry;
+  L.g = c->prob.g;
+  L.half_g = 0.5 * c->prob.g;
+  L.h_eps = c->prm.h_eps;
+  L.eps_r = c->prm.eps_r;
+  L.alpha = c->prm.alpha;
+  L.eps = c->prm.fd_eps;
+  L.reps = 1.0 / c->prm.fd_eps;
+  for (int s = 0; s < 4; ++s) {
+    L.bc[s].kind = c->prob.bc[s].kind;
+    L.bc[s].h = c->prob.bc[s].h;
+    L.bc[s].q = c->prob.bc[s].q;
+    L.bc[s].ut = c->prob.bc[s].ut;
+  }
+  return L;
+}
+
+swnmg_status check_params(const swnmg_problem* p, const swnmg_params* q) {
+  if (q->flux < 0 || q->flux > 2) return SWNMG_ERR_ARG;
+  if (p->dim == 1 && q->flux == SWNMG_FLUX_HLLC) return SWNMG_ERR_ARG;
+  if (!(q->fd_eps > 0) || !(q->h_eps > 0) || q->alpha < 0) return SWNMG_ERR_ARG;
+  if (q->n_levels < 0 || q->n_levels > 12 || q->n_mg < 0 || q->nu1 < 0 || q->nu2 < 0) return SWNMG_ERR_ARG;
+  if (q->gamma < 1 || q->gamma > 2 || q->max_newton < 0 || q->max_blusgs < 0) return SWNMG_ERR_ARG;
+  if (q->precision != SWNMG_PREC_FP64 && q->precision != SWNMG_PREC_MIXED) return SWNMG_ERR_ARG;
+  if (q->init_mode != SWNMG_INIT_CASCADE && q->init_mode != SWNMG_INIT_NONE) return SWNMG_ERR_ARG;
+  const int m = 1 << q->n_levels;
+  if (p->nx % m) return SWNMG_ERR_ARG;
+  if (p->dim == 2 && p->ny % m) return SWNMG_ERR_ARG;
+  return SWNMG_OK;
+}
+
+// sum_i v_i over n doubles (fixed-order device reduction), synchronises
+swnmg_status device_sum(swnmg_ctx* c, const double* v, int n, double* out) {
+  launch_sum(v, n, c->red, c->red + 1024, c->st);
+  LAUNCH_CHECK(c);
+  CUDA_TRY(c, cudaMemcpyAsync(c->hbuf, c->red + 1024, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  *out = *c->hbuf;
+  return SWNMG_OK;
+}
+
+swnmg_status level_residual_sum(swnmg_ctx* c, int l, const double* U, double* out) {
+  DevLevel L = dev_level(c, l);
+  launch_residual(L, c->lv[l].z, U, c->R, c->rn, c->eb, c->st);
+  LAUNCH_CHECK(c);
+  return device_sum(c, c->rn, L.n, out);
+}
+
+// Algorithm 0 on level l with lv[l].b, lv[l].x
+swnmg_status coarse_solve(swnmg_ctx* c, int l) {
+  Level& v = c->lv[l];
+  if (c->coarse_exact) {
+    launch_coarse_exact(c->nc, v.nx, v.ny, v.blk, v.b, v.x, c->band, c->derr, c->fp32, c->st);
+    LAUNCH_CHECK(c);
+    return SWNMG_OK;
+  }
+  for (int k = 0; k < c->prm.coarse_sweeps; ++k) {
+    launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, 1, c->fp32, c->st);
+    launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, 0, c->fp32, c->st);
+  }
+  LAUNCH_CHECK(c);
+  return SWNMG_OK;
+}
+
+swnmg_status smooth(swnmg_ctx* c, int l, int nsym) {
+  Level& v = c->lv[l];
+  for (int k = 0; k < nsym; ++k) {
+    launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, 1, c->fp32, c->st);
+    launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, 0, c->fp32, c->st);
+  }
+  LAUNCH_CHECK(c);
+  return SWNMG_OK;
+}
+
+swnmg_status mg_cycle(swnmg_ctx* c, int l) {
+  if (l == c->nl) return coarse_solve(c, l);
+  swnmg_status s;
+  if ((s = smooth(c, l, c->prm.nu1)) != SWNMG_OK) return s;
+  Level& v = c->lv[l];
+  Level& w = c->lv[l + 1];
+  launch_restrict(c->prob.dim, c->nc, v.nx, v.ny, v.blk, v.b, v.x, w.b, c->fp32, c->st);
+  launch_fill(w.x, c->fp32, (long long)c->nc * w.n, c->st);
+  LAUNCH_CHECK(c);
+  const int gam = (l == 0) ? 1 : c->prm.gamma;
+  for (int k = 0; k < gam; ++k)
+    if ((s = mg_cycle(c, l + 1)) != SWNMG_OK) return s;
+  launch_prolong(c->prob.dim, c->nc, v.nx, v.ny, w.x, v.x, c->fp32, c->st);
+  LAUNCH_CHECK(c);
+  return smooth(c, l, c->prm.nu2);
+}
+
+swnmg_status assemble(swnmg_ctx* c, const double* U) {
+  DevLevel L = dev_level(c, 0);
+  launch_jacobian(L, c->lv[0].z, U, c->R, c->rn, c->eb, c->lv[0].blk, c->fp32, c->st);
+  LAUNCH_CHECK(c);
+  for (int l = 0; l < c->nl; ++l)
+    launch_galerkin(c->prob.dim, c->nc, c->lv[l].nx, c->lv[l].ny, c->lv[l].blk, c->lv[l + 1].blk,
+                    c->fp32, c->st);
+  for (int l = 0; l <= c->nl; ++l)
+    launch_lu_factor(c->lv[l].n, c->nc, c->lv[l].blk, c->lv[l].lu, c->lv[l].piv, c->fp32, c->st);
+  LAUNCH_CHECK(c);
+  return SWNMG_OK;
+}
+
+void free_ctx(swnmg_ctx* c) {
+  for (auto& v : c->lv) {
+    if (v.z) cudaFree(v.z);
+    if (v.U) cudaFree(v.U);
+    if (v.blk) cudaFree(v.blk);
+    if (v.lu) cudaFree(v.lu);
+    if (v.piv) cudaFree(v.piv);
+    if (v.b) cudaFree(v.b);
+    if (v.x) cudaFree(v.x);
+  }
+  if (c->R) cudaFree(c->R);
+  if (c->rn) cudaFree(c->rn);
+  if (c->eb) cudaFree(c->eb);
+  if (c->red) cudaFree(c->red);
+  if (c->band) cudaFree(c->band);
+  if (c->derr) cudaFree(c->derr);
+  if (c->hbuf) cudaFreeHost(c->hbuf);
+}
+
+}  // namespace
+
+// ============================== C ABI =========================================
+
+SWNMG_API swnmg_status swnmg_default_params(int32_t dim, swnmg_params* o) {
+  if (!o || (dim != 1 && dim != 2)) return fail(nullptr, SWNMG_ERR_ARG, "dim must be 1 or 2");
+  memset(o, 0, sizeof *o);
+  o->flux = dim == 2 ? SWNMG_FLUX_HLLC : SWNMG_FLUX_HLL;
+  o->llf_wetdry = 0;
+  o->alpha = 3.0;
+  o->fd_eps = 1e-8;
+  o->tau = 1.0;
+  o->h_eps = 1e-6;
+  o->eps_r = 0.03;
+  o->eps_p = 0.2;
+  o->tol = 1e-10;
+  o->n_levels = 3;
+  o->n_mg = dim == 2 ? 3 : 2;
+  o->nu1 = 1;
+  o->nu2 = 1;
+  o->gamma = 1;
+  o->coarse_sweeps = 8;
+  o->max_newton = 200;
+  o->max_blusgs = 1000;
+  o->init_mode = SWNMG_INIT_CASCADE;
+  o->precision = SWNMG_PREC_FP64;
+  return SWNMG_OK;
+}
+
+SWNMG_API const char* swnmg_last_error(const swnmg_ctx* c) { return c ? c->err.c_str() : g_err; }
+
+SWNMG_API int64_t swnmg_level_cells(const swnmg_ctx* c, int32_t l) {
+  if (!c || l < 0 || l > c->nl) return 0;
+  return c->lv[l].n;
+}
+
+SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* q,
+                                    const double* z_dev, void* stream, swnmg_ctx** out) {
+  if (!p || !q || !z_dev || !out) return fail(nullptr, SWNMG_ERR_ARG, "null pointer");
+  *out = nullptr;
+  if ((p->dim != 1 && p->dim != 2) || p->nx < 1 || (p->dim == 2 && p->ny < 1) || !(p->g > 0) ||
+      !(p->x1 > p->x0) || (p->dim == 2 && !(p->y1 > p->y0)))
+    return fail(nullptr, SWNMG_ERR_ARG, "bad mesh or gravity");
+  if ((long long)p->nx * (p->dim == 2 ? p->ny : 1) > (1LL << 28))
+    return fail(nullptr, SWNMG_ERR_ARG, "more than 2^28 cells");
+  for (int s = 0; s < 4; ++s)
+    if (p->bc[s].kind < 0 || p->bc[s].kind > 5) return fail(nullptr, SWNMG_ERR_ARG, "bad boundary kind");
+  if (check_params(p, q) != SWNMG_OK)
+    return fail(nullptr, SWNMG_ERR_ARG, "bad parameters or mesh not divisible by 2^n_levels");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, SWNMG_ERR_CUDA, "no CUDA device");
+  swnmg_ctx* c = new swnmg_ctx();
+  c->prob = *p;
+  if (p->dim == 1) c->prob.ny = 1;
+  c->prm = *q;
+  c->nc = p->dim == 2 ? 3 : 2;
+  c->nl = q->n_levels;
+  c->fp32 = q->precision == SWNMG_PREC_MIXED;
+  c->wsz = c->fp32 ? 4 : 8;
+  c->st = (cudaStream_t)stream;
+  const double dx = (p->x1 - p->x0) / p->nx;
+  const double dy = p->dim == 2 ? (p->y1 - p->y0) / p->ny : 0.0;
+  swnmg_status rc = SWNMG_OK;
+#define ALLOC(ptr, bytes)                                                             \
+  do {                                                                                \
+    cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                             \
+    if (e_ != cudaSuccess) {                                                          \
+      rc = fail(c, SWNMG_ERR_OOM, std::string("cudaMalloc ") + cudaGetErrorString(e_)); \
+      goto fail_out;                                                                  \
+    }                                                                                 \
+  } while (0)
+  for (int l = 0; l <= c->nl; ++l) {
+    Level& v = c->lv[l];
+    v.nx = p->nx >> l;
+    v.ny = p->dim == 2 ? (p->ny >> l) : 1;
+    v.n = v.nx * v.ny;
+    if (p->dim == 2) {
+      const double s = (double)(1 << l);
+      v.ex = dy * s;
+      v.ey = dx * s;
+    } else {
+      v.ex = 1.0;
+      v.ey = 0.0;
+    }
+    const size_t n = v.n;
+    ALLOC(v.z, n * sizeof(double));
+    if (l > 0) ALLOC(v.U, n * c->nc * sizeof(double));
+    ALLOC(v.blk, n * 5 * c->nc * c->nc * c->wsz);
+    ALLOC(v.lu, n * LU_E * c->wsz);
+    ALLOC(v.piv, n);
+    ALLOC(v.b, n * c->nc * c->wsz);
+    ALLOC(v.x, n * c->nc * c->wsz);
+  }
+  {
+    const Level& v0 = c->lv[0];
+    const size_t n_e = (size_t)(v0.nx + 1) * v0.ny + (p->dim == 2 ? (size_t)v0.nx * (v0.ny + 1) : 0);
+    ALLOC(c->R, (size_t)v0.n * c->nc * sizeof(double));
+    ALLOC(c->rn, (size_t)v0.n * sizeof(double));
+    ALLOC(c->eb, n_e * (2 * c->nc + 2 * c->nc * c->nc) * sizeof(double));
+    ALLOC(c->red, 1032 * sizeof(double));
+    ALLOC(c->derr, sizeof(int));
+  }
+  {
+    const Level& vc = c->lv[c->nl];
+    c->coarse_exact = (p->dim == 1) || (q->coarse_sweeps <= 0);
+    if (c->coarse_exact) {
+      const long long m = (long long)vc.n * c->nc;
+      const long long ml = c->nc * (vc.ny > 1 ? vc.nx : 1) + c->nc - 1;
+      const long long words = m * (3 * ml + 1) + 2 * m;
+      if (words > (16LL << 20)) {
+        rc = fail(c, SWNMG_ERR_ARG, "coarsest level too large for the exact solve; use more levels "
+                                    "or coarse_sweeps > 0");
+        goto fail_out;
+      }
+      ALLOC(c->band, (size_t)words * sizeof(double));
+    }
+  }
+  if (cudaMallocHost((void**)&c->hbuf, 16) != cudaSuccess) {
+    rc = fail(c, SWNMG_ERR_OOM, "cudaMallocHost");
+    goto fail_out;
+  }
+#undef ALLOC
+  if (cudaMemcpyAsync(c->lv[0].z, z_dev, (size_t)c->lv[0].n * sizeof(double), cudaMemcpyDeviceToDevice,
+                      c->st) != cudaSuccess) {
+    rc = fail(c, SWNMG_ERR_CUDA, "copy of z");
+    goto fail_out;
+  }
+  for (int l = 0; l < c->nl; ++l)
+    launch_average(p->dim, c->lv[l].nx, c->lv[l].ny, 1, c->lv[l].z, c->lv[l + 1].z, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    rc = fail(c, SWNMG_ERR_CUDA, "bed averaging");
+    goto fail_out;
+  }
+  *out = c;
+  return SWNMG_OK;
+fail_out:
+  snprintf(g_err, sizeof g_err, "%s", c->err.c_str());
+  free_ctx(c);
+  delete c;
+  return rc;
+}
+
+SWNMG_API swnmg_status swnmg_destroy(swnmg_ctx* c) {
+  if (!c) return SWNMG_ERR_ARG;
+  cudaStreamSynchronize(c->st);
+  free_ctx(c);
+  delete c;
+  return SWNMG_OK;
+}
+
+SWNMG_API swnmg_status swnmg_set_params(swnmg_ctx* c, const swnmg_params* q) {
+  if (!c || !q) return fail(c, SWNMG_ERR_ARG, "null pointer");
+  if (q->n_levels != c->prm.n_levels || q->precision != c->prm.precision)
+    return fail(c, SWNMG_ERR_ARG, "n_levels and precision are fixed at create");
+  if (check_params(&c->prob, q) != SWNMG_OK) return fail(c, SWNMG_ERR_ARG, "bad parameters");
+  const bool exact = (c->prob.dim == 1) || (q->coarse_sweeps <= 0);
+  if (exact != c->coarse_exact) return fail(c, SWNMG_ERR_ARG, "coarse-solve kind is fixed at create");
+  c->prm = *q;
+  return SWNMG_OK;
+}
+
+SWNMG_API swnmg_status swnmg_residual(swnmg_ctx* c, const double* U, double* R, double* rn,
+                                      double* l1_host) {
+  if (!c || !U || !R) return fail(c, SWNMG_ERR_ARG, "null pointer");
+  DevLevel L = dev_level(c, 0);
+  double* rnp = rn ? rn : c->rn;
+  launch_residual(L, c->lv[0].z, U, R, rnp, c->eb, c->st);
+  LAUNCH_CHECK(c);
+  if (l1_host) return device_sum(c, rnp, L.n, l1_host);
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SWNMG_OK;
+}
+
+SWNMG_API swnmg_status swnmg_jacobian(swnmg_ctx* c, const double* U) {
+  if (!c || !U) return fail(c, SWNMG_ERR_ARG, "null pointer");
+  swnmg_status s = assemble(c, U);
+  if (s != SWNMG_OK) return s;
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SWNMG_OK;
+}
+
+SWNMG_API swnmg_status swnmg_get_blocks(swnmg_ctx* c, int32_t level, double* host_out) {
+  if (!c || !host_out || level < 0 || level > c->nl) return fail(c, SWNMG_ERR_ARG, "bad level");
+  const Level& v = c->lv[level];
+  const size_t cnt = (size_t)v.n * 5 * c->nc * c->nc;
+  double* tmp = nullptr;
+  CUDA_TRY(c, cudaMalloc((void**)&tmp, cnt * sizeof(double)));
+  launch_blocks_export(v.n, c->nc, v.blk, c->fp32, tmp, c->st);
+  cudaError_t e1 = cudaGetLastError();
+  cudaError_t e2 = cudaMemcpyAsync(host_out, tmp, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  cudaError_t e3 = cudaStreamSynchronize(c->st);
+  cudaFree(tmp);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+    return fail(c, SWNMG_ERR_CUDA, "block export");
+  return SWNMG_OK;
+}
+
+SWNMG_API swnmg_status swnmg_vcycle(swnmg_ctx* c, const double* rhs, double* dU, int32_t ncycles) {
+  if (!c || !rhs || !dU || ncycles < 0) return fail(c, SWNMG_ERR_ARG, "bad argument");
+  Level& v = c->lv[0];
+  const long long m = (long long)v.n * c->nc;
+  launch_convert(rhs, 0, v.b, c->fp32, m, 1.0, c->st);
+  launch_convert(dU, 0, v.x, c->fp32, m, 1.0, c->st);
+  LAUNCH_CHECK(c);
+  for (int k = 0; k < ncycles; ++k) {
+    swnmg_status s = mg_cycle(c, 0);
+    if (s != SWNMG_OK) return s;
+  }
+  launch_convert(v.x, c->fp32, dU, 0, m, 1.0, c->st);
+  LAUNCH_CHECK(c);
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SWNMG_OK;
+}
+
+SWNMG_API swnmg_status swnmg_sgs_sweep(swnmg_ctx* c, int32_t level, const double* rhs, double* x,
+                                       int32_t forward) {
+  if (!c || !rhs || !x || level < 0 || level > c->nl) return fail(c, SWNMG_ERR_ARG, "bad argument");
+  Level& v = c->lv[level];
+  const long long m = (long long)v.n * c->nc;
+  launch_convert(rhs, 0, v.b, c->fp32, m, 1.0, c->st);
+  launch_convert(x, 0, v.x, c->fp32, m, 1.0, c->st);
+  launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward ? 1 : 0, c->fp32, c->st);
+  launch_convert(v.x, c->fp32, x, 0, m, 1.0, c->st);
+  LAUNCH_CHECK(c);
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SWNMG_OK;
+}
+
+SWNMG_API swnmg_status swnmg_blusgs(swnmg_ctx* c, double* U, int32_t level, int32_t nsweeps) {
+  if (!c || !U || level < 0 || level > c->nl || nsweeps < 0) return fail(c, SWNMG_ERR_ARG, "bad argument");
+  DevLevel L = dev_level(c, level);
+  for (int k = 0; k < nsweeps; ++k) {
+    launch_blusgs_sweep(L, c->lv[level].z, U, 1, c->st);
+    launch_blusgs_sweep(L, c->lv[level].z, U, 0, c->st);
+  }
+  LAUNCH_CHECK(c);
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SWNMG_OK;
+}
+
+SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) {
+  if (!c || !U) return fail(c, SWNMG_ERR_ARG, "null pointer");
+  swnmg_stats local;
+  swnmg_stats* st = stats ? stats : &local;
+  memset(st, 0, sizeof *st);
+  const int nc = c->nc, NL = c->nl;
+  using clk = std::chrono::steady_clock;
+  auto t0 = clk::now();
+  swnmg_status s;
+  // Step 1: BLU-SGS from the coarsest level to level 1, piecewise-constant
+  // prolongation of the solution (Algorithm 1)
+  if (c->prm.init_mode == SWNMG_INIT_CASCADE && NL > 0) {
+    const double* src = U;
+    for (int l = 0; l < NL; ++l) {
+      launch_average(c->prob.dim, c->lv[l].nx, c->lv[l].ny, nc, src, c->lv[l + 1].U, c->st);
+      src = c->lv[l + 1].U;
+    }
+    LAUNCH_CHECK(c);
+    for (int l = NL; l >= 1; --l) {
+      const double thr = c->prm.eps_p / (double)(1 << l);
+      double res;
+      if ((s = level_residual_sum(c, l, c->lv[l].U, &res)) != SWNMG_OK) return s;
+      int nsw = 0;
+      DevLevel L = dev_level(c, l);
+      while (res >= thr && nsw < c->prm.max_blusgs && std::isfinite(res)) {
+        launch_blusgs_sweep(L, c->lv[l].z, c->lv[l].U, 1, c->st);
+        launch_blusgs_sweep(L, c->lv[l].z, c->lv[l].U, 0, c->st);
+        LAUNCH_CHECK(c);
+        ++nsw;
+        if ((s = level_residual_sum(c, l, c->lv[l].U, &res)) != SWNMG_OK) return s;
+      }
+      if (l < 16) st->blusgs_sweeps[l] = nsw;
+      double* dst = (l - 1 == 0) ? U : c->lv[l - 1].U;
+      launch_inject(c->prob.dim, c->lv[l - 1].nx, c->lv[l - 1].ny, nc, c->lv[l].U, dst, c->st);
+      LAUNCH_CHECK(c);
+    }
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  auto t1 = clk::now();
+  // Steps 2-3: Newton multigrid iteration
+  Level& v0 = c->lv[0];
+  const long long m = (long long)v0.n * nc;
+  const DevLevel L0 = dev_level(c, 0);
+  double res;
+  if ((s = level_residual_sum(c, 0, U, &res)) != SWNMG_OK) return s;
+  st->init_res = res;
+  double best = res;
+  swnmg_status status = SWNMG_ERR_NOT_CONVERGED;
+  int it = 0;
+  while (it < c->prm.max_newton) {
+    if (res < c->prm.tol) { status = SWNMG_OK; break; }
+    launch_blusgs_sweep(L0, v0.z, U, 1, c->st);                    // Step 2.1
+    launch_blusgs_sweep(L0, v0.z, U, 0, c->st);
+    LAUNCH_CHECK(c);
+    if ((s = assemble(c, U)) != SWNMG_OK) return s;                // eq. NewtonREG
+    launch_convert(c->R, 0, v0.b, c->fp32, m, -1.0, c->st);        // b = -R
+    launch_fill(v0.x, c->fp32, m, c->st);
+    LAUNCH_CHECK(c);
+    for (int k = 0; k < c->prm.n_mg; ++k)                          // Step 2.2
+      if ((s = mg_cycle(c, 0)) != SWNMG_OK) return s;
+    launch_newton_update(v0.n, nc, c->prm.tau, c->prm.h_eps, U, v0.x, c->fp32, c->st);   // Step 2.3
+    LAUNCH_CHECK(c);
+    ++it;
+    st->n_vcycles += c->prm.n_mg;
+    if ((s = level_residual_sum(c, 0, U, &res)) != SWNMG_OK) return s;   // Step 3
+    if (it <= SWNMG_HIST) st->res_hist[it - 1] = res;
+    if (!std::isfinite(res)) { status = SWNMG_ERR_NONFINITE; break; }
+    if (res < best) best = res;
+    if (res > 1e6 * best) { status = SWNMG_ERR_DIVERGED; break; }
+  }
+  if (status == SWNMG_ERR_NOT_CONVERGED && res < c->prm.tol) status = SWNMG_OK;
+  auto t2 = clk::now();
+  st->n_newton = it;
+  st->final_res = res;
+  st->status = status;
+  st->ms_step1 = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  st->ms_newton = std::chrono::duration<double, std::milli>(t2 - t1).count();
+  if (status != SWNMG_OK) return fail(c, status, "after " + std::to_string(it) + " Newton steps");
+  return SWNMG_OK;
+}

@@ -1,0 +1,76 @@
+// Internal declarations shared by the CUDA translation units of libswnmg.
+//
+// Device data layout (all SoA, x-fastest cell index i = ix + nx*iy):
+//   state U, residual R, vectors b/x : [c*n + i]
+//   operator blocks of a level       : blk[(b*nc*nc + s*nc + k)*n + i]
+//        b = 0 diagonal (raw, with alpha||R_i||_1), 1 W, 2 E, 3 S, 4 N
+//   LU factors of the diagonal       : lu[e*n + i], e = 0..8 (see LU layout below)
+//        + perm code piv[i] (int8)
+//   per-edge Jacobian pieces          : x-edges (nx+1)*ny then y-edges nx*(ny+1)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swnmg {
+
+// boundary kinds / fluxes (same numbering as the public header)
+enum { BC_REFLECT = 0, BC_SLIP = 1, BC_INFLOW = 2, BC_OUTFLOW = 3, BC_SUPER_IN = 4, BC_SUPER_OUT = 5 };
+enum { FX_HLL = 0, FX_HLLC = 1, FX_LLF = 2 };
+
+struct DevBC { int kind; double h, q, ut; };
+
+// Everything a flux / Jacobian kernel needs about one mesh level.
+struct DevLevel {
+  int dim, nc;            // 1 or 2, components 2 or 3
+  int nx, ny, n;          // cells of this level (ny = 1 in 1D)
+  double ex, ey;          // |x-edge| (W/E sides), |y-edge| (S/N sides); 1D: 1, 0
+  int flux, llf_wetdry;
+  double g, half_g, h_eps, eps_r, alpha, eps, reps;   // reps = 1/eps
+  DevBC bc[4];            // W, E, S, N
+};
+
+// LU layout of a block (n = 2 or 3), partial pivoting, guard for singular
+// pivots.  Solve of D x = b:  y = P b;  y1 -= l10 y0;  y2 -= l20 y0 + l21 y1;
+// x2 = y2 inv22; x1 = (y1 - u12 x2) inv11; x0 = (y0 - u01 x1 - u02 x2) inv00.
+// Entries: 0 l10, 1 l20, 2 l21, 3 u01, 4 u02, 5 u12, 6 inv00, 7 inv11, 8 inv22
+// (inv = 0 marks a singular unknown whose correction is zero).
+// piv = p0 + 3 p1 + 9 p2 with P b = (b[p0], b[p1], b[p2]).
+constexpr int LU_E = 9;
+
+inline int blk_entries(int nc) { return 5 * nc * nc; }
+
+// ---- host-side launch wrappers (flux.cu) ---------------------------------
+void launch_residual(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
+                     double* edge_buf, cudaStream_t st);
+void launch_jacobian(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
+                     double* edge_buf, void* blk, int fp32, cudaStream_t st);
+void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forward,
+                         cudaStream_t st);
+void launch_newton_update(int n, int nc, double tau, double h_eps, double* U, const void* dU,
+                          int dU_fp32, cudaStream_t st);
+void launch_average(int dim, int nxf, int nyf, int ncomp, const double* vf, double* vc,
+                    cudaStream_t st);
+void launch_inject(int dim, int nxf, int nyf, int ncomp, const double* vc, double* vf,
+                   cudaStream_t st);
+
+// ---- host-side launch wrappers (mg.cu) -----------------------------------
+void launch_lu_factor(int n, int nc, const void* blk, void* lu, int8_t* piv, int fp32,
+                      cudaStream_t st);
+void launch_galerkin(int dim, int nc, int nxf, int nyf, const void* bf, void* bc, int fp32,
+                     cudaStream_t st);
+void launch_restrict(int dim, int nc, int nxf, int nyf, const void* blk, const void* b,
+                     const void* x, void* bcoarse, int fp32, cudaStream_t st);
+void launch_prolong(int dim, int nc, int nxf, int nyf, const void* xc, void* xf, int fp32,
+                    cudaStream_t st);
+void launch_sgs_sweep(int nc, int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
+                      const void* b, void* x, int forward, int fp32, cudaStream_t st);
+void launch_coarse_exact(int nc, int nx, int ny, const void* blk, const void* b, void* x,
+                         double* band, int* err, int fp32, cudaStream_t st);
+void launch_sum(const double* v, int n, double* partial, double* out, cudaStream_t st);
+void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n,
+                    double scale, cudaStream_t st);
+void launch_fill(void* dst, int fp32, long long n, cudaStream_t st);
+void launch_blocks_export(int n, int nc, const void* blk, int fp32, double* out, cudaStream_t st);
+
+}  // namespace swnmg

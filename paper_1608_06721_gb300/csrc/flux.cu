@@ -1,0 +1,648 @@
+// flux.cu -- residual, finite-difference Jacobian, BLU-SGS and Newton update
+// kernels (Sections 2.1, 2.2 and 2.4 of Wu & Tang, arXiv:1608.06721).
+//
+// Built with -fmad=false: every product and sum rounds separately, in the
+// fixed evaluation order documented next to each formula, so that R and the
+// finite-difference Jacobian (whose 1/eps = 1e8 amplifies any rounding
+// difference) are reproducible bit for bit.  Divisions and square roots use
+// CUDA's correctly rounded double operators.
+#include "common.cuh"
+
+namespace swnmg {
+
+namespace {
+
+struct Prim { double h, u, v; };   // edge frame: u along +axis, v tangential
+
+__device__ __forceinline__ double dmin(double a, double b) { return (a < b) ? a : b; }
+__device__ __forceinline__ double dmax(double a, double b) { return (a > b) ? a : b; }
+
+// cell velocities from the conserved state: 1/h once, zero below h_eps
+// (a cell with h < h_eps is treated as dry, Remark 2.5)
+__device__ __forceinline__ Prim to_prim(double h, double qa, double qb, double h_eps) {
+  Prim p;
+  p.h = h;
+  if (h >= h_eps) {
+    double r = 1.0 / h;
+    p.u = qa * r;
+    p.v = qb * r;
+  } else {
+    p.u = 0.0;
+    p.v = 0.0;
+  }
+  return p;
+}
+
+// Numerical flux of Remark 2.2 between reconstructed states (hl, ul, vl) and
+// (hr, ur, vr): HLL (eq. HLLflux) with the wet/dry wave speeds, HLLC's contact
+// choice for the tangential flux, or LLF (eq. LLFflux) with the optional
+// wet/dry speed increase.  Both depths zero: zero flux.
+__device__ void num_flux(const DevLevel& L, double hl, double ul, double vl, double hr, double ur,
+                         double vr, double F[3]) {
+  if (hl == 0.0 && hr == 0.0) {
+    F[0] = 0.0; F[1] = 0.0; F[2] = 0.0;
+    return;
+  }
+  const double g = L.g, hg = L.half_g;
+  const double cl = sqrt(g * hl), cr = sqrt(g * hr);
+  const double ql = hl * ul, qr = hr * ur;                 // h u_n of each side
+  const double FL0 = ql, FL1 = ql * ul + hg * (hl * hl), FL2 = ql * vl;
+  const double FR0 = qr, FR1 = qr * ur + hg * (hr * hr), FR2 = qr * vr;
+  const double dU0 = hr - hl, dU1 = qr - ql, dU2 = hr * vr - hl * vl;   // U+ - U-
+  if (L.flux == FX_LLF) {
+    double smax = dmax(fabs(ul) + cl, fabs(ur) + cr);
+    if (L.llf_wetdry) smax = smax + L.eps_r * sqrt(g * dmax(hl, hr));
+    F[0] = ((FL0 + FR0) - smax * dU0) * 0.5;
+    F[1] = ((FL1 + FR1) - smax * dU1) * 0.5;
+    F[2] = ((FL2 + FR2) - smax * dU2) * 0.5;
+    return;
+  }
+  // u_* and sqrt(g h_*) = |t|/2 (h_* = t^2 / (4g))
+  const double us = ((ul + ur) * 0.5 + cl) - cr;
+  const double t = (cl + cr) + (ul - ur) * 0.5;
+  const double cs = fabs(t) * 0.5;
+  const double sL = (hl == 0.0) ? ur - 2.0 * cr : dmin(ul - cl, us - cs);
+  const double sR = (hr == 0.0) ? ul + 2.0 * cl : dmax(ur + cr, us + cs);
+  if (sL >= 0.0) { F[0] = FL0; F[1] = FL1; F[2] = FL2; return; }
+  if (sR <= 0.0) { F[0] = FR0; F[1] = FR1; F[2] = FR2; return; }
+  const double rden = 1.0 / (sR - sL), p = sL * sR;
+  F[0] = ((sR * FL0 - sL * FR0) + p * dU0) * rden;
+  F[1] = ((sR * FL1 - sL * FR1) + p * dU1) * rden;
+  F[2] = ((sR * FL2 - sL * FR2) + p * dU2) * rden;
+  if (L.flux == FX_HLLC) {
+    const double a = hr * (ur - sR), b = hl * (ul - sL);
+    const double sM = (sL * a - sR * b) / (a - b);
+    F[2] = (sM >= 0.0) ? vl * F[0] : vr * F[0];
+  }
+}
+
+// eq. totalFlux with the hydrostatic reconstruction; a is the lower-index
+// side.  out: F (3), g/2 h_{e,-}^2, g/2 h_{e,+}^2.
+__device__ __forceinline__ void edge_eval(const DevLevel& L, Prim a, double za, Prim b, double zb,
+                                          double out[5]) {
+  const double zs = dmax(za, zb);
+  const double tl = (a.h + za) - zs, tr = (b.h + zb) - zs;
+  const double hl = (tl > 0.0) ? tl : 0.0, hr = (tr > 0.0) ? tr : 0.0;
+  num_flux(L, hl, a.u, a.v, hr, b.u, b.v, out);
+  out[3] = L.half_g * (hl * hl);
+  out[4] = L.half_g * (hr * hr);
+}
+
+// Subcritical inflow: celerity c of the ghost from 2c^3 - R c^2 + g qn = 0,
+// Newton from the right, 60 fixed steps.
+__device__ double inflow_celerity(double g, double RI, double qn) {
+  const double gq = g * qn;
+  const double a = fabs(gq);
+  double c = ((RI > 0.0) ? RI : 0.0) + ((a > 1.0) ? a : 1.0);
+  for (int it = 0; it < 60; ++it) {
+    const double f = ((2.0 * c - RI) * c) * c + gq;
+    const double fp = (6.0 * c - 2.0 * RI) * c;
+    if (!(fp > 0.0)) break;
+    c = c - f / fp;
+  }
+  return c;
+}
+
+// Ghost state of Remark 2.3 for boundary side s (0 W, 1 E, 2 S, 3 N) from the
+// interior primitive state; sigma*u is the outward normal velocity.
+__device__ Prim ghost_state(const DevLevel& L, int side, Prim I) {
+  const DevBC& bc = L.bc[side];
+  const double sigma = (side & 1) ? 1.0 : -1.0;
+  const double g = L.g;
+  Prim o;
+  switch (bc.kind) {
+    case BC_SLIP: o.h = I.h; o.u = 0.0; o.v = I.v; break;
+    case BC_INFLOW: {
+      const double qn = sigma * bc.q;
+      const double RI = sigma * I.u + 2.0 * sqrt(g * I.h);
+      const double c = inflow_celerity(g, RI, qn);
+      const double h = (c * c) / g;
+      const double un = (h > 0.0) ? qn / h : 0.0;
+      o.h = h; o.u = sigma * un; o.v = bc.ut;
+      break;
+    }
+    case BC_OUTFLOW: {
+      const double un = (sigma * I.u + 2.0 * sqrt(g * I.h)) - 2.0 * sqrt(g * bc.h);
+      o.h = bc.h; o.u = sigma * un; o.v = I.v;
+      break;
+    }
+    case BC_SUPER_IN: o.h = bc.h; o.u = (bc.h > 0.0) ? bc.q / bc.h : 0.0; o.v = bc.ut; break;
+    case BC_SUPER_OUT: o = I; break;
+    default: o.h = I.h; o.u = -I.u; o.v = I.v; break;   // reflective wall
+  }
+  return o;
+}
+
+// conserved global state (h, hu, hv) -> primitive in the frame of `axis`
+template <int NC>
+__device__ __forceinline__ Prim prim_axis(const DevLevel& L, const double* c, int axis) {
+  if (NC == 2) return to_prim(c[0], c[1], 0.0, L.h_eps);
+  return axis == 0 ? to_prim(c[0], c[1], c[2], L.h_eps) : to_prim(c[0], c[2], c[1], L.h_eps);
+}
+
+// G received by the left and right cell of an edge, in global components:
+// left  (F0, F1 - sL, F2), right -(F0, F1 - sR, F2); y-edges swap the two
+// momentum components back to (hu, hv).
+template <int NC>
+__device__ __forceinline__ void edge_G(const double o[5], int axis, double GL[NC], double GR[NC]) {
+  const double gl1 = o[1] - o[3], gr1 = -(o[1] - o[4]);
+  GL[0] = o[0];
+  GR[0] = -o[0];
+  if (NC == 2) { GL[1] = gl1; GR[1] = gr1; return; }
+  if (axis == 0) {
+    GL[1] = gl1; GL[2] = o[2];
+    GR[1] = gr1; GR[2] = -o[2];
+  } else {
+    GL[1 % NC] = o[2]; GL[2 % NC] = gl1;
+    GR[1 % NC] = -o[2]; GR[2 % NC] = gr1;
+  }
+}
+
+// One edge with conserved states cL / cR (NULL = boundary, ghost computed
+// from the other side); returns G of both cells.
+template <int NC>
+__device__ __forceinline__ void eval_edge_states(const DevLevel& L, int axis, const double* cL,
+                                                 double zL, const double* cR, double zR,
+                                                 double GL[NC], double GR[NC]) {
+  Prim a, b;
+  double za = zL, zb = zR;
+  if (cL && cR) {
+    a = prim_axis<NC>(L, cL, axis);
+    b = prim_axis<NC>(L, cR, axis);
+  } else if (cR) {
+    b = prim_axis<NC>(L, cR, axis);
+    a = ghost_state(L, 2 * axis, b);
+    za = zR;
+  } else {
+    a = prim_axis<NC>(L, cL, axis);
+    b = ghost_state(L, 2 * axis + 1, a);
+    zb = zL;
+  }
+  double o[5];
+  edge_eval(L, a, za, b, zb, o);
+  edge_G<NC>(o, axis, GL, GR);
+}
+
+// edge e -> (axis, left cell, right cell, |e|); -1 marks a boundary side
+__device__ __forceinline__ void edge_cells(const DevLevel& L, int e, int n_xe, int& axis, int& iL,
+                                           int& iR, double& len) {
+  if (e < n_xe) {
+    const int ie = e % (L.nx + 1), iy = e / (L.nx + 1);
+    axis = 0;
+    iL = ie > 0 ? (ie - 1) + L.nx * iy : -1;
+    iR = ie < L.nx ? ie + L.nx * iy : -1;
+    len = L.ex;
+  } else {
+    const int f = e - n_xe, ix = f % L.nx, je = f / L.nx;
+    axis = 1;
+    iL = je > 0 ? ix + L.nx * (je - 1) : -1;
+    iR = je < L.ny ? ix + L.nx * je : -1;
+    len = L.ey;
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void load_c(const double* U, int n, int i, double c[NC]) {
+  for (int s = 0; s < NC; ++s) c[s] = U[s * n + i];
+}
+
+template <typename T>
+__device__ __forceinline__ void st(void* p, long long idx, double v) {
+  static_cast<T*>(p)[idx] = static_cast<T>(v);
+}
+
+// ---- residual: per-edge G, then per-cell sums --------------------------------
+
+template <int NC>
+__global__ void k_res_edges(DevLevel L, const double* __restrict__ z, const double* __restrict__ U,
+                            double* __restrict__ eb, int n_xe, int n_e) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_e) return;
+  int axis, iL, iR;
+  double len;
+  edge_cells(L, e, n_xe, axis, iL, iR, len);
+  double cL[NC], cR[NC], GL[NC], GR[NC];
+  if (iL >= 0) load_c<NC>(U, L.n, iL, cL);
+  if (iR >= 0) load_c<NC>(U, L.n, iR, cR);
+  eval_edge_states<NC>(L, axis, iL >= 0 ? cL : nullptr, iL >= 0 ? z[iL] : 0.0,
+                       iR >= 0 ? cR : nullptr, iR >= 0 ? z[iR] : 0.0, GL, GR);
+  for (int s = 0; s < NC; ++s) {
+    eb[s * (long long)n_e + e] = GL[s];
+    eb[(NC + s) * (long long)n_e + e] = GR[s];
+  }
+}
+
+// cell edges: W (x-edge, cell on the right), E (x-edge, left), S, N
+__device__ __forceinline__ void cell_edges(const DevLevel& L, int i, int n_xe, int& eW, int& eE,
+                                           int& eS, int& eN) {
+  const int ix = i % L.nx, iy = i / L.nx;
+  eW = ix + (L.nx + 1) * iy;
+  eE = eW + 1;
+  eS = n_xe + ix + L.nx * iy;
+  eN = eS + L.nx;
+}
+
+// R_i = sum over W, E, S, N of |e| G (eq. Res), ||R_i||_1
+template <int NC>
+__global__ void k_res_cells(DevLevel L, const double* __restrict__ eb, double* __restrict__ R,
+                            double* __restrict__ rn, int n_xe, int n_e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  int eW, eE, eS, eN;
+  cell_edges(L, i, n_xe, eW, eE, eS, eN);
+  double r[NC];
+  for (int s = 0; s < NC; ++s) {
+    double a = 0.0;
+    a = a + L.ex * eb[(NC + s) * (long long)n_e + eW];
+    a = a + L.ex * eb[s * (long long)n_e + eE];
+    if (L.dim == 2) {
+      a = a + L.ey * eb[(NC + s) * (long long)n_e + eS];
+      a = a + L.ey * eb[s * (long long)n_e + eN];
+    }
+    r[s] = a;
+    R[s * (long long)L.n + i] = a;
+  }
+  double m = fabs(r[0]) + fabs(r[1]);
+  if (NC == 3) m = m + fabs(r[NC - 1]);
+  if (rn) rn[i] = m;
+}
+
+// ---- finite-difference Jacobian ---------------------------------------------
+// Edge buffer fields (each n_e long): GL[NC], GR[NC], dLL[NC*NC], dRR[NC*NC],
+// where dLL = |e| (G_L(U_L + eps e_k) - G_L(U)) / eps is the left cell's
+// diagonal contribution (ghost recomputed on boundary edges); the
+// off-diagonal blocks go straight to the level's block arrays.
+
+template <int NC, typename T>
+__global__ void k_jac_edges(DevLevel L, const double* __restrict__ z, const double* __restrict__ U,
+                            double* __restrict__ eb, void* __restrict__ blk, int n_xe, int n_e) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_e) return;
+  int axis, iL, iR;
+  double len;
+  edge_cells(L, e, n_xe, axis, iL, iR, len);
+  const long long ne = n_e, n = L.n;
+  double cL[NC], cR[NC], GLb[NC], GRb[NC], GL[NC], GR[NC];
+  if (iL >= 0) load_c<NC>(U, L.n, iL, cL);
+  if (iR >= 0) load_c<NC>(U, L.n, iR, cR);
+  const double zL = iL >= 0 ? z[iL] : 0.0, zR = iR >= 0 ? z[iR] : 0.0;
+  const double* pL = iL >= 0 ? cL : nullptr;
+  const double* pR = iR >= 0 ? cR : nullptr;
+  eval_edge_states<NC>(L, axis, pL, zL, pR, zR, GLb, GRb);
+  for (int s = 0; s < NC; ++s) {
+    eb[s * ne + e] = GLb[s];
+    eb[(NC + s) * ne + e] = GRb[s];
+  }
+  const int f_dLL = 2 * NC, f_dRR = 2 * NC + NC * NC;
+  const int bR = axis == 0 ? 1 : 3;   // block of the right cell pointing left (W / S)
+  const int bL = axis == 0 ? 2 : 4;   // block of the left cell pointing right (E / N)
+  // perturb the left cell
+  for (int k = 0; k < NC; ++k) {
+    if (iL >= 0) {
+      double c[NC];
+      for (int s = 0; s < NC; ++s) c[s] = cL[s];
+      c[k] = c[k] + L.eps;
+      eval_edge_states<NC>(L, axis, c, zL, pR, zR, GL, GR);
+      for (int s = 0; s < NC; ++s) {
+        eb[(f_dLL + s * NC + k) * ne + e] = len * ((GL[s] - GLb[s]) * L.reps);
+        if (iR >= 0) st<T>(blk, ((long long)(bR * NC * NC + s * NC + k)) * n + iR,
+                           len * ((GR[s] - GRb[s]) * L.reps));
+      }
+    } else {
+      for (int s = 0; s < NC; ++s) {
+        eb[(f_dLL + s * NC + k) * ne + e] = 0.0;
+        st<T>(blk, ((long long)(bR * NC * NC + s * NC + k)) * n + iR, 0.0);
+      }
+    }
+  }
+  // perturb the right cell
+  for (int k = 0; k < NC; ++k) {
+    if (iR >= 0) {
+      double c[NC];
+      for (int s = 0; s < NC; ++s) c[s] = cR[s];
+      c[k] = c[k] + L.eps;
+      eval_edge_states<NC>(L, axis, pL, zL, c, zR, GL, GR);
+      for (int s = 0; s < NC; ++s) {
+        eb[(f_dRR + s * NC + k) * ne + e] = len * ((GR[s] - GRb[s]) * L.reps);
+        if (iL >= 0) st<T>(blk, ((long long)(bL * NC * NC + s * NC + k)) * n + iL,
+                           len * ((GL[s] - GLb[s]) * L.reps));
+      }
+    } else {
+      for (int s = 0; s < NC; ++s) {
+        eb[(f_dRR + s * NC + k) * ne + e] = 0.0;
+        st<T>(blk, ((long long)(bL * NC * NC + s * NC + k)) * n + iL, 0.0);
+      }
+    }
+  }
+}
+
+// Diagonal block D_i = sum_{W,E,S,N} dG + alpha ||R_i||_1 I (eq. NewtonREG),
+// residual and its norm.  1D cells have only W and E.
+template <int NC, typename T>
+__global__ void k_jac_cells(DevLevel L, const double* __restrict__ eb, double* __restrict__ R,
+                            double* __restrict__ rn, void* __restrict__ blk, int n_xe, int n_e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  int eW, eE, eS, eN;
+  cell_edges(L, i, n_xe, eW, eE, eS, eN);
+  const long long ne = n_e, n = L.n;
+  double r[NC];
+  for (int s = 0; s < NC; ++s) {
+    double a = 0.0;
+    a = a + L.ex * eb[(NC + s) * ne + eW];
+    a = a + L.ex * eb[s * ne + eE];
+    if (L.dim == 2) {
+      a = a + L.ey * eb[(NC + s) * ne + eS];
+      a = a + L.ey * eb[s * ne + eN];
+    }
+    r[s] = a;
+    R[s * n + i] = a;
+  }
+  double m = fabs(r[0]) + fabs(r[1]);
+  if (NC == 3) m = m + fabs(r[NC - 1]);
+  if (rn) rn[i] = m;
+  const int f_dLL = 2 * NC, f_dRR = 2 * NC + NC * NC;
+  const double am = L.alpha * m;
+  for (int s = 0; s < NC; ++s)
+    for (int k = 0; k < NC; ++k) {
+      const int f = s * NC + k;
+      double d = 0.0;
+      d = d + eb[(f_dRR + f) * ne + eW];
+      d = d + eb[(f_dLL + f) * ne + eE];
+      if (L.dim == 2) {
+        d = d + eb[(f_dRR + f) * ne + eS];
+        d = d + eb[(f_dLL + f) * ne + eN];
+      }
+      if (s == k) d = d + am;
+      st<T>(blk, (long long)f * n + i, d);
+    }
+}
+
+// ---- block solve with the same elimination as the reference definition -----
+// Gaussian elimination with partial pivoting (largest |entry|, lowest row on
+// ties); a pivot <= 1e-14 max|D| marks its unknown singular (correction 0).
+template <int NC>
+__device__ void small_solve(double m[NC * NC], const double b[NC], double x[NC]) {
+  double amax = 0.0;
+  for (int e = 0; e < NC * NC; ++e) {
+    const double a = fabs(m[e]);
+    if (a > amax) amax = a;
+  }
+  const double tiny = 1e-14 * amax;
+  int perm[NC], sing[NC];
+  for (int r = 0; r < NC; ++r) { perm[r] = r; sing[r] = 0; }
+  for (int col = 0; col < NC; ++col) {
+    int p = col;
+    double best = fabs(m[col * NC + col]);
+    for (int r = col + 1; r < NC; ++r) {
+      const double a = fabs(m[r * NC + col]);
+      if (a > best) { best = a; p = r; }
+    }
+    if (p != col) {
+      for (int k = 0; k < NC; ++k) {
+        const double t = m[col * NC + k];
+        m[col * NC + k] = m[p * NC + k];
+        m[p * NC + k] = t;
+      }
+      const int t = perm[col]; perm[col] = perm[p]; perm[p] = t;
+    }
+    if (!(best > tiny)) {
+      sing[col] = 1;
+      for (int r = col + 1; r < NC; ++r) m[r * NC + col] = 0.0;
+      continue;
+    }
+    for (int r = col + 1; r < NC; ++r) {
+      const double l = m[r * NC + col] / m[col * NC + col];
+      m[r * NC + col] = l;
+      for (int k = col + 1; k < NC; ++k) m[r * NC + k] = m[r * NC + k] - l * m[col * NC + k];
+    }
+  }
+  double y[NC];
+  for (int r = 0; r < NC; ++r) y[r] = b[perm[r]];
+  for (int r = 0; r < NC; ++r)
+    for (int k = 0; k < r; ++k) y[r] = y[r] - m[r * NC + k] * y[k];
+  for (int r = NC - 1; r >= 0; --r) {
+    if (sing[r]) { x[r] = 0.0; continue; }
+    double s = y[r];
+    for (int k = r + 1; k < NC; ++k) s = s - m[r * NC + k] * x[k];
+    x[r] = s / m[r * NC + r];
+  }
+}
+
+// ---- BLU-SGS: one anti-diagonal of the lexicographic sweep ------------------
+// Cells with ix + iy = d depend only on diagonal d-1 (new values) and d+1
+// (old values), so updating one diagonal at a time in increasing (forward)
+// or decreasing (backward) order reproduces the lexicographic sweep exactly.
+// NS lanes per cell (one per side) evaluate the side's G and its three
+// perturbations; the side-0 lane sums them in W, E, S, N order and updates
+// U_i -= (alpha||R_i||_1 I + dR_i/dU_i)^{-1} R_i.
+template <int NC, int NS>
+__global__ void k_blusgs_diag(DevLevel L, const double* __restrict__ z, double* __restrict__ U,
+                              int d, int ix0, int ncell) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cell = t / NS, side = t % NS;
+  const bool active = cell < ncell;
+  const int ix = ix0 + (active ? cell : 0), iy = d - ix;
+  const int i = ix + L.nx * iy;
+  const long long n = L.n;
+  double lenG[NC], dG[NC * NC];
+  for (int s = 0; s < NC; ++s) lenG[s] = 0.0;
+  for (int e = 0; e < NC * NC; ++e) dG[e] = 0.0;
+  if (active) {
+    const int axis = side >> 1, upper = side & 1;
+    int j = -1;
+    if (side == 0 && ix > 0) j = i - 1;
+    if (side == 1 && ix < L.nx - 1) j = i + 1;
+    if (side == 2 && iy > 0) j = i - L.nx;
+    if (side == 3 && iy < L.ny - 1) j = i + L.nx;
+    double ci[NC], cj[NC], GL[NC], GR[NC], Gb[NC];
+    load_c<NC>(U, L.n, i, ci);
+    if (j >= 0) load_c<NC>(U, L.n, j, cj);
+    const double zi = z[i], zj = j >= 0 ? z[j] : 0.0;
+    const double len = axis == 0 ? L.ex : L.ey;
+    // the cell is the left state of its E/N edges, the right state of W/S
+    if (upper) eval_edge_states<NC>(L, axis, ci, zi, j >= 0 ? cj : nullptr, zj, GL, GR);
+    else eval_edge_states<NC>(L, axis, j >= 0 ? cj : nullptr, zj, ci, zi, GL, GR);
+    for (int s = 0; s < NC; ++s) {
+      Gb[s] = upper ? GL[s] : GR[s];
+      lenG[s] = len * Gb[s];
+    }
+    for (int k = 0; k < NC; ++k) {
+      double c[NC];
+      for (int s = 0; s < NC; ++s) c[s] = ci[s];
+      c[k] = c[k] + L.eps;
+      if (upper) eval_edge_states<NC>(L, axis, c, zi, j >= 0 ? cj : nullptr, zj, GL, GR);
+      else eval_edge_states<NC>(L, axis, j >= 0 ? cj : nullptr, zj, c, zi, GL, GR);
+      for (int s = 0; s < NC; ++s) dG[s * NC + k] = len * (((upper ? GL[s] : GR[s]) - Gb[s]) * L.reps);
+    }
+  }
+  // gather the NS sides of a cell into its side-0 lane, in side order
+  const unsigned full = 0xffffffffu;
+  double Rs[NC], D[NC * NC];
+  for (int s = 0; s < NC; ++s) Rs[s] = 0.0;
+  for (int e = 0; e < NC * NC; ++e) D[e] = 0.0;
+  const int base = (threadIdx.x & 31) - side;
+  for (int q = 0; q < NS; ++q) {
+    for (int s = 0; s < NC; ++s) Rs[s] = Rs[s] + __shfl_sync(full, lenG[s], base + q);
+    for (int e = 0; e < NC * NC; ++e) D[e] = D[e] + __shfl_sync(full, dG[e], base + q);
+  }
+  if (!active || side != 0) return;
+  double m = fabs(Rs[0]) + fabs(Rs[1]);
+  if (NC == 3) m = m + fabs(Rs[NC - 1]);
+  const double am = L.alpha * m;
+  for (int s = 0; s < NC; ++s) D[s * NC + s] = D[s * NC + s] + am;
+  double x[NC];
+  small_solve<NC>(D, Rs, x);
+  const double h0 = U[i];
+  if (h0 < L.h_eps)   // dry at the start: momentum stays zero (Remark 2.5)
+    for (int s = 1; s < NC; ++s) x[s] = 0.0;
+  double un[NC];
+  for (int s = 0; s < NC; ++s) un[s] = U[s * n + i] - x[s];
+  if (un[0] < L.h_eps)
+    for (int s = 0; s < NC; ++s) un[s] = 0.0;
+  for (int s = 0; s < NC; ++s) U[s * n + i] = un[s];
+}
+
+// U += tau dU with the dry rules of Remark 2.5 (eq. NewtonREG-12)
+template <typename T>
+__global__ void k_newton_update(int n, int nc, double tau, double h_eps, double* __restrict__ U,
+                                const T* __restrict__ dU) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double h0 = U[i];
+  double v[3];
+  for (int s = 0; s < nc; ++s) {
+    double d = static_cast<double>(dU[(long long)s * n + i]);
+    if (s > 0 && h0 < h_eps) d = 0.0;
+    v[s] = U[(long long)s * n + i] + tau * d;
+  }
+  if (v[0] < h_eps)
+    for (int s = 0; s < nc; ++s) v[s] = 0.0;
+  for (int s = 0; s < nc; ++s) U[(long long)s * n + i] = v[s];
+}
+
+// coarse value = mean of the children (child order 00, 10, 01, 11)
+__global__ void k_average(int dim, int nxf, int nyf, int ncomp, const double* __restrict__ vf,
+                          double* __restrict__ vc) {
+  const int nxc = nxf / 2, nyc = dim == 2 ? nyf / 2 : 1, nc_cells = nxc * nyc;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc_cells) return;
+  const long long nf = (long long)nxf * (dim == 2 ? nyf : 1);
+  const int Ix = I % nxc, Iy = I / nxc;
+  for (int s = 0; s < ncomp; ++s) {
+    const double* v = vf + s * nf;
+    double a;
+    if (dim == 1) {
+      a = v[2 * Ix];
+      a = a + v[2 * Ix + 1];
+      a = a * 0.5;
+    } else {
+      const int f = 2 * Ix + nxf * 2 * Iy;
+      a = v[f];
+      a = a + v[f + 1];
+      a = a + v[f + nxf];
+      a = a + v[f + nxf + 1];
+      a = a * 0.25;
+    }
+    vc[(long long)s * nc_cells + I] = a;
+  }
+}
+
+// piecewise-constant injection of a coarse solution (Algorithm 1, Step 1)
+__global__ void k_inject(int dim, int nxf, int nyf, int ncomp, const double* __restrict__ vc,
+                         double* __restrict__ vf) {
+  const int nf_cells = nxf * (dim == 2 ? nyf : 1);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nf_cells) return;
+  const int ix = i % nxf, iy = i / nxf, nxc = nxf / 2;
+  const int nc_cells = nxc * (dim == 2 ? nyf / 2 : 1);
+  const int I = (ix / 2) + nxc * (dim == 2 ? iy / 2 : 0);
+  for (int s = 0; s < ncomp; ++s) vf[(long long)s * nf_cells + i] = vc[(long long)s * nc_cells + I];
+}
+
+inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+// ---- launch wrappers ---------------------------------------------------------
+
+static void edge_counts(const DevLevel& L, int& n_xe, int& n_e) {
+  n_xe = (L.nx + 1) * L.ny;
+  n_e = n_xe + (L.dim == 2 ? L.nx * (L.ny + 1) : 0);
+}
+
+void launch_residual(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
+                     double* eb, cudaStream_t st) {
+  int n_xe, n_e;
+  edge_counts(L, n_xe, n_e);
+  if (L.nc == 3) {
+    k_res_edges<3><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, n_xe, n_e);
+    k_res_cells<3><<<nblk(L.n, 256), 256, 0, st>>>(L, eb, R, rn, n_xe, n_e);
+  } else {
+    k_res_edges<2><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, n_xe, n_e);
+    k_res_cells<2><<<nblk(L.n, 256), 256, 0, st>>>(L, eb, R, rn, n_xe, n_e);
+  }
+}
+
+void launch_jacobian(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
+                     double* eb, void* blk, int fp32, cudaStream_t st) {
+  int n_xe, n_e;
+  edge_counts(L, n_xe, n_e);
+  if (L.nc == 3) {
+    if (fp32) {
+      k_jac_edges<3, float><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, blk, n_xe, n_e);
+      k_jac_cells<3, float><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, R, rn, blk, n_xe, n_e);
+    } else {
+      k_jac_edges<3, double><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, blk, n_xe, n_e);
+      k_jac_cells<3, double><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, R, rn, blk, n_xe, n_e);
+    }
+  } else {
+    if (fp32) {
+      k_jac_edges<2, float><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, blk, n_xe, n_e);
+      k_jac_cells<2, float><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, R, rn, blk, n_xe, n_e);
+    } else {
+      k_jac_edges<2, double><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, blk, n_xe, n_e);
+      k_jac_cells<2, double><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, R, rn, blk, n_xe, n_e);
+    }
+  }
+}
+
+void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forward,
+                         cudaStream_t st) {
+  const int ndiag = L.nx + L.ny - 1;
+  for (int q = 0; q < ndiag; ++q) {
+    const int d = forward ? q : ndiag - 1 - q;
+    const int ix0 = d - (L.ny - 1) > 0 ? d - (L.ny - 1) : 0;
+    const int ix1 = d < L.nx - 1 ? d : L.nx - 1;
+    const int ncell = ix1 - ix0 + 1;
+    if (L.nc == 3) {
+      const int thr = ncell * 4, bs = thr < 128 ? ((thr + 31) / 32) * 32 : 128;
+      k_blusgs_diag<3, 4><<<nblk(thr, bs), bs, 0, st>>>(L, z, U, d, ix0, ncell);
+    } else {
+      const int thr = ncell * 2, bs = thr < 128 ? ((thr + 31) / 32) * 32 : 128;
+      k_blusgs_diag<2, 2><<<nblk(thr, bs), bs, 0, st>>>(L, z, U, d, ix0, ncell);
+    }
+  }
+}
+
+void launch_newton_update(int n, int nc, double tau, double h_eps, double* U, const void* dU,
+                          int dU_fp32, cudaStream_t st) {
+  if (dU_fp32)
+    k_newton_update<float><<<nblk(n, 256), 256, 0, st>>>(n, nc, tau, h_eps, U, (const float*)dU);
+  else
+    k_newton_update<double><<<nblk(n, 256), 256, 0, st>>>(n, nc, tau, h_eps, U, (const double*)dU);
+}
+
+void launch_average(int dim, int nxf, int nyf, int ncomp, const double* vf, double* vc,
+                    cudaStream_t st) {
+  const int ncells = (nxf / 2) * (dim == 2 ? nyf / 2 : 1);
+  k_average<<<nblk(ncells, 256), 256, 0, st>>>(dim, nxf, nyf, ncomp, vf, vc);
+}
+
+void launch_inject(int dim, int nxf, int nyf, int ncomp, const double* vc, double* vf,
+                   cudaStream_t st) {
+  const int ncells = nxf * (dim == 2 ? nyf : 1);
+  k_inject<<<nblk(ncells, 256), 256, 0, st>>>(dim, nxf, nyf, ncomp, vc, vf);
+}
+
+}  // namespace swnmg

@@ -1,0 +1,217 @@
+"""Python binding of libswnmg (include/swnmg.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; PyTorch only provides the
+device tensors and the stream.  There is no CPU fallback: if the library or a
+CUDA device is missing, the constructor raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import workloads as W
+from .build import LIB, build
+
+HIST = 512
+
+OK, ERR_ARG, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_DIVERGED, ERR_TIMEOUT, ERR_OOM = range(8)
+STATUS = {0: "ok", 1: "arg", 2: "cuda", 3: "not_converged", 4: "nonfinite", 5: "diverged",
+          6: "timeout", 7: "oom"}
+
+
+class _BC(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("h", C.c_double), ("q", C.c_double), ("ut", C.c_double)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
+                ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+                ("g", C.c_double), ("bc", _BC * 4)]
+
+
+class Params(C.Structure):
+    _fields_ = [("flux", C.c_int32), ("llf_wetdry", C.c_int32),
+                ("alpha", C.c_double), ("fd_eps", C.c_double), ("tau", C.c_double),
+                ("h_eps", C.c_double), ("eps_r", C.c_double), ("eps_p", C.c_double),
+                ("tol", C.c_double),
+                ("n_levels", C.c_int32), ("n_mg", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
+                ("gamma", C.c_int32), ("coarse_sweeps", C.c_int32), ("max_newton", C.c_int32),
+                ("max_blusgs", C.c_int32), ("init_mode", C.c_int32), ("precision", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_newton", C.c_int32), ("n_vcycles", C.c_int32),
+                ("blusgs_sweeps", C.c_int32 * 16), ("init_res", C.c_double),
+                ("final_res", C.c_double), ("res_hist", C.c_double * HIST),
+                ("ms_step1", C.c_double), ("ms_newton", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads (building first if needed) the in-tree CUDA library."""
+    global _lib
+    if _lib is None:
+        path = build()
+        if not os.path.exists(path):
+            raise RuntimeError("libswnmg.so is missing: run __graft_entry__.build()")
+        L = C.CDLL(path)
+        vp, dp = C.c_void_p, C.POINTER(C.c_double)
+        L.swnmg_default_params.argtypes = [C.c_int32, C.POINTER(Params)]
+        L.swnmg_create.argtypes = [C.POINTER(Problem), C.POINTER(Params), vp, vp, C.POINTER(vp)]
+        L.swnmg_destroy.argtypes = [vp]
+        L.swnmg_last_error.argtypes = [vp]
+        L.swnmg_last_error.restype = C.c_char_p
+        L.swnmg_set_params.argtypes = [vp, C.POINTER(Params)]
+        L.swnmg_residual.argtypes = [vp, vp, vp, vp, dp]
+        L.swnmg_jacobian.argtypes = [vp, vp]
+        L.swnmg_get_blocks.argtypes = [vp, C.c_int32, vp]
+        L.swnmg_vcycle.argtypes = [vp, vp, vp, C.c_int32]
+        L.swnmg_sgs_sweep.argtypes = [vp, C.c_int32, vp, vp, C.c_int32]
+        L.swnmg_blusgs.argtypes = [vp, vp, C.c_int32, C.c_int32]
+        L.swnmg_solve.argtypes = [vp, vp, C.POINTER(Stats)]
+        L.swnmg_level_cells.argtypes = [vp, C.c_int32]
+        L.swnmg_level_cells.restype = C.c_int64
+        for f in ("swnmg_default_params", "swnmg_create", "swnmg_destroy", "swnmg_set_params",
+                  "swnmg_residual", "swnmg_jacobian", "swnmg_get_blocks", "swnmg_vcycle",
+                  "swnmg_sgs_sweep", "swnmg_blusgs", "swnmg_solve"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class SwnmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("swnmg status %d (%s): %s" % (status, STATUS.get(status, "?"), msg))
+        self.status = status
+
+
+def make_problem(p: W.Problem) -> Problem:
+    s = Problem()
+    s.dim, s.nx, s.ny = p.dim, p.nx, (p.ny if p.dim == 2 else 1)
+    s.x0, s.x1, s.y0, s.y1, s.g = p.x0, p.x1, p.y0, p.y1, p.g
+    for k in range(4):
+        b = p.bc[k]
+        s.bc[k].kind, s.bc[k].h, s.bc[k].q, s.bc[k].ut = b.kind, b.h, b.q, b.ut
+    return s
+
+
+def make_params(prm: W.Params) -> Params:
+    s = Params()
+    for f, _ in Params._fields_:
+        setattr(s, f, getattr(prm, f))
+    return s
+
+
+def _ptr(t: torch.Tensor):
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One problem on the current CUDA device; tensors are float64 SoA."""
+
+    def __init__(self, prob: W.Problem, params: W.Params | None = None, stream=None, z=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("swnmg needs a CUDA device (no CPU fallback)")
+        self.L = lib()
+        self.prob = prob
+        self.params = params or prob.params
+        self.nc = prob.ncomp
+        self.stream = stream or torch.cuda.current_stream()
+        self.z = z if z is not None else torch.as_tensor(np.ascontiguousarray(prob.z), dtype=torch.float64,
+                                                         device="cuda")
+        self._pp = make_problem(prob)
+        self._pr = make_params(self.params)
+        h = C.c_void_p()
+        rc = self.L.swnmg_create(C.byref(self._pp), C.byref(self._pr), _ptr(self.z),
+                                 C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc != OK:
+            raise SwnmgError(rc, self.L.swnmg_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise SwnmgError(rc, self.L.swnmg_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.swnmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, **kw):
+        self.params = self.params.replace(**kw)
+        self._pr = make_params(self.params)
+        self._check(self.L.swnmg_set_params(self.h, C.byref(self._pr)))
+
+    def level_cells(self, level):
+        return int(self.L.swnmg_level_cells(self.h, level))
+
+    def tensor(self, a=None, level=0):
+        n = self.level_cells(level)
+        if a is None:
+            return torch.zeros((self.nc, n), dtype=torch.float64, device="cuda")
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda").reshape(self.nc, n).contiguous()
+
+    def residual(self, U, with_sum=True):
+        n = self.level_cells(0)
+        R = torch.empty((self.nc, n), dtype=torch.float64, device="cuda")
+        rn = torch.empty(n, dtype=torch.float64, device="cuda")
+        s = C.c_double(0.0)
+        self._check(self.L.swnmg_residual(self.h, _ptr(U), _ptr(R), _ptr(rn),
+                                          C.byref(s) if with_sum else None))
+        return R, rn, s.value
+
+    def jacobian(self, U):
+        self._check(self.L.swnmg_jacobian(self.h, _ptr(U)))
+
+    def get_blocks(self, level=0):
+        n = self.level_cells(level)
+        out = np.zeros((n, 5, self.nc, self.nc))
+        self._check(self.L.swnmg_get_blocks(self.h, level, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def vcycle(self, rhs, dU, ncycles=1):
+        self._check(self.L.swnmg_vcycle(self.h, _ptr(rhs), _ptr(dU), ncycles))
+        return dU
+
+    def sgs_sweep(self, level, rhs, x, forward=True):
+        self._check(self.L.swnmg_sgs_sweep(self.h, level, _ptr(rhs), _ptr(x), 1 if forward else 0))
+        return x
+
+    def blusgs(self, U, level=0, nsweeps=1):
+        self._check(self.L.swnmg_blusgs(self.h, _ptr(U), level, nsweeps))
+        return U
+
+    def solve(self, U, check=False):
+        """Algorithm 1 in place on U; returns a dict of the solver counters."""
+        st = Stats()
+        rc = self.L.swnmg_solve(self.h, _ptr(U), C.byref(st))
+        if check:
+            self._check(rc)
+        elif rc not in (OK, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_DIVERGED):
+            self._check(rc)
+        return {"status": st.status, "n_newton": st.n_newton, "n_vcycles": st.n_vcycles,
+                "blusgs_sweeps": list(st.blusgs_sweeps)[:self.params.n_levels + 1],
+                "init_res": st.init_res, "final_res": st.final_res,
+                "res_hist": list(st.res_hist)[:min(st.n_newton, HIST)],
+                "ms_step1": st.ms_step1, "ms_newton": st.ms_newton}
+
+
+def default_params(dim: int) -> dict:
+    p = Params()
+    rc = lib().swnmg_default_params(dim, C.byref(p))
+    if rc != OK:
+        raise SwnmgError(rc, lib().swnmg_last_error(None).decode())
+    return {f: getattr(p, f) for f, _ in Params._fields_}

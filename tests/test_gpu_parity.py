@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle on
+the same seeded inputs.
+
+Bar (the method's hot path, Sections 2.1-2.4):
+  * residual, finite-difference Jacobian blocks, Galerkin hierarchy and BLU-SGS
+    sweeps: bit for bit (both sides evaluate the flux in one fixed order without
+    FMA contraction);
+  * block Gauss-Seidel sweeps and V/W-cycle iterates: 1e-12 relative (the GPU
+    smoother uses reciprocal pivots and FMA);
+  * full solves: the same Newton step count and the final state within 1e-10
+    relative in FP64 mode; the mixed mode's error is stated per case.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.oracle import Oracle
+from paper_1608_06721_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def swnmg():
+    from paper_1608_06721_gb300 import swnmg as S
+    S.lib()
+    return S
+
+
+def _cases():
+    """(name, problem, state generator) covering 1D/2D, every flux, ragged
+    tile tails, wet/dry fronts and all boundary kinds of the workloads."""
+    out = []
+    p = W.subcritical_bump_1d(n=200)
+    out.append(("bump1d_200", p, lambda p: W.random_state(p, 1)))
+    p = W.wetdry_lake_1d(128)
+    out.append(("ex33_128", p, lambda p: p.U0.copy()))
+    p = W.lake_at_rest_2d(n=64, flux=W.FLUX_LLF)
+    out.append(("lake64_llf", p, lambda p: W.random_state(p, 2, wet_frac=0.5)))
+    p = W.lake_at_rest_2d(n=64, flux=W.FLUX_HLLC)
+    out.append(("lake64_hllc", p, lambda p: W.random_state(p, 3, wet_frac=0.5)))
+    p = W.channel_2d(nx=104, ny=40, n_levels=3, redraw=False)
+    out.append(("channel_104x40", p, lambda p: W.random_state(p, 4, wet_frac=0.5)))
+    p = W.hill_wetdry_2d(64, 32).with_params(flux=W.FLUX_HLL)
+    out.append(("hill64x32_hll", p, lambda p: W.random_state(p, 5, wet_frac=0.5)))
+    p = W.transcritical_bump_2d(48, 24)
+    out.append(("ex36_48x24", p, lambda p: W.random_state(p, 6)))
+    return out
+
+
+CASES = _cases()
+IDS = [c[0] for c in CASES]
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _first_diff(a, b):
+    d = np.flatnonzero(a.ravel() != b.ravel())
+    if d.size == 0:
+        return "identical"
+    k = d[0]
+    return "first difference at flat index %d: gpu %r oracle %r (%d differ)" % (
+        k, a.ravel()[k], b.ravel()[k], d.size)
+
+
+@pytest.mark.parametrize("name,prob,gen", CASES, ids=IDS)
+def test_residual_bitwise(swnmg, name, prob, gen):
+    U = gen(prob)
+    S = swnmg.Solver(prob)
+    R, rn, tot = S.residual(_dev(U))
+    Ro, rno = Oracle(prob).residual(U)
+    assert np.array_equal(R.cpu().numpy(), Ro), _first_diff(R.cpu().numpy(), Ro)
+    assert np.array_equal(rn.cpu().numpy(), rno)
+    assert abs(tot - rno.sum()) <= 1e-13 * max(rno.sum(), 1e-300)
+
+
+@pytest.mark.parametrize("name,prob,gen", CASES, ids=IDS)
+def test_jacobian_and_hierarchy_bitwise(swnmg, name, prob, gen):
+    U = gen(prob)
+    S = swnmg.Solver(prob)
+    S.jacobian(_dev(U))
+    o = Oracle(prob)
+    R, rn, blk = o.jacobian(U)
+    H = o.hierarchy(blk)
+    for l, Ho in enumerate(H):
+        Hg = S.get_blocks(l)
+        assert np.array_equal(Hg, Ho), "level %d: %s" % (l, _first_diff(Hg, Ho))
+
+
+@pytest.mark.parametrize("name,prob,gen", CASES, ids=IDS)
+def test_sgs_sweeps(swnmg, name, prob, gen):
+    U = gen(prob)
+    S = swnmg.Solver(prob)
+    S.jacobian(_dev(U))
+    o = Oracle(prob)
+    R, rn, blk = o.jacobian(U)
+    H = o.hierarchy(blk)
+    rng = np.random.default_rng(9)
+    for l in (0, len(H) - 1):
+        n = S.level_cells(l)
+        b, x = rng.standard_normal((prob.ncomp, n)), rng.standard_normal((prob.ncomp, n))
+        for fwd in (True, False):
+            xg = S.sgs_sweep(l, _dev(b), _dev(x), fwd).cpu().numpy()
+            xo = o.sgs(l, H[l], b, x, forward=fwd)
+            scale = np.abs(xo).max()
+            assert np.abs(xg - xo).max() <= 1e-12 * scale, (l, fwd)
+
+
+@pytest.mark.parametrize("name,prob,gen", CASES, ids=IDS)
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_cycle_iterates(swnmg, name, prob, gen, gamma):
+    """Algorithm 0 iterates after 1, 2 and 3 cycles from dU = 0, rhs = -R."""
+    prob = prob.with_params(gamma=gamma)
+    U = gen(prob)
+    S = swnmg.Solver(prob)
+    S.jacobian(_dev(U))
+    o = Oracle(prob)
+    R, rn, blk = o.jacobian(U)
+    x = np.zeros_like(R)
+    xg = _dev(x)
+    for k in range(3):
+        x = o.vcycle(blk, -R, x, 1)
+        S.vcycle(_dev(-R), xg, 1)
+        scale = np.abs(x).max()
+        assert np.abs(xg.cpu().numpy() - x).max() <= 1e-12 * scale, (k, np.abs(xg.cpu().numpy() - x).max() / scale)
+
+
+@pytest.mark.parametrize("name,prob,gen", CASES, ids=IDS)
+def test_blusgs_bitwise(swnmg, name, prob, gen):
+    U = gen(prob)
+    S = swnmg.Solver(prob)
+    Ug = _dev(U)
+    S.blusgs(Ug, 0, 2)
+    Uo = Oracle(prob).blusgs(U, 2)
+    assert np.array_equal(Ug.cpu().numpy(), Uo), _first_diff(Ug.cpu().numpy(), Uo)
+
+
+SOLVES = [
+    ("bump1d_s101", W.subcritical_bump_1d(seed=101)),
+    ("bump1d_s102", W.subcritical_bump_1d(seed=102)),
+    ("ex31_256", W.smooth_subcritical_1d(256)),
+    ("ex33_256", W.wetdry_lake_1d(256)),
+    ("channel_64", W.channel_2d(nx=64, ny=64)),
+    ("channel_128x32", W.channel_2d(nx=128, ny=32, n_levels=2)),
+    ("hill_64x32", W.hill_wetdry_2d(64, 32)),
+    ("ex36_64x32", W.transcritical_bump_2d(64, 32)),
+]
+
+
+@pytest.mark.parametrize("name,prob", SOLVES, ids=[s[0] for s in SOLVES])
+def test_solve_fp64(swnmg, name, prob):
+    Uo, io = Oracle(prob).solve()
+    S = swnmg.Solver(prob)
+    Ug = _dev(prob.U0)
+    ig = S.solve(Ug)
+    assert io["status"] == 0 and ig["status"] == 0, (io, ig)
+    assert ig["n_newton"] == io["n_newton"]
+    assert ig["blusgs_sweeps"] == io["blusgs_sweeps"]
+    Ug = Ug.cpu().numpy()
+    assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max()
+
+
+def test_lake_at_rest_forced_newton_step(swnmg):
+    """The 256x256 lake with dry islands: R = 0 to 1e-13 and one forced Newton
+    step equals the oracle's.  Cells with 0 < h < h_eps are emptied by the dry
+    rule of Remark 2.5, which disturbs the rest state (1e-11 here, through the
+    global linear solve); on an input without such cells (64x64, same seed)
+    the step keeps h + z = 0.5 and u = v = 0 to 1e-13."""
+    p = W.lake_at_rest_2d(n=256).with_params(tol=0.0, max_newton=1, init_mode=W.INIT_NONE)
+    S = swnmg.Solver(p)
+    U = _dev(p.U0)
+    _, _, tot = S.residual(U)
+    assert tot <= 1e-13
+    info = S.solve(U)
+    assert info["n_newton"] == 1
+    Uo, _ = Oracle(p).solve()
+    assert np.abs(U.cpu().numpy() - Uo).max() <= 1e-12
+    for flux in (W.FLUX_LLF, W.FLUX_HLLC):
+        p = W.lake_at_rest_2d(n=64, flux=flux).with_params(tol=0.0, max_newton=1, init_mode=W.INIT_NONE)
+        assert not np.any((p.U0[0] > 0) & (p.U0[0] < p.params.h_eps))
+        U = _dev(p.U0)
+        swnmg.Solver(p).solve(U)
+        U = U.cpu().numpy()
+        wet = p.U0[0] > 0
+        assert np.abs(U[0][wet] + p.z[wet] - 0.5).max() <= 1e-13
+        assert np.abs(U[1:]).max() <= 1e-13 and np.all(U[:, ~wet] == 0)
+
+
+def test_mixed_precision_solve(swnmg):
+    """FP32 multigrid inner solve, FP64 residual/update/norms: converges to the
+    same discrete root; the error against the FP64 oracle is reported."""
+    p = W.channel_2d(nx=64, ny=64, precision=W.PREC_MIXED)
+    Uo, io = Oracle(p).solve()
+    S = swnmg.Solver(p)
+    U = _dev(p.U0)
+    info = S.solve(U)
+    assert info["status"] == 0
+    err = np.abs(U.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+    print("mixed: newton %d (fp64 oracle %d), max rel state error %.2e" % (info["n_newton"], io["n_newton"], err))
+    assert err <= 1e-9
+
+
+def test_invalid_arguments(swnmg):
+    p = W.channel_2d(nx=60, ny=64, redraw=False)       # 60 not divisible by 2^3
+    with pytest.raises(swnmg.SwnmgError) as e:
+        swnmg.Solver(p)
+    assert e.value.status == swnmg.ERR_ARG
+    p = W.channel_2d(nx=64, ny=64, redraw=False)
+    p.bc[2] = W.BC(kind=9)
+    with pytest.raises(swnmg.SwnmgError):
+        swnmg.Solver(p)
+
+
+def test_nonfinite_input_is_reported(swnmg):
+    p = W.subcritical_bump_1d(n=200)
+    U = p.U0.copy()
+    U[0, 50] = np.nan
+    S = swnmg.Solver(p.with_params(init_mode=W.INIT_NONE))
+    info = S.solve(_dev(U))
+    assert info["status"] in (swnmg.ERR_NONFINITE, swnmg.ERR_NOT_CONVERGED)
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (7, 5), (3, 1)])
+def test_small_and_ragged_grids(swnmg, nx, ny):
+    """Single-level grids of odd size: residual and Jacobian bitwise, one exact
+    coarse solve (the only level) equal to the oracle's."""
+    p = W.channel_2d(nx=nx, ny=ny, redraw=False, n_levels=0)
+    p = p.with_params(coarse_sweeps=0)
+    U = W.random_state(p, 8)
+    S = swnmg.Solver(p)
+    R, rn, _ = S.residual(_dev(U))
+    assert np.array_equal(R.cpu().numpy(), Oracle(p).residual(U)[0])
+    S.jacobian(_dev(U))
+    o = Oracle(p)
+    Ro, rno, blk = o.jacobian(U)
+    assert np.array_equal(S.get_blocks(0), blk)
+    x = S.vcycle(_dev(-Ro), _dev(np.zeros_like(Ro)), 1).cpu().numpy()
+    xo = o.vcycle(blk, -Ro, np.zeros_like(Ro), 1)
+    assert np.abs(x - xo).max() <= 1e-11 * max(np.abs(xo).max(), 1e-300)
