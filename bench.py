@@ -1,0 +1,359 @@
+"""Benchmark: Newton multigrid steady solve of the 2D partial-dry channel.
+
+Workload: 1024 x 1024 cells on [0,4] x [0,1], 16 seeded Gaussian bumps with
+dry tops, inflow discharge hu ~ U[0.5, 1.5] at x = 0, outflow depth 0.6 at
+x = 4, reflective walls, LLF flux with the wet/dry speed increase; mixed
+precision (FP32 multigrid inner solve, FP64 residual / Jacobian / update /
+norms), W-cycles (gamma = 2, N_L = 6, N_mg = 3), eps_p = 2, tol 1e-10.
+
+One step = one complete swnmg_solve (Algorithm 1 including its Step 1) from
+the same initial state, with inputs resident in HBM.  value = cells x
+multigrid cycles / second over the timed steps; ms_per_step = time to
+sum ||R_i||_1 < 1e-10.  The FP64 path is timed on the same problem and
+reported beside it.  e2e repeats the mixed solve through host buffers
+(pinned H2D of the initial state, D2H of the steady state inside the timed
+region).  Multi-GPU: independent replicas (the lexicographic sweeps do not
+shard), weak scaling.
+
+--impl reference times the CPU FP64 oracle (the reference restatement of the
+method) on a bounded sample of the same workload: one Newton step
+(BLU-SGS sweep, Jacobian, N_mg cycles, update) from the initial state.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell*cycles/s to residual 1e-10 at 1024^2 (mixed FP32-MG / FP64), time to 1e-10"
+UNIT = "cell*cycles/s"
+NX = NY = 1024
+LEVELS = 6
+
+
+def workload(precision, nx=NX, ny=NY):
+    from paper_1608_06721_gb300 import workloads as W
+    p = W.channel_2d(seed=301, nx=nx, ny=ny, precision=precision)
+    return p.with_params(gamma=2, eps_p=2.0, n_levels=LEVELS, n_mg=3, tol=1e-10, max_newton=200)
+
+
+def config_dict(p, flush):
+    prm = p.params
+    return {"workload": "2D partial-dry channel %dx%d (LLF, W-cycle N_L=%d, N_mg=%d, eps_p=%g, seed 301)"
+            % (p.nx, p.ny, prm.n_levels, prm.n_mg, prm.eps_p),
+            "cells": p.n, "precision": "mixed FP32 multigrid / FP64 residual+update",
+            "l2": flush, "tol": prm.tol}
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- peaks
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            hbm = d.get("hbm_gbs") or d.get("hbm_GBps")
+            if hbm:
+                return float(hbm), "measured (MEASURED_PEAKS.json hbm_gbs)"
+        except (ValueError, OSError):
+            pass
+    return 6800.0, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+# FP64 unit peak of GB300: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz = 0.63e12
+# FP64 instructions/s (1.26 TFLOP/s counting an FMA as two); the flux
+# kernels are compiled without FMA contraction, so one counted add, mul,
+# div or sqrt is compared against one instruction slot.
+FP64_OPS_PEAK = 152 * 2 * 2.07e9
+
+
+def algorithmic(cls, p, fp32):
+    """(bound, units per launch) of one launch of a kernel class at level 0:
+    bytes for the HBM-bound smoother, FP64 operations for the flux kernels
+    (operation counts per cell are derived in the design doc)."""
+    n, nc = p.n, p.ncomp
+    w = 4 if fp32 else 8
+    if cls == "sgs_fine":
+        return "hbm", n * ((5 * nc * nc - nc * nc + 9 + 3 + 2 * nc) * w + 1)   # blocks, LU, b, x in/out, piv
+    if cls == "blusgs":
+        return "alu", n * 1320.0
+    if cls == "jacobian":
+        return "alu", n * 880.0
+    if cls == "residual":
+        return "alu", n * 125.0
+    return None, None
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1608_06721_gb300 import swnmg, workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    p = workload(W.PREC_MIXED, args.nx, args.nx)
+    stream = torch.cuda.current_stream()
+    S = swnmg.Solver(p, stream=stream)
+    U0 = torch.as_tensor(p.U0, dtype=torch.float64, device=dev).contiguous()
+    U = torch.empty_like(U0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def one_solve():
+        U.copy_(U0)
+        info = S.solve(U)
+        if info["status"] != 0:
+            raise RuntimeError("solve did not converge: %s" % info)
+        return info
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+    S.set_timing(True)
+    n0 = swnmg.lib().swnmg_launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    total_ms, cycles, infos = 0.0, 0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = one_solve()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        cycles += info["n_vcycles"]
+        infos.append(info)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = swnmg.lib().swnmg_launch_count() - n0
+    timing = S.get_timing()
+    S.set_timing(False)
+    total_ms = max_over_ranks(total_ms)
+    value = world * p.n * cycles / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the dominant kernel class (live CUDA events on the solver's stream)
+    dom = max((k for k in timing if timing[k][1] > 0), key=lambda k: timing[k][0])
+    bound, units = algorithmic(dom, p, True)
+    roof = None
+    if bound is not None:
+        avg_ms = timing[dom][0] / timing[dom][1]
+        if bound == "hbm":
+            pk, src = peaks()
+            ach = units / (avg_ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk, "unit": "GB/s",
+                    "frac": ach / pk, "traffic": None, "peak_source": src}
+        else:
+            ach = units / (avg_ms * 1e-3) / 1e12
+            pk = FP64_OPS_PEAK / 1e12
+            roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": pk,
+                    "unit": "TFLOP/s (FP64 ops, no FMA)", "frac": ach / pk, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz"}
+    total_dev = sum(v[0] for v in timing.values())
+    shares = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / total_dev, 4) if total_dev else 0}
+              for k, v in timing.items() if v[1] > 0}
+
+    # FP64 path on the same problem
+    fp64 = None
+    if args.fp64_steps > 0 and rank == 0:
+        p64 = workload(W.PREC_FP64, args.nx, args.nx)
+        S64 = swnmg.Solver(p64, stream=stream)
+        U64 = torch.empty_like(U0)
+        U64.copy_(U0)
+        S64.solve(U64)   # warm-up
+        t64, c64, n64 = 0.0, 0, 0
+        for _ in range(args.fp64_steps):
+            U64.copy_(U0)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            i64 = S64.solve(U64)
+            e1.record(stream)
+            e1.synchronize()
+            t64 += e0.elapsed_time(e1)
+            c64 += i64["n_vcycles"]
+            n64 = i64["n_newton"]
+        diff = float((U64 - U).abs().max() / U64.abs().max())
+        fp64 = {"ms_per_step": t64 / args.fp64_steps, "cell_cycles_per_s": p.n * c64 / (t64 * 1e-3),
+                "n_newton": n64, "status": i64["status"], "max_rel_diff_mixed_vs_fp64": diff}
+        S64.close()
+
+    # end to end through the public API with host buffers
+    hU0 = torch.empty(U0.shape, dtype=torch.float64, pin_memory=True)
+    hU0.copy_(U0.cpu())
+    hU = torch.empty_like(hU0).pin_memory()
+    e2e_ms, e2e_cycles = 0.0, 0
+    for _ in range(max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        U.copy_(hU0, non_blocking=True)
+        info = S.solve(U)
+        hU.copy_(U, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_cycles += info["n_vcycles"]
+    e2e_ms = max_over_ranks(e2e_ms)
+    e2e = {"value": world * p.n * e2e_cycles / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": int(hU0.numel() * 8), "d2h_bytes_per_step": int(hU.numel() * 8),
+           "ms_per_step": e2e_ms / max(1, args.e2e_steps)}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (FP32 multigrid, FP64 residual/update)",
+           "data": "synthetic (seeded Gaussian-bump topography)", "config": config_dict(p, "256 MB flush between steps; working set > L2"),
+           "newton_steps": infos[-1]["n_newton"], "cycles_per_solve": infos[-1]["n_vcycles"],
+           "step1_blusgs_sweeps": infos[-1]["blusgs_sweeps"], "final_res": infos[-1]["final_res"],
+           "fp64": fp64, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+           "roofline": roof, "kernels": shares}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_sample(args.nx, args.cpu_sample_steps)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_sample(nx, nsteps=1):
+    """The CPU oracle on a bounded sample of the same workload: nsteps Newton
+    steps (BLU-SGS sweep, Jacobian, N_mg cycles, update) from the initial
+    state, one host thread."""
+    from oracle.oracle import Oracle
+    from paper_1608_06721_gb300 import workloads as W
+    p = workload(W.PREC_FP64, nx, nx)
+    o = Oracle(p, init_mode=W.INIT_NONE, max_newton=nsteps, tol=0.0)
+    t0 = time.perf_counter()
+    U, info = o.solve()
+    dt = time.perf_counter() - t0
+    return {"value": p.n * info["n_vcycles"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d Newton step(s) of the %dx%d workload from its initial state (Step 2 only), "
+                      "FP64 oracle, %.1f s" % (nsteps, nx, nx, dt), "seconds": dt}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_sample(args.nx, 1)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        r = cpu_sample(args.nx, 1)
+        vals.append(r["value"])
+        secs += r["seconds"]
+    value = sum(vals) / len(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded Gaussian-bump topography)",
+           "config": {"workload": "2D partial-dry channel %dx%d, one Newton step per step" % (args.nx, args.nx)},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "one Newton step (Step 2) of the %dx%d workload per step" % (args.nx, args.nx)},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=NX)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-sample-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--levels", type=int, default=LEVELS)
+    args = ap.parse_args()
+    globals()["LEVELS"] = args.levels
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

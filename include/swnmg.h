@@ -161,6 +161,33 @@ SWNMG_API swnmg_status swnmg_blusgs(swnmg_ctx* ctx, double* U_dev, int32_t level
  * Returns SWNMG_OK on convergence (sum ||R_i||_1 < tol). */
 SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* ctx, double* U_dev, swnmg_stats* st);
 
+/* Kernel classes timed by swnmg_set_timing (CUDA events on the context's
+ * stream around each launch of that class). */
+enum {
+  SWNMG_T_RESIDUAL = 0,     /* residual (eq. Res) */
+  SWNMG_T_JACOBIAN = 1,     /* FD Jacobian + regularisation, level 0 */
+  SWNMG_T_GALERKIN = 2,     /* coarse operators and block LU of all levels */
+  SWNMG_T_SGS_FINE = 3,     /* block SGS half-sweep on level 0 */
+  SWNMG_T_SGS_COARSE = 4,   /* block SGS half-sweeps on levels >= 1 */
+  SWNMG_T_TRANSFER = 5,     /* restriction, prolongation, zero fill */
+  SWNMG_T_BLUSGS = 6,       /* BLU-SGS half-sweep (any level) */
+  SWNMG_T_UPDATE = 7,       /* Newton update */
+  SWNMG_T_COARSE_EXACT = 8, /* exact coarsest-level solve */
+  SWNMG_T_COUNT = 9
+};
+
+/* Enables (1) or disables (0) per-class kernel timing and clears the totals. */
+SWNMG_API swnmg_status swnmg_set_timing(swnmg_ctx* ctx, int32_t enable);
+
+/* Accumulated device milliseconds and launch counts per class since the last
+ * swnmg_set_timing(ctx, 1); ms_out and launches_out hold SWNMG_T_COUNT
+ * entries.  Synchronises the stream. */
+SWNMG_API swnmg_status swnmg_get_timing(swnmg_ctx* ctx, double* ms_out, int64_t* launches_out);
+
+/* Total number of CUDA kernels this library has launched in this process
+ * (all contexts); differences around a region count its launches. */
+SWNMG_API int64_t swnmg_launch_count(void);
+
 /* Number of cells of level l (0 if l is out of range). */
 SWNMG_API int64_t swnmg_level_cells(const swnmg_ctx* ctx, int32_t level);
 

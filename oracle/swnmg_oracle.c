@@ -185,18 +185,25 @@ static void edge_eval(const orc_cfg* c, double hL, double uL, double vL, double 
 
 /* Subcritical inflow with prescribed outward discharge qn (< 0): the ghost
  * celerity c = sqrt(g h_g) solves qn/h_g + 2c = R_I, i.e.
- * 2c^3 - R_I c^2 + g qn = 0.  Newton's method from the right (the cubic is
- * convex there), a fixed 60 steps so that both implementations take the same
- * path. */
+ * f(c) = 2c^3 - R_I c^2 + g qn = 0.  f is convex and increasing right of its
+ * largest root, so Newton's method started right of the root (c = R_I, or 1,
+ * doubled until f > 0) decreases monotonically; it stops when an iterate no
+ * longer decreases (or after 60 steps). */
 static double inflow_celerity(double g, double RI, double qn) {
   double gq = g * qn;
-  double a = fabs(gq);
-  double c = ((RI > 0.0) ? RI : 0.0) + ((a > 1.0) ? a : 1.0);
+  double c = (RI > 0.0) ? RI : 1.0;
+  for (int k = 0; k < 200; ++k) {
+    double f = ((2.0 * c - RI) * c) * c + gq;
+    if (f > 0.0) break;
+    c = 2.0 * c;
+  }
   for (int it = 0; it < 60; ++it) {
     double f = ((2.0 * c - RI) * c) * c + gq;
     double fp = (6.0 * c - 2.0 * RI) * c;
     if (!(fp > 0.0)) break;
-    c = c - f / fp;
+    double cn = c - f / fp;
+    if (!(cn < c)) break;
+    c = cn;
   }
   return c;
 }
@@ -828,7 +835,8 @@ int orc_solve(const orc_cfg* c, const double* z0, double* U0, orc_stats* st) {
   double best = res;
   st->init_res = res;
   int status = ST_NOT_CONVERGED, it = 0;
-  while (it < c->max_newton) {
+  if (!isfinite(res) || !finite_vec(U0, (size_t)n * nc)) status = ST_NONFINITE;
+  while (status == ST_NOT_CONVERGED && it < c->max_newton) {
     if (res < c->tol) { status = ST_OK; break; }
     orc_blusgs(c, 0, zl[0], U0, 1);                         /* Step 2.1 */
     orc_jacobian(c, 0, zl[0], U0, R, NULL, blk);            /* eq. NewtonREG */

@@ -2,6 +2,7 @@
 // host side of Algorithm 1 (NMGM) and Algorithm 0 (gamma-cycle).
 #include <chrono>
 #include <cmath>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -56,8 +57,17 @@ struct swnmg_ctx {
   double* red = nullptr;    // reduction partials (1024) + result
   double* band = nullptr;   // exact coarse-solve scratch
   int* derr = nullptr;
-  double* hbuf = nullptr;   // pinned host scalar
+  int* sgs_sync = nullptr;  // ticket / abort / per-strip progress of the wavefront sweeps
+  int* sticky = nullptr;    // set by a device wait that ran out of its bound
+  double* hbuf = nullptr;   // pinned host scalars
   bool coarse_exact = false;
+  // per-class kernel timing: event pairs resolved at synchronisation points
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_class;     // class of pair k (events 2k, 2k+1)
+  int ev_used = 0;
+  double t_ms[SWNMG_T_COUNT] = {0};
+  long long t_n[SWNMG_T_COUNT] = {0};
   std::string err;
 };
 
@@ -121,6 +131,36 @@ swnmg_status check_params(const swnmg_problem* p, const swnmg_params* q) {
   return SWNMG_OK;
 }
 
+// ---- kernel timing ------------------------------------------------------------
+void timing_resolve(swnmg_ctx* c) {
+  if (c->ev_used == 0) return;
+  cudaEventSynchronize(c->ev_pool[2 * (c->ev_used - 1) + 1]);
+  for (int k = 0; k < c->ev_used; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[2 * k], c->ev_pool[2 * k + 1]) == cudaSuccess) {
+      c->t_ms[c->ev_class[k]] += ms;
+      c->t_n[c->ev_class[k]] += 1;
+    }
+  }
+  c->ev_used = 0;
+}
+
+// RAII scope: records start/stop events around the launches of one class
+struct TimedScope {
+  swnmg_ctx* c;
+  int k = -1;
+  TimedScope(swnmg_ctx* ctx, int cls) : c(ctx) {
+    if (!c->timing) return;
+    if (c->ev_used * 2 + 2 > (int)c->ev_pool.size()) timing_resolve(c);
+    k = c->ev_used++;
+    c->ev_class[k] = cls;
+    cudaEventRecord(c->ev_pool[2 * k], c->st);
+  }
+  ~TimedScope() {
+    if (k >= 0) cudaEventRecord(c->ev_pool[2 * k + 1], c->st);
+  }
+};
+
 // sum_i v_i over n doubles (fixed-order device reduction), synchronises
 swnmg_status device_sum(swnmg_ctx* c, const double* v, int n, double* out) {
   launch_sum(v, n, c->red, c->red + 1024, c->st);
@@ -131,34 +171,62 @@ swnmg_status device_sum(swnmg_ctx* c, const double* v, int n, double* out) {
   return SWNMG_OK;
 }
 
+// reports a device-side wait that ran out of its bound (the wavefront sweeps)
+swnmg_status check_sticky(swnmg_ctx* c) {
+  int* h = reinterpret_cast<int*>(c->hbuf + 1);
+  CUDA_TRY(c, cudaMemcpyAsync(h, c->sticky, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  if (*h) {
+    cudaMemsetAsync(c->sticky, 0, sizeof(int), c->st);
+    return fail(c, SWNMG_ERR_TIMEOUT, "a wavefront sweep waited past its bound");
+  }
+  return SWNMG_OK;
+}
+
 swnmg_status level_residual_sum(swnmg_ctx* c, int l, const double* U, double* out) {
   DevLevel L = dev_level(c, l);
-  launch_residual(L, c->lv[l].z, U, c->R, c->rn, c->eb, c->st);
+  {
+    TimedScope ts(c, SWNMG_T_RESIDUAL);
+    launch_residual(L, c->lv[l].z, U, c->R, c->rn, c->eb, c->st);
+  }
   LAUNCH_CHECK(c);
   return device_sum(c, c->rn, L.n, out);
+}
+
+void sgs_half(swnmg_ctx* c, int l, int forward) {
+  Level& v = c->lv[l];
+  TimedScope ts(c, l == 0 ? SWNMG_T_SGS_FINE : SWNMG_T_SGS_COARSE);
+  launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward, c->fp32, c->sgs_sync,
+                   c->sticky, c->st);
+}
+
+void blusgs_half(swnmg_ctx* c, int l, double* U, int forward) {
+  DevLevel L = dev_level(c, l);
+  TimedScope ts(c, SWNMG_T_BLUSGS);
+  launch_blusgs_sweep(L, c->lv[l].z, U, forward, c->st);
 }
 
 // Algorithm 0 on level l with lv[l].b, lv[l].x
 swnmg_status coarse_solve(swnmg_ctx* c, int l) {
   Level& v = c->lv[l];
   if (c->coarse_exact) {
+    TimedScope ts(c, SWNMG_T_COARSE_EXACT);
     launch_coarse_exact(c->nc, v.nx, v.ny, v.blk, v.b, v.x, c->band, c->derr, c->fp32, c->st);
     LAUNCH_CHECK(c);
     return SWNMG_OK;
   }
   for (int k = 0; k < c->prm.coarse_sweeps; ++k) {
-    launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, 1, c->fp32, c->st);
-    launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, 0, c->fp32, c->st);
+    sgs_half(c, l, 1);
+    sgs_half(c, l, 0);
   }
   LAUNCH_CHECK(c);
   return SWNMG_OK;
 }
 
 swnmg_status smooth(swnmg_ctx* c, int l, int nsym) {
-  Level& v = c->lv[l];
   for (int k = 0; k < nsym; ++k) {
-    launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, 1, c->fp32, c->st);
-    launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, 0, c->fp32, c->st);
+    sgs_half(c, l, 1);
+    sgs_half(c, l, 0);
   }
   LAUNCH_CHECK(c);
   return SWNMG_OK;
@@ -170,26 +238,37 @@ swnmg_status mg_cycle(swnmg_ctx* c, int l) {
   if ((s = smooth(c, l, c->prm.nu1)) != SWNMG_OK) return s;
   Level& v = c->lv[l];
   Level& w = c->lv[l + 1];
-  launch_restrict(c->prob.dim, c->nc, v.nx, v.ny, v.blk, v.b, v.x, w.b, c->fp32, c->st);
-  launch_fill(w.x, c->fp32, (long long)c->nc * w.n, c->st);
+  {
+    TimedScope ts(c, SWNMG_T_TRANSFER);
+    launch_restrict(c->prob.dim, c->nc, v.nx, v.ny, v.blk, v.b, v.x, w.b, c->fp32, c->st);
+    launch_fill(w.x, c->fp32, (long long)c->nc * w.n, c->st);
+  }
   LAUNCH_CHECK(c);
   const int gam = (l == 0) ? 1 : c->prm.gamma;
   for (int k = 0; k < gam; ++k)
     if ((s = mg_cycle(c, l + 1)) != SWNMG_OK) return s;
-  launch_prolong(c->prob.dim, c->nc, v.nx, v.ny, w.x, v.x, c->fp32, c->st);
+  {
+    TimedScope ts(c, SWNMG_T_TRANSFER);
+    launch_prolong(c->prob.dim, c->nc, v.nx, v.ny, w.x, v.x, c->fp32, c->st);
+  }
   LAUNCH_CHECK(c);
   return smooth(c, l, c->prm.nu2);
 }
 
 swnmg_status assemble(swnmg_ctx* c, const double* U) {
   DevLevel L = dev_level(c, 0);
-  launch_jacobian(L, c->lv[0].z, U, c->R, c->rn, c->eb, c->lv[0].blk, c->fp32, c->st);
+  {
+    TimedScope ts(c, SWNMG_T_JACOBIAN);
+    launch_jacobian(L, c->lv[0].z, U, c->R, c->rn, c->eb, c->lv[0].blk, c->fp32, c->st);
+  }
   LAUNCH_CHECK(c);
+  TimedScope ts(c, SWNMG_T_GALERKIN);
   for (int l = 0; l < c->nl; ++l)
     launch_galerkin(c->prob.dim, c->nc, c->lv[l].nx, c->lv[l].ny, c->lv[l].blk, c->lv[l + 1].blk,
                     c->fp32, c->st);
   for (int l = 0; l <= c->nl; ++l)
-    launch_lu_factor(c->lv[l].n, c->nc, c->lv[l].blk, c->lv[l].lu, c->lv[l].piv, c->fp32, c->st);
+    launch_lu_factor(c->lv[l].nx, c->lv[l].ny, c->nc, c->lv[l].blk, c->lv[l].lu, c->lv[l].piv, c->fp32,
+                     c->st);
   LAUNCH_CHECK(c);
   return SWNMG_OK;
 }
@@ -210,7 +289,11 @@ void free_ctx(swnmg_ctx* c) {
   if (c->red) cudaFree(c->red);
   if (c->band) cudaFree(c->band);
   if (c->derr) cudaFree(c->derr);
+  if (c->sgs_sync) cudaFree(c->sgs_sync);
+  if (c->sticky) cudaFree(c->sticky);
   if (c->hbuf) cudaFreeHost(c->hbuf);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  c->ev_pool.clear();
 }
 
 }  // namespace
@@ -298,11 +381,17 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
       v.ey = 0.0;
     }
     const size_t n = v.n;
+    const size_t P = (size_t)skew_slots(v.nx, v.ny);   // strip-skewed operator slots
     ALLOC(v.z, n * sizeof(double));
     if (l > 0) ALLOC(v.U, n * c->nc * sizeof(double));
-    ALLOC(v.blk, n * 5 * c->nc * c->nc * c->wsz);
-    ALLOC(v.lu, n * LU_E * c->wsz);
-    ALLOC(v.piv, n);
+    ALLOC(v.blk, P * 5 * c->nc * c->nc * c->wsz);
+    ALLOC(v.lu, P * LU_E * c->wsz);
+    ALLOC(v.piv, P);
+    if (cudaMemset(v.blk, 0, P * 5 * c->nc * c->nc * c->wsz) != cudaSuccess ||
+        cudaMemset(v.lu, 0, P * LU_E * c->wsz) != cudaSuccess || cudaMemset(v.piv, 0, P) != cudaSuccess) {
+      rc = fail(c, SWNMG_ERR_CUDA, "memset of the operator arrays");
+      goto fail_out;
+    }
     ALLOC(v.b, n * c->nc * c->wsz);
     ALLOC(v.x, n * c->nc * c->wsz);
   }
@@ -314,6 +403,8 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
     ALLOC(c->eb, n_e * (2 * c->nc + 2 * c->nc * c->nc) * sizeof(double));
     ALLOC(c->red, 1032 * sizeof(double));
     ALLOC(c->derr, sizeof(int));
+    ALLOC(c->sgs_sync, sizeof(int) * (2 + (v0.ny + 31) / 32 + 8));
+    ALLOC(c->sticky, sizeof(int));
   }
   {
     const Level& vc = c->lv[c->nl];
@@ -330,7 +421,11 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
       ALLOC(c->band, (size_t)words * sizeof(double));
     }
   }
-  if (cudaMallocHost((void**)&c->hbuf, 16) != cudaSuccess) {
+  if (cudaMemsetAsync(c->sticky, 0, sizeof(int), c->st) != cudaSuccess) {
+    rc = fail(c, SWNMG_ERR_CUDA, "memset");
+    goto fail_out;
+  }
+  if (cudaMallocHost((void**)&c->hbuf, 32) != cudaSuccess) {
     rc = fail(c, SWNMG_ERR_OOM, "cudaMallocHost");
     goto fail_out;
   }
@@ -400,7 +495,7 @@ SWNMG_API swnmg_status swnmg_get_blocks(swnmg_ctx* c, int32_t level, double* hos
   const size_t cnt = (size_t)v.n * 5 * c->nc * c->nc;
   double* tmp = nullptr;
   CUDA_TRY(c, cudaMalloc((void**)&tmp, cnt * sizeof(double)));
-  launch_blocks_export(v.n, c->nc, v.blk, c->fp32, tmp, c->st);
+  launch_blocks_export(v.nx, v.ny, c->nc, v.blk, c->fp32, tmp, c->st);
   cudaError_t e1 = cudaGetLastError();
   cudaError_t e2 = cudaMemcpyAsync(host_out, tmp, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->st);
   cudaError_t e3 = cudaStreamSynchronize(c->st);
@@ -423,8 +518,7 @@ SWNMG_API swnmg_status swnmg_vcycle(swnmg_ctx* c, const double* rhs, double* dU,
   }
   launch_convert(v.x, c->fp32, dU, 0, m, 1.0, c->st);
   LAUNCH_CHECK(c);
-  CUDA_TRY(c, cudaStreamSynchronize(c->st));
-  return SWNMG_OK;
+  return check_sticky(c);
 }
 
 SWNMG_API swnmg_status swnmg_sgs_sweep(swnmg_ctx* c, int32_t level, const double* rhs, double* x,
@@ -434,19 +528,20 @@ SWNMG_API swnmg_status swnmg_sgs_sweep(swnmg_ctx* c, int32_t level, const double
   const long long m = (long long)v.n * c->nc;
   launch_convert(rhs, 0, v.b, c->fp32, m, 1.0, c->st);
   launch_convert(x, 0, v.x, c->fp32, m, 1.0, c->st);
-  launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward ? 1 : 0, c->fp32, c->st);
+  launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward ? 1 : 0, c->fp32,
+                   c->sgs_sync, c->sticky, c->st);
   launch_convert(v.x, c->fp32, x, 0, m, 1.0, c->st);
   LAUNCH_CHECK(c);
-  CUDA_TRY(c, cudaStreamSynchronize(c->st));
-  return SWNMG_OK;
+  return check_sticky(c);
 }
 
 SWNMG_API swnmg_status swnmg_blusgs(swnmg_ctx* c, double* U, int32_t level, int32_t nsweeps) {
   if (!c || !U || level < 0 || level > c->nl || nsweeps < 0) return fail(c, SWNMG_ERR_ARG, "bad argument");
   DevLevel L = dev_level(c, level);
+  (void)L;
   for (int k = 0; k < nsweeps; ++k) {
-    launch_blusgs_sweep(L, c->lv[level].z, U, 1, c->st);
-    launch_blusgs_sweep(L, c->lv[level].z, U, 0, c->st);
+    blusgs_half(c, level, U, 1);
+    blusgs_half(c, level, U, 0);
   }
   LAUNCH_CHECK(c);
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
@@ -477,9 +572,10 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
       if ((s = level_residual_sum(c, l, c->lv[l].U, &res)) != SWNMG_OK) return s;
       int nsw = 0;
       DevLevel L = dev_level(c, l);
+      (void)L;
       while (res >= thr && nsw < c->prm.max_blusgs && std::isfinite(res)) {
-        launch_blusgs_sweep(L, c->lv[l].z, c->lv[l].U, 1, c->st);
-        launch_blusgs_sweep(L, c->lv[l].z, c->lv[l].U, 0, c->st);
+        blusgs_half(c, l, c->lv[l].U, 1);
+        blusgs_half(c, l, c->lv[l].U, 0);
         LAUNCH_CHECK(c);
         ++nsw;
         if ((s = level_residual_sum(c, l, c->lv[l].U, &res)) != SWNMG_OK) return s;
@@ -500,12 +596,12 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
   if ((s = level_residual_sum(c, 0, U, &res)) != SWNMG_OK) return s;
   st->init_res = res;
   double best = res;
-  swnmg_status status = SWNMG_ERR_NOT_CONVERGED;
+  swnmg_status status = std::isfinite(res) ? SWNMG_ERR_NOT_CONVERGED : SWNMG_ERR_NONFINITE;
   int it = 0;
-  while (it < c->prm.max_newton) {
+  while (status == SWNMG_ERR_NOT_CONVERGED && it < c->prm.max_newton) {
     if (res < c->prm.tol) { status = SWNMG_OK; break; }
-    launch_blusgs_sweep(L0, v0.z, U, 1, c->st);                    // Step 2.1
-    launch_blusgs_sweep(L0, v0.z, U, 0, c->st);
+    blusgs_half(c, 0, U, 1);                                       // Step 2.1
+    blusgs_half(c, 0, U, 0);
     LAUNCH_CHECK(c);
     if ((s = assemble(c, U)) != SWNMG_OK) return s;                // eq. NewtonREG
     launch_convert(c->R, 0, v0.b, c->fp32, m, -1.0, c->st);        // b = -R
@@ -513,10 +609,14 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
     LAUNCH_CHECK(c);
     for (int k = 0; k < c->prm.n_mg; ++k)                          // Step 2.2
       if ((s = mg_cycle(c, 0)) != SWNMG_OK) return s;
-    launch_newton_update(v0.n, nc, c->prm.tau, c->prm.h_eps, U, v0.x, c->fp32, c->st);   // Step 2.3
+    {
+      TimedScope ts(c, SWNMG_T_UPDATE);                            // Step 2.3
+      launch_newton_update(v0.n, nc, c->prm.tau, c->prm.h_eps, U, v0.x, c->fp32, c->st);
+    }
     LAUNCH_CHECK(c);
     ++it;
     st->n_vcycles += c->prm.n_mg;
+    if ((s = check_sticky(c)) != SWNMG_OK) return s;
     if ((s = level_residual_sum(c, 0, U, &res)) != SWNMG_OK) return s;   // Step 3
     if (it <= SWNMG_HIST) st->res_hist[it - 1] = res;
     if (!std::isfinite(res)) { status = SWNMG_ERR_NONFINITE; break; }
@@ -533,3 +633,28 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
   if (status != SWNMG_OK) return fail(c, status, "after " + std::to_string(it) + " Newton steps");
   return SWNMG_OK;
 }
+
+SWNMG_API swnmg_status swnmg_set_timing(swnmg_ctx* c, int32_t enable) {
+  if (!c) return fail(c, SWNMG_ERR_ARG, "null context");
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  c->ev_used = 0;
+  for (int k = 0; k < SWNMG_T_COUNT; ++k) { c->t_ms[k] = 0; c->t_n[k] = 0; }
+  if (enable && c->ev_pool.empty()) {
+    const int pairs = 4096;
+    c->ev_pool.resize(2 * pairs);
+    c->ev_class.resize(pairs);
+    for (auto& e : c->ev_pool) CUDA_TRY(c, cudaEventCreate(&e));
+  }
+  c->timing = enable != 0;
+  return SWNMG_OK;
+}
+
+SWNMG_API swnmg_status swnmg_get_timing(swnmg_ctx* c, double* ms_out, int64_t* n_out) {
+  if (!c || !ms_out || !n_out) return fail(c, SWNMG_ERR_ARG, "null pointer");
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  timing_resolve(c);
+  for (int k = 0; k < SWNMG_T_COUNT; ++k) { ms_out[k] = c->t_ms[k]; n_out[k] = c->t_n[k]; }
+  return SWNMG_OK;
+}
+
+SWNMG_API int64_t swnmg_launch_count(void) { return launches_total(); }

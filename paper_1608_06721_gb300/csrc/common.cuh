@@ -1,12 +1,20 @@
 // Internal declarations shared by the CUDA translation units of libswnmg.
 //
-// Device data layout (all SoA, x-fastest cell index i = ix + nx*iy):
-//   state U, residual R, vectors b/x : [c*n + i]
-//   operator blocks of a level       : blk[(b*nc*nc + s*nc + k)*n + i]
+// Device data layout (SoA, x-fastest cell index i = ix + nx*iy):
+//   state U, residual R, vectors b/x : [c*n + i]  (row-major)
+//   operator blocks of a level       : blk[(b*nc*nc + s*nc + k)*P + spos(i)]
 //        b = 0 diagonal (raw, with alpha||R_i||_1), 1 W, 2 E, 3 S, 4 N
-//   LU factors of the diagonal       : lu[e*n + i], e = 0..8 (see LU layout below)
-//        + perm code piv[i] (int8)
+//   LU factors of the diagonal       : lu[e*P + spos(i)], e = 0..8 (LU layout below)
+//        + perm code piv[spos(i)] (int8)
 //   per-edge Jacobian pieces          : x-edges (nx+1)*ny then y-edges nx*(ny+1)
+//
+// Strip-skewed operator layout.  Rows are grouped in strips of 32; cell
+// (ix, iy) of strip t = iy/32, lane k = iy%32 sits on skewed diagonal
+// d = ix + k and is stored at spos = (t*(nx+31) + d)*32 + k.  The block
+// Gauss-Seidel wavefront updates one skewed diagonal of a strip per warp
+// step (lane k at column d - k), so every step reads one contiguous line of
+// 32 values per entry, in either sweep direction.  P = strips*(nx+31)*32
+// slots per entry (padding slots are never read as data).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -40,11 +48,22 @@ constexpr int LU_E = 9;
 
 inline int blk_entries(int nc) { return 5 * nc * nc; }
 
+__host__ __device__ __forceinline__ long long skew_pos(int ix, int iy, int nx) {
+  return ((long long)(iy >> 5) * (nx + 31) + (ix + (iy & 31))) * 32 + (iy & 31);
+}
+__host__ __device__ __forceinline__ long long skew_slots(int nx, int ny) {
+  return (long long)((ny + 31) >> 5) * (nx + 31) * 32;
+}
+
+// process-wide count of kernel launches issued by the library
+void count_launches(long long k);
+long long launches_total();
+
 // ---- host-side launch wrappers (flux.cu) ---------------------------------
 void launch_residual(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
                      double* edge_buf, cudaStream_t st);
 void launch_jacobian(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
-                     double* edge_buf, void* blk, int fp32, cudaStream_t st);
+                     double* edge_buf, void* blk, int fp32, cudaStream_t st);   // blk skewed
 void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forward,
                          cudaStream_t st);
 void launch_newton_update(int n, int nc, double tau, double h_eps, double* U, const void* dU,
@@ -55,7 +74,7 @@ void launch_inject(int dim, int nxf, int nyf, int ncomp, const double* vc, doubl
                    cudaStream_t st);
 
 // ---- host-side launch wrappers (mg.cu) -----------------------------------
-void launch_lu_factor(int n, int nc, const void* blk, void* lu, int8_t* piv, int fp32,
+void launch_lu_factor(int nx, int ny, int nc, const void* blk, void* lu, int8_t* piv, int fp32,
                       cudaStream_t st);
 void launch_galerkin(int dim, int nc, int nxf, int nyf, const void* bf, void* bc, int fp32,
                      cudaStream_t st);
@@ -64,13 +83,15 @@ void launch_restrict(int dim, int nc, int nxf, int nyf, const void* blk, const v
 void launch_prolong(int dim, int nc, int nxf, int nyf, const void* xc, void* xf, int fp32,
                     cudaStream_t st);
 void launch_sgs_sweep(int nc, int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
-                      const void* b, void* x, int forward, int fp32, cudaStream_t st);
+                      const void* b, void* x, int forward, int fp32, int* sync, int* sticky_err,
+                      cudaStream_t st);
 void launch_coarse_exact(int nc, int nx, int ny, const void* blk, const void* b, void* x,
                          double* band, int* err, int fp32, cudaStream_t st);
 void launch_sum(const double* v, int n, double* partial, double* out, cudaStream_t st);
 void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n,
                     double scale, cudaStream_t st);
 void launch_fill(void* dst, int fp32, long long n, cudaStream_t st);
-void launch_blocks_export(int n, int nc, const void* blk, int fp32, double* out, cudaStream_t st);
+void launch_blocks_export(int nx, int ny, int nc, const void* blk, int fp32, double* out,
+                          cudaStream_t st);
 
 }  // namespace swnmg

@@ -88,17 +88,24 @@ __device__ __forceinline__ void edge_eval(const DevLevel& L, Prim a, double za, 
   out[4] = L.half_g * (hr * hr);
 }
 
-// Subcritical inflow: celerity c of the ghost from 2c^3 - R c^2 + g qn = 0,
-// Newton from the right, 60 fixed steps.
+// Subcritical inflow: celerity c of the ghost from f(c) = 2c^3 - R c^2 + g qn
+// = 0.  Start right of the largest root (c = R, or 1, doubled until f > 0),
+// then Newton steps while the iterate keeps decreasing (at most 60).
 __device__ double inflow_celerity(double g, double RI, double qn) {
   const double gq = g * qn;
-  const double a = fabs(gq);
-  double c = ((RI > 0.0) ? RI : 0.0) + ((a > 1.0) ? a : 1.0);
+  double c = (RI > 0.0) ? RI : 1.0;
+  for (int k = 0; k < 200; ++k) {
+    const double f = ((2.0 * c - RI) * c) * c + gq;
+    if (f > 0.0) break;
+    c = 2.0 * c;
+  }
   for (int it = 0; it < 60; ++it) {
     const double f = ((2.0 * c - RI) * c) * c + gq;
     const double fp = (6.0 * c - 2.0 * RI) * c;
     if (!(fp > 0.0)) break;
-    c = c - f / fp;
+    const double cn = c - f / fp;
+    if (!(cn < c)) break;
+    c = cn;
   }
   return c;
 }
@@ -243,9 +250,11 @@ __device__ __forceinline__ void cell_edges(const DevLevel& L, int i, int n_xe, i
 }
 
 // R_i = sum over W, E, S, N of |e| G (eq. Res), ||R_i||_1
+// (a non-finite cell state makes ||R_i||_1 NaN, so that the sums report it:
+// the reconstruction's max(0, .) would otherwise hide a NaN depth)
 template <int NC>
-__global__ void k_res_cells(DevLevel L, const double* __restrict__ eb, double* __restrict__ R,
-                            double* __restrict__ rn, int n_xe, int n_e) {
+__global__ void k_res_cells(DevLevel L, const double* __restrict__ eb, const double* __restrict__ U,
+                            double* __restrict__ R, double* __restrict__ rn, int n_xe, int n_e) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.n) return;
   int eW, eE, eS, eN;
@@ -264,7 +273,9 @@ __global__ void k_res_cells(DevLevel L, const double* __restrict__ eb, double* _
   }
   double m = fabs(r[0]) + fabs(r[1]);
   if (NC == 3) m = m + fabs(r[NC - 1]);
-  if (rn) rn[i] = m;
+  bool fin = true;
+  for (int s = 0; s < NC; ++s) fin = fin && isfinite(U[(long long)s * L.n + i]);
+  if (rn) rn[i] = fin ? m : __longlong_as_double(0x7ff8000000000000LL);
 }
 
 // ---- finite-difference Jacobian ---------------------------------------------
@@ -281,7 +292,9 @@ __global__ void k_jac_edges(DevLevel L, const double* __restrict__ z, const doub
   int axis, iL, iR;
   double len;
   edge_cells(L, e, n_xe, axis, iL, iR, len);
-  const long long ne = n_e, n = L.n;
+  const long long ne = n_e, P = skew_slots(L.nx, L.ny);
+  const long long sL = iL >= 0 ? skew_pos(iL % L.nx, iL / L.nx, L.nx) : 0;
+  const long long sR = iR >= 0 ? skew_pos(iR % L.nx, iR / L.nx, L.nx) : 0;
   double cL[NC], cR[NC], GLb[NC], GRb[NC], GL[NC], GR[NC];
   if (iL >= 0) load_c<NC>(U, L.n, iL, cL);
   if (iR >= 0) load_c<NC>(U, L.n, iR, cR);
@@ -305,13 +318,13 @@ __global__ void k_jac_edges(DevLevel L, const double* __restrict__ z, const doub
       eval_edge_states<NC>(L, axis, c, zL, pR, zR, GL, GR);
       for (int s = 0; s < NC; ++s) {
         eb[(f_dLL + s * NC + k) * ne + e] = len * ((GL[s] - GLb[s]) * L.reps);
-        if (iR >= 0) st<T>(blk, ((long long)(bR * NC * NC + s * NC + k)) * n + iR,
+        if (iR >= 0) st<T>(blk, ((long long)(bR * NC * NC + s * NC + k)) * P + sR,
                            len * ((GR[s] - GRb[s]) * L.reps));
       }
     } else {
       for (int s = 0; s < NC; ++s) {
         eb[(f_dLL + s * NC + k) * ne + e] = 0.0;
-        st<T>(blk, ((long long)(bR * NC * NC + s * NC + k)) * n + iR, 0.0);
+        st<T>(blk, ((long long)(bR * NC * NC + s * NC + k)) * P + sR, 0.0);
       }
     }
   }
@@ -324,13 +337,13 @@ __global__ void k_jac_edges(DevLevel L, const double* __restrict__ z, const doub
       eval_edge_states<NC>(L, axis, pL, zL, c, zR, GL, GR);
       for (int s = 0; s < NC; ++s) {
         eb[(f_dRR + s * NC + k) * ne + e] = len * ((GR[s] - GRb[s]) * L.reps);
-        if (iL >= 0) st<T>(blk, ((long long)(bL * NC * NC + s * NC + k)) * n + iL,
+        if (iL >= 0) st<T>(blk, ((long long)(bL * NC * NC + s * NC + k)) * P + sL,
                            len * ((GL[s] - GLb[s]) * L.reps));
       }
     } else {
       for (int s = 0; s < NC; ++s) {
         eb[(f_dRR + s * NC + k) * ne + e] = 0.0;
-        st<T>(blk, ((long long)(bL * NC * NC + s * NC + k)) * n + iL, 0.0);
+        st<T>(blk, ((long long)(bL * NC * NC + s * NC + k)) * P + sL, 0.0);
       }
     }
   }
@@ -345,7 +358,8 @@ __global__ void k_jac_cells(DevLevel L, const double* __restrict__ eb, double* _
   if (i >= L.n) return;
   int eW, eE, eS, eN;
   cell_edges(L, i, n_xe, eW, eE, eS, eN);
-  const long long ne = n_e, n = L.n;
+  const long long ne = n_e, n = L.n, P = skew_slots(L.nx, L.ny);
+  const long long si = skew_pos(i % L.nx, i / L.nx, L.nx);
   double r[NC];
   for (int s = 0; s < NC; ++s) {
     double a = 0.0;
@@ -374,7 +388,7 @@ __global__ void k_jac_cells(DevLevel L, const double* __restrict__ eb, double* _
         d = d + eb[(f_dLL + f) * ne + eN];
       }
       if (s == k) d = d + am;
-      st<T>(blk, (long long)f * n + i, d);
+      st<T>(blk, (long long)f * P + si, d);
     }
 }
 
@@ -573,19 +587,21 @@ static void edge_counts(const DevLevel& L, int& n_xe, int& n_e) {
 
 void launch_residual(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
                      double* eb, cudaStream_t st) {
+  count_launches(2);
   int n_xe, n_e;
   edge_counts(L, n_xe, n_e);
   if (L.nc == 3) {
     k_res_edges<3><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, n_xe, n_e);
-    k_res_cells<3><<<nblk(L.n, 256), 256, 0, st>>>(L, eb, R, rn, n_xe, n_e);
+    k_res_cells<3><<<nblk(L.n, 256), 256, 0, st>>>(L, eb, U, R, rn, n_xe, n_e);
   } else {
     k_res_edges<2><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, n_xe, n_e);
-    k_res_cells<2><<<nblk(L.n, 256), 256, 0, st>>>(L, eb, R, rn, n_xe, n_e);
+    k_res_cells<2><<<nblk(L.n, 256), 256, 0, st>>>(L, eb, U, R, rn, n_xe, n_e);
   }
 }
 
 void launch_jacobian(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
                      double* eb, void* blk, int fp32, cudaStream_t st) {
+  count_launches(2);
   int n_xe, n_e;
   edge_counts(L, n_xe, n_e);
   if (L.nc == 3) {
@@ -609,24 +625,23 @@ void launch_jacobian(const DevLevel& L, const double* z, const double* U, double
 
 void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forward,
                          cudaStream_t st) {
+  count_launches(L.nx + L.ny - 1);
   const int ndiag = L.nx + L.ny - 1;
   for (int q = 0; q < ndiag; ++q) {
     const int d = forward ? q : ndiag - 1 - q;
     const int ix0 = d - (L.ny - 1) > 0 ? d - (L.ny - 1) : 0;
     const int ix1 = d < L.nx - 1 ? d : L.nx - 1;
     const int ncell = ix1 - ix0 + 1;
-    if (L.nc == 3) {
-      const int thr = ncell * 4, bs = thr < 128 ? ((thr + 31) / 32) * 32 : 128;
-      k_blusgs_diag<3, 4><<<nblk(thr, bs), bs, 0, st>>>(L, z, U, d, ix0, ncell);
-    } else {
-      const int thr = ncell * 2, bs = thr < 128 ? ((thr + 31) / 32) * 32 : 128;
-      k_blusgs_diag<2, 2><<<nblk(thr, bs), bs, 0, st>>>(L, z, U, d, ix0, ncell);
-    }
+    // one warp per block: the FP64 pipe of an SM serves one warp, so the
+    // cells of a diagonal are spread over as many SMs as possible
+    if (L.nc == 3) k_blusgs_diag<3, 4><<<nblk(ncell * 4, 32), 32, 0, st>>>(L, z, U, d, ix0, ncell);
+    else k_blusgs_diag<2, 2><<<nblk(ncell * 2, 32), 32, 0, st>>>(L, z, U, d, ix0, ncell);
   }
 }
 
 void launch_newton_update(int n, int nc, double tau, double h_eps, double* U, const void* dU,
                           int dU_fp32, cudaStream_t st) {
+  count_launches(1);
   if (dU_fp32)
     k_newton_update<float><<<nblk(n, 256), 256, 0, st>>>(n, nc, tau, h_eps, U, (const float*)dU);
   else
@@ -635,12 +650,14 @@ void launch_newton_update(int n, int nc, double tau, double h_eps, double* U, co
 
 void launch_average(int dim, int nxf, int nyf, int ncomp, const double* vf, double* vc,
                     cudaStream_t st) {
+  count_launches(1);
   const int ncells = (nxf / 2) * (dim == 2 ? nyf / 2 : 1);
   k_average<<<nblk(ncells, 256), 256, 0, st>>>(dim, nxf, nyf, ncomp, vf, vc);
 }
 
 void launch_inject(int dim, int nxf, int nyf, int ncomp, const double* vc, double* vf,
                    cudaStream_t st) {
+  count_launches(1);
   const int ncells = nxf * (dim == 2 ? nyf : 1);
   k_inject<<<nblk(ncells, 256), 256, 0, st>>>(dim, nxf, nyf, ncomp, vc, vf);
 }

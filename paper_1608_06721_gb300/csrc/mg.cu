@@ -1,6 +1,8 @@
 // mg.cu -- geometric multigrid pieces of Section 2.3 (eq. MatrixForm,
 // ProjectAR, Project, correction; Algorithm 0's smoother and coarse solve),
 // templated on the working precision (double, or float in the mixed mode).
+#include <atomic>
+
 #include "common.cuh"
 
 namespace swnmg {
@@ -16,16 +18,24 @@ template <typename T> __device__ __forceinline__ T tabs(T a) { return a < T(0) ?
 // 1e-14 max|D| marks a singular unknown (its reciprocal pivot is stored as 0,
 // so its correction is 0).
 template <int NC, typename T>
-__global__ void k_lu_factor(int n, const T* __restrict__ blk, T* __restrict__ lu,
+__global__ void k_lu_factor(int nx, int ny, const T* __restrict__ blk, T* __restrict__ lu,
                             int8_t* __restrict__ piv) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const long long P = skew_slots(nx, ny);
+  const long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (slot >= P) return;
+  // slot -> cell: lane k of strip t on skewed diagonal d is (d - k, 32 t + k)
+  const int k = (int)(slot & 31);
+  const long long line = slot >> 5;
+  const int t = (int)(line / (nx + 31)), d = (int)(line % (nx + 31));
+  const int ix = d - k, iy = 32 * t + k;
+  if (ix < 0 || ix >= nx || iy >= ny) return;
+  const long long i = slot;
   T m[NC][NC];
   T amax = T(0);
   for (int s = 0; s < NC; ++s)
-    for (int k = 0; k < NC; ++k) {
-      m[s][k] = blk[(long long)(s * NC + k) * n + i];
-      amax = tabs(m[s][k]) > amax ? tabs(m[s][k]) : amax;
+    for (int q = 0; q < NC; ++q) {
+      m[s][q] = blk[(long long)(s * NC + q) * P + i];
+      amax = tabs(m[s][q]) > amax ? tabs(m[s][q]) : amax;
     }
   const T tiny = T(1e-14) * amax;
   int perm[3] = {0, 1, 2};
@@ -36,8 +46,8 @@ __global__ void k_lu_factor(int n, const T* __restrict__ blk, T* __restrict__ lu
     for (int r = c + 1; r < NC; ++r)
       if (tabs(m[r][c]) > best) { best = tabs(m[r][c]); p = r; }
     if (p != c) {
-      for (int k = 0; k < NC; ++k) { T t = m[c][k]; m[c][k] = m[p][k]; m[p][k] = t; }
-      int t = perm[c]; perm[c] = perm[p]; perm[p] = t;
+      for (int q = 0; q < NC; ++q) { T tt = m[c][q]; m[c][q] = m[p][q]; m[p][q] = tt; }
+      int tt = perm[c]; perm[c] = perm[p]; perm[p] = tt;
     }
     if (!(best > tiny)) {
       for (int r = c + 1; r < NC; ++r) m[r][c] = T(0);
@@ -48,40 +58,40 @@ __global__ void k_lu_factor(int n, const T* __restrict__ blk, T* __restrict__ lu
     for (int r = c + 1; r < NC; ++r) {
       const T l = m[r][c] * inv[c];
       m[r][c] = l;
-      for (int k = c + 1; k < NC; ++k) m[r][k] = m[r][k] - l * m[c][k];
+      for (int q = c + 1; q < NC; ++q) m[r][q] = m[r][q] - l * m[c][q];
     }
   }
-  const long long N = n;
   if (NC == 3) {
-    lu[0 * N + i] = m[1][0]; lu[1 * N + i] = m[2][0]; lu[2 * N + i] = m[2][1];
-    lu[3 * N + i] = m[0][1]; lu[4 * N + i] = m[0][2]; lu[5 * N + i] = m[1][2];
-    lu[6 * N + i] = inv[0]; lu[7 * N + i] = inv[1]; lu[8 * N + i] = inv[2];
+    lu[0 * P + i] = m[1][0]; lu[1 * P + i] = m[2 % NC][0]; lu[2 * P + i] = m[2 % NC][1];
+    lu[3 * P + i] = m[0][1]; lu[4 * P + i] = m[0][2 % NC]; lu[5 * P + i] = m[1][2 % NC];
+    lu[6 * P + i] = inv[0]; lu[7 * P + i] = inv[1]; lu[8 * P + i] = inv[2];
     piv[i] = (int8_t)(perm[0] + 3 * perm[1] + 9 * perm[2]);
   } else {
-    lu[0 * N + i] = m[1][0]; lu[1 * N + i] = T(0); lu[2 * N + i] = T(0);
-    lu[3 * N + i] = m[0][1]; lu[4 * N + i] = T(0); lu[5 * N + i] = T(0);
-    lu[6 * N + i] = inv[0]; lu[7 * N + i] = inv[1]; lu[8 * N + i] = T(0);
+    lu[0 * P + i] = m[1][0]; lu[1 * P + i] = T(0); lu[2 * P + i] = T(0);
+    lu[3 * P + i] = m[0][1]; lu[4 * P + i] = T(0); lu[5 * P + i] = T(0);
+    lu[6 * P + i] = inv[0]; lu[7 * P + i] = inv[1]; lu[8 * P + i] = T(0);
     piv[i] = (int8_t)(perm[0] + 3 * perm[1]);
   }
 }
 
+// LU solve with the factors of one cell read from 9 values L[e*ls]
 template <int NC, typename T>
-__device__ __forceinline__ void lu_apply(const T* __restrict__ lu, int8_t pv, long long N, int i,
-                                         const T r[NC], T x[NC]) {
+__device__ __forceinline__ void lu_apply_v(const T* __restrict__ L, int ls, int8_t pv, const T r[NC],
+                                           T x[NC]) {
   const int p0 = pv % 3, p1 = (pv / 3) % 3, p2 = pv / 9;
   if (NC == 3) {
-    T y0 = r[p0], y1 = r[p1], y2 = r[p2 % NC];
-    y1 = y1 - lu[0 * N + i] * y0;
-    y2 = y2 - lu[1 * N + i] * y0 - lu[2 * N + i] * y1;
-    const T x2 = y2 * lu[8 * N + i];
-    const T x1 = (y1 - lu[5 * N + i] * x2) * lu[7 * N + i];
-    const T x0 = (y0 - lu[3 * N + i] * x1 - lu[4 * N + i] * x2) * lu[6 * N + i];
+    T y0 = r[p0], y1 = r[p1 % NC], y2 = r[p2 % NC];
+    y1 = y1 - L[0 * ls] * y0;
+    y2 = y2 - L[1 * ls] * y0 - L[2 * ls] * y1;
+    const T x2 = y2 * L[8 * ls];
+    const T x1 = (y1 - L[5 * ls] * x2) * L[7 * ls];
+    const T x0 = (y0 - L[3 * ls] * x1 - L[4 * ls] * x2) * L[6 * ls];
     x[0] = x0; x[1 % NC] = x1; x[2 % NC] = x2;
   } else {
     T y0 = r[p0], y1 = r[p1 % NC];
-    y1 = y1 - lu[0 * N + i] * y0;
-    const T x1 = y1 * lu[7 * N + i];
-    const T x0 = (y0 - lu[3 * N + i] * x1) * lu[6 * N + i];
+    y1 = y1 - L[0 * ls] * y0;
+    const T x1 = y1 * L[7 * ls];
+    const T x0 = (y0 - L[3 * ls] * x1) * L[6 * ls];
     x[0] = x0; x[1 % NC] = x1;
   }
 }
@@ -94,13 +104,15 @@ __global__ void k_galerkin(int dim, int nxf, int nyf, const T* __restrict__ bf, 
   const int nxc = nxf / 2, nyc = dim == 2 ? nyf / 2 : 1, ncc = nxc * nyc;
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= ncc) return;
-  const long long nf = (long long)nxf * (dim == 2 ? nyf : 1), nc_ = ncc;
+  const int nyff = dim == 2 ? nyf : 1;
+  const long long Pf = skew_slots(nxf, nyff), Pc = skew_slots(nxc, nyc);
   const int BS = NC * NC;
   const int Ix = I % nxc, Iy = I / nxc;
-#define FB(cell, b, e) bf[((long long)(b) * BS + (e)) * nf + (cell)]
-#define CB(b, e) bc[((long long)(b) * BS + (e)) * nc_ + I]
+  const long long sc = skew_pos(Ix, Iy, nxc);
+#define FB(pos, b, e) bf[((long long)(b) * BS + (e)) * Pf + (pos)]
+#define CB(b, e) bc[((long long)(b) * BS + (e)) * Pc + sc]
   if (dim == 1) {
-    const int c0 = 2 * Ix, c1 = c0 + 1;
+    const long long c0 = skew_pos(2 * Ix, 0, nxf), c1 = skew_pos(2 * Ix + 1, 0, nxf);
     for (int e = 0; e < BS; ++e) {
       CB(0, e) = ((FB(c0, 0, e) + FB(c1, 0, e)) + FB(c0, 2, e)) + FB(c1, 1, e);
       CB(1, e) = FB(c0, 1, e);
@@ -110,7 +122,8 @@ __global__ void k_galerkin(int dim, int nxf, int nyf, const T* __restrict__ bf, 
     }
     return;
   }
-  const int c00 = 2 * Ix + nxf * 2 * Iy, c10 = c00 + 1, c01 = c00 + nxf, c11 = c01 + 1;
+  const long long c00 = skew_pos(2 * Ix, 2 * Iy, nxf), c10 = skew_pos(2 * Ix + 1, 2 * Iy, nxf);
+  const long long c01 = skew_pos(2 * Ix, 2 * Iy + 1, nxf), c11 = skew_pos(2 * Ix + 1, 2 * Iy + 1, nxf);
   for (int e = 0; e < BS; ++e) {
     T d = FB(c00, 0, e) + FB(c10, 0, e);
     d = d + FB(c01, 0, e);
@@ -134,16 +147,17 @@ template <int NC, typename T>
 __device__ __forceinline__ void lin_resid(int dim, int nx, int ny, const T* __restrict__ blk,
                                           const T* __restrict__ b, const T* __restrict__ x, int i,
                                           T r[NC]) {
-  const long long n = (long long)nx * ny;
+  const long long n = (long long)nx * ny, P = skew_slots(nx, ny);
   const int BS = NC * NC;
   const int ix = i % nx, iy = i / nx;
+  const long long si = skew_pos(ix, iy, nx);
   int nb[4] = {ix > 0 ? i - 1 : -1, ix < nx - 1 ? i + 1 : -1, iy > 0 ? i - nx : -1,
                iy < ny - 1 ? i + nx : -1};
   T xi[NC];
   for (int k = 0; k < NC; ++k) xi[k] = x[k * n + i];
   for (int s = 0; s < NC; ++s) {
     T a = b[s * n + i];
-    for (int k = 0; k < NC; ++k) a = a - blk[(long long)(s * NC + k) * n + i] * xi[k];
+    for (int k = 0; k < NC; ++k) a = a - blk[(long long)(s * NC + k) * P + si] * xi[k];
     r[s] = a;
   }
   const int nsd = dim == 2 ? 4 : 2;
@@ -154,7 +168,7 @@ __device__ __forceinline__ void lin_resid(int dim, int nx, int ny, const T* __re
     for (int k = 0; k < NC; ++k) xj[k] = x[k * n + j];
     for (int s = 0; s < NC; ++s)
       for (int k = 0; k < NC; ++k)
-        r[s] = r[s] - blk[((long long)(1 + side) * BS + s * NC + k) * n + i] * xj[k];
+        r[s] = r[s] - blk[((long long)(1 + side) * BS + s * NC + k) * P + si] * xj[k];
   }
 }
 
@@ -195,33 +209,253 @@ __global__ void k_prolong(int dim, int nc, int nxf, int nyf, const T* __restrict
   for (int s = 0; s < nc; ++s) xf[(long long)s * nf + i] = xf[(long long)s * nf + i] + xc[(long long)s * ncc + I];
 }
 
-// ---- block Gauss-Seidel, one anti-diagonal of the lexicographic order --------
-// x_i <- D_i^{-1} (b_i - A_W x_W - A_E x_E - A_S x_S - A_N x_N)
+// ---- block Gauss-Seidel sweep: strip-pipelined wavefront ---------------------
+// x_i <- D_i^{-1} (b_i - A_W x_W - A_E x_E - A_S x_S - A_N x_N) in lexicographic
+// order (forward) or its reverse (backward).  One warp owns a strip of 32 rows;
+// lane k handles row k of the strip and runs k columns behind lane k-1, so a
+// warp step updates one skewed diagonal of the strip: the "new" west value is
+// the lane's own previous result, the "new" south value comes from the lane
+// below by shuffle, and the "old" east / north values have not been written
+// yet.  Strip q starts a column once strip q-1 has published that its last
+// row passed it (progress counter, release/acquire).  Strips are claimed in
+// order through an atomic ticket, so a strip only ever waits for one that a
+// running warp already owns.
+//
+// The operator of a warp step is one contiguous line per entry in the
+// strip-skewed layout; lane 0 streams chunks of S lines of all entries into a
+// double-buffered shared-memory ring with cp.async.bulk (completion on an
+// mbarrier) while the warp computes the previous chunk.
+//
+// Every wait is bounded.  When one expires the kernel sets the sticky error
+// word and the abort flag, waits (bounded) for its own copies in flight, and
+// returns; the other strips see the abort flag and return as well.
+// sync layout: [0] ticket, [1] abort, [2 .. 2+nstrips) progress.
+constexpr int SGS_PUBLISH = 4;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <typename T> struct SgsChunk { static constexpr int S = sizeof(T) == 4 ? 16 : 8; };
+
 template <int NC, typename T>
-__global__ void k_sgs_diag(int nx, int ny, const T* __restrict__ blk, const T* __restrict__ lu,
-                           const int8_t* __restrict__ piv, const T* __restrict__ b, T* __restrict__ x,
-                           int d, int ix0, int ncell) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const int ix = ix0 + c, iy = d - ix, i = ix + nx * iy;
-  const long long n = (long long)nx * ny;
-  const int BS = NC * NC;
-  int nb[4] = {ix > 0 ? i - 1 : -1, ix < nx - 1 ? i + 1 : -1, iy > 0 ? i - nx : -1,
-               iy < ny - 1 ? i + nx : -1};
-  T r[NC];
-  for (int s = 0; s < NC; ++s) r[s] = b[s * n + i];
-  for (int side = 0; side < 4; ++side) {
-    const int j = nb[side];
-    if (j < 0) continue;
-    T xj[NC];
-    for (int k = 0; k < NC; ++k) xj[k] = x[k * n + j];
-    for (int s = 0; s < NC; ++s)
-      for (int k = 0; k < NC; ++k)
-        r[s] = r[s] - blk[((long long)(1 + side) * BS + s * NC + k) * n + i] * xj[k];
+__host__ __device__ constexpr int sgs_entries() { return 4 * NC * NC + LU_E; }   // W, E, S, N blocks + LU
+
+template <int NC, typename T>
+__host__ __device__ constexpr size_t sgs_stage_bytes() {
+  return (size_t)sgs_entries<NC, T>() * SgsChunk<T>::S * 32 * sizeof(T) + SgsChunk<T>::S * 32;
+}
+
+template <int NC, typename T>
+size_t sgs_smem_bytes() { return 128 + 2 * sgs_stage_bytes<NC, T>(); }
+
+// bounded wait of every lane for one chunk; warp-uniform result, false when
+// the bound expired for some lane
+__device__ __forceinline__ bool chunk_wait(uint64_t* bar, unsigned parity, int limit) {
+  bool ok = false;
+  for (int it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(bar, parity);
+  return __all_sync(0xffffffffu, ok) != 0;
+}
+
+template <int NC, typename T, bool FWD>
+__global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __restrict__ blk,
+                                                     const T* __restrict__ lu,
+                                                     const int8_t* __restrict__ piv,
+                                                     const T* __restrict__ b, T* x, int* sync,
+                                                     int* sticky_err, int nstrips, int spin_limit) {
+  constexpr int S = SgsChunk<T>::S;
+  constexpr int BS = NC * NC;
+  constexpr int NOFF = 4 * BS, NE = NOFF + LU_E;
+  constexpr size_t STAGE = sgs_stage_bytes<NC, T>();
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  T* vals[2] = {reinterpret_cast<T*>(smem + 128), reinterpret_cast<T*>(smem + 128 + STAGE)};
+  int8_t* pvs[2] = {reinterpret_cast<int8_t*>(smem + 128 + (size_t)NE * S * 32 * sizeof(T)),
+                    reinterpret_cast<int8_t*>(smem + 128 + STAGE + (size_t)NE * S * 32 * sizeof(T))};
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x;
+  const long long n = (long long)nx * ny, P = skew_slots(nx, ny);
+  if (lane == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    fence_proxy_async();
   }
-  T xi[NC];
-  lu_apply<NC, T>(lu, piv[i], n, i, r, xi);
-  for (int s = 0; s < NC; ++s) x[s * n + i] = xi[s];
+  __syncwarp();
+  unsigned parity[2] = {0u, 0u};
+  // logical W, E, S, N -> physical block (1 W, 2 E, 3 S, 4 N) -> entry base in a stage
+  const int oW = (FWD ? 0 : 1) * BS, oE = (FWD ? 1 : 0) * BS, oS = (FWD ? 2 : 3) * BS,
+            oN = (FWD ? 3 : 2) * BS;
+  const int lagk = FWD ? lane : 31 - lane;
+  const int nsteps = nx + 31, nchunks = (nsteps + S - 1) / S;
+  const int wait_limit = spin_limit;
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(&sync[0], 1);
+    q = __shfl_sync(FULL, q, 0);
+    if (q >= nstrips) return;
+    const int ps = FWD ? q : nstrips - 1 - q;
+    const long long line_base = (long long)ps * (nx + 31);
+    // lane 0 issues chunk j into stage st
+    auto issue = [&](int j, int st) {
+      const int s0 = j * S, cnt = min(S, nsteps - s0);
+      const int dlo = FWD ? s0 : nx + 31 - s0 - cnt;
+      const long long off = (line_base + dlo) * 32;
+      const unsigned vb = (unsigned)(cnt * 32 * sizeof(T));
+      fence_proxy_async();
+      mbar_expect_tx(&bar[st], vb * NE + (unsigned)(cnt * 32));
+      for (int e = 0; e < NOFF; ++e)
+        bulk_g2s(vals[st] + (size_t)e * S * 32, blk + (long long)(BS + e) * P + off, vb, &bar[st]);
+      for (int e = 0; e < LU_E; ++e)
+        bulk_g2s(vals[st] + (size_t)(NOFF + e) * S * 32, lu + (long long)e * P + off, vb, &bar[st]);
+      bulk_g2s(pvs[st], piv + off, (unsigned)(cnt * 32), &bar[st]);
+    };
+    bool inflight[2] = {false, false};
+    if (lane == 0) {
+      issue(0, 0);
+      if (nchunks > 1) issue(1, 1);
+    }
+    inflight[0] = true;
+    inflight[1] = nchunks > 1;
+    const int y = ps * 32 + lane;
+    const bool rowok = y < ny;
+    const int yS = FWD ? y - 1 : y + 1, yN = FWD ? y + 1 : y - 1;
+    const bool hasS = FWD ? (y > 0) : (y < ny - 1);
+    const bool hasN = FWD ? (y < ny - 1) : (y > 0);
+    int known = 0;
+    bool failed = false;
+    T xprev[NC], res[NC];
+    for (int k = 0; k < NC; ++k) { xprev[k] = T(0); res[k] = T(0); }
+    for (int j = 0; j < nchunks && !failed; ++j) {
+      const int st = j & 1;
+      if (!chunk_wait(&bar[st], parity[st], wait_limit)) {
+        if (lane == 0) atomicOr(sticky_err, 1);
+        failed = true;
+        break;
+      }
+      parity[st] ^= 1u;
+      inflight[st] = false;
+      const T* V = vals[st];
+      const int8_t* PV = pvs[st];
+      const int s0 = j * S, cnt = min(S, nsteps - s0);
+      for (int s = s0; s < s0 + cnt; ++s) {
+        const int line = FWD ? s - s0 : cnt - 1 - (s - s0);
+        const int c = s - lagk;
+        const bool act = rowok && c >= 0 && c < nx;
+        T xS[NC];
+        for (int k = 0; k < NC; ++k)
+          xS[k] = FWD ? __shfl_up_sync(FULL, res[k], 1) : __shfl_down_sync(FULL, res[k], 1);
+        if (q > 0 && s < nx) {
+          const int need = s + 1;
+          if (known < need) {
+            int p = 0, it = 0;
+            do {
+              if (lane == 0) {
+                p = ld_acquire(&sync[2 + q - 1]);
+                if (p < need && ld_acquire(&sync[1])) p = -1;
+              }
+              p = __shfl_sync(FULL, p, 0);
+              if (p >= need || p < 0) break;
+              __nanosleep(32);
+            } while (++it < spin_limit);
+            if (p < need) {
+              if (lane == 0 && p >= 0) atomicOr(sticky_err, 1);
+              failed = true;
+              break;
+            }
+            known = p;
+          }
+        }
+        if (act) {
+          const int px = FWD ? c : nx - 1 - c;
+          const long long i = (long long)px + (long long)nx * y;
+          if (lagk == 0 && hasS) {
+            const long long jj = (long long)px + (long long)nx * yS;
+            for (int k = 0; k < NC; ++k) xS[k] = __ldcg(&x[k * n + jj]);
+          }
+          const T* Vl = V + line * 32 + lane;
+          const int ES = S * 32;   // stride between entries in the stage
+          T r[NC];
+          for (int s2 = 0; s2 < NC; ++s2) r[s2] = b[s2 * n + i];
+          if (c > 0)
+            for (int s2 = 0; s2 < NC; ++s2)
+              for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oW + s2 * NC + k) * ES] * xprev[k];
+          if (c < nx - 1) {
+            const long long jj = FWD ? i + 1 : i - 1;
+            T xe[NC];
+            for (int k = 0; k < NC; ++k) xe[k] = __ldcg(&x[k * n + jj]);
+            for (int s2 = 0; s2 < NC; ++s2)
+              for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oE + s2 * NC + k) * ES] * xe[k];
+          }
+          if (hasS)
+            for (int s2 = 0; s2 < NC; ++s2)
+              for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oS + s2 * NC + k) * ES] * xS[k];
+          if (hasN) {
+            const long long jj = (long long)px + (long long)nx * yN;
+            T xn[NC];
+            for (int k = 0; k < NC; ++k) xn[k] = __ldcg(&x[k * n + jj]);
+            for (int s2 = 0; s2 < NC; ++s2)
+              for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oN + s2 * NC + k) * ES] * xn[k];
+          }
+          lu_apply_v<NC, T>(Vl + (size_t)NOFF * ES, ES, PV[line * 32 + lane], r, res);
+          for (int k = 0; k < NC; ++k) {
+            x[k * n + i] = res[k];
+            xprev[k] = res[k];
+          }
+        }
+        __syncwarp();
+        if (lagk == 31 && act && ((c + 1) % SGS_PUBLISH == 0 || c == nx - 1)) {
+          __threadfence();
+          st_release(&sync[2 + q], c + 1);
+        }
+      }
+      __syncwarp();
+      if (!failed && j + 2 < nchunks) {
+        if (lane == 0) issue(j + 2, st);
+        inflight[st] = true;
+      }
+    }
+    if (failed) {
+      // stop the other strips, then let this warp's copies land before leaving
+      if (lane == 0) st_release(&sync[1], 1);
+      for (int st = 0; st < 2; ++st)
+        if (inflight[st]) chunk_wait(&bar[st], parity[st], wait_limit);
+      return;
+    }
+  }
 }
 
 // ---- exact coarse solve: banded Gaussian elimination, partial pivoting -------
@@ -241,19 +475,21 @@ __global__ void k_coarse_exact(int nx, int ny, const T* __restrict__ blk, const 
   __shared__ double s_amax;
   for (long long e = threadIdx.x; e < (long long)m * ldab; e += blockDim.x) band[e] = 0.0;
   __syncthreads();
+  const long long P = skew_slots(nx, ny);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int ix = i % nx, iy = i / nx;
+    const long long si = skew_pos(ix, iy, nx);
     int nb[4] = {ix > 0 ? i - 1 : -1, ix < nx - 1 ? i + 1 : -1, iy > 0 ? i - nx : -1,
                  iy < ny - 1 ? i + nx : -1};
     for (int s = 0; s < NC; ++s) {
       rhs[i * NC + s] = (double)b[(long long)s * n + i];
       sing[i * NC + s] = 0;
-      for (int k = 0; k < NC; ++k) AB(i * NC + s, i * NC + k) = (double)blk[(long long)(s * NC + k) * n + i];
+      for (int k = 0; k < NC; ++k) AB(i * NC + s, i * NC + k) = (double)blk[(long long)(s * NC + k) * P + si];
       for (int side = 0; side < 4; ++side) {
         const int j = nb[side];
         if (j < 0) continue;
         for (int k = 0; k < NC; ++k)
-          AB(i * NC + s, j * NC + k) = (double)blk[((long long)(1 + side) * BS + s * NC + k) * n + i];
+          AB(i * NC + s, j * NC + k) = (double)blk[((long long)(1 + side) * BS + s * NC + k) * P + si];
       }
     }
   }
@@ -356,33 +592,41 @@ __global__ void k_fill0(T* __restrict__ d, long long n) {
 }
 
 template <typename T>
-__global__ void k_export(int n, int nc, const T* __restrict__ blk, double* __restrict__ out) {
+__global__ void k_export(int nx, int ny, int nc, const T* __restrict__ blk, double* __restrict__ out) {
+  const int n = nx * ny;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const long long P = skew_slots(nx, ny), si = skew_pos(i % nx, i / nx, nx);
   const int BS = nc * nc;
   for (int b = 0; b < 5; ++b)
     for (int e = 0; e < BS; ++e)
-      out[((long long)i * 5 + b) * BS + e] = (double)blk[((long long)b * BS + e) * n + i];
+      out[((long long)i * 5 + b) * BS + e] = (double)blk[((long long)b * BS + e) * P + si];
 }
 
 }  // namespace
 
 // ---- launch wrappers ----------------------------------------------------------
 
-void launch_lu_factor(int n, int nc, const void* blk, void* lu, int8_t* piv, int fp32,
+static std::atomic<long long> g_launches{0};
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+void launch_lu_factor(int nx, int ny, int nc, const void* blk, void* lu, int8_t* piv, int fp32,
                       cudaStream_t st) {
-  const int g = nblk(n, 128);
+  count_launches(1);
+  const int g = nblk(skew_slots(nx, ny), 128);
   if (nc == 3) {
-    if (fp32) k_lu_factor<3, float><<<g, 128, 0, st>>>(n, (const float*)blk, (float*)lu, piv);
-    else k_lu_factor<3, double><<<g, 128, 0, st>>>(n, (const double*)blk, (double*)lu, piv);
+    if (fp32) k_lu_factor<3, float><<<g, 128, 0, st>>>(nx, ny, (const float*)blk, (float*)lu, piv);
+    else k_lu_factor<3, double><<<g, 128, 0, st>>>(nx, ny, (const double*)blk, (double*)lu, piv);
   } else {
-    if (fp32) k_lu_factor<2, float><<<g, 128, 0, st>>>(n, (const float*)blk, (float*)lu, piv);
-    else k_lu_factor<2, double><<<g, 128, 0, st>>>(n, (const double*)blk, (double*)lu, piv);
+    if (fp32) k_lu_factor<2, float><<<g, 128, 0, st>>>(nx, ny, (const float*)blk, (float*)lu, piv);
+    else k_lu_factor<2, double><<<g, 128, 0, st>>>(nx, ny, (const double*)blk, (double*)lu, piv);
   }
 }
 
 void launch_galerkin(int dim, int nc, int nxf, int nyf, const void* bf, void* bc, int fp32,
                      cudaStream_t st) {
+  count_launches(1);
   const int ncc = (nxf / 2) * (dim == 2 ? nyf / 2 : 1);
   const int g = nblk(ncc, 128);
   if (nc == 3) {
@@ -396,6 +640,7 @@ void launch_galerkin(int dim, int nc, int nxf, int nyf, const void* bf, void* bc
 
 void launch_restrict(int dim, int nc, int nxf, int nyf, const void* blk, const void* b,
                      const void* x, void* bcoarse, int fp32, cudaStream_t st) {
+  count_launches(1);
   const int ncc = (nxf / 2) * (dim == 2 ? nyf / 2 : 1);
   const int g = nblk(ncc, 128);
 #define RL(NC, T) k_restrict<NC, T><<<g, 128, 0, st>>>(dim, nxf, nyf, (const T*)blk, (const T*)b, \
@@ -407,31 +652,46 @@ void launch_restrict(int dim, int nc, int nxf, int nyf, const void* blk, const v
 
 void launch_prolong(int dim, int nc, int nxf, int nyf, const void* xc, void* xf, int fp32,
                     cudaStream_t st) {
+  count_launches(1);
   const int nf = nxf * (dim == 2 ? nyf : 1);
   if (fp32) k_prolong<float><<<nblk(nf, 256), 256, 0, st>>>(dim, nc, nxf, nyf, (const float*)xc, (float*)xf);
   else k_prolong<double><<<nblk(nf, 256), 256, 0, st>>>(dim, nc, nxf, nyf, (const double*)xc, (double*)xf);
 }
 
-void launch_sgs_sweep(int nc, int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
-                      const void* b, void* x, int forward, int fp32, cudaStream_t st) {
-  const int ndiag = nx + ny - 1;
-  for (int q = 0; q < ndiag; ++q) {
-    const int d = forward ? q : ndiag - 1 - q;
-    const int ix0 = d - (ny - 1) > 0 ? d - (ny - 1) : 0;
-    const int ix1 = d < nx - 1 ? d : nx - 1;
-    const int ncell = ix1 - ix0 + 1;
-    const int bs = ncell < 128 ? ((ncell + 31) / 32) * 32 : 128;
-    const int g = nblk(ncell, bs);
-#define SL(NC, T) k_sgs_diag<NC, T><<<g, bs, 0, st>>>(nx, ny, (const T*)blk, (const T*)lu, piv, \
-                                                       (const T*)b, (T*)x, d, ix0, ncell)
-    if (nc == 3) { if (fp32) SL(3, float); else SL(3, double); }
-    else { if (fp32) SL(2, float); else SL(2, double); }
-#undef SL
+template <int NC, typename T, bool F>
+static void sgs_launch(int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
+                       const void* b, void* x, int* sync, int* sticky, cudaStream_t st) {
+  const int nstrips = (ny + 31) / 32;
+  const size_t smem = sgs_smem_bytes<NC, T>();
+  static bool configured = false;   // per template instance
+  if (!configured) {
+    cudaFuncSetAttribute(k_sgs_strip<NC, T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
   }
+  k_sgs_strip<NC, T, F><<<nstrips, 32, smem, st>>>(nx, ny, (const T*)blk, (const T*)lu, piv,
+                                                    (const T*)b, (T*)x, sync, sticky, nstrips, 1 << 22);
+}
+
+void launch_sgs_sweep(int nc, int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
+                      const void* b, void* x, int forward, int fp32, int* sync, int* sticky_err,
+                      cudaStream_t st) {
+  count_launches(1);
+  const int nstrips = (ny + 31) / 32;
+  cudaMemsetAsync(sync, 0, sizeof(int) * (2 + nstrips), st);
+#define SL(NC, T, F) sgs_launch<NC, T, F>(nx, ny, blk, lu, piv, b, x, sync, sticky_err, st)
+  if (nc == 3) {
+    if (fp32) { if (forward) SL(3, float, true); else SL(3, float, false); }
+    else { if (forward) SL(3, double, true); else SL(3, double, false); }
+  } else {
+    if (fp32) { if (forward) SL(2, float, true); else SL(2, float, false); }
+    else { if (forward) SL(2, double, true); else SL(2, double, false); }
+  }
+#undef SL
 }
 
 void launch_coarse_exact(int nc, int nx, int ny, const void* blk, const void* b, void* x,
                          double* band, int* err, int fp32, cudaStream_t st) {
+  count_launches(1);
 #define CL(NC, T) k_coarse_exact<NC, T><<<1, 256, 0, st>>>(nx, ny, (const T*)blk, (const T*)b, (T*)x, band, err)
   if (nc == 3) { if (fp32) CL(3, float); else CL(3, double); }
   else { if (fp32) CL(2, float); else CL(2, double); }
@@ -439,6 +699,7 @@ void launch_coarse_exact(int nc, int nx, int ny, const void* blk, const void* b,
 }
 
 void launch_sum(const double* v, int n, double* partial, double* out, cudaStream_t st) {
+  count_launches(2);
   int g = nblk(n, 256);
   if (g > 1024) g = 1024;
   if (g < 1) g = 1;
@@ -448,6 +709,7 @@ void launch_sum(const double* v, int n, double* partial, double* out, cudaStream
 
 void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n,
                     double scale, cudaStream_t st) {
+  count_launches(1);
   const int g = (int)(n / 256 + 1 > 4096 ? 4096 : n / 256 + 1);
   if (src_fp32 && dst_fp32) k_convert<float, float><<<g, 256, 0, st>>>((const float*)src, (float*)dst, n, scale);
   else if (src_fp32) k_convert<float, double><<<g, 256, 0, st>>>((const float*)src, (double*)dst, n, scale);
@@ -456,14 +718,18 @@ void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long
 }
 
 void launch_fill(void* dst, int fp32, long long n, cudaStream_t st) {
+  count_launches(1);
   const int g = (int)(n / 256 + 1 > 4096 ? 4096 : n / 256 + 1);
   if (fp32) k_fill0<float><<<g, 256, 0, st>>>((float*)dst, n);
   else k_fill0<double><<<g, 256, 0, st>>>((double*)dst, n);
 }
 
-void launch_blocks_export(int n, int nc, const void* blk, int fp32, double* out, cudaStream_t st) {
-  if (fp32) k_export<float><<<nblk(n, 128), 128, 0, st>>>(n, nc, (const float*)blk, out);
-  else k_export<double><<<nblk(n, 128), 128, 0, st>>>(n, nc, (const double*)blk, out);
+void launch_blocks_export(int nx, int ny, int nc, const void* blk, int fp32, double* out,
+                          cudaStream_t st) {
+  count_launches(1);
+  const int n = nx * ny;
+  if (fp32) k_export<float><<<nblk(n, 128), 128, 0, st>>>(nx, ny, nc, (const float*)blk, out);
+  else k_export<double><<<nblk(n, 128), 128, 0, st>>>(nx, ny, nc, (const double*)blk, out);
 }
 
 }  // namespace swnmg

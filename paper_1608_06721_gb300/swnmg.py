@@ -74,14 +74,21 @@ def lib():
         L.swnmg_sgs_sweep.argtypes = [vp, C.c_int32, vp, vp, C.c_int32]
         L.swnmg_blusgs.argtypes = [vp, vp, C.c_int32, C.c_int32]
         L.swnmg_solve.argtypes = [vp, vp, C.POINTER(Stats)]
+        L.swnmg_set_timing.argtypes = [vp, C.c_int32]
+        L.swnmg_get_timing.argtypes = [vp, dp, C.POINTER(C.c_int64)]
         L.swnmg_level_cells.argtypes = [vp, C.c_int32]
         L.swnmg_level_cells.restype = C.c_int64
         for f in ("swnmg_default_params", "swnmg_create", "swnmg_destroy", "swnmg_set_params",
                   "swnmg_residual", "swnmg_jacobian", "swnmg_get_blocks", "swnmg_vcycle",
-                  "swnmg_sgs_sweep", "swnmg_blusgs", "swnmg_solve"):
+                  "swnmg_sgs_sweep", "swnmg_blusgs", "swnmg_solve", "swnmg_set_timing",
+                  "swnmg_get_timing"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
+
+
+KERNEL_CLASSES = ["residual", "jacobian", "galerkin_lu", "sgs_fine", "sgs_coarse", "transfer",
+                  "blusgs", "update", "coarse_exact"]
 
 
 class SwnmgError(RuntimeError):
@@ -193,6 +200,17 @@ class Solver:
     def blusgs(self, U, level=0, nsweeps=1):
         self._check(self.L.swnmg_blusgs(self.h, _ptr(U), level, nsweeps))
         return U
+
+    def set_timing(self, enable=True):
+        self._check(self.L.swnmg_set_timing(self.h, 1 if enable else 0))
+
+    def get_timing(self):
+        """{class: (device ms, launches)} accumulated since set_timing(True)."""
+        k = len(KERNEL_CLASSES)
+        ms = (C.c_double * k)()
+        nl = (C.c_int64 * k)()
+        self._check(self.L.swnmg_get_timing(self.h, ms, nl))
+        return {name: (ms[i], nl[i]) for i, name in enumerate(KERNEL_CLASSES)}
 
     def solve(self, U, check=False):
         """Algorithm 1 in place on U; returns a dict of the solver counters."""

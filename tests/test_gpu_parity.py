@@ -219,7 +219,7 @@ def test_nonfinite_input_is_reported(swnmg):
     U[0, 50] = np.nan
     S = swnmg.Solver(p.with_params(init_mode=W.INIT_NONE))
     info = S.solve(_dev(U))
-    assert info["status"] in (swnmg.ERR_NONFINITE, swnmg.ERR_NOT_CONVERGED)
+    assert info["status"] == swnmg.ERR_NONFINITE
 
 
 @pytest.mark.parametrize("nx,ny", [(1, 1), (7, 5), (3, 1)])
