@@ -188,6 +188,31 @@ SWNMG_API swnmg_status swnmg_get_timing(swnmg_ctx* ctx, double* ms_out, int64_t*
  * (all contexts); differences around a region count its launches. */
 SWNMG_API int64_t swnmg_launch_count(void);
 
+/* The residual of swnmg_residual (eq. Res, same kernels, same bits) for
+ * callers that cannot allocate device memory -- code running in a host
+ * callback, where CUDA calls such as cudaMalloc are not allowed; code inside
+ * a runtime that owns all device memory through its own pool; loops that
+ * cannot take cudaMalloc/cudaFree's implicit device synchronisation.  The
+ * paper has no counterpart: it is an interface convenience only.
+ *
+ * Needs no context.  Inputs and outputs are the caller's device arrays: z
+ * (n), U (ncomp*n), R (ncomp*n), rnorm (n, nullable: ||R_i||_1), l1_dev
+ * (one double, nullable: sum_i ||R_i||_1).  Work is enqueued on `stream`
+ * (a cudaStream_t, NULL = legacy default) and the call returns without
+ * waiting.  Scratch comes from one fixed device array of 2^20 doubles
+ * (8 MiB) that every GPU loading the library keeps until the process exits;
+ * a grid needs 2*ncomp*(edges) + 1024 doubles of it (+ n when rnorm is
+ * NULL), i.e. about 256x256 cells in 2D -- larger grids return
+ * SWNMG_ERR_ARG with the reason in swnmg_last_error(NULL).  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the one array, so calls that may overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. */
+SWNMG_API swnmg_status swnmg_residual_noalloc(const swnmg_problem* prob, const swnmg_params* prm,
+                                              const double* z_dev, const double* U_dev,
+                                              double* R_dev, double* rnorm_dev, double* l1_dev,
+                                              void* stream);
+
 /* Number of cells of level l (0 if l is out of range). */
 SWNMG_API int64_t swnmg_level_cells(const swnmg_ctx* ctx, int32_t level);
 

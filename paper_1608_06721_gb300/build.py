@@ -22,6 +22,7 @@ UNITS = {
     "flux.cu": ["-fmad=false"],
     "mg.cu": [],
     "api.cu": [],
+    "noalloc.cu": [],
 }
 
 

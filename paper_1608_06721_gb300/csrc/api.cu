@@ -44,6 +44,8 @@ char g_err[512] = "";
 
 }  // namespace
 
+void swnmg::set_static_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
 struct swnmg_ctx {
   swnmg_problem prob;
   swnmg_params prm;

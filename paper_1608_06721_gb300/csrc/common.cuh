@@ -55,6 +55,9 @@ __host__ __device__ __forceinline__ long long skew_slots(int nx, int ny) {
   return (long long)((ny + 31) >> 5) * (nx + 31) * 32;
 }
 
+// sets the text that swnmg_last_error(NULL) returns
+void set_static_error(const char* msg);
+
 // process-wide count of kernel launches issued by the library
 void count_launches(long long k);
 long long launches_total();

@@ -76,6 +76,8 @@ def lib():
         L.swnmg_solve.argtypes = [vp, vp, C.POINTER(Stats)]
         L.swnmg_set_timing.argtypes = [vp, C.c_int32]
         L.swnmg_get_timing.argtypes = [vp, dp, C.POINTER(C.c_int64)]
+        L.swnmg_residual_noalloc.argtypes = [C.POINTER(Problem), C.POINTER(Params), vp, vp, vp, vp, vp, vp]
+        L.swnmg_residual_noalloc.restype = C.c_int
         L.swnmg_level_cells.argtypes = [vp, C.c_int32]
         L.swnmg_level_cells.restype = C.c_int64
         for f in ("swnmg_default_params", "swnmg_create", "swnmg_destroy", "swnmg_set_params",
@@ -225,6 +227,22 @@ class Solver:
                 "init_res": st.init_res, "final_res": st.final_res,
                 "res_hist": list(st.res_hist)[:min(st.n_newton, HIST)],
                 "ms_step1": st.ms_step1, "ms_newton": st.ms_newton}
+
+
+def residual_noalloc(prob: W.Problem, z, U, R, rnorm=None, l1=None, params: W.Params | None = None,
+                     stream=None):
+    """swnmg_residual_noalloc: the residual without a context and without any
+    device allocation by the library (scratch is a fixed device array), for
+    callers that must not allocate.  z, U, R (and rnorm, l1 when given) are
+    the caller's float64 CUDA tensors; the work is enqueued on `stream`."""
+    L = lib()
+    pp, pr = make_problem(prob), make_params(params or prob.params)
+    st = stream or torch.cuda.current_stream()
+    rc = L.swnmg_residual_noalloc(C.byref(pp), C.byref(pr), _ptr(z), _ptr(U), _ptr(R),
+                                  _ptr(rnorm) if rnorm is not None else None,
+                                  _ptr(l1) if l1 is not None else None, C.c_void_p(st.cuda_stream))
+    if rc != OK:
+        raise SwnmgError(rc, L.swnmg_last_error(None).decode())
 
 
 def default_params(dim: int) -> dict:
