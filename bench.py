@@ -133,11 +133,11 @@ def algorithmic(cls, p, fp32):
     if cls == "sgs_fine":
         return "hbm", n * ((5 * nc * nc - nc * nc + 9 + 3 + 2 * nc) * w + 1)   # blocks, LU, b, x in/out, piv
     if cls == "blusgs":
-        return "alu", n * 1320.0
+        return "alu", n * 1020.0
     if cls == "jacobian":
-        return "alu", n * 880.0
+        return "alu", n * 1035.0
     if cls == "residual":
-        return "alu", n * 125.0
+        return "alu", n * 130.0
     return None, None
 
 

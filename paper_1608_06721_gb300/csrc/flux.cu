@@ -51,7 +51,9 @@ __device__ void num_flux(const DevLevel& L, double hl, double ul, double vl, dou
   const double dU0 = hr - hl, dU1 = qr - ql, dU2 = hr * vr - hl * vl;   // U+ - U-
   if (L.flux == FX_LLF) {
     double smax = dmax(fabs(ul) + cl, fabs(ur) + cr);
-    if (L.llf_wetdry) smax = smax + L.eps_r * sqrt(g * dmax(hl, hr));
+    // sqrt(g max(h-, h+)) equals max(sqrt(g h-), sqrt(g h+)) bit for bit:
+    // scaling by g > 0 and the correctly rounded sqrt are both monotone
+    if (L.llf_wetdry) smax = smax + L.eps_r * dmax(cl, cr);
     F[0] = ((FL0 + FR0) - smax * dU0) * 0.5;
     F[1] = ((FL1 + FR1) - smax * dU1) * 0.5;
     F[2] = ((FL2 + FR2) - smax * dU2) * 0.5;
@@ -447,71 +449,113 @@ __device__ void small_solve(double m[NC * NC], const double b[NC], double x[NC])
 // Cells with ix + iy = d depend only on diagonal d-1 (new values) and d+1
 // (old values), so updating one diagonal at a time in increasing (forward)
 // or decreasing (backward) order reproduces the lexicographic sweep exactly.
-// NS lanes per cell (one per side) evaluate the side's G and its three
-// perturbations; the side-0 lane sums them in W, E, S, N order and updates
-// U_i -= (alpha||R_i||_1 I + dR_i/dU_i)^{-1} R_i.
-template <int NC, int NS>
-__global__ void k_blusgs_diag(DevLevel L, const double* __restrict__ z, double* __restrict__ U,
-                              int d, int ix0, int ncell) {
+// Each cell has a group of lanes, one per (side, perturbation p): p = 0
+// evaluates the side's G at U_i, p = k+1 at U_i + eps e_k.  All lanes run the
+// same edge evaluation (the cell is put on the edge's left or right by
+// selection, not by branching); the p = 0 lane of a side shares 1/h_i and the
+// neighbour's velocities with its perturbation lanes (the same values they
+// would compute).  The group's first lane sums the sides in W, E, S, N order
+// and updates U_i -= (alpha||R_i||_1 I + dR_i/dU_i)^{-1} R_i.
+template <int NC, int NS, int GRP>
+__global__ void __launch_bounds__(32) k_blusgs_diag(DevLevel L, const double* __restrict__ z,
+                                                    double* __restrict__ U, int d, int ix0, int ncell) {
+  constexpr int NP = NC + 1;                 // perturbations incl. the base
+  const unsigned full = 0xffffffffu;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int cell = t / NS, side = t % NS;
-  const bool active = cell < ncell;
-  const int ix = ix0 + (active ? cell : 0), iy = d - ix;
+  const int lane = threadIdx.x & 31;
+  const int cell = t / GRP, g = t % GRP;
+  const int side = g / NP, p = g % NP;
+  const int gbase = lane - g;                // first lane of the cell's group
+  const bool cell_ok = cell < ncell;
+  const bool act = cell_ok && side < NS;
+  const int ix = ix0 + (cell_ok ? cell : 0), iy = d - ix;
   const int i = ix + L.nx * iy;
   const long long n = L.n;
-  double lenG[NC], dG[NC * NC];
-  for (int s = 0; s < NC; ++s) lenG[s] = 0.0;
-  for (int e = 0; e < NC * NC; ++e) dG[e] = 0.0;
-  if (active) {
-    const int axis = side >> 1, upper = side & 1;
-    int j = -1;
-    if (side == 0 && ix > 0) j = i - 1;
-    if (side == 1 && ix < L.nx - 1) j = i + 1;
-    if (side == 2 && iy > 0) j = i - L.nx;
-    if (side == 3 && iy < L.ny - 1) j = i + L.nx;
-    double ci[NC], cj[NC], GL[NC], GR[NC], Gb[NC];
-    load_c<NC>(U, L.n, i, ci);
-    if (j >= 0) load_c<NC>(U, L.n, j, cj);
-    const double zi = z[i], zj = j >= 0 ? z[j] : 0.0;
-    const double len = axis == 0 ? L.ex : L.ey;
-    // the cell is the left state of its E/N edges, the right state of W/S
-    if (upper) eval_edge_states<NC>(L, axis, ci, zi, j >= 0 ? cj : nullptr, zj, GL, GR);
-    else eval_edge_states<NC>(L, axis, j >= 0 ? cj : nullptr, zj, ci, zi, GL, GR);
-    for (int s = 0; s < NC; ++s) {
-      Gb[s] = upper ? GL[s] : GR[s];
-      lenG[s] = len * Gb[s];
-    }
-    for (int k = 0; k < NC; ++k) {
-      double c[NC];
-      for (int s = 0; s < NC; ++s) c[s] = ci[s];
-      c[k] = c[k] + L.eps;
-      if (upper) eval_edge_states<NC>(L, axis, c, zi, j >= 0 ? cj : nullptr, zj, GL, GR);
-      else eval_edge_states<NC>(L, axis, j >= 0 ? cj : nullptr, zj, c, zi, GL, GR);
-      for (int s = 0; s < NC; ++s) dG[s * NC + k] = len * (((upper ? GL[s] : GR[s]) - Gb[s]) * L.reps);
+  const int sd = side < NS ? side : 0;
+  const int axis = sd >> 1, upper = sd & 1;
+  int j = -1;
+  if (act) {
+    if (sd == 0 && ix > 0) j = i - 1;
+    if (sd == 1 && ix < L.nx - 1) j = i + 1;
+    if (sd == 2 && iy > 0) j = i - L.nx;
+    if (sd == 3 && iy < L.ny - 1) j = i + L.nx;
+  }
+  double ci[NC];
+  for (int s = 0; s < NC; ++s) ci[s] = act ? U[s * n + i] : 0.0;
+  const double zi = act ? z[i] : 0.0, zj = (j >= 0) ? z[j] : zi;
+  // base lane: 1/h_i and the neighbour's primitive state
+  double rinv = 0.0;
+  Prim nb{0.0, 0.0, 0.0};
+  if (act && p == 0) {
+    if (ci[0] >= L.h_eps) rinv = 1.0 / ci[0];
+    if (j >= 0) {
+      double cj[NC];
+      for (int s = 0; s < NC; ++s) cj[s] = U[s * n + j];
+      nb = prim_axis<NC>(L, cj, axis);
     }
   }
-  // gather the NS sides of a cell into its side-0 lane, in side order
-  const unsigned full = 0xffffffffu;
+  const int src0 = gbase + sd * NP;          // the side's p = 0 lane
+  rinv = __shfl_sync(full, rinv, src0);
+  nb.h = __shfl_sync(full, nb.h, src0);
+  nb.u = __shfl_sync(full, nb.u, src0);
+  nb.v = __shfl_sync(full, nb.v, src0);
+  double G[NC];
+  for (int s = 0; s < NC; ++s) G[s] = 0.0;
+  if (act) {
+    double c[NC];
+    for (int s = 0; s < NC; ++s) c[s] = ci[s];
+    if (p > 0) c[p - 1] = c[p - 1] + L.eps;
+    // the cell's velocities: 1/h only changes with the depth perturbation
+    Prim me;
+    me.h = c[0];
+    const double qa = (NC == 2) ? c[1] : (axis == 0 ? c[1] : c[NC - 1]);
+    const double qb = (NC == 2) ? 0.0 : (axis == 0 ? c[NC - 1] : c[1]);
+    if (c[0] >= L.h_eps) {
+      const double r = (p == 1) ? 1.0 / c[0] : rinv;
+      me.u = qa * r;
+      me.v = qb * r;
+    } else {
+      me.u = 0.0;
+      me.v = 0.0;
+    }
+    Prim other = (j >= 0) ? nb : ghost_state(L, sd, me);
+    const double zo = (j >= 0) ? zj : zi;
+    const Prim a = upper ? me : other, b = upper ? other : me;
+    const double za = upper ? zi : zo, zb = upper ? zo : zi;
+    double o[5], GL[NC], GR[NC];
+    edge_eval(L, a, za, b, zb, o);
+    edge_G<NC>(o, axis, GL, GR);
+    for (int s = 0; s < NC; ++s) G[s] = upper ? GL[s] : GR[s];
+  }
+  // p = 0 lanes hold |e| G; p = k+1 lanes column k of |e| dG/dU_i
+  const double len = axis == 0 ? L.ex : L.ey;
+  double v[NC];
+  for (int s = 0; s < NC; ++s) {
+    const double gb = __shfl_sync(full, G[s], src0);
+    v[s] = (p == 0) ? len * G[s] : len * ((G[s] - gb) * L.reps);
+  }
+  // gather on the group's first lane in side order
   double Rs[NC], D[NC * NC];
   for (int s = 0; s < NC; ++s) Rs[s] = 0.0;
   for (int e = 0; e < NC * NC; ++e) D[e] = 0.0;
-  const int base = (threadIdx.x & 31) - side;
-  for (int q = 0; q < NS; ++q) {
-    for (int s = 0; s < NC; ++s) Rs[s] = Rs[s] + __shfl_sync(full, lenG[s], base + q);
-    for (int e = 0; e < NC * NC; ++e) D[e] = D[e] + __shfl_sync(full, dG[e], base + q);
-  }
-  if (!active || side != 0) return;
+  for (int q = 0; q < NS; ++q)
+    for (int pp = 0; pp < NP; ++pp)
+      for (int s = 0; s < NC; ++s) {
+        const double w = __shfl_sync(full, v[s], gbase + q * NP + pp);
+        if (pp == 0) Rs[s] = Rs[s] + w;
+        else D[s * NC + (pp - 1)] = D[s * NC + (pp - 1)] + w;
+      }
+  if (!cell_ok || g != 0) return;
   double m = fabs(Rs[0]) + fabs(Rs[1]);
   if (NC == 3) m = m + fabs(Rs[NC - 1]);
   const double am = L.alpha * m;
   for (int s = 0; s < NC; ++s) D[s * NC + s] = D[s * NC + s] + am;
   double x[NC];
   small_solve<NC>(D, Rs, x);
-  const double h0 = U[i];
-  if (h0 < L.h_eps)   // dry at the start: momentum stays zero (Remark 2.5)
+  if (ci[0] < L.h_eps)   // dry at the start: momentum stays zero (Remark 2.5)
     for (int s = 1; s < NC; ++s) x[s] = 0.0;
   double un[NC];
-  for (int s = 0; s < NC; ++s) un[s] = U[s * n + i] - x[s];
+  for (int s = 0; s < NC; ++s) un[s] = ci[s] - x[s];
   if (un[0] < L.h_eps)
     for (int s = 0; s < NC; ++s) un[s] = 0.0;
   for (int s = 0; s < NC; ++s) U[s * n + i] = un[s];
@@ -632,10 +676,10 @@ void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forw
     const int ix0 = d - (L.ny - 1) > 0 ? d - (L.ny - 1) : 0;
     const int ix1 = d < L.nx - 1 ? d : L.nx - 1;
     const int ncell = ix1 - ix0 + 1;
-    // one warp per block: the FP64 pipe of an SM serves one warp, so the
-    // cells of a diagonal are spread over as many SMs as possible
-    if (L.nc == 3) k_blusgs_diag<3, 4><<<nblk(ncell * 4, 32), 32, 0, st>>>(L, z, U, d, ix0, ncell);
-    else k_blusgs_diag<2, 2><<<nblk(ncell * 2, 32), 32, 0, st>>>(L, z, U, d, ix0, ncell);
+    // one warp per block so that a diagonal's cells spread over the SMs
+    // (the FP64 pipe of an SM is shared by its warps)
+    if (L.nc == 3) k_blusgs_diag<3, 4, 16><<<nblk(ncell * 16, 32), 32, 0, st>>>(L, z, U, d, ix0, ncell);
+    else k_blusgs_diag<2, 2, 8><<<nblk(ncell * 8, 32), 32, 0, st>>>(L, z, U, d, ix0, ncell);
   }
 }
 

@@ -359,6 +359,26 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
     bool failed = false;
     T xprev[NC], res[NC];
     for (int k = 0; k < NC; ++k) { xprev[k] = T(0); res[k] = T(0); }
+    // right-hand side and the "old" east / north values of the lane's cell
+    // at logical column c, loaded one step ahead (they are written at step
+    // c + lagk + 2 at the earliest: by this lane, by the lane above, or by
+    // the next strip after this one has published column c + 2)
+    auto load_cell = [&](int c, T* bb, T* xe, T* xn) {
+      const int px = FWD ? c : nx - 1 - c;
+      const long long i = (long long)px + (long long)nx * y;
+      for (int k = 0; k < NC; ++k) bb[k] = b[k * n + i];
+      if (c < nx - 1) {
+        const long long jj = FWD ? i + 1 : i - 1;
+        for (int k = 0; k < NC; ++k) xe[k] = x[k * n + jj];
+      }
+      if (hasN) {
+        const long long jj = (long long)px + (long long)nx * yN;
+        for (int k = 0; k < NC; ++k) xn[k] = x[k * n + jj];
+      }
+    };
+    T cb[NC], cxe[NC], cxn[NC];
+    for (int k = 0; k < NC; ++k) { cb[k] = T(0); cxe[k] = T(0); cxn[k] = T(0); }
+    if (rowok && lagk == 0) load_cell(0, cb, cxe, cxn);
     for (int j = 0; j < nchunks && !failed; ++j) {
       const int st = j & 1;
       if (!chunk_wait(&bar[st], parity[st], wait_limit)) {
@@ -375,6 +395,10 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
         const int line = FWD ? s - s0 : cnt - 1 - (s - s0);
         const int c = s - lagk;
         const bool act = rowok && c >= 0 && c < nx;
+        // prefetch the next step's cell data
+        T nb_[NC], nxe[NC], nxn[NC];
+        for (int k = 0; k < NC; ++k) { nb_[k] = T(0); nxe[k] = T(0); nxn[k] = T(0); }
+        if (rowok && c + 1 >= 0 && c + 1 < nx) load_cell(c + 1, nb_, nxe, nxn);
         T xS[NC];
         for (int k = 0; k < NC; ++k)
           xS[k] = FWD ? __shfl_up_sync(FULL, res[k], 1) : __shfl_down_sync(FULL, res[k], 1);
@@ -402,40 +426,33 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
         if (act) {
           const int px = FWD ? c : nx - 1 - c;
           const long long i = (long long)px + (long long)nx * y;
-          if (lagk == 0 && hasS) {
+          if (lagk == 0 && hasS) {   // south value from the previous strip (after acquire)
             const long long jj = (long long)px + (long long)nx * yS;
             for (int k = 0; k < NC; ++k) xS[k] = __ldcg(&x[k * n + jj]);
           }
           const T* Vl = V + line * 32 + lane;
           const int ES = S * 32;   // stride between entries in the stage
           T r[NC];
-          for (int s2 = 0; s2 < NC; ++s2) r[s2] = b[s2 * n + i];
+          for (int s2 = 0; s2 < NC; ++s2) r[s2] = cb[s2];
           if (c > 0)
             for (int s2 = 0; s2 < NC; ++s2)
               for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oW + s2 * NC + k) * ES] * xprev[k];
-          if (c < nx - 1) {
-            const long long jj = FWD ? i + 1 : i - 1;
-            T xe[NC];
-            for (int k = 0; k < NC; ++k) xe[k] = __ldcg(&x[k * n + jj]);
+          if (c < nx - 1)
             for (int s2 = 0; s2 < NC; ++s2)
-              for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oE + s2 * NC + k) * ES] * xe[k];
-          }
+              for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oE + s2 * NC + k) * ES] * cxe[k];
           if (hasS)
             for (int s2 = 0; s2 < NC; ++s2)
               for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oS + s2 * NC + k) * ES] * xS[k];
-          if (hasN) {
-            const long long jj = (long long)px + (long long)nx * yN;
-            T xn[NC];
-            for (int k = 0; k < NC; ++k) xn[k] = __ldcg(&x[k * n + jj]);
+          if (hasN)
             for (int s2 = 0; s2 < NC; ++s2)
-              for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oN + s2 * NC + k) * ES] * xn[k];
-          }
+              for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oN + s2 * NC + k) * ES] * cxn[k];
           lu_apply_v<NC, T>(Vl + (size_t)NOFF * ES, ES, PV[line * 32 + lane], r, res);
           for (int k = 0; k < NC; ++k) {
             x[k * n + i] = res[k];
             xprev[k] = res[k];
           }
         }
+        for (int k = 0; k < NC; ++k) { cb[k] = nb_[k]; cxe[k] = nxe[k]; cxn[k] = nxn[k]; }
         __syncwarp();
         if (lagk == 31 && act && ((c + 1) % SGS_PUBLISH == 0 || c == nx - 1)) {
           __threadfence();
