@@ -4,7 +4,8 @@ Workload: 1024 x 1024 cells on [0,4] x [0,1], 16 seeded Gaussian bumps with
 dry tops, inflow discharge hu ~ U[0.5, 1.5] at x = 0, outflow depth 0.6 at
 x = 4, reflective walls, LLF flux with the wet/dry speed increase; mixed
 precision (FP32 multigrid inner solve, FP64 residual / Jacobian / update /
-norms), W-cycles (gamma = 2, N_L = 6, N_mg = 3), eps_p = 2, tol 1e-10.
+norms), W-cycles (gamma = 2, N_L = 7 with an exact solve on the 8 x 8
+coarsest level, N_mg = 3), eps_p = 2, tol 1e-10.
 
 One step = one complete swnmg_solve (Algorithm 1 including its Step 1) from
 the same initial state, with inputs resident in HBM.  value = cells x
@@ -35,18 +36,19 @@ sys.path.insert(0, ROOT)
 METRIC = "cell*cycles/s to residual 1e-10 at 1024^2 (mixed FP32-MG / FP64), time to 1e-10"
 UNIT = "cell*cycles/s"
 NX = NY = 1024
-LEVELS = 6
+LEVELS = 7
 
 
 def workload(precision, nx=NX, ny=NY):
     from paper_1608_06721_gb300 import workloads as W
     p = W.channel_2d(seed=301, nx=nx, ny=ny, precision=precision)
-    return p.with_params(gamma=2, eps_p=2.0, n_levels=LEVELS, n_mg=3, tol=1e-10, max_newton=200)
+    return p.with_params(gamma=2, eps_p=2.0, n_levels=LEVELS, n_mg=3, coarse_sweeps=0, tol=1e-10,
+                         max_newton=200)
 
 
 def config_dict(p, flush):
     prm = p.params
-    return {"workload": "2D partial-dry channel %dx%d (LLF, W-cycle N_L=%d, N_mg=%d, eps_p=%g, seed 301)"
+    return {"workload": "2D partial-dry channel %dx%d (LLF, W-cycle N_L=%d exact coarsest, N_mg=%d, eps_p=%g, seed 301)"
             % (p.nx, p.ny, prm.n_levels, prm.n_mg, prm.eps_p),
             "cells": p.n, "precision": "mixed FP32 multigrid / FP64 residual+update",
             "l2": flush, "tol": prm.tol}

@@ -57,12 +57,16 @@ struct swnmg_ctx {
   double* rn = nullptr;     // ||R_i||_1
   double* eb = nullptr;     // per-edge Jacobian pieces (level-0 size)
   double* red = nullptr;    // reduction partials (1024) + result
-  double* band = nullptr;   // exact coarse-solve scratch
+  double* band = nullptr;   // exact coarse-solve scratch (banded elimination, large m)
+  void* cinv = nullptr;     // guarded inverse of the coarsest operator (small m)
+  void* caug = nullptr;     // its m x 2m elimination array
+  int* csing = nullptr;
   int* derr = nullptr;
   int* sgs_sync = nullptr;  // ticket / abort / per-strip progress of the wavefront sweeps
   int* sticky = nullptr;    // set by a device wait that ran out of its bound
   double* hbuf = nullptr;   // pinned host scalars
   bool coarse_exact = false;
+  bool coarse_inverse = false;   // exact coarse solve through X = A^-1 (guarded)
   // per-class kernel timing: event pairs resolved at synchronisation points
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -205,12 +209,18 @@ void sgs_half(swnmg_ctx* c, int l, int forward) {
 void blusgs_half(swnmg_ctx* c, int l, double* U, int forward) {
   DevLevel L = dev_level(c, l);
   TimedScope ts(c, SWNMG_T_BLUSGS);
-  launch_blusgs_sweep(L, c->lv[l].z, U, forward, c->st);
+  launch_blusgs_sweep(L, c->lv[l].z, U, forward, c->sgs_sync, c->sticky, c->st);
 }
 
 // Algorithm 0 on level l with lv[l].b, lv[l].x
 swnmg_status coarse_solve(swnmg_ctx* c, int l) {
   Level& v = c->lv[l];
+  if (c->coarse_inverse) {
+    TimedScope ts(c, SWNMG_T_COARSE_EXACT);
+    launch_coarse_apply(c->nc, v.n, c->cinv, v.b, v.x, c->fp32, c->st);
+    LAUNCH_CHECK(c);
+    return SWNMG_OK;
+  }
   if (c->coarse_exact) {
     TimedScope ts(c, SWNMG_T_COARSE_EXACT);
     launch_coarse_exact(c->nc, v.nx, v.ny, v.blk, v.b, v.x, c->band, c->derr, c->fp32, c->st);
@@ -271,6 +281,10 @@ swnmg_status assemble(swnmg_ctx* c, const double* U) {
   for (int l = 0; l <= c->nl; ++l)
     launch_lu_factor(c->lv[l].nx, c->lv[l].ny, c->nc, c->lv[l].blk, c->lv[l].lu, c->lv[l].piv, c->fp32,
                      c->st);
+  if (c->coarse_inverse) {
+    const Level& vc = c->lv[c->nl];
+    launch_coarse_inverse(c->nc, vc.nx, vc.ny, vc.blk, c->caug, c->cinv, c->csing, c->fp32, c->st);
+  }
   LAUNCH_CHECK(c);
   return SWNMG_OK;
 }
@@ -290,6 +304,9 @@ void free_ctx(swnmg_ctx* c) {
   if (c->eb) cudaFree(c->eb);
   if (c->red) cudaFree(c->red);
   if (c->band) cudaFree(c->band);
+  if (c->cinv) cudaFree(c->cinv);
+  if (c->caug) cudaFree(c->caug);
+  if (c->csing) cudaFree(c->csing);
   if (c->derr) cudaFree(c->derr);
   if (c->sgs_sync) cudaFree(c->sgs_sync);
   if (c->sticky) cudaFree(c->sticky);
@@ -411,7 +428,13 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
   {
     const Level& vc = c->lv[c->nl];
     c->coarse_exact = (p->dim == 1) || (q->coarse_sweeps <= 0);
-    if (c->coarse_exact) {
+    const long long mc = (long long)vc.n * c->nc;
+    c->coarse_inverse = c->coarse_exact && mc <= 384;
+    if (c->coarse_inverse) {
+      ALLOC(c->cinv, (size_t)(mc * mc) * c->wsz);
+      ALLOC(c->caug, (size_t)(2 * mc * mc) * c->wsz);
+      ALLOC(c->csing, (size_t)mc * sizeof(int));
+    } else if (c->coarse_exact) {
       const long long m = (long long)vc.n * c->nc;
       const long long ml = c->nc * (vc.ny > 1 ? vc.nx : 1) + c->nc - 1;
       const long long words = m * (3 * ml + 1) + 2 * m;

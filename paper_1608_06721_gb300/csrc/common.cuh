@@ -67,8 +67,8 @@ void launch_residual(const DevLevel& L, const double* z, const double* U, double
                      double* edge_buf, cudaStream_t st);
 void launch_jacobian(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
                      double* edge_buf, void* blk, int fp32, cudaStream_t st);   // blk skewed
-void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forward,
-                         cudaStream_t st);
+void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forward, int* sync,
+                         int* sticky_err, cudaStream_t st);
 void launch_newton_update(int n, int nc, double tau, double h_eps, double* U, const void* dU,
                           int dU_fp32, cudaStream_t st);
 void launch_average(int dim, int nxf, int nyf, int ncomp, const double* vf, double* vc,
@@ -90,6 +90,10 @@ void launch_sgs_sweep(int nc, int nx, int ny, const void* blk, const void* lu, c
                       cudaStream_t st);
 void launch_coarse_exact(int nc, int nx, int ny, const void* blk, const void* b, void* x,
                          double* band, int* err, int fp32, cudaStream_t st);
+void launch_coarse_inverse(int nc, int nx, int ny, const void* blk, void* aug, void* X, int* sing,
+                           int fp32, cudaStream_t st);
+void launch_coarse_apply(int nc, int n, const void* X, const void* b, void* x, int fp32,
+                         cudaStream_t st);
 void launch_sum(const double* v, int n, double* partial, double* out, cudaStream_t st);
 void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n,
                     double scale, cudaStream_t st);

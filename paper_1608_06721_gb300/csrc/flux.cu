@@ -448,7 +448,8 @@ __device__ void small_solve(double m[NC * NC], const double b[NC], double x[NC])
 // ---- BLU-SGS: one anti-diagonal of the lexicographic sweep ------------------
 // Cells with ix + iy = d depend only on diagonal d-1 (new values) and d+1
 // (old values), so updating one diagonal at a time in increasing (forward)
-// or decreasing (backward) order reproduces the lexicographic sweep exactly.
+// or decreasing (backward) order reproduces the lexicographic sweep exactly
+// (the whole sweep runs in one cooperative launch, k_blusgs_sweep below).
 // Each cell has a group of lanes, one per (side, perturbation p): p = 0
 // evaluates the side's G at U_i, p = k+1 at U_i + eps e_k.  All lanes run the
 // same edge evaluation (the cell is put on the edge's left or right by
@@ -456,14 +457,18 @@ __device__ void small_solve(double m[NC * NC], const double b[NC], double x[NC])
 // neighbour's velocities with its perturbation lanes (the same values they
 // would compute).  The group's first lane sums the sides in W, E, S, N order
 // and updates U_i -= (alpha||R_i||_1 I + dR_i/dU_i)^{-1} R_i.
-template <int NC, int NS, int GRP>
-__global__ void __launch_bounds__(32) k_blusgs_diag(DevLevel L, const double* __restrict__ z,
-                                                    double* __restrict__ U, int d, int ix0, int ncell) {
+template <bool L2>
+__device__ __forceinline__ double ldU(const double* p) { return L2 ? __ldcg(p) : *p; }
+
+// One cell group of a BLU-SGS diagonal.  With L2 = true the state is read
+// through L2 only (the persistent sweep, where other SMs update it during the
+// launch).  All 32 lanes of the warp must call it together.
+template <int NC, int NS, int GRP, bool L2>
+__device__ __forceinline__ void blusgs_group(const DevLevel& L, const double* __restrict__ z,
+                                             double* U, int d, int ix0, int ncell, int cell, int g) {
   constexpr int NP = NC + 1;                 // perturbations incl. the base
   const unsigned full = 0xffffffffu;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const int cell = t / GRP, g = t % GRP;
   const int side = g / NP, p = g % NP;
   const int gbase = lane - g;                // first lane of the cell's group
   const bool cell_ok = cell < ncell;
@@ -481,7 +486,7 @@ __global__ void __launch_bounds__(32) k_blusgs_diag(DevLevel L, const double* __
     if (sd == 3 && iy < L.ny - 1) j = i + L.nx;
   }
   double ci[NC];
-  for (int s = 0; s < NC; ++s) ci[s] = act ? U[s * n + i] : 0.0;
+  for (int s = 0; s < NC; ++s) ci[s] = act ? ldU<L2>(&U[s * n + i]) : 0.0;
   const double zi = act ? z[i] : 0.0, zj = (j >= 0) ? z[j] : zi;
   // base lane: 1/h_i and the neighbour's primitive state
   double rinv = 0.0;
@@ -490,7 +495,7 @@ __global__ void __launch_bounds__(32) k_blusgs_diag(DevLevel L, const double* __
     if (ci[0] >= L.h_eps) rinv = 1.0 / ci[0];
     if (j >= 0) {
       double cj[NC];
-      for (int s = 0; s < NC; ++s) cj[s] = U[s * n + j];
+      for (int s = 0; s < NC; ++s) cj[s] = ldU<L2>(&U[s * n + j]);
       nb = prim_axis<NC>(L, cj, axis);
     }
   }
@@ -559,6 +564,58 @@ __global__ void __launch_bounds__(32) k_blusgs_diag(DevLevel L, const double* __
   if (un[0] < L.h_eps)
     for (int s = 0; s < NC; ++s) un[s] = 0.0;
   for (int s = 0; s < NC; ++s) U[s * n + i] = un[s];
+}
+
+// ---- BLU-SGS: whole half-sweep in one cooperative launch -------------------
+// Every block walks the anti-diagonals in sweep order; after a diagonal the
+// blocks meet at a grid barrier (arrival counter, release/acquire), so the
+// next diagonal sees the new values.  The barrier wait is bounded: on expiry
+// the kernel sets the sticky error word and the abort flag, and every block
+// leaves at its next barrier.  sync: [0] arrivals, [1] abort.
+__device__ __forceinline__ int ld_acq(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int NC, int NS, int GRP>
+__global__ void __launch_bounds__(128) k_blusgs_sweep(DevLevel L, const double* __restrict__ z,
+                                                      double* U, int forward, int* sync,
+                                                      int* sticky_err, int spin_limit) {
+  __shared__ int s_go;
+  const int ndiag = L.nx + L.ny - 1;
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
+  const int cpw = 32 / GRP;                     // cells per warp and round
+  for (int q = 0; q < ndiag; ++q) {
+    const int d = forward ? q : ndiag - 1 - q;
+    const int ix0 = d - (L.ny - 1) > 0 ? d - (L.ny - 1) : 0;
+    const int ix1 = d < L.nx - 1 ? d : L.nx - 1;
+    const int ncell = ix1 - ix0 + 1;
+    for (int c0 = gw * cpw; c0 < ncell; c0 += nw * cpw)   // warp-uniform loop
+      blusgs_group<NC, NS, GRP, true>(L, z, U, d, ix0, ncell, c0 + (threadIdx.x & 31) / GRP,
+                                      (threadIdx.x & 31) % GRP);
+    // grid barrier
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&sync[0], 1);
+      const int target = (q + 1) * gridDim.x;
+      int ok = 0;
+      for (int it = 0; it < spin_limit; ++it) {
+        if (ld_acq(&sync[0]) >= target) { ok = 1; break; }
+        if (ld_acq(&sync[1])) break;
+        __nanosleep(20);
+      }
+      if (!ok) {
+        if (!ld_acq(&sync[1])) atomicOr(sticky_err, 1);
+        atomicExch(&sync[1], 1);
+      }
+      s_go = ok;
+    }
+    __syncthreads();
+    if (!s_go) return;
+  }
 }
 
 // U += tau dU with the dry rules of Remark 2.5 (eq. NewtonREG-12)
@@ -667,20 +724,26 @@ void launch_jacobian(const DevLevel& L, const double* z, const double* U, double
   }
 }
 
-void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forward,
-                         cudaStream_t st) {
-  count_launches(L.nx + L.ny - 1);
-  const int ndiag = L.nx + L.ny - 1;
-  for (int q = 0; q < ndiag; ++q) {
-    const int d = forward ? q : ndiag - 1 - q;
-    const int ix0 = d - (L.ny - 1) > 0 ? d - (L.ny - 1) : 0;
-    const int ix1 = d < L.nx - 1 ? d : L.nx - 1;
-    const int ncell = ix1 - ix0 + 1;
-    // one warp per block so that a diagonal's cells spread over the SMs
-    // (the FP64 pipe of an SM is shared by its warps)
-    if (L.nc == 3) k_blusgs_diag<3, 4, 16><<<nblk(ncell * 16, 32), 32, 0, st>>>(L, z, U, d, ix0, ncell);
-    else k_blusgs_diag<2, 2, 8><<<nblk(ncell * 8, 32), 32, 0, st>>>(L, z, U, d, ix0, ncell);
+void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forward, int* sync,
+                         int* sticky_err, cudaStream_t st) {
+  count_launches(1);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   }
+  cudaMemsetAsync(sync, 0, 2 * sizeof(int), st);
+  // one block of 4 warps per SM (co-resident by cooperative launch); a
+  // diagonal's cells are dealt to the warps in rounds
+  int fw = forward;
+  int spin = 1 << 22;
+  DevLevel Lc = L;
+  void* args[] = {(void*)&Lc, (void*)&z, (void*)&U, (void*)&fw, (void*)&sync, (void*)&sticky_err, (void*)&spin};
+  if (L.nc == 3)
+    cudaLaunchCooperativeKernel((const void*)k_blusgs_sweep<3, 4, 16>, dim3(nsm), dim3(128), args, 0, st);
+  else
+    cudaLaunchCooperativeKernel((const void*)k_blusgs_sweep<2, 2, 8>, dim3(nsm), dim3(128), args, 0, st);
 }
 
 void launch_newton_update(int n, int nc, double tau, double h_eps, double* U, const void* dU,

@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
   const int oW = (FWD ? 0 : 1) * BS, oE = (FWD ? 1 : 0) * BS, oS = (FWD ? 2 : 3) * BS,
             oN = (FWD ? 3 : 2) * BS;
   const int lagk = FWD ? lane : 31 - lane;
-  const int nsteps = nx + 31, nchunks = (nsteps + S - 1) / S;
+  const int nsteps_full = nx + 31;
   const int wait_limit = spin_limit;
   for (;;) {
     int q = 0;
@@ -329,10 +329,16 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
     if (q >= nstrips) return;
     const int ps = FWD ? q : nstrips - 1 - q;
     const long long line_base = (long long)ps * (nx + 31);
+    // the strip's valid rows; in a forward sweep its last valid lane finishes
+    // at step nx + rows - 2, in a backward sweep the leading lane is lane 31
+    // (lag 0) only when it is valid, so short strips keep the full skew there
+    const int rows = min(32, ny - ps * 32);
+    const int nsteps = FWD ? nx + rows - 1 : nsteps_full;
+    const int nchunks = (nsteps + S - 1) / S;
     // lane 0 issues chunk j into stage st
     auto issue = [&](int j, int st) {
       const int s0 = j * S, cnt = min(S, nsteps - s0);
-      const int dlo = FWD ? s0 : nx + 31 - s0 - cnt;
+      const int dlo = FWD ? s0 : nsteps_full - s0 - cnt;
       const long long off = (line_base + dlo) * 32;
       const unsigned vb = (unsigned)(cnt * 32 * sizeof(T));
       fence_proxy_async();
@@ -376,6 +382,9 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
         for (int k = 0; k < NC; ++k) xn[k] = x[k * n + jj];
       }
     };
+    T sbuf[SGS_PUBLISH][NC];   // previous strip's last row, current group of columns
+    for (int t = 0; t < SGS_PUBLISH; ++t)
+      for (int k = 0; k < NC; ++k) sbuf[t][k] = T(0);
     T cb[NC], cxe[NC], cxn[NC];
     for (int k = 0; k < NC; ++k) { cb[k] = T(0); cxe[k] = T(0); cxn[k] = T(0); }
     if (rowok && lagk == 0) load_cell(0, cb, cxe, cxn);
@@ -402,8 +411,9 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
         T xS[NC];
         for (int k = 0; k < NC; ++k)
           xS[k] = FWD ? __shfl_up_sync(FULL, res[k], 1) : __shfl_down_sync(FULL, res[k], 1);
-        if (q > 0 && s < nx) {
-          const int need = s + 1;
+        if (q > 0 && s < nx && (s & (SGS_PUBLISH - 1)) == 0) {
+          // the previous strip's last row, SGS_PUBLISH columns at a time
+          const int need = min(s + SGS_PUBLISH, nx);
           if (known < need) {
             int p = 0, it = 0;
             do {
@@ -427,8 +437,15 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
           const int px = FWD ? c : nx - 1 - c;
           const long long i = (long long)px + (long long)nx * y;
           if (lagk == 0 && hasS) {   // south value from the previous strip (after acquire)
-            const long long jj = (long long)px + (long long)nx * yS;
-            for (int k = 0; k < NC; ++k) xS[k] = __ldcg(&x[k * n + jj]);
+            if ((c & (SGS_PUBLISH - 1)) == 0) {
+              for (int t = 0; t < SGS_PUBLISH; ++t)
+                if (c + t < nx) {
+                  const int pxt = FWD ? c + t : nx - 1 - (c + t);
+                  const long long jj = (long long)pxt + (long long)nx * yS;
+                  for (int k = 0; k < NC; ++k) sbuf[t][k] = __ldcg(&x[k * n + jj]);
+                }
+            }
+            for (int k = 0; k < NC; ++k) xS[k] = sbuf[c & (SGS_PUBLISH - 1)][k];
           }
           const T* Vl = V + line * 32 + lane;
           const int ES = S * 32;   // stride between entries in the stage
@@ -454,7 +471,7 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
         }
         for (int k = 0; k < NC; ++k) { cb[k] = nb_[k]; cxe[k] = nxe[k]; cxn[k] = nxn[k]; }
         __syncwarp();
-        if (lagk == 31 && act && ((c + 1) % SGS_PUBLISH == 0 || c == nx - 1)) {
+        if (lagk == 31 && act && q + 1 < nstrips && ((c + 1) % SGS_PUBLISH == 0 || c == nx - 1)) {
           __threadfence();
           st_release(&sync[2 + q], c + 1);
         }
@@ -565,6 +582,124 @@ __global__ void k_coarse_exact(int nx, int ny, const T* __restrict__ blk, const 
     for (int r = 0; r < m; ++r) x[(long long)(r % NC) * n + r / NC] = (T)rhs[r];
     if (err) *err = 0;
   }
+}
+
+// ---- exact coarse solve: guarded inverse -------------------------------------
+// For a small coarsest level (m = NC*n unknowns, cell-major i*NC + s) the
+// solve of Algorithm 0 is x = X b with X the "guarded inverse": Gaussian
+// elimination with partial pivoting (largest |entry|, lowest row on ties) on
+// [A | I], a pivot <= 1e-14 max|A| leaving its unknown at zero, then back
+// substitution for every unit right-hand side.  The solve is linear in b, so
+// X b equals that elimination applied to b.  X is formed once per Newton step
+// (one CTA) and applied at every visit of the coarsest level.
+// aug: m x 2m working array (row-major), X: m x m column-major.
+template <int NC, typename T>
+__global__ void k_coarse_inverse(int nx, int ny, const T* __restrict__ blk, T* __restrict__ aug,
+                                 T* __restrict__ X, int* __restrict__ sing) {
+  const int n = nx * ny, m = n * NC, w = 2 * m;
+  const long long P = skew_slots(nx, ny);
+  const int BS = NC * NC;
+  __shared__ T s_amax[32];
+  __shared__ int s_p, s_sing;
+  for (long long e = threadIdx.x; e < (long long)m * w; e += blockDim.x) aug[e] = T(0);
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int ix = i % nx, iy = i / nx;
+    const long long si = skew_pos(ix, iy, nx);
+    int nb[4] = {ix > 0 ? i - 1 : -1, ix < nx - 1 ? i + 1 : -1, iy > 0 ? i - nx : -1,
+                 iy < ny - 1 ? i + nx : -1};
+    for (int s = 0; s < NC; ++s) {
+      const long long row = (long long)(i * NC + s) * w;
+      for (int k = 0; k < NC; ++k) aug[row + i * NC + k] = blk[(long long)(s * NC + k) * P + si];
+      for (int side = 0; side < 4; ++side) {
+        const int j = nb[side];
+        if (j < 0) continue;
+        for (int k = 0; k < NC; ++k)
+          aug[row + j * NC + k] = blk[((long long)(1 + side) * BS + s * NC + k) * P + si];
+      }
+      aug[row + m + i * NC + s] = T(1);
+      sing[i * NC + s] = 0;
+    }
+  }
+  __syncthreads();
+  // max |A| (A part only)
+  T a = T(0);
+  for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) {
+    const T v = tabs(aug[(e / m) * w + (e % m)]);
+    a = v > a ? v : a;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const T b2 = __shfl_down_sync(0xffffffffu, a, o);
+    a = b2 > a ? b2 : a;
+  }
+  if ((threadIdx.x & 31) == 0) s_amax[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T mx = T(0);
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) mx = s_amax[q] > mx ? s_amax[q] : mx;
+    s_amax[0] = mx;
+  }
+  __syncthreads();
+  const T tiny = T(1e-14) * s_amax[0];
+  for (int c = 0; c < m; ++c) {
+    if (threadIdx.x == 0) {
+      int p = c;
+      T best = tabs(aug[(long long)c * w + c]);
+      for (int r = c + 1; r < m; ++r) {
+        const T v = tabs(aug[(long long)r * w + c]);
+        if (v > best) { best = v; p = r; }
+      }
+      s_p = p;
+      s_sing = !(best > tiny);
+      if (s_sing) sing[c] = 1;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != c)
+      for (int k = threadIdx.x; k < w; k += blockDim.x) {
+        const T t = aug[(long long)c * w + k];
+        aug[(long long)c * w + k] = aug[(long long)p * w + k];
+        aug[(long long)p * w + k] = t;
+      }
+    __syncthreads();
+    if (!s_sing) {
+      // multipliers first (kept in column c below the pivot, which the back
+      // substitution never reads), then the row updates
+      const T piv = aug[(long long)c * w + c];
+      for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) aug[(long long)r * w + c] /= piv;
+      __syncthreads();
+      const int rows = m - c - 1, cols = w - c - 1;
+      for (long long e = threadIdx.x; e < (long long)rows * cols; e += blockDim.x) {
+        const int r = c + 1 + (int)(e / cols), k = c + 1 + (int)(e % cols);
+        aug[(long long)r * w + k] -= aug[(long long)r * w + c] * aug[(long long)c * w + k];
+      }
+    }
+    __syncthreads();
+  }
+  // back substitution, one unit right-hand side per thread
+  for (int jcol = threadIdx.x; jcol < m; jcol += blockDim.x) {
+    for (int r = m - 1; r >= 0; --r) {
+      T v;
+      if (sing[r]) v = T(0);
+      else {
+        T acc = aug[(long long)r * w + m + jcol];
+        for (int k = r + 1; k < m; ++k) acc -= aug[(long long)r * w + k] * X[(long long)jcol * m + k];
+        v = acc / aug[(long long)r * w + r];
+      }
+      X[(long long)jcol * m + r] = v;
+    }
+  }
+}
+
+// x = X b on the coarsest level (SoA vectors, cell-major unknowns)
+template <int NC, typename T>
+__global__ void k_coarse_apply(int n, const T* __restrict__ X, const T* __restrict__ b, T* __restrict__ x) {
+  const int m = n * NC;
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= m) return;
+  T acc = T(0);
+  for (int jcol = 0; jcol < m; ++jcol) acc += X[(long long)jcol * m + u] * b[(long long)(jcol % NC) * n + jcol / NC];
+  x[(long long)(u % NC) * n + u / NC] = acc;
 }
 
 // fixed-order sum: per-block tree partials, then one block over the partials
@@ -713,6 +848,24 @@ void launch_coarse_exact(int nc, int nx, int ny, const void* blk, const void* b,
   if (nc == 3) { if (fp32) CL(3, float); else CL(3, double); }
   else { if (fp32) CL(2, float); else CL(2, double); }
 #undef CL
+}
+
+void launch_coarse_inverse(int nc, int nx, int ny, const void* blk, void* aug, void* X, int* sing,
+                           int fp32, cudaStream_t st) {
+  count_launches(1);
+#define CI(NC, T) k_coarse_inverse<NC, T><<<1, 1024, 0, st>>>(nx, ny, (const T*)blk, (T*)aug, (T*)X, sing)
+  if (nc == 3) { if (fp32) CI(3, float); else CI(3, double); }
+  else { if (fp32) CI(2, float); else CI(2, double); }
+#undef CI
+}
+
+void launch_coarse_apply(int nc, int n, const void* X, const void* b, void* x, int fp32, cudaStream_t st) {
+  count_launches(1);
+  const int m = n * nc;
+#define CA(NC, T) k_coarse_apply<NC, T><<<nblk(m, 128), 128, 0, st>>>(n, (const T*)X, (const T*)b, (T*)x)
+  if (nc == 3) { if (fp32) CA(3, float); else CA(3, double); }
+  else { if (fp32) CA(2, float); else CA(2, double); }
+#undef CA
 }
 
 void launch_sum(const double* v, int n, double* partial, double* out, cudaStream_t st) {

@@ -45,6 +45,10 @@ def _cases():
     out.append(("hill64x32_hll", p, lambda p: W.random_state(p, 5, wet_frac=0.5)))
     p = W.transcritical_bump_2d(48, 24)
     out.append(("ex36_48x24", p, lambda p: W.random_state(p, 6)))
+    # three 32-row strips (the last partial) and a width that is not a
+    # multiple of the wavefront's 4-column publication group
+    p = W.channel_2d(nx=66, ny=70, n_levels=1, redraw=False)
+    out.append(("channel_66x70", p, lambda p: W.random_state(p, 7, wet_frac=0.5)))
     return out
 
 
