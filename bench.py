@@ -127,19 +127,20 @@ FP64_OPS_PEAK = 152 * 2 * 2.07e9
 
 
 def algorithmic(cls, p, fp32):
-    """(bound, units per launch) of one launch of a kernel class at level 0:
-    bytes for the HBM-bound smoother, FP64 operations for the flux kernels
-    (operation counts per cell are derived in the design doc)."""
-    n, nc = p.n, p.ncomp
+    """(bound, algorithmic units per cell) of a kernel class: bytes for the
+    block-SGS smoother, FP64 operations for the flux kernels (counts per cell
+    derived in the design doc).  Multiplied by the cells the timed launches
+    processed, as reported by the library."""
+    nc = p.ncomp
     w = 4 if fp32 else 8
-    if cls == "sgs_fine":
-        return "hbm", n * ((5 * nc * nc - nc * nc + 9 + 3 + 2 * nc) * w + 1)   # blocks, LU, b, x in/out, piv
-    if cls == "blusgs":
-        return "alu", n * 1020.0
+    if cls in ("sgs_fine", "sgs_coarse"):
+        return "hbm", (5 * nc * nc - nc * nc + 9 + 3 + 2 * nc) * w + 1   # blocks, LU, b, x in/out, piv
+    if cls in ("blusgs", "blusgs_coarse"):
+        return "alu", 1020.0
     if cls == "jacobian":
-        return "alu", n * 1035.0
+        return "alu", 1035.0
     if cls == "residual":
-        return "alu", n * 130.0
+        return "alu", 130.0
     return None, None
 
 
@@ -216,23 +217,27 @@ def run_gpu(args):
 
     # roofline of the dominant kernel class (live CUDA events on the solver's stream)
     dom = max((k for k in timing if timing[k][1] > 0), key=lambda k: timing[k][0])
-    bound, units = algorithmic(dom, p, True)
+    bound, per_cell = algorithmic(dom, p, True)
     roof = None
     if bound is not None:
         avg_ms = timing[dom][0] / timing[dom][1]
+        units = per_cell * timing[dom][2] / timing[dom][1]    # per launch
         if bound == "hbm":
             pk, src = peaks()
             ach = units / (avg_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk, "unit": "GB/s",
-                    "frac": ach / pk, "traffic": None, "peak_source": src}
+                    "frac": ach / pk, "traffic": None, "peak_source": src,
+                    "units_per_launch": units, "avg_launch_ms": avg_ms}
         else:
             ach = units / (avg_ms * 1e-3) / 1e12
             pk = FP64_OPS_PEAK / 1e12
             roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": pk,
                     "unit": "TFLOP/s (FP64 ops, no FMA)", "frac": ach / pk, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz"}
+                    "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz",
+                    "units_per_launch": units, "avg_launch_ms": avg_ms}
     total_dev = sum(v[0] for v in timing.values())
-    shares = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / total_dev, 4) if total_dev else 0}
+    shares = {k: {"ms": round(v[0], 3), "launches": v[1], "cells": v[2],
+                  "share": round(v[0] / total_dev, 4) if total_dev else 0}
               for k, v in timing.items() if v[1] > 0}
 
     # FP64 path on the same problem

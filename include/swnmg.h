@@ -170,19 +170,22 @@ enum {
   SWNMG_T_SGS_FINE = 3,     /* block SGS half-sweep on level 0 */
   SWNMG_T_SGS_COARSE = 4,   /* block SGS half-sweeps on levels >= 1 */
   SWNMG_T_TRANSFER = 5,     /* restriction, prolongation, zero fill */
-  SWNMG_T_BLUSGS = 6,       /* BLU-SGS half-sweep (any level) */
+  SWNMG_T_BLUSGS = 6,       /* BLU-SGS half-sweep on level 0 (Step 2.1) */
   SWNMG_T_UPDATE = 7,       /* Newton update */
   SWNMG_T_COARSE_EXACT = 8, /* exact coarsest-level solve */
-  SWNMG_T_COUNT = 9
+  SWNMG_T_BLUSGS_COARSE = 9,/* BLU-SGS half-sweeps on levels >= 1 (Step 1) */
+  SWNMG_T_COUNT = 10
 };
 
 /* Enables (1) or disables (0) per-class kernel timing and clears the totals. */
 SWNMG_API swnmg_status swnmg_set_timing(swnmg_ctx* ctx, int32_t enable);
 
-/* Accumulated device milliseconds and launch counts per class since the last
- * swnmg_set_timing(ctx, 1); ms_out and launches_out hold SWNMG_T_COUNT
- * entries.  Synchronises the stream. */
-SWNMG_API swnmg_status swnmg_get_timing(swnmg_ctx* ctx, double* ms_out, int64_t* launches_out);
+/* Accumulated device milliseconds, launch counts and cells processed (the
+ * level's cells summed over the timed launches) per class since the last
+ * swnmg_set_timing(ctx, 1); each array holds SWNMG_T_COUNT entries.
+ * Synchronises the stream. */
+SWNMG_API swnmg_status swnmg_get_timing(swnmg_ctx* ctx, double* ms_out, int64_t* launches_out,
+                                        double* cells_out);
 
 /* Total number of CUDA kernels this library has launched in this process
  * (all contexts); differences around a region count its launches. */

@@ -71,9 +71,11 @@ struct swnmg_ctx {
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_class;     // class of pair k (events 2k, 2k+1)
+  std::vector<double> ev_cells;  // cells processed inside pair k
   int ev_used = 0;
   double t_ms[SWNMG_T_COUNT] = {0};
   long long t_n[SWNMG_T_COUNT] = {0};
+  double t_cells[SWNMG_T_COUNT] = {0};
   std::string err;
 };
 
@@ -146,6 +148,7 @@ void timing_resolve(swnmg_ctx* c) {
     if (cudaEventElapsedTime(&ms, c->ev_pool[2 * k], c->ev_pool[2 * k + 1]) == cudaSuccess) {
       c->t_ms[c->ev_class[k]] += ms;
       c->t_n[c->ev_class[k]] += 1;
+      c->t_cells[c->ev_class[k]] += c->ev_cells[k];
     }
   }
   c->ev_used = 0;
@@ -155,11 +158,12 @@ void timing_resolve(swnmg_ctx* c) {
 struct TimedScope {
   swnmg_ctx* c;
   int k = -1;
-  TimedScope(swnmg_ctx* ctx, int cls) : c(ctx) {
+  TimedScope(swnmg_ctx* ctx, int cls, double cells = 0.0) : c(ctx) {
     if (!c->timing) return;
     if (c->ev_used * 2 + 2 > (int)c->ev_pool.size()) timing_resolve(c);
     k = c->ev_used++;
     c->ev_class[k] = cls;
+    c->ev_cells[k] = cells;
     cudaEventRecord(c->ev_pool[2 * k], c->st);
   }
   ~TimedScope() {
@@ -192,7 +196,7 @@ swnmg_status check_sticky(swnmg_ctx* c) {
 swnmg_status level_residual_sum(swnmg_ctx* c, int l, const double* U, double* out) {
   DevLevel L = dev_level(c, l);
   {
-    TimedScope ts(c, SWNMG_T_RESIDUAL);
+    TimedScope ts(c, SWNMG_T_RESIDUAL, L.n);
     launch_residual(L, c->lv[l].z, U, c->R, c->rn, c->eb, c->st);
   }
   LAUNCH_CHECK(c);
@@ -201,14 +205,14 @@ swnmg_status level_residual_sum(swnmg_ctx* c, int l, const double* U, double* ou
 
 void sgs_half(swnmg_ctx* c, int l, int forward) {
   Level& v = c->lv[l];
-  TimedScope ts(c, l == 0 ? SWNMG_T_SGS_FINE : SWNMG_T_SGS_COARSE);
+  TimedScope ts(c, l == 0 ? SWNMG_T_SGS_FINE : SWNMG_T_SGS_COARSE, v.n);
   launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward, c->fp32, c->sgs_sync,
                    c->sticky, c->st);
 }
 
 void blusgs_half(swnmg_ctx* c, int l, double* U, int forward) {
   DevLevel L = dev_level(c, l);
-  TimedScope ts(c, SWNMG_T_BLUSGS);
+  TimedScope ts(c, l == 0 ? SWNMG_T_BLUSGS : SWNMG_T_BLUSGS_COARSE, L.n);
   launch_blusgs_sweep(L, c->lv[l].z, U, forward, c->sgs_sync, c->sticky, c->st);
 }
 
@@ -270,7 +274,7 @@ swnmg_status mg_cycle(swnmg_ctx* c, int l) {
 swnmg_status assemble(swnmg_ctx* c, const double* U) {
   DevLevel L = dev_level(c, 0);
   {
-    TimedScope ts(c, SWNMG_T_JACOBIAN);
+    TimedScope ts(c, SWNMG_T_JACOBIAN, L.n);
     launch_jacobian(L, c->lv[0].z, U, c->R, c->rn, c->eb, c->lv[0].blk, c->fp32, c->st);
   }
   LAUNCH_CHECK(c);
@@ -663,22 +667,28 @@ SWNMG_API swnmg_status swnmg_set_timing(swnmg_ctx* c, int32_t enable) {
   if (!c) return fail(c, SWNMG_ERR_ARG, "null context");
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   c->ev_used = 0;
-  for (int k = 0; k < SWNMG_T_COUNT; ++k) { c->t_ms[k] = 0; c->t_n[k] = 0; }
+  for (int k = 0; k < SWNMG_T_COUNT; ++k) { c->t_ms[k] = 0; c->t_n[k] = 0; c->t_cells[k] = 0; }
   if (enable && c->ev_pool.empty()) {
     const int pairs = 4096;
     c->ev_pool.resize(2 * pairs);
     c->ev_class.resize(pairs);
+    c->ev_cells.resize(pairs);
     for (auto& e : c->ev_pool) CUDA_TRY(c, cudaEventCreate(&e));
   }
   c->timing = enable != 0;
   return SWNMG_OK;
 }
 
-SWNMG_API swnmg_status swnmg_get_timing(swnmg_ctx* c, double* ms_out, int64_t* n_out) {
-  if (!c || !ms_out || !n_out) return fail(c, SWNMG_ERR_ARG, "null pointer");
+SWNMG_API swnmg_status swnmg_get_timing(swnmg_ctx* c, double* ms_out, int64_t* n_out,
+                                        double* cells_out) {
+  if (!c || !ms_out || !n_out || !cells_out) return fail(c, SWNMG_ERR_ARG, "null pointer");
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   timing_resolve(c);
-  for (int k = 0; k < SWNMG_T_COUNT; ++k) { ms_out[k] = c->t_ms[k]; n_out[k] = c->t_n[k]; }
+  for (int k = 0; k < SWNMG_T_COUNT; ++k) {
+    ms_out[k] = c->t_ms[k];
+    n_out[k] = c->t_n[k];
+    cells_out[k] = c->t_cells[k];
+  }
   return SWNMG_OK;
 }
 

@@ -75,7 +75,7 @@ def lib():
         L.swnmg_blusgs.argtypes = [vp, vp, C.c_int32, C.c_int32]
         L.swnmg_solve.argtypes = [vp, vp, C.POINTER(Stats)]
         L.swnmg_set_timing.argtypes = [vp, C.c_int32]
-        L.swnmg_get_timing.argtypes = [vp, dp, C.POINTER(C.c_int64)]
+        L.swnmg_get_timing.argtypes = [vp, dp, C.POINTER(C.c_int64), dp]
         L.swnmg_residual_noalloc.argtypes = [C.POINTER(Problem), C.POINTER(Params), vp, vp, vp, vp, vp, vp]
         L.swnmg_residual_noalloc.restype = C.c_int
         L.swnmg_level_cells.argtypes = [vp, C.c_int32]
@@ -90,7 +90,7 @@ def lib():
 
 
 KERNEL_CLASSES = ["residual", "jacobian", "galerkin_lu", "sgs_fine", "sgs_coarse", "transfer",
-                  "blusgs", "update", "coarse_exact"]
+                  "blusgs", "update", "coarse_exact", "blusgs_coarse"]
 
 
 class SwnmgError(RuntimeError):
@@ -207,12 +207,13 @@ class Solver:
         self._check(self.L.swnmg_set_timing(self.h, 1 if enable else 0))
 
     def get_timing(self):
-        """{class: (device ms, launches)} accumulated since set_timing(True)."""
+        """{class: (device ms, launches, cells processed)} since set_timing(True)."""
         k = len(KERNEL_CLASSES)
         ms = (C.c_double * k)()
         nl = (C.c_int64 * k)()
-        self._check(self.L.swnmg_get_timing(self.h, ms, nl))
-        return {name: (ms[i], nl[i]) for i, name in enumerate(KERNEL_CLASSES)}
+        cells = (C.c_double * k)()
+        self._check(self.L.swnmg_get_timing(self.h, ms, nl, cells))
+        return {name: (ms[i], nl[i], cells[i]) for i, name in enumerate(KERNEL_CLASSES)}
 
     def solve(self, U, check=False):
         """Algorithm 1 in place on U; returns a dict of the solver counters."""
