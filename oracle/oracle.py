@@ -80,6 +80,8 @@ def lib():
         _lib.orc_average.argtypes = [cfgp, C.c_int, C.c_int, P, P]
         _lib.orc_solve.argtypes = [cfgp, P, P, C.POINTER(Stats)]
         _lib.orc_level_cells.argtypes = [cfgp, C.c_int]
+        _lib.orc_transpose_blocks.argtypes = [cfgp, C.c_int, P, P]
+        _lib.orc_adjoint.argtypes = [cfgp, P, P, P, P, P, P, C.c_int]
     return _lib
 
 
@@ -224,6 +226,23 @@ class Oracle:
         self.L.orc_blusgs(C.byref(self.cfg), level, _p(np.ascontiguousarray(z, dtype=np.float64)),
                           _p(U), nsweeps)
         return U
+
+    def transpose_blocks(self, blk, level=0):
+        out = np.zeros_like(np.ascontiguousarray(blk, dtype=np.float64))
+        self.L.orc_transpose_blocks(C.byref(self.cfg), level, _p(np.ascontiguousarray(blk)), _p(out))
+        return out
+
+    def adjoint(self, U, g, ncycles=0, z=None):
+        """(lambda, lambda^T dR/dz, lambda^T dR/dq[4]) at U for g = (dL/dU)^T."""
+        z = self.prob.z if z is None else z
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        lam = np.zeros_like(U)
+        dRz = np.zeros(U.shape[1])
+        dRq = np.zeros(4)
+        self.L.orc_adjoint(C.byref(self.cfg), _p(np.ascontiguousarray(z, dtype=np.float64)), _p(U), _p(g),
+                           _p(lam), _p(dRz), _p(dRq), ncycles)
+        return lam, dRz, dRq
 
     def solve(self, U0=None):
         U = np.array(self.prob.U0 if U0 is None else U0, dtype=np.float64, copy=True)

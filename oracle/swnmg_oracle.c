@@ -869,3 +869,117 @@ int orc_solve(const orc_cfg* c, const double* z0, double* U0, orc_stats* st) {
   for (int l = 0; l <= NL; ++l) { free(zl[l]); free(Ul[l]); }
   return status;
 }
+
+/* ---- discrete adjoint (not in the paper) ---------------------------------
+ * At a steady state U_s (R(U_s, z, q) = 0) and for a loss L(U, z), the
+ * implicit function theorem gives the derivative of U_s with respect to z as
+ * -J^{-1} dR/dz with J = dR/dU, so
+ *   dL/dz = dL/dz|_direct - lambda^T dR/dz,   dL/dq = -lambda^T dR/dq,
+ *   J^T lambda = (dL/dU)^T.
+ * J is the finite-difference Jacobian of eq. NumerDiff with its
+ * regularisation (negligible at a steady state).  lambda solves the
+ * transposed system with the same multigrid: the transposed operator's
+ * Galerkin hierarchy is the transpose of the forward one (P^T A^T P =
+ * (P^T A P)^T) and its smoother is block Gauss-Seidel on A^T.  dR/dz and
+ * dR/dq are central differences with step ADJ_DELTA, contracted with lambda
+ * (these derivatives are not part of the paper's method; the central form
+ * keeps their error near 1e-10 where a forward difference would leave 1e-8
+ * per term, which cancellation in lambda^T dR/dz magnifies).
+ */
+#define ADJ_DELTA 1e-6
+
+/* transposed blocks: D'_i = D_i^T, and the block of cell i towards its
+ * neighbour j in A^T is the transpose of cell j's block towards i in A */
+static void transpose_blocks(const orc_cfg* c, const lvl* L, const double* blk, double* out) {
+  int nc = ncomp(c), bs = nc * nc;
+  for (int i = 0; i < L->n; ++i) {
+    double* o = out + (size_t)i * 5 * bs;
+    const double* D = blk + (size_t)i * 5 * bs;
+    for (int s = 0; s < nc; ++s)
+      for (int k = 0; k < nc; ++k) o[s * nc + k] = D[k * nc + s];
+    for (int side = 0; side < 4; ++side) {
+      double* ob = o + (1 + side) * bs;
+      int j = (side < nsides(c)) ? nbr(L, i, side) : -1;
+      if (j < 0) { for (int e = 0; e < bs; ++e) ob[e] = 0.0; continue; }
+      const double* A = blk + ((size_t)j * 5 + 1 + (side ^ 1)) * bs;   /* j's block towards i */
+      for (int s = 0; s < nc; ++s)
+        for (int k = 0; k < nc; ++k) ob[s * nc + k] = A[k * nc + s];
+    }
+  }
+}
+
+int orc_transpose_blocks(const orc_cfg* c, int l, const double* blk, double* out) {
+  lvl L = level_geom(c, l);
+  transpose_blocks(c, &L, blk, out);
+  return ST_OK;
+}
+
+/* lambda^T dR/dz (n values) and lambda^T dR/dq (per side, inflow sides only) */
+static void adjoint_vjp(const orc_cfg* c, const lvl* L, const double* z, const double* U,
+                        const double* lam, double* dRz, double* dRq) {
+  int nc = ncomp(c), n = L->n;
+  double d = ADJ_DELTA, r2d = 1.0 / (2.0 * ADJ_DELTA);
+  double* zp = (double*)malloc(sizeof(double) * n);
+  double* zm = (double*)malloc(sizeof(double) * n);
+  memcpy(zp, z, sizeof(double) * n);
+  memcpy(zm, z, sizeof(double) * n);
+  for (int j = 0; j < n; ++j) {
+    double acc = 0.0;
+    zp[j] = z[j] + d;
+    zm[j] = z[j] - d;
+    for (int side = 0; side < nsides(c); ++side) {
+      double len = side_len(L, side), Gm[3], Gp[3];
+      cell_G(c, L, zm, U, j, side, -1, 0, 0.0, Gm);          /* the cell itself */
+      cell_G(c, L, zp, U, j, side, -1, 0, 0.0, Gp);
+      for (int s = 0; s < nc; ++s) acc = acc + lam[s * n + j] * (len * ((Gp[s] - Gm[s]) * r2d));
+      int k = nbr(L, j, side);
+      if (k >= 0) {                                            /* the neighbour across it */
+        cell_G(c, L, zm, U, k, side ^ 1, -1, 0, 0.0, Gm);
+        cell_G(c, L, zp, U, k, side ^ 1, -1, 0, 0.0, Gp);
+        for (int s = 0; s < nc; ++s) acc = acc + lam[s * n + k] * (len * ((Gp[s] - Gm[s]) * r2d));
+      }
+    }
+    zp[j] = z[j];
+    zm[j] = z[j];
+    dRz[j] = acc;
+  }
+  free(zp);
+  free(zm);
+  for (int side = 0; side < 4; ++side) {
+    dRq[side] = 0.0;
+    if (side >= nsides(c) || c->bc[side].kind != BC_INFLOW_DISCHARGE) continue;
+    orc_cfg cp = *c, cm = *c;
+    cp.bc[side].q = c->bc[side].q + d;
+    cm.bc[side].q = c->bc[side].q - d;
+    double acc = 0.0, len = side_len(L, side);
+    for (int i = 0; i < n; ++i) {
+      if (nbr(L, i, side) >= 0) continue;
+      double Gm[3], Gp[3];
+      cell_G(&cm, L, z, U, i, side, -1, 0, 0.0, Gm);
+      cell_G(&cp, L, z, U, i, side, -1, 0, 0.0, Gp);
+      for (int s = 0; s < nc; ++s) acc = acc + lam[s * n + i] * (len * ((Gp[s] - Gm[s]) * r2d));
+    }
+    dRq[side] = acc;
+  }
+}
+
+/* lambda (nc*n), lambda^T dR/dz (n) and lambda^T dR/dq (4) at U for the
+ * right-hand side g = (dL/dU)^T; ncycles > 0: that many cycles of Algorithm 0
+ * on A^T from lambda = 0, ncycles <= 0: exact dense solve. */
+int orc_adjoint(const orc_cfg* c, const double* z, const double* U, const double* g, double* lam,
+                double* dRz, double* dRq, int ncycles) {
+  if (check_cfg(c)) return ST_ARG;
+  lvl L = level_geom(c, 0);
+  int nc = ncomp(c), bs = nc * nc, n = L.n;
+  double* R = (double*)malloc(sizeof(double) * (size_t)n * nc);
+  double* blk = (double*)malloc(sizeof(double) * (size_t)n * 5 * bs);
+  double* blkT = (double*)malloc(sizeof(double) * (size_t)n * 5 * bs);
+  orc_jacobian(c, 0, z, U, R, NULL, blk);
+  transpose_blocks(c, &L, blk, blkT);
+  for (int e = 0; e < n * nc; ++e) lam[e] = 0.0;
+  if (ncycles <= 0) dense_solve(c, &L, blkT, g, lam);
+  else orc_vcycle(c, blkT, g, lam, ncycles);
+  adjoint_vjp(c, &L, z, U, lam, dRz, dRq);
+  free(R); free(blk); free(blkT);
+  return ST_OK;
+}

@@ -260,7 +260,8 @@ def channel_2d(seed: int = 301, nx: int = 1024, ny: int = 1024, n_bumps: int = 1
     amp, wid, cx, cy, q = bumps
     p = Problem("channel2d", 2, nx, ny, 0.0, 4.0, 0.0, 1.0, None, None, _walls(),
                 Params(flux=FLUX_LLF, llf_wetdry=1, n_levels=n_levels, n_mg=3, precision=precision),
-                meta={"seed": seed, "redraw_k": k, "q_in": q})
+                meta={"seed": seed, "redraw_k": k, "q_in": q,
+                      "bumps": (amp, wid, cx, cy)})
     X, Y = p.centres()
     p.z = gaussian_bumps(X, Y, amp, wid, cx, cy)
     h = np.maximum(0.0, 0.6 - p.z)
@@ -318,3 +319,22 @@ def random_state(p: Problem, seed: int, wet_frac: float = 1.0, u_scale: float = 
     U = np.stack(comps)
     U[:, h == 0.0] = 0.0
     return U
+
+
+def adjoint_case(seed: int = 501, n: int = 512, n_gauges: int = 64, n_levels: int = 7):
+    """Gradient workload: the partial-dry channel at n x n (FP64, W-cycles,
+    exact coarsest solve), a loss over n_gauges distinct initially wet gauge
+    cells L = sum (h + z - eta_obs)^2, where eta_obs comes from a forward
+    solve on the bed with every bump amplitude scaled by (1 + 0.05 xi),
+    xi ~ U[-1, 1].  Returns (problem, z_obs, gauge indices); eta_obs is
+    computed by the caller's solver."""
+    p = channel_2d(seed=seed, nx=n, ny=n, n_levels=n_levels)
+    p = p.with_params(gamma=2, eps_p=2.0, coarse_sweeps=0)
+    amp, wid, cx, cy = p.meta["bumps"]
+    rng = np.random.default_rng(seed + 7)
+    xi = rng.uniform(-1.0, 1.0, len(amp))
+    X, Y = p.centres()
+    z_obs = gaussian_bumps(X, Y, amp * (1.0 + 0.05 * xi), wid, cx, cy)
+    wet = np.flatnonzero(p.U0[0] > 0.05)
+    gauges = np.sort(rng.choice(wet, size=n_gauges, replace=False))
+    return p, z_obs, gauges
