@@ -216,6 +216,38 @@ SWNMG_API swnmg_status swnmg_residual_noalloc(const swnmg_problem* prob, const s
                                               double* R_dev, double* rnorm_dev, double* l1_dev,
                                               void* stream);
 
+/* Discrete adjoint of the steady state (an extension; the paper solves the
+ * forward problem only).  At a steady state U* (R(U*, z, q) = 0) and for a
+ * loss L(U*, z, q) with gradient g = dL/dU, the implicit function theorem
+ * gives dL/dz = (direct part) - lambda^T dR/dz and dL/dq = -lambda^T dR/dq,
+ * where lambda solves J^T lambda = g and J is the regularised
+ * finite-difference Jacobian of eq. NewtonREG at U* (the alpha||R_i||_1 term
+ * vanishes at a steady state).  lambda is found by Algorithm 0 applied to
+ * J^T: the transposed Galerkin hierarchy (P^T J^T P = (P^T J P)^T, eq.
+ * ProjectAR) with block SGS on J^T, in FP64 whatever the precision of ctx.
+ *
+ *   U_dev     (ncomp*n) the steady state, usually the output of swnmg_solve
+ *   g_dev     (ncomp*n) dL/dU
+ *   lam_dev   (ncomp*n) out: lambda, cycles started from lambda = 0
+ *   dRz_dev   (n) out: lambda^T dR/dz, one value per cell bed
+ *   dRq_host  (4 doubles, nullable) out: lambda^T dR/dq of each side's
+ *             prescribed discharge (sides W, E, S, N; 0 unless the side is
+ *             SWNMG_BC_INFLOW_DISCHARGE)
+ *   max_cycles cycles of Algorithm 0 at most (>= 1)
+ *   rtol      > 0: stop once sum_i ||(g - J^T lambda)_i||_1 <= rtol *
+ *             sum_i ||g_i||_1 (checked after every cycle);
+ *             <= 0: run exactly max_cycles cycles
+ *   cycles_out (nullable) cycles run
+ * dR/dz and dR/dq are central differences with step 1e-6 of the edge terms
+ * of eq. Res.  The FP64 transposed hierarchy is allocated on the first call
+ * and kept in ctx; the forward operators of swnmg_jacobian are left
+ * untouched.  Returns SWNMG_ERR_NOT_CONVERGED (with the outputs written) if
+ * rtol > 0 is not met within max_cycles, SWNMG_ERR_NONFINITE if the linear
+ * residual is not finite.  Synchronises the stream. */
+SWNMG_API swnmg_status swnmg_adjoint(swnmg_ctx* ctx, const double* U_dev, const double* g_dev,
+                                     double* lam_dev, double* dRz_dev, double* dRq_host,
+                                     int32_t max_cycles, double rtol, int32_t* cycles_out);
+
 /* Number of cells of level l (0 if l is out of range). */
 SWNMG_API int64_t swnmg_level_cells(const swnmg_ctx* ctx, int32_t level);
 

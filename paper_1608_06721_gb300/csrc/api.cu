@@ -42,6 +42,17 @@ const char* status_text(swnmg_status s) {
 
 char g_err[512] = "";
 
+// A multigrid operator hierarchy (the Jacobian's, or its transpose's)
+struct Hier {
+  Level* lv;
+  int nl, fp32;
+  bool coarse_exact, coarse_inverse;
+  void* cinv;
+  void* caug;
+  int* csing;
+  double* band;
+};
+
 }  // namespace
 
 void swnmg::set_static_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
@@ -67,6 +78,16 @@ struct swnmg_ctx {
   double* hbuf = nullptr;   // pinned host scalars
   bool coarse_exact = false;
   bool coarse_inverse = false;   // exact coarse solve through X = A^-1 (guarded)
+  // transposed (adjoint) operator hierarchy, FP64, allocated on first use
+  bool adj_ready = false;
+  Level alv[13];
+  void* acinv = nullptr;
+  void* acaug = nullptr;
+  int* acsing = nullptr;
+  double* aband = nullptr;
+  double* adj_A = nullptr;   // FP64 Jacobian at U* before transposition
+  double* adj_cz = nullptr;      // per-edge z contributions (2 per edge)
+  double* adj_cell = nullptr;    // per-cell scratch (n)
   // per-class kernel timing: event pairs resolved at synchronisation points
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -80,6 +101,14 @@ struct swnmg_ctx {
 };
 
 namespace {
+
+Hier fwd_hier(swnmg_ctx* c) {
+  return Hier{c->lv, c->nl, c->fp32, c->coarse_exact, c->coarse_inverse, c->cinv, c->caug, c->csing, c->band};
+}
+
+Hier adj_hier(swnmg_ctx* c) {
+  return Hier{c->alv, c->nl, 0, c->coarse_exact, c->coarse_inverse, c->acinv, c->acaug, c->acsing, c->aband};
+}
 
 swnmg_status fail(swnmg_ctx* c, swnmg_status s, const std::string& msg) {
   std::string m = std::string(status_text(s)) + ": " + msg;
@@ -203,10 +232,10 @@ swnmg_status level_residual_sum(swnmg_ctx* c, int l, const double* U, double* ou
   return device_sum(c, c->rn, L.n, out);
 }
 
-void sgs_half(swnmg_ctx* c, int l, int forward) {
-  Level& v = c->lv[l];
+void sgs_half(swnmg_ctx* c, const Hier& H, int l, int forward) {
+  Level& v = H.lv[l];
   TimedScope ts(c, l == 0 ? SWNMG_T_SGS_FINE : SWNMG_T_SGS_COARSE, v.n);
-  launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward, c->fp32, c->sgs_sync,
+  launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward, H.fp32, c->sgs_sync,
                    c->sticky, c->st);
 }
 
@@ -216,59 +245,74 @@ void blusgs_half(swnmg_ctx* c, int l, double* U, int forward) {
   launch_blusgs_sweep(L, c->lv[l].z, U, forward, c->sgs_sync, c->sticky, c->st);
 }
 
-// Algorithm 0 on level l with lv[l].b, lv[l].x
-swnmg_status coarse_solve(swnmg_ctx* c, int l) {
-  Level& v = c->lv[l];
-  if (c->coarse_inverse) {
+// Algorithm 0 on level l of hierarchy H (lv[l].b, lv[l].x)
+swnmg_status coarse_solve(swnmg_ctx* c, const Hier& H, int l) {
+  Level& v = H.lv[l];
+  if (H.coarse_inverse) {
     TimedScope ts(c, SWNMG_T_COARSE_EXACT);
-    launch_coarse_apply(c->nc, v.n, c->cinv, v.b, v.x, c->fp32, c->st);
+    launch_coarse_apply(c->nc, v.n, H.cinv, v.b, v.x, H.fp32, c->st);
     LAUNCH_CHECK(c);
     return SWNMG_OK;
   }
-  if (c->coarse_exact) {
+  if (H.coarse_exact) {
     TimedScope ts(c, SWNMG_T_COARSE_EXACT);
-    launch_coarse_exact(c->nc, v.nx, v.ny, v.blk, v.b, v.x, c->band, c->derr, c->fp32, c->st);
+    launch_coarse_exact(c->nc, v.nx, v.ny, v.blk, v.b, v.x, H.band, c->derr, H.fp32, c->st);
     LAUNCH_CHECK(c);
     return SWNMG_OK;
   }
   for (int k = 0; k < c->prm.coarse_sweeps; ++k) {
-    sgs_half(c, l, 1);
-    sgs_half(c, l, 0);
+    sgs_half(c, H, l, 1);
+    sgs_half(c, H, l, 0);
   }
   LAUNCH_CHECK(c);
   return SWNMG_OK;
 }
 
-swnmg_status smooth(swnmg_ctx* c, int l, int nsym) {
+swnmg_status smooth(swnmg_ctx* c, const Hier& H, int l, int nsym) {
   for (int k = 0; k < nsym; ++k) {
-    sgs_half(c, l, 1);
-    sgs_half(c, l, 0);
+    sgs_half(c, H, l, 1);
+    sgs_half(c, H, l, 0);
   }
   LAUNCH_CHECK(c);
   return SWNMG_OK;
 }
 
-swnmg_status mg_cycle(swnmg_ctx* c, int l) {
-  if (l == c->nl) return coarse_solve(c, l);
+swnmg_status mg_cycle(swnmg_ctx* c, const Hier& H, int l) {
+  if (l == H.nl) return coarse_solve(c, H, l);
   swnmg_status s;
-  if ((s = smooth(c, l, c->prm.nu1)) != SWNMG_OK) return s;
-  Level& v = c->lv[l];
-  Level& w = c->lv[l + 1];
+  if ((s = smooth(c, H, l, c->prm.nu1)) != SWNMG_OK) return s;
+  Level& v = H.lv[l];
+  Level& w = H.lv[l + 1];
   {
     TimedScope ts(c, SWNMG_T_TRANSFER);
-    launch_restrict(c->prob.dim, c->nc, v.nx, v.ny, v.blk, v.b, v.x, w.b, c->fp32, c->st);
-    launch_fill(w.x, c->fp32, (long long)c->nc * w.n, c->st);
+    launch_restrict(c->prob.dim, c->nc, v.nx, v.ny, v.blk, v.b, v.x, w.b, H.fp32, c->st);
+    launch_fill(w.x, H.fp32, (long long)c->nc * w.n, c->st);
   }
   LAUNCH_CHECK(c);
   const int gam = (l == 0) ? 1 : c->prm.gamma;
   for (int k = 0; k < gam; ++k)
-    if ((s = mg_cycle(c, l + 1)) != SWNMG_OK) return s;
+    if ((s = mg_cycle(c, H, l + 1)) != SWNMG_OK) return s;
   {
     TimedScope ts(c, SWNMG_T_TRANSFER);
-    launch_prolong(c->prob.dim, c->nc, v.nx, v.ny, w.x, v.x, c->fp32, c->st);
+    launch_prolong(c->prob.dim, c->nc, v.nx, v.ny, w.x, v.x, H.fp32, c->st);
   }
   LAUNCH_CHECK(c);
-  return smooth(c, l, c->prm.nu2);
+  return smooth(c, H, l, c->prm.nu2);
+}
+
+// Galerkin coarse operators, block LU factors and the coarse inverse of H
+// from its level-0 blocks
+void build_hier(swnmg_ctx* c, const Hier& H) {
+  TimedScope ts(c, SWNMG_T_GALERKIN);
+  for (int l = 0; l < H.nl; ++l)
+    launch_galerkin(c->prob.dim, c->nc, H.lv[l].nx, H.lv[l].ny, H.lv[l].blk, H.lv[l + 1].blk, H.fp32,
+                    c->st);
+  for (int l = 0; l <= H.nl; ++l)
+    launch_lu_factor(H.lv[l].nx, H.lv[l].ny, c->nc, H.lv[l].blk, H.lv[l].lu, H.lv[l].piv, H.fp32, c->st);
+  if (H.coarse_inverse) {
+    const Level& vc = H.lv[H.nl];
+    launch_coarse_inverse(c->nc, vc.nx, vc.ny, vc.blk, H.caug, H.cinv, H.csing, H.fp32, c->st);
+  }
 }
 
 swnmg_status assemble(swnmg_ctx* c, const double* U) {
@@ -278,22 +322,26 @@ swnmg_status assemble(swnmg_ctx* c, const double* U) {
     launch_jacobian(L, c->lv[0].z, U, c->R, c->rn, c->eb, c->lv[0].blk, c->fp32, c->st);
   }
   LAUNCH_CHECK(c);
-  TimedScope ts(c, SWNMG_T_GALERKIN);
-  for (int l = 0; l < c->nl; ++l)
-    launch_galerkin(c->prob.dim, c->nc, c->lv[l].nx, c->lv[l].ny, c->lv[l].blk, c->lv[l + 1].blk,
-                    c->fp32, c->st);
-  for (int l = 0; l <= c->nl; ++l)
-    launch_lu_factor(c->lv[l].nx, c->lv[l].ny, c->nc, c->lv[l].blk, c->lv[l].lu, c->lv[l].piv, c->fp32,
-                     c->st);
-  if (c->coarse_inverse) {
-    const Level& vc = c->lv[c->nl];
-    launch_coarse_inverse(c->nc, vc.nx, vc.ny, vc.blk, c->caug, c->cinv, c->csing, c->fp32, c->st);
-  }
+  build_hier(c, fwd_hier(c));
   LAUNCH_CHECK(c);
   return SWNMG_OK;
 }
 
 void free_ctx(swnmg_ctx* c) {
+  for (auto& v : c->alv) {
+    if (v.blk) cudaFree(v.blk);
+    if (v.lu) cudaFree(v.lu);
+    if (v.piv) cudaFree(v.piv);
+    if (v.b) cudaFree(v.b);
+    if (v.x) cudaFree(v.x);
+  }
+  if (c->acinv) cudaFree(c->acinv);
+  if (c->acaug) cudaFree(c->acaug);
+  if (c->acsing) cudaFree(c->acsing);
+  if (c->aband) cudaFree(c->aband);
+  if (c->adj_cz) cudaFree(c->adj_cz);
+  if (c->adj_A) cudaFree(c->adj_A);
+  if (c->adj_cell) cudaFree(c->adj_cell);
   for (auto& v : c->lv) {
     if (v.z) cudaFree(v.z);
     if (v.U) cudaFree(v.U);
@@ -541,8 +589,9 @@ SWNMG_API swnmg_status swnmg_vcycle(swnmg_ctx* c, const double* rhs, double* dU,
   launch_convert(rhs, 0, v.b, c->fp32, m, 1.0, c->st);
   launch_convert(dU, 0, v.x, c->fp32, m, 1.0, c->st);
   LAUNCH_CHECK(c);
+  const Hier H = fwd_hier(c);
   for (int k = 0; k < ncycles; ++k) {
-    swnmg_status s = mg_cycle(c, 0);
+    swnmg_status s = mg_cycle(c, H, 0);
     if (s != SWNMG_OK) return s;
   }
   launch_convert(v.x, c->fp32, dU, 0, m, 1.0, c->st);
@@ -637,7 +686,7 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
     launch_fill(v0.x, c->fp32, m, c->st);
     LAUNCH_CHECK(c);
     for (int k = 0; k < c->prm.n_mg; ++k)                          // Step 2.2
-      if ((s = mg_cycle(c, 0)) != SWNMG_OK) return s;
+      if ((s = mg_cycle(c, fwd_hier(c), 0)) != SWNMG_OK) return s;
     {
       TimedScope ts(c, SWNMG_T_UPDATE);                            // Step 2.3
       launch_newton_update(v0.n, nc, c->prm.tau, c->prm.h_eps, U, v0.x, c->fp32, c->st);
@@ -660,6 +709,136 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
   st->ms_step1 = std::chrono::duration<double, std::milli>(t1 - t0).count();
   st->ms_newton = std::chrono::duration<double, std::milli>(t2 - t1).count();
   if (status != SWNMG_OK) return fail(c, status, "after " + std::to_string(it) + " Newton steps");
+  return SWNMG_OK;
+}
+
+namespace {
+
+// FP64 transposed hierarchy and adjoint scratch, allocated on first use
+swnmg_status adjoint_alloc(swnmg_ctx* c) {
+  if (c->adj_ready) return SWNMG_OK;
+  const int nc = c->nc, bs = nc * nc;
+#define AALLOC(ptr, bytes)                                                                   \
+  do {                                                                                       \
+    cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                                    \
+    if (e_ != cudaSuccess) return fail(c, SWNMG_ERR_OOM, std::string("adjoint cudaMalloc ") + \
+                                                              cudaGetErrorString(e_));       \
+  } while (0)
+  for (int l = 0; l <= c->nl; ++l) {
+    const Level& f = c->lv[l];
+    Level& v = c->alv[l];
+    v.nx = f.nx;
+    v.ny = f.ny;
+    v.n = f.n;
+    v.ex = f.ex;
+    v.ey = f.ey;
+    const size_t P = (size_t)skew_slots(v.nx, v.ny);
+    if (!v.blk) AALLOC(v.blk, P * 5 * bs * sizeof(double));
+    if (!v.lu) AALLOC(v.lu, P * LU_E * sizeof(double));
+    if (!v.piv) AALLOC(v.piv, P);
+    if (!v.b) AALLOC(v.b, (size_t)v.n * nc * sizeof(double));
+    if (!v.x) AALLOC(v.x, (size_t)v.n * nc * sizeof(double));
+    CUDA_TRY(c, cudaMemset(v.blk, 0, P * 5 * bs * sizeof(double)));
+    CUDA_TRY(c, cudaMemset(v.lu, 0, P * LU_E * sizeof(double)));
+    CUDA_TRY(c, cudaMemset(v.piv, 0, P));
+  }
+  const Level& v0 = c->lv[0];
+  const size_t P0 = (size_t)skew_slots(v0.nx, v0.ny);
+  if (!c->adj_A) AALLOC(c->adj_A, P0 * 5 * bs * sizeof(double));
+  CUDA_TRY(c, cudaMemset(c->adj_A, 0, P0 * 5 * bs * sizeof(double)));
+  const size_t n_e = (size_t)(v0.nx + 1) * v0.ny + (c->prob.dim == 2 ? (size_t)v0.nx * (v0.ny + 1) : 0);
+  if (!c->adj_cz) AALLOC(c->adj_cz, 2 * n_e * sizeof(double));
+  if (!c->adj_cell) AALLOC(c->adj_cell, (size_t)v0.n * sizeof(double));
+  const Level& vc = c->lv[c->nl];
+  const long long mc = (long long)vc.n * nc;
+  if (c->coarse_inverse) {
+    if (!c->acinv) AALLOC(c->acinv, (size_t)(mc * mc) * sizeof(double));
+    if (!c->acaug) AALLOC(c->acaug, (size_t)(2 * mc * mc) * sizeof(double));
+    if (!c->acsing) AALLOC(c->acsing, (size_t)mc * sizeof(int));
+  } else if (c->coarse_exact) {
+    const long long ml = nc * (vc.ny > 1 ? vc.nx : 1) + nc - 1;
+    const long long words = mc * (3 * ml + 1) + 2 * mc;
+    if (!c->aband) AALLOC(c->aband, (size_t)words * sizeof(double));
+  }
+#undef AALLOC
+  c->adj_ready = true;
+  return SWNMG_OK;
+}
+
+}  // namespace
+
+SWNMG_API swnmg_status swnmg_adjoint(swnmg_ctx* c, const double* U, const double* g, double* lam,
+                                     double* dRz, double* dRq_host, int32_t max_cycles, double rtol,
+                                     int32_t* cycles_out) {
+  if (!c || !U || !g || !lam || !dRz || max_cycles < 1) return fail(c, SWNMG_ERR_ARG, "bad argument");
+  if (!(rtol == rtol)) return fail(c, SWNMG_ERR_ARG, "rtol is NaN");
+  if (cycles_out) *cycles_out = 0;
+  swnmg_status s = adjoint_alloc(c);
+  if (s != SWNMG_OK) return s;
+  const int nc = c->nc;
+  const DevLevel L = dev_level(c, 0);
+  Level& a0 = c->alv[0];
+  const long long m = (long long)a0.n * nc;
+  // J at U* in FP64, then J^T in the strip-skewed layout and its hierarchy
+  {
+    TimedScope ts(c, SWNMG_T_JACOBIAN, L.n);
+    launch_jacobian(L, c->lv[0].z, U, c->R, c->rn, c->eb, c->adj_A, 0, c->st);
+    launch_transpose_blocks(nc, a0.nx, a0.ny, c->adj_A, 0, (double*)a0.blk, c->st);
+  }
+  LAUNCH_CHECK(c);
+  const Hier H = adj_hier(c);
+  build_hier(c, H);
+  LAUNCH_CHECK(c);
+  launch_convert(g, 0, a0.b, 0, m, 1.0, c->st);
+  launch_fill(a0.x, 0, m, c->st);
+  LAUNCH_CHECK(c);
+  double gnorm = 0.0, rnorm = 0.0;
+  if (rtol > 0) {
+    launch_abs_cells(a0.n, nc, g, c->adj_cell, c->st);
+    LAUNCH_CHECK(c);
+    if ((s = device_sum(c, c->adj_cell, a0.n, &gnorm)) != SWNMG_OK) return s;
+    if (!std::isfinite(gnorm)) return fail(c, SWNMG_ERR_NONFINITE, "adjoint: g is not finite");
+  }
+  int k = 0;
+  swnmg_status status = SWNMG_OK;
+  while (k < max_cycles) {
+    if ((s = mg_cycle(c, H, 0)) != SWNMG_OK) return s;
+    ++k;
+    if (rtol > 0) {
+      if ((s = check_sticky(c)) != SWNMG_OK) return s;
+      launch_lin_resid_abs(c->prob.dim, nc, a0.nx, a0.ny, a0.blk, a0.b, a0.x, 0, c->adj_cell, c->st);
+      LAUNCH_CHECK(c);
+      if ((s = device_sum(c, c->adj_cell, a0.n, &rnorm)) != SWNMG_OK) return s;
+      if (!std::isfinite(rnorm)) { status = SWNMG_ERR_NONFINITE; break; }
+      if (rnorm <= rtol * gnorm) break;
+      if (k == max_cycles) status = SWNMG_ERR_NOT_CONVERGED;
+    }
+  }
+  if (cycles_out) *cycles_out = k;
+  if ((s = check_sticky(c)) != SWNMG_OK) return s;
+  launch_convert(a0.x, 0, lam, 0, m, 1.0, c->st);
+  // lambda^T dR/dz and lambda^T dR/dq (central differences of the edge terms)
+  const double delta = 1e-6;
+  launch_adjoint_z(L, c->lv[0].z, U, lam, delta, c->adj_cz, dRz, c->st);
+  LAUNCH_CHECK(c);
+  if (dRq_host) {
+    const int nsides = c->prob.dim == 2 ? 4 : 2;
+    for (int side = 0; side < 4; ++side) {
+      dRq_host[side] = 0.0;
+      if (side >= nsides || c->prob.bc[side].kind != SWNMG_BC_INFLOW_DISCHARGE) continue;
+      launch_adjoint_q(L, side, c->lv[0].z, U, lam, delta, c->adj_cell, c->st);
+      LAUNCH_CHECK(c);
+      if ((s = device_sum(c, c->adj_cell, L.n, &dRq_host[side])) != SWNMG_OK) return s;
+    }
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  if (status != SWNMG_OK)
+  {
+    char msg[160];
+    snprintf(msg, sizeof msg, "adjoint: after %d cycles sum ||g - J^T lambda||_1 = %.3e, sum ||g||_1 = %.3e", k,
+             rnorm, gnorm);
+    return fail(c, status, msg);
+  }
   return SWNMG_OK;
 }
 

@@ -71,6 +71,10 @@ void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forw
                          int* sticky_err, cudaStream_t st);
 void launch_newton_update(int n, int nc, double tau, double h_eps, double* U, const void* dU,
                           int dU_fp32, cudaStream_t st);
+void launch_adjoint_z(const DevLevel& L, const double* z, const double* U, const double* lam, double delta,
+                      double* cz, double* dRz, cudaStream_t st);
+void launch_adjoint_q(const DevLevel& L, int side, const double* z, const double* U, const double* lam,
+                      double delta, double* out, cudaStream_t st);
 void launch_average(int dim, int nxf, int nyf, int ncomp, const double* vf, double* vc,
                     cudaStream_t st);
 void launch_inject(int dim, int nxf, int nyf, int ncomp, const double* vc, double* vf,
@@ -95,6 +99,11 @@ void launch_coarse_inverse(int nc, int nx, int ny, const void* blk, void* aug, v
 void launch_coarse_apply(int nc, int n, const void* X, const void* b, void* x, int fp32,
                          cudaStream_t st);
 void launch_sum(const double* v, int n, double* partial, double* out, cudaStream_t st);
+void launch_transpose_blocks(int nc, int nx, int ny, const void* src, int src_fp32, double* dst,
+                             cudaStream_t st);
+void launch_lin_resid_abs(int dim, int nc, int nx, int ny, const void* blk, const void* b, const void* x,
+                          int fp32, double* out, cudaStream_t st);
+void launch_abs_cells(int n, int nc, const double* v, double* out, cudaStream_t st);
 void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n,
                     double scale, cudaStream_t st);
 void launch_fill(void* dst, int fp32, long long n, cudaStream_t st);

@@ -618,6 +618,92 @@ __global__ void __launch_bounds__(128) k_blusgs_sweep(DevLevel L, const double* 
   }
 }
 
+// ---- adjoint: lambda^T dR/dz and lambda^T dR/dq --------------------------------
+// Central differences (step delta) of the edge terms with respect to the bed of
+// either cell, contracted with lambda of both cells: cz[e] for the left cell's
+// bed, cz[n_e + e] for the right cell's.  A boundary ghost's bed is the
+// interior bed, so it moves with it.
+template <int NC>
+__global__ void k_adj_z_edges(DevLevel L, const double* __restrict__ z, const double* __restrict__ U,
+                              const double* __restrict__ lam, double delta, double* __restrict__ cz,
+                              int n_xe, int n_e) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_e) return;
+  int axis, iL, iR;
+  double len;
+  edge_cells(L, e, n_xe, axis, iL, iR, len);
+  double cL[NC], cR[NC], lL[NC], lR[NC];
+  if (iL >= 0) { load_c<NC>(U, L.n, iL, cL); load_c<NC>(lam, L.n, iL, lL); }
+  if (iR >= 0) { load_c<NC>(U, L.n, iR, cR); load_c<NC>(lam, L.n, iR, lR); }
+  const double zL = iL >= 0 ? z[iL] : 0.0, zR = iR >= 0 ? z[iR] : 0.0;
+  const double* pL = iL >= 0 ? cL : nullptr;
+  const double* pR = iR >= 0 ? cR : nullptr;
+  const double r2d = 1.0 / (2.0 * delta);
+  for (int which = 0; which < 2; ++which) {
+    const int cell = which == 0 ? iL : iR;
+    double acc = 0.0;
+    if (cell >= 0) {
+      double GLp[NC], GRp[NC], GLm[NC], GRm[NC];
+      if (which == 0) {
+        eval_edge_states<NC>(L, axis, pL, zL + delta, pR, zR, GLp, GRp);
+        eval_edge_states<NC>(L, axis, pL, zL - delta, pR, zR, GLm, GRm);
+      } else {
+        eval_edge_states<NC>(L, axis, pL, zL, pR, zR + delta, GLp, GRp);
+        eval_edge_states<NC>(L, axis, pL, zL, pR, zR - delta, GLm, GRm);
+      }
+      for (int s = 0; s < NC; ++s) {
+        if (iL >= 0) acc += lL[s] * (len * ((GLp[s] - GLm[s]) * r2d));
+        if (iR >= 0) acc += lR[s] * (len * ((GRp[s] - GRm[s]) * r2d));
+      }
+    }
+    cz[(long long)which * n_e + e] = acc;
+  }
+}
+
+__global__ void k_adj_z_cells(DevLevel L, const double* __restrict__ cz, double* __restrict__ dRz, int n_xe,
+                              int n_e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  int eW, eE, eS, eN;
+  cell_edges(L, i, n_xe, eW, eE, eS, eN);
+  double a = cz[(long long)n_e + eW] + cz[eE];
+  if (L.dim == 2) a = a + cz[(long long)n_e + eS] + cz[eN];
+  dRz[i] = a;
+}
+
+// per boundary cell of `side`: lambda . |e| (G(q + delta) - G(q - delta)) / (2 delta)
+template <int NC>
+__global__ void k_adj_q_cells(DevLevel Lp, DevLevel Lm, int side, const double* __restrict__ z,
+                              const double* __restrict__ U, const double* __restrict__ lam, double delta,
+                              double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Lp.n) return;
+  const int ix = i % Lp.nx, iy = i / Lp.nx;
+  const bool on = (side == 0 && ix == 0) || (side == 1 && ix == Lp.nx - 1) ||
+                  (side == 2 && iy == 0) || (side == 3 && iy == Lp.ny - 1);
+  double acc = 0.0;
+  if (on) {
+    const int axis = side >> 1, upper = side & 1;
+    const double len = axis == 0 ? Lp.ex : Lp.ey;
+    double c[NC], l[NC], GLp[NC], GRp[NC], GLm[NC], GRm[NC];
+    load_c<NC>(U, Lp.n, i, c);
+    load_c<NC>(lam, Lp.n, i, l);
+    if (upper) {
+      eval_edge_states<NC>(Lp, axis, c, z[i], nullptr, 0.0, GLp, GRp);
+      eval_edge_states<NC>(Lm, axis, c, z[i], nullptr, 0.0, GLm, GRm);
+    } else {
+      eval_edge_states<NC>(Lp, axis, nullptr, 0.0, c, z[i], GLp, GRp);
+      eval_edge_states<NC>(Lm, axis, nullptr, 0.0, c, z[i], GLm, GRm);
+    }
+    const double r2d = 1.0 / (2.0 * delta);
+    for (int s = 0; s < NC; ++s) {
+      const double gp = upper ? GLp[s] : GRp[s], gm = upper ? GLm[s] : GRm[s];
+      acc += l[s] * (len * ((gp - gm) * r2d));
+    }
+  }
+  out[i] = acc;
+}
+
 // U += tau dU with the dry rules of Remark 2.5 (eq. NewtonREG-12)
 template <typename T>
 __global__ void k_newton_update(int n, int nc, double tau, double h_eps, double* __restrict__ U,
@@ -744,6 +830,26 @@ void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forw
     cudaLaunchCooperativeKernel((const void*)k_blusgs_sweep<3, 4, 16>, dim3(nsm), dim3(128), args, 0, st);
   else
     cudaLaunchCooperativeKernel((const void*)k_blusgs_sweep<2, 2, 8>, dim3(nsm), dim3(128), args, 0, st);
+}
+
+void launch_adjoint_z(const DevLevel& L, const double* z, const double* U, const double* lam, double delta,
+                      double* cz, double* dRz, cudaStream_t st) {
+  count_launches(2);
+  int n_xe, n_e;
+  edge_counts(L, n_xe, n_e);
+  if (L.nc == 3) k_adj_z_edges<3><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, lam, delta, cz, n_xe, n_e);
+  else k_adj_z_edges<2><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, lam, delta, cz, n_xe, n_e);
+  k_adj_z_cells<<<nblk(L.n, 256), 256, 0, st>>>(L, cz, dRz, n_xe, n_e);
+}
+
+void launch_adjoint_q(const DevLevel& L, int side, const double* z, const double* U, const double* lam,
+                      double delta, double* out, cudaStream_t st) {
+  count_launches(1);
+  DevLevel Lp = L, Lm = L;
+  Lp.bc[side].q = L.bc[side].q + delta;
+  Lm.bc[side].q = L.bc[side].q - delta;
+  if (L.nc == 3) k_adj_q_cells<3><<<nblk(L.n, 128), 128, 0, st>>>(Lp, Lm, side, z, U, lam, delta, out);
+  else k_adj_q_cells<2><<<nblk(L.n, 128), 128, 0, st>>>(Lp, Lm, side, z, U, lam, delta, out);
 }
 
 void launch_newton_update(int n, int nc, double tau, double h_eps, double* U, const void* dU,

@@ -702,6 +702,55 @@ __global__ void k_coarse_apply(int n, const T* __restrict__ X, const T* __restri
   x[(long long)(u % NC) * n + u / NC] = acc;
 }
 
+// ---- adjoint support ----------------------------------------------------------
+// Transposed block operator (FP64): D'_i = D_i^T, and the block of cell i
+// towards neighbour j is the transpose of j's block towards i.
+template <int NC, typename T>
+__global__ void k_transpose_blocks(int nx, int ny, const T* __restrict__ src, double* __restrict__ dst) {
+  const int n = nx * ny;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long P = skew_slots(nx, ny);
+  const int BS = NC * NC;
+  const int ix = i % nx, iy = i / nx;
+  const long long si = skew_pos(ix, iy, nx);
+  for (int s = 0; s < NC; ++s)
+    for (int k = 0; k < NC; ++k) dst[(long long)(s * NC + k) * P + si] = (double)src[(long long)(k * NC + s) * P + si];
+  const int nb[4] = {ix > 0 ? i - 1 : -1, ix < nx - 1 ? i + 1 : -1, iy > 0 ? i - nx : -1,
+                     iy < ny - 1 ? i + nx : -1};
+  for (int side = 0; side < 4; ++side) {
+    const int j = nb[side];
+    const long long sj = j >= 0 ? skew_pos(j % nx, j / nx, nx) : 0;
+    const int back = side ^ 1;   // j's side facing i
+    for (int s = 0; s < NC; ++s)
+      for (int k = 0; k < NC; ++k)
+        dst[((long long)(1 + side) * BS + s * NC + k) * P + si] =
+            j >= 0 ? (double)src[((long long)(1 + back) * BS + k * NC + s) * P + sj] : 0.0;
+  }
+}
+
+// ||b - A x||_1 per cell
+template <int NC, typename T>
+__global__ void k_lin_resid_abs(int dim, int nx, int ny, const T* __restrict__ blk, const T* __restrict__ b,
+                                const T* __restrict__ x, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx * ny) return;
+  T r[NC];
+  lin_resid<NC, T>(dim, nx, ny, blk, b, x, i, r);
+  double a = 0.0;
+  for (int s = 0; s < NC; ++s) a += fabs((double)r[s]);
+  out[i] = a;
+}
+
+// sum_s |v_s| per cell (SoA, nc components)
+__global__ void k_abs_cells(int n, int nc, const double* __restrict__ v, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = 0.0;
+  for (int s = 0; s < nc; ++s) a += fabs(v[(long long)s * n + i]);
+  out[i] = a;
+}
+
 // fixed-order sum: per-block tree partials, then one block over the partials
 __global__ void k_sum_partial(const double* __restrict__ v, int n, double* __restrict__ part) {
   __shared__ double sh[256];
@@ -866,6 +915,31 @@ void launch_coarse_apply(int nc, int n, const void* X, const void* b, void* x, i
   if (nc == 3) { if (fp32) CA(3, float); else CA(3, double); }
   else { if (fp32) CA(2, float); else CA(2, double); }
 #undef CA
+}
+
+void launch_transpose_blocks(int nc, int nx, int ny, const void* src, int src_fp32, double* dst,
+                             cudaStream_t st) {
+  count_launches(1);
+  const int g = nblk(nx * ny, 128);
+#define TB(NC, T) k_transpose_blocks<NC, T><<<g, 128, 0, st>>>(nx, ny, (const T*)src, dst)
+  if (nc == 3) { if (src_fp32) TB(3, float); else TB(3, double); }
+  else { if (src_fp32) TB(2, float); else TB(2, double); }
+#undef TB
+}
+
+void launch_lin_resid_abs(int dim, int nc, int nx, int ny, const void* blk, const void* b, const void* x,
+                          int fp32, double* out, cudaStream_t st) {
+  count_launches(1);
+  const int g = nblk(nx * ny, 128);
+#define LR(NC, T) k_lin_resid_abs<NC, T><<<g, 128, 0, st>>>(dim, nx, ny, (const T*)blk, (const T*)b, (const T*)x, out)
+  if (nc == 3) { if (fp32) LR(3, float); else LR(3, double); }
+  else { if (fp32) LR(2, float); else LR(2, double); }
+#undef LR
+}
+
+void launch_abs_cells(int n, int nc, const double* v, double* out, cudaStream_t st) {
+  count_launches(1);
+  k_abs_cells<<<nblk(n, 256), 256, 0, st>>>(n, nc, v, out);
 }
 
 void launch_sum(const double* v, int n, double* partial, double* out, cudaStream_t st) {

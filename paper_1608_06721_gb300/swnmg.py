@@ -7,6 +7,7 @@ CUDA device is missing, the constructor raises.
 from __future__ import annotations
 
 import ctypes as C
+import dataclasses
 import os
 
 import numpy as np
@@ -78,12 +79,13 @@ def lib():
         L.swnmg_get_timing.argtypes = [vp, dp, C.POINTER(C.c_int64), dp]
         L.swnmg_residual_noalloc.argtypes = [C.POINTER(Problem), C.POINTER(Params), vp, vp, vp, vp, vp, vp]
         L.swnmg_residual_noalloc.restype = C.c_int
+        L.swnmg_adjoint.argtypes = [vp, vp, vp, vp, vp, dp, C.c_int32, C.c_double, C.POINTER(C.c_int32)]
         L.swnmg_level_cells.argtypes = [vp, C.c_int32]
         L.swnmg_level_cells.restype = C.c_int64
         for f in ("swnmg_default_params", "swnmg_create", "swnmg_destroy", "swnmg_set_params",
                   "swnmg_residual", "swnmg_jacobian", "swnmg_get_blocks", "swnmg_vcycle",
                   "swnmg_sgs_sweep", "swnmg_blusgs", "swnmg_solve", "swnmg_set_timing",
-                  "swnmg_get_timing"):
+                  "swnmg_get_timing", "swnmg_adjoint"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -228,6 +230,65 @@ class Solver:
                 "init_res": st.init_res, "final_res": st.final_res,
                 "res_hist": list(st.res_hist)[:min(st.n_newton, HIST)],
                 "ms_step1": st.ms_step1, "ms_newton": st.ms_newton}
+
+    def adjoint(self, U, g, max_cycles=100, rtol=1e-12, check=True):
+        """swnmg_adjoint: lambda with J(U)^T lambda = g by multigrid cycles on the
+        transposed hierarchy, lambda^T dR/dz (n) and lambda^T dR/dq (4 sides).
+        Returns (lam, dRz, dRq, cycles)."""
+        n = self.level_cells(0)
+        lam = torch.empty((self.nc, n), dtype=torch.float64, device="cuda")
+        dRz = torch.empty(n, dtype=torch.float64, device="cuda")
+        dRq = (C.c_double * 4)()
+        cyc = C.c_int32(0)
+        rc = self.L.swnmg_adjoint(self.h, _ptr(U), _ptr(g), _ptr(lam), _ptr(dRz), dRq, max_cycles,
+                                  rtol, C.byref(cyc))
+        if check or rc != ERR_NOT_CONVERGED:
+            self._check(rc)
+        return lam, dRz, np.array(list(dRq)), cyc.value
+
+
+def with_discharge(prob: W.Problem, q) -> W.Problem:
+    """prob with the prescribed discharge of side s replaced by q[s]."""
+    bc = [dataclasses.replace(b, q=float(q[k])) for k, b in enumerate(prob.bc)]
+    return dataclasses.replace(prob, bc=bc)
+
+
+class SteadySWE(torch.autograd.Function):
+    """U* = NMGM(z, q): Algorithm 1 run to its tolerance, with the discrete
+    adjoint (swnmg_adjoint) as the backward pass:
+        grad_z = -lambda^T dR/dz,  grad_q = -lambda^T dR/dq,  J^T lambda = grad_U.
+    z: (n,) float64 CUDA bed; q: (4,) float64 discharge per side (only
+    inflow-discharge sides carry a gradient); U0: initial state (ncomp, n)
+    for the solve.  The loss's own dependence on z (e.g. through h + z) is
+    added by autograd outside this function."""
+
+    @staticmethod
+    def forward(ctx, z, q, prob, params, U0, adj_cycles, adj_rtol):
+        qh = q.detach().cpu().numpy()
+        solver = Solver(with_discharge(prob, qh), params, z=z.detach().contiguous())
+        U = U0.detach().clone().contiguous()
+        solver.solve(U, check=True)
+        ctx.solver = solver
+        ctx.adj = (adj_cycles, adj_rtol)
+        ctx.q_meta = (q.device, q.dtype)
+        ctx.save_for_backward(U)
+        return U
+
+    @staticmethod
+    def backward(ctx, gU):
+        (U,) = ctx.saved_tensors
+        _, dRz, dRq, _ = ctx.solver.adjoint(U, gU.contiguous(), ctx.adj[0], ctx.adj[1])
+        gq = torch.as_tensor(-dRq, dtype=ctx.q_meta[1], device=ctx.q_meta[0])
+        return -dRz, gq, None, None, None, None, None
+
+
+def steady_state(z, q, prob: W.Problem, params: W.Params | None = None, U0=None, adj_cycles=400,
+                 adj_rtol=1e-10):
+    """Differentiable steady state: SteadySWE.apply with defaults."""
+    params = params or prob.params
+    if U0 is None:
+        U0 = torch.as_tensor(np.ascontiguousarray(prob.U0), dtype=torch.float64, device="cuda")
+    return SteadySWE.apply(z, q, prob, params, U0, adj_cycles, adj_rtol)
 
 
 def residual_noalloc(prob: W.Problem, z, U, R, rnorm=None, l1=None, params: W.Params | None = None,

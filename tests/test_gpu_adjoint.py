@@ -1,0 +1,232 @@
+"""GPU discrete adjoint (swnmg_adjoint and the SteadySWE autograd function)
+against the CPU oracle's adjoint and against central differences of re-solved
+steady states.  The paper solves the forward problem only; the adjoint is
+the implicit-function-theorem gradient of its steady state:
+    J^T lambda = dL/dU,   dL/dz = dL/dz|direct - lambda^T dR/dz,
+    dL/dq = -lambda^T dR/dq,
+with J the regularised finite-difference Jacobian of eq. NewtonREG.
+
+Bar: lambda within 1e-9 of the oracle's (relative to max |lambda|), the
+vector-Jacobian products within 1e-8 (they are central differences with the
+same step on both sides, evaluated in different summation orders); fixed
+cycle counts within 1e-10 (the forward cycles' bar is 1e-12 per cycle);
+gradients of the gauge loss within 1e-6 of the oracle's pipeline (relative to
+the gradient's maximum) and of central differences of re-solved steady
+states (relative to the larger of |difference quotient| and the gradient's
+maximum: cells far from the gauges have gradients below the quotient's
+noise).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.oracle import Oracle
+from paper_1608_06721_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def swnmg():
+    from paper_1608_06721_gb300 import swnmg as S
+    S.lib()
+    return S
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _cases():
+    """(name, problem, state seed, oracle cycles: 0 = dense exact solve)."""
+    return [
+        ("bump1d_200", W.subcritical_bump_1d(n=200), 11, 0),
+        ("smooth1d_256", W.smooth_subcritical_1d(n=256), 12, 0),
+        ("ex33_128", W.wetdry_lake_1d(128), 13, 0),
+        ("channel_32x16", W.channel_2d(nx=32, ny=16, n_levels=2, redraw=False).with_params(
+            gamma=2, coarse_sweeps=0), 14, 0),
+        ("channel_104x40", W.channel_2d(nx=104, ny=40, n_levels=3, redraw=False).with_params(
+            coarse_sweeps=0), 15, 80),
+        ("lake64_llf", W.lake_at_rest_2d(n=64, flux=W.FLUX_LLF), 16, 80),
+        ("channel_66x70", W.channel_2d(nx=66, ny=70, n_levels=1, redraw=False), 17, 80),
+    ]
+
+
+CASES = _cases()
+IDS = [c[0] for c in CASES]
+
+
+def _inputs(prob, seed):
+    U = W.random_state(prob, seed, wet_frac=0.7) if prob.dim == 2 else W.random_state(prob, seed)
+    g = np.random.default_rng(seed + 1000).standard_normal(U.shape)
+    return U, g
+
+
+@pytest.mark.parametrize("name,prob,seed,ocyc", CASES, ids=IDS)
+def test_adjoint_matches_oracle(swnmg, name, prob, seed, ocyc):
+    U, g = _inputs(prob, seed)
+    lam_o, dRz_o, dRq_o = Oracle(prob).adjoint(U, g, ncycles=ocyc)
+    S = swnmg.Solver(prob)
+    lam, dRz, dRq, cyc = S.adjoint(_dev(U), _dev(g), max_cycles=400, rtol=1e-14)
+    assert 1 <= cyc < 400
+    lam, dRz = lam.cpu().numpy(), dRz.cpu().numpy()
+    scale = np.abs(lam_o).max()
+    assert np.abs(lam - lam_o).max() <= 1e-9 * scale, np.abs(lam - lam_o).max() / scale
+    zs = max(np.abs(dRz_o).max(), 1e-300)
+    assert np.abs(dRz - dRz_o).max() <= 1e-8 * zs, np.abs(dRz - dRz_o).max() / zs
+    for s in range(4):
+        assert abs(dRq[s] - dRq_o[s]) <= 1e-8 * max(abs(dRq_o).max(), 1e-300), (s, dRq, dRq_o)
+        if s >= 2 * prob.dim or prob.bc[s].kind != W.BC_INFLOW_DISCHARGE:
+            assert dRq[s] == 0.0
+
+
+@pytest.mark.parametrize("name,prob,seed,ocyc", CASES[:5], ids=IDS[:5])
+def test_adjoint_fixed_cycles_match_oracle(swnmg, name, prob, seed, ocyc):
+    """rtol <= 0 runs exactly max_cycles cycles of Algorithm 0 on J^T from 0."""
+    U, g = _inputs(prob, seed)
+    for k in (1, 3):
+        lam_o, _, _ = Oracle(prob).adjoint(U, g, ncycles=k)
+        lam, _, _, cyc = swnmg.Solver(prob).adjoint(_dev(U), _dev(g), max_cycles=k, rtol=0.0)
+        assert cyc == k
+        lam = lam.cpu().numpy()
+        assert np.abs(lam - lam_o).max() <= 1e-10 * np.abs(lam_o).max()
+
+
+def test_adjoint_reports_unmet_tolerance_and_bad_args(swnmg):
+    prob = CASES[4][1]
+    U, g = _inputs(prob, 15)
+    S = swnmg.Solver(prob)
+    lam, dRz, dRq, cyc = S.adjoint(_dev(U), _dev(g), max_cycles=1, rtol=1e-30, check=False)
+    assert cyc == 1 and np.isfinite(lam.cpu().numpy()).all()
+    with pytest.raises(swnmg.SwnmgError) as e:
+        S.adjoint(_dev(U), _dev(g), max_cycles=1, rtol=1e-30)
+    assert e.value.status == swnmg.ERR_NOT_CONVERGED
+    with pytest.raises(swnmg.SwnmgError) as e:
+        S.adjoint(_dev(U), _dev(g), max_cycles=0)
+    assert e.value.status == swnmg.ERR_ARG
+    # the forward operators are left as they were
+    S.jacobian(_dev(U))
+    b0 = S.get_blocks(0)
+    S.adjoint(_dev(U), _dev(g), max_cycles=2, rtol=0.0)
+    assert np.array_equal(S.get_blocks(0), b0)
+
+
+def _loss(U0, z, gauges, eta):
+    return float(np.sum((U0[gauges] + z[gauges] - eta) ** 2))
+
+
+def _kink_free(p, U, gap, hmin=0.05, reach=2):
+    """Cells whose bed differs from every neighbour's by more than gap (so that
+    max(z_i, z_j) of the reconstruction is smooth within the step) and whose
+    (2 reach + 1)^2 neighbourhood is wet (h > hmin: no dry reset or wet/dry
+    switch moves with the step)."""
+    z = p.z.reshape(p.ny, p.nx)
+    ok = np.ones_like(z, dtype=bool)
+    dzx = np.abs(np.diff(z, axis=1)) <= gap
+    dzy = np.abs(np.diff(z, axis=0)) <= gap
+    ok[:, :-1] &= ~dzx
+    ok[:, 1:] &= ~dzx
+    ok[:-1, :] &= ~dzy
+    ok[1:, :] &= ~dzy
+    wet = U[0].reshape(p.ny, p.nx) > hmin
+    pad = np.pad(wet, reach, constant_values=True)   # outside the mesh: no constraint
+    near = np.ones_like(wet)
+    for dy in range(-reach, reach + 1):
+        for dx in range(-reach, reach + 1):
+            near &= pad[reach + dy:reach + dy + p.ny, reach + dx:reach + dx + p.nx]
+    return np.flatnonzero((ok & near).ravel())
+
+
+def _gpu_steady(swnmg, prob, z, U0=None, **kw):
+    S = swnmg.Solver(prob.with_params(**kw) if kw else prob, z=_dev(z))
+    U = _dev(prob.U0 if U0 is None else U0)
+    info = S.solve(U)
+    return S, U, info
+
+
+def test_gauge_loss_gradient_512_against_resolved_central_differences(swnmg):
+    """The gradient workload: 512 x 512 partial-dry channel, 64 gauges.  The
+    autograd gradient (SteadySWE) against central differences of the loss
+    with steady states re-solved on the GPU, at 32 cells and for the inflow
+    discharge."""
+    p, z_obs, gauges = W.adjoint_case(n=512)
+    _, Uobs, info = _gpu_steady(swnmg, p, z_obs)
+    assert info["status"] == 0, info
+    eta = (Uobs[0] + _dev(z_obs))[gauges].cpu().numpy()
+    z = _dev(p.z).requires_grad_(True)
+    q = torch.tensor([b.q for b in p.bc], dtype=torch.float64, requires_grad=True)
+    U = swnmg.steady_state(z, q, p, adj_rtol=1e-11)
+    gi = torch.as_tensor(gauges, device="cuda")
+    loss = ((U[0][gi] + z[gi] - _dev(eta)) ** 2).sum()
+    loss.backward()
+    dLdz = z.grad.cpu().numpy()
+    dLdq = q.grad.numpy()
+    Us = U.detach()
+    Uh = Us.cpu().numpy()
+    assert np.isfinite(dLdz).all() and np.abs(dLdz).max() > 0
+    # FP64 re-solves of this grid bottom out near sum ||R_i||_1 = 2e-12, so
+    # they stop at 1e-11 (a perturbed steady state then carries ~1e-13 error,
+    # 1e-9 of the loss difference at d = 1e-4)
+    d = 1e-4
+    cells = _kink_free(p, Uh, gap=10 * d)
+    rng = np.random.default_rng(7)
+    big = cells[np.argsort(-np.abs(dLdz[cells]))[:16]]
+    rest = rng.choice(np.setdiff1d(cells, big), 16, replace=False)
+    gmax = np.abs(dLdz).max()
+    warm = dict(init_mode=W.INIT_NONE, tol=1e-11, max_newton=40)
+    for j in np.concatenate([big, rest]):
+        Ls = []
+        for sgn in (1, -1):
+            zj = p.z.copy()
+            zj[j] += sgn * d
+            _, Uj, info = _gpu_steady(swnmg, p, zj, Uh, **warm)
+            assert info["status"] == 0, (j, info)
+            Ls.append(_loss(Uj[0].cpu().numpy(), zj, gauges, eta))
+        fd = (Ls[0] - Ls[1]) / (2 * d)
+        assert abs(dLdz[j] - fd) <= 1e-6 * max(abs(fd), gmax), (j, dLdz[j], fd)
+    assert p.bc[0].kind == W.BC_INFLOW_DISCHARGE
+    Ls = []
+    for sgn in (1, -1):
+        qs = [b.q for b in p.bc]
+        qs[0] += sgn * d
+        pq = swnmg.with_discharge(p, qs)
+        _, Uq, info = _gpu_steady(swnmg, pq, p.z, Uh, **warm)
+        assert info["status"] == 0, info
+        Ls.append(_loss(Uq[0].cpu().numpy(), p.z, gauges, eta))
+    fd = (Ls[0] - Ls[1]) / (2 * d)
+    assert abs(dLdq[0] - fd) <= 1e-6 * abs(fd), (dLdq[0], fd)
+    assert dLdq[1] == dLdq[2] == dLdq[3] == 0.0
+
+
+def test_gauge_loss_gradient_matches_oracle_pipeline(swnmg):
+    """The same gradient recipe at 128 x 128, computed end to end by both sides
+    from the same seeded inputs (each side solves its own observation and
+    steady state): the gradients agree within 1e-6 of their maximum."""
+    p, z_obs, gauges = W.adjoint_case(n=128, n_gauges=32, n_levels=5)
+    # oracle pipeline
+    import dataclasses
+    po = dataclasses.replace(p, z=z_obs)
+    Uobs_o, info = Oracle(po).solve()
+    assert info["status"] == 0
+    eta_o = Uobs_o[0][gauges] + z_obs[gauges]
+    Us_o, info = Oracle(p).solve()
+    assert info["status"] == 0
+    g = np.zeros_like(Us_o)
+    g[0][gauges] = 2 * (Us_o[0][gauges] + p.z[gauges] - eta_o)
+    _, dRz_o, dRq_o = Oracle(p).adjoint(Us_o, g, ncycles=60)
+    grad_o = -dRz_o
+    grad_o[gauges] += 2 * (Us_o[0][gauges] + p.z[gauges] - eta_o)
+    # GPU pipeline
+    _, Uobs, info = _gpu_steady(swnmg, p, z_obs)
+    assert info["status"] == 0
+    eta = (Uobs[0] + _dev(z_obs))[gauges].cpu().numpy()
+    assert np.abs(eta - eta_o).max() <= 1e-9
+    z = _dev(p.z).requires_grad_(True)
+    q = torch.tensor([b.q for b in p.bc], dtype=torch.float64, requires_grad=True)
+    U = swnmg.steady_state(z, q, p, adj_rtol=1e-11)
+    gi = torch.as_tensor(gauges, device="cuda")
+    ((U[0][gi] + z[gi] - _dev(eta)) ** 2).sum().backward()
+    grad = z.grad.cpu().numpy()
+    scale = np.abs(grad_o).max()
+    assert np.abs(grad - grad_o).max() <= 1e-6 * scale, np.abs(grad - grad_o).max() / scale
+    assert abs(q.grad[0].item() + dRq_o[0]) <= 1e-6 * abs(dRq_o[0])
