@@ -248,6 +248,58 @@ SWNMG_API swnmg_status swnmg_adjoint(swnmg_ctx* ctx, const double* U_dev, const 
                                      double* lam_dev, double* dRz_dev, double* dRq_host,
                                      int32_t max_cycles, double rtol, int32_t* cycles_out);
 
+/* ---- batches: many independent 2D problems solved together --------------
+ * The batched form of Algorithm 1 (an extension; the paper solves one
+ * problem at a time).  B problems -- 2D, any sizes, each with its own bed,
+ * boundary data and number of levels -- share the other solver parameters.
+ * Every step of Algorithm 1 runs for all of them in lockstep: each kernel
+ * launch covers every problem still iterating (a per-problem work list), so
+ * the wavefront sweeps of small levels and small problems fill the GPU
+ * together.  Each problem goes through exactly the steps, stop tests and
+ * arithmetic of swnmg_solve on its own and ends bit-identical to it.
+ * Restrictions: dim = 2, 1 <= B <= 256, one stream; the coarsest level of
+ * every problem is solved by the guarded inverse (coarse_sweeps <= 0 and at
+ * most 128 coarsest cells) or, for all problems alike, by coarse_sweeps
+ * symmetric SGS sweeps (coarse_sweeps > 0). */
+typedef struct swnmg_batch swnmg_batch;
+
+/* Creates a batch: probs[B]; n_levels[B] replaces prm->n_levels per problem
+ * (each nx, ny divisible by 2^n_levels[p]); z_dev[B] are the beds (n_p
+ * doubles each, copied).  Allocates one context's workspace per problem. */
+SWNMG_API swnmg_status swnmg_batch_create(const swnmg_problem* probs, const int32_t* n_levels, int32_t B,
+                                          const swnmg_params* prm, const double* const* z_dev,
+                                          void* stream, swnmg_batch** out);
+
+SWNMG_API swnmg_status swnmg_batch_destroy(swnmg_batch* bt);
+
+/* Text of the last failure of bt (static storage when bt is NULL). */
+SWNMG_API const char* swnmg_batch_last_error(const swnmg_batch* bt);
+
+/* Algorithm 1 for every problem: U_dev[p] (3*n_p doubles) holds the initial
+ * data on entry and the steady state on return; stats (nullable) receives B
+ * records.  Returns SWNMG_OK when every problem converged, otherwise the
+ * status of the first problem that did not (all statuses are in stats). */
+SWNMG_API swnmg_status swnmg_batch_solve(swnmg_batch* bt, double* const* U_dev, swnmg_stats* stats);
+
+/* 1: run the N_mg cycles of each Newton step from a CUDA graph captured on
+ * first use (one graph for the whole batch: the per-problem masks it reads
+ * are device arrays); 0: launch them one by one.  Results are identical. */
+SWNMG_API swnmg_status swnmg_batch_set_graph(swnmg_batch* bt, int32_t enable);
+
+/* Autotuner: times the candidate shared-memory staging depths of the SGS
+ * sweep on every level and the candidate BLU-SGS grid sizes on this batch
+ * (BLU-SGS on scratch copies of U_dev, which is not modified) and keeps the
+ * fastest.  sgs_chunk (13 entries) and blusgs_blocks (nullable) receive the
+ * choices.  Tuning changes speed only, never results.  Synchronises. */
+SWNMG_API swnmg_status swnmg_batch_tune(swnmg_batch* bt, double* const* U_dev, int32_t* sgs_chunk,
+                                        int32_t* blusgs_blocks);
+
+/* Sets the tuning by hand: sgs_chunk (13 entries, each 4, 8 or 16 in MIXED
+ * precision and 2, 4 or 8 in FP64; NULL keeps them), blusgs_blocks (<= 0
+ * keeps it; otherwise at most the co-resident limit). */
+SWNMG_API swnmg_status swnmg_batch_set_tuning(swnmg_batch* bt, const int32_t* sgs_chunk,
+                                              int32_t blusgs_blocks);
+
 /* Number of cells of level l (0 if l is out of range). */
 SWNMG_API int64_t swnmg_level_cells(const swnmg_ctx* ctx, int32_t level);
 

@@ -23,6 +23,7 @@ UNITS = {
     "mg.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
+    "batch.cu": [],
 }
 
 

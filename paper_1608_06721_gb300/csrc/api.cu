@@ -7,24 +7,12 @@
 #include <cstring>
 #include <string>
 
-#include "common.cuh"
-#include "../../include/swnmg.h"
+#include "ctx.cuh"
 
 using namespace swnmg;
 
 namespace {
 
-struct Level {
-  int nx = 0, ny = 0, n = 0;
-  double ex = 0, ey = 0;
-  double* z = nullptr;      // bed at cell centres
-  double* U = nullptr;      // Step 1 state (levels >= 1)
-  void* blk = nullptr;      // 5 blocks (raw diagonal first), working precision
-  void* lu = nullptr;       // LU of the diagonal
-  int8_t* piv = nullptr;
-  void* b = nullptr;        // right-hand side of A x = b
-  void* x = nullptr;        // iterate
-};
 
 const char* status_text(swnmg_status s) {
   switch (s) {
@@ -57,48 +45,6 @@ struct Hier {
 
 void swnmg::set_static_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
 
-struct swnmg_ctx {
-  swnmg_problem prob;
-  swnmg_params prm;
-  int nc = 0, nl = 0, fp32 = 0;
-  size_t wsz = 8;           // bytes per working-precision value
-  cudaStream_t st = nullptr;
-  Level lv[13];
-  double* R = nullptr;      // residual scratch (level-0 size)
-  double* rn = nullptr;     // ||R_i||_1
-  double* eb = nullptr;     // per-edge Jacobian pieces (level-0 size)
-  double* red = nullptr;    // reduction partials (1024) + result
-  double* band = nullptr;   // exact coarse-solve scratch (banded elimination, large m)
-  void* cinv = nullptr;     // guarded inverse of the coarsest operator (small m)
-  void* caug = nullptr;     // its m x 2m elimination array
-  int* csing = nullptr;
-  int* derr = nullptr;
-  int* sgs_sync = nullptr;  // ticket / abort / per-strip progress of the wavefront sweeps
-  int* sticky = nullptr;    // set by a device wait that ran out of its bound
-  double* hbuf = nullptr;   // pinned host scalars
-  bool coarse_exact = false;
-  bool coarse_inverse = false;   // exact coarse solve through X = A^-1 (guarded)
-  // transposed (adjoint) operator hierarchy, FP64, allocated on first use
-  bool adj_ready = false;
-  Level alv[13];
-  void* acinv = nullptr;
-  void* acaug = nullptr;
-  int* acsing = nullptr;
-  double* aband = nullptr;
-  double* adj_A = nullptr;   // FP64 Jacobian at U* before transposition
-  double* adj_cz = nullptr;      // per-edge z contributions (2 per edge)
-  double* adj_cell = nullptr;    // per-cell scratch (n)
-  // per-class kernel timing: event pairs resolved at synchronisation points
-  bool timing = false;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<int> ev_class;     // class of pair k (events 2k, 2k+1)
-  std::vector<double> ev_cells;  // cells processed inside pair k
-  int ev_used = 0;
-  double t_ms[SWNMG_T_COUNT] = {0};
-  long long t_n[SWNMG_T_COUNT] = {0};
-  double t_cells[SWNMG_T_COUNT] = {0};
-  std::string err;
-};
 
 namespace {
 
@@ -872,3 +818,5 @@ SWNMG_API swnmg_status swnmg_get_timing(swnmg_ctx* c, double* ms_out, int64_t* n
 }
 
 SWNMG_API int64_t swnmg_launch_count(void) { return launches_total(); }
+
+DevLevel swnmg::ctx_dev_level(const swnmg_ctx* c, int l) { return dev_level(c, l); }

@@ -55,6 +55,53 @@ __host__ __device__ __forceinline__ long long skew_slots(int nx, int ny) {
   return (long long)((ny + 31) >> 5) * (nx + 31) * 32;
 }
 
+// ---- batches of independent problems ------------------------------------
+// One problem at one level of a batch: what the batched kernels read.  A
+// batch keeps one table of these per level (problem p at entry p).
+struct BItem {
+  DevLevel L;                   // geometry, boundary data, parameters
+  const double* z;              // level bed
+  double* U;                    // level state (level 0: the caller's state)
+  double* R;                    // residual and ||R_i||_1 (problem workspace)
+  double* rn;
+  double* eb;                   // per-edge scratch (problem workspace)
+  double* red;                  // reduction partials (1024 doubles)
+  void* blk;                    // level operator, LU factors, MG vectors
+  void* lu;
+  int8_t* piv;
+  void* b;
+  void* x;
+  void* cinv;                   // coarsest level: guarded inverse and its scratch
+  void* caug;
+  int* csing;
+  int n_xe, n_e;                // x-edges, all edges
+  int strip0;                   // first SGS progress slot of this problem
+  int has;                      // the problem has this level
+};
+
+constexpr int BATCH_MAX = 256;
+
+// problem owning block blk: the largest p with bstart[p] <= blk
+__device__ __forceinline__ int batch_find(const int* bstart, int B, int blk) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bstart[mid] <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One batched launch over a per-problem index domain: blocks of 128 threads,
+// problem p owns blocks [bstart[p], bstart[p+1]); mask[p] == 0 skips it.
+struct BLaunch {
+  const BItem* items;
+  const int* bstart;
+  int nblocks;
+  int B;
+  const int* mask;
+};
+
 // sets the text that swnmg_last_error(NULL) returns
 void set_static_error(const char* msg);
 
@@ -79,6 +126,20 @@ void launch_average(int dim, int nxf, int nyf, int ncomp, const double* vf, doub
                     cudaStream_t st);
 void launch_inject(int dim, int nxf, int nyf, int ncomp, const double* vc, double* vf,
                    cudaStream_t st);
+
+// batched forms (2D, three components); bl.items is the level's table
+void launch_b_residual(const BLaunch& edges, const BLaunch& cells, cudaStream_t st);
+void launch_b_jacobian(const BLaunch& edges, const BLaunch& cells, int fp32, cudaStream_t st);
+void launch_b_newton_update(const BLaunch& cells, double tau, double h_eps, int fp32, cudaStream_t st);
+// coarse cells of level l+1 (bl over the coarse domain, fine table separately)
+void launch_b_average(const BLaunch& coarse, const BItem* fine_items, cudaStream_t st);
+// fine cells of level l-1 (bl over the fine domain, coarse table separately)
+void launch_b_inject(const BLaunch& fine, const BItem* coarse_items, cudaStream_t st);
+// one half-sweep over every masked problem's level; nsteps = max diagonals,
+// blocks = cooperative grid size, sync: [0] arrivals, [1] abort (zeroed here)
+void launch_b_blusgs_sweep(const BItem* items, const int* mask, int B, int nsteps, int forward, int blocks,
+                           int* sync, int* sticky_err, cudaStream_t st);
+int b_blusgs_max_blocks_per_sm();
 
 // ---- host-side launch wrappers (mg.cu) -----------------------------------
 void launch_lu_factor(int nx, int ny, int nc, const void* blk, void* lu, int8_t* piv, int fp32,
@@ -109,5 +170,22 @@ void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long
 void launch_fill(void* dst, int fp32, long long n, cudaStream_t st);
 void launch_blocks_export(int nx, int ny, int nc, const void* blk, int fp32, double* out,
                           cudaStream_t st);
+
+// batched forms (2D, three components)
+// sum_i ||R_i||_1 of every masked problem into out[p] (max_n: the table's largest level)
+void launch_b_sum(const BItem* items, const int* mask, int B, int max_n, double* out, cudaStream_t st);
+void launch_b_lu_factor(const BLaunch& slots, int fp32, cudaStream_t st);
+void launch_b_galerkin(const BLaunch& coarse, const BItem* fine_items, int fp32, cudaStream_t st);
+void launch_b_restrict(const BLaunch& coarse, const BItem* fine_items, int fp32, cudaStream_t st);
+void launch_b_prolong(const BLaunch& fine, const BItem* coarse_items, int fp32, cudaStream_t st);
+void launch_b_fill_x(const BLaunch& cells, int fp32, cudaStream_t st);
+void launch_b_neg_residual(const BLaunch& cells, int fp32, cudaStream_t st);   // b = -R
+// strip tickets (problem, processing index) in claim order; chunk = staged
+// lines per buffer (4, 8 or 16); sync: [0] ticket, [1] abort, [2..] progress
+void launch_b_sgs_sweep(const BItem* items, const int2* tickets, int ntickets, int nslots, const int* mask,
+                        int forward, int fp32, int chunk, int* sync, int* sticky_err, cudaStream_t st);
+size_t b_sgs_smem_bytes(int fp32, int chunk);
+void launch_b_coarse_inverse(const BItem* items, const int* mask, int B, int fp32, cudaStream_t st);
+void launch_b_coarse_apply(const BItem* items, const int* mask, int B, int max_m, int fp32, cudaStream_t st);
 
 }  // namespace swnmg

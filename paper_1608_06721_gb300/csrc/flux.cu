@@ -223,10 +223,9 @@ __device__ __forceinline__ void st(void* p, long long idx, double v) {
 // ---- residual: per-edge G, then per-cell sums --------------------------------
 
 template <int NC>
-__global__ void k_res_edges(DevLevel L, const double* __restrict__ z, const double* __restrict__ U,
-                            double* __restrict__ eb, int n_xe, int n_e) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n_e) return;
+__device__ __forceinline__ void res_edge(const DevLevel& L, const double* __restrict__ z,
+                                         const double* __restrict__ U, double* __restrict__ eb, int n_xe,
+                                         int n_e, int e) {
   int axis, iL, iR;
   double len;
   edge_cells(L, e, n_xe, axis, iL, iR, len);
@@ -239,6 +238,13 @@ __global__ void k_res_edges(DevLevel L, const double* __restrict__ z, const doub
     eb[s * (long long)n_e + e] = GL[s];
     eb[(NC + s) * (long long)n_e + e] = GR[s];
   }
+}
+
+template <int NC>
+__global__ void k_res_edges(DevLevel L, const double* __restrict__ z, const double* __restrict__ U,
+                            double* __restrict__ eb, int n_xe, int n_e) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n_e) res_edge<NC>(L, z, U, eb, n_xe, n_e, e);
 }
 
 // cell edges: W (x-edge, cell on the right), E (x-edge, left), S, N
@@ -255,10 +261,9 @@ __device__ __forceinline__ void cell_edges(const DevLevel& L, int i, int n_xe, i
 // (a non-finite cell state makes ||R_i||_1 NaN, so that the sums report it:
 // the reconstruction's max(0, .) would otherwise hide a NaN depth)
 template <int NC>
-__global__ void k_res_cells(DevLevel L, const double* __restrict__ eb, const double* __restrict__ U,
-                            double* __restrict__ R, double* __restrict__ rn, int n_xe, int n_e) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L.n) return;
+__device__ __forceinline__ void res_cell(const DevLevel& L, const double* __restrict__ eb,
+                                         const double* __restrict__ U, double* __restrict__ R,
+                                         double* __restrict__ rn, int n_xe, int n_e, int i) {
   int eW, eE, eS, eN;
   cell_edges(L, i, n_xe, eW, eE, eS, eN);
   double r[NC];
@@ -280,6 +285,13 @@ __global__ void k_res_cells(DevLevel L, const double* __restrict__ eb, const dou
   if (rn) rn[i] = fin ? m : __longlong_as_double(0x7ff8000000000000LL);
 }
 
+template <int NC>
+__global__ void k_res_cells(DevLevel L, const double* __restrict__ eb, const double* __restrict__ U,
+                            double* __restrict__ R, double* __restrict__ rn, int n_xe, int n_e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L.n) res_cell<NC>(L, eb, U, R, rn, n_xe, n_e, i);
+}
+
 // ---- finite-difference Jacobian ---------------------------------------------
 // Edge buffer fields (each n_e long): GL[NC], GR[NC], dLL[NC*NC], dRR[NC*NC],
 // where dLL = |e| (G_L(U_L + eps e_k) - G_L(U)) / eps is the left cell's
@@ -287,10 +299,9 @@ __global__ void k_res_cells(DevLevel L, const double* __restrict__ eb, const dou
 // off-diagonal blocks go straight to the level's block arrays.
 
 template <int NC, typename T>
-__global__ void k_jac_edges(DevLevel L, const double* __restrict__ z, const double* __restrict__ U,
-                            double* __restrict__ eb, void* __restrict__ blk, int n_xe, int n_e) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n_e) return;
+__device__ __forceinline__ void jac_edge(const DevLevel& L, const double* __restrict__ z,
+                                         const double* __restrict__ U, double* __restrict__ eb,
+                                         void* __restrict__ blk, int n_xe, int n_e, int e) {
   int axis, iL, iR;
   double len;
   edge_cells(L, e, n_xe, axis, iL, iR, len);
@@ -351,13 +362,19 @@ __global__ void k_jac_edges(DevLevel L, const double* __restrict__ z, const doub
   }
 }
 
+template <int NC, typename T>
+__global__ void k_jac_edges(DevLevel L, const double* __restrict__ z, const double* __restrict__ U,
+                            double* __restrict__ eb, void* __restrict__ blk, int n_xe, int n_e) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n_e) jac_edge<NC, T>(L, z, U, eb, blk, n_xe, n_e, e);
+}
+
 // Diagonal block D_i = sum_{W,E,S,N} dG + alpha ||R_i||_1 I (eq. NewtonREG),
 // residual and its norm.  1D cells have only W and E.
 template <int NC, typename T>
-__global__ void k_jac_cells(DevLevel L, const double* __restrict__ eb, double* __restrict__ R,
-                            double* __restrict__ rn, void* __restrict__ blk, int n_xe, int n_e) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L.n) return;
+__device__ __forceinline__ void jac_cell(const DevLevel& L, const double* __restrict__ eb,
+                                         double* __restrict__ R, double* __restrict__ rn,
+                                         void* __restrict__ blk, int n_xe, int n_e, int i) {
   int eW, eE, eS, eN;
   cell_edges(L, i, n_xe, eW, eE, eS, eN);
   const long long ne = n_e, n = L.n, P = skew_slots(L.nx, L.ny);
@@ -392,6 +409,13 @@ __global__ void k_jac_cells(DevLevel L, const double* __restrict__ eb, double* _
       if (s == k) d = d + am;
       st<T>(blk, (long long)f * P + si, d);
     }
+}
+
+template <int NC, typename T>
+__global__ void k_jac_cells(DevLevel L, const double* __restrict__ eb, double* __restrict__ R,
+                            double* __restrict__ rn, void* __restrict__ blk, int n_xe, int n_e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L.n) jac_cell<NC, T>(L, eb, R, rn, blk, n_xe, n_e, i);
 }
 
 // ---- block solve with the same elimination as the reference definition -----
@@ -706,10 +730,8 @@ __global__ void k_adj_q_cells(DevLevel Lp, DevLevel Lm, int side, const double* 
 
 // U += tau dU with the dry rules of Remark 2.5 (eq. NewtonREG-12)
 template <typename T>
-__global__ void k_newton_update(int n, int nc, double tau, double h_eps, double* __restrict__ U,
-                                const T* __restrict__ dU) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void newton_update_cell(int n, int nc, double tau, double h_eps,
+                                                   double* __restrict__ U, const T* __restrict__ dU, int i) {
   const double h0 = U[i];
   double v[3];
   for (int s = 0; s < nc; ++s) {
@@ -722,12 +744,17 @@ __global__ void k_newton_update(int n, int nc, double tau, double h_eps, double*
   for (int s = 0; s < nc; ++s) U[(long long)s * n + i] = v[s];
 }
 
+template <typename T>
+__global__ void k_newton_update(int n, int nc, double tau, double h_eps, double* __restrict__ U,
+                                const T* __restrict__ dU) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) newton_update_cell<T>(n, nc, tau, h_eps, U, dU, i);
+}
+
 // coarse value = mean of the children (child order 00, 10, 01, 11)
-__global__ void k_average(int dim, int nxf, int nyf, int ncomp, const double* __restrict__ vf,
-                          double* __restrict__ vc) {
+__device__ __forceinline__ void average_cell(int dim, int nxf, int nyf, int ncomp, const double* __restrict__ vf,
+                                             double* __restrict__ vc, int I) {
   const int nxc = nxf / 2, nyc = dim == 2 ? nyf / 2 : 1, nc_cells = nxc * nyc;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= nc_cells) return;
   const long long nf = (long long)nxf * (dim == 2 ? nyf : 1);
   const int Ix = I % nxc, Iy = I / nxc;
   for (int s = 0; s < ncomp; ++s) {
@@ -749,16 +776,188 @@ __global__ void k_average(int dim, int nxf, int nyf, int ncomp, const double* __
   }
 }
 
+__global__ void k_average(int dim, int nxf, int nyf, int ncomp, const double* __restrict__ vf,
+                          double* __restrict__ vc) {
+  const int nc_cells = (nxf / 2) * (dim == 2 ? nyf / 2 : 1);
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I < nc_cells) average_cell(dim, nxf, nyf, ncomp, vf, vc, I);
+}
+
 // piecewise-constant injection of a coarse solution (Algorithm 1, Step 1)
-__global__ void k_inject(int dim, int nxf, int nyf, int ncomp, const double* __restrict__ vc,
-                         double* __restrict__ vf) {
+__device__ __forceinline__ void inject_cell(int dim, int nxf, int nyf, int ncomp, const double* __restrict__ vc,
+                                            double* __restrict__ vf, int i) {
   const int nf_cells = nxf * (dim == 2 ? nyf : 1);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nf_cells) return;
   const int ix = i % nxf, iy = i / nxf, nxc = nxf / 2;
   const int nc_cells = nxc * (dim == 2 ? nyf / 2 : 1);
   const int I = (ix / 2) + nxc * (dim == 2 ? iy / 2 : 0);
   for (int s = 0; s < ncomp; ++s) vf[(long long)s * nf_cells + i] = vc[(long long)s * nc_cells + I];
+}
+
+__global__ void k_inject(int dim, int nxf, int nyf, int ncomp, const double* __restrict__ vc,
+                         double* __restrict__ vf) {
+  const int nf_cells = nxf * (dim == 2 ? nyf : 1);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nf_cells) inject_cell(dim, nxf, nyf, ncomp, vc, vf, i);
+}
+
+// ---- batched forms -------------------------------------------------------------
+// The same per-edge / per-cell bodies; the block's problem comes from the
+// launch's block table (blocks of 128 threads), so every problem of a batch
+// gets exactly the arithmetic of its own single-problem launch.
+#define BATCH_PROLOGUE(bl)                                        \
+  const int p_ = batch_find((bl).bstart, (bl).B, blockIdx.x);     \
+  if (!(bl).mask[p_]) return;                                     \
+  const BItem* it = (bl).items + p_;                              \
+  const int idx = (blockIdx.x - (bl).bstart[p_]) * 128 + threadIdx.x;
+
+template <int NC>
+__global__ void __launch_bounds__(128) kb_res_edges(BLaunch bl) {
+  BATCH_PROLOGUE(bl)
+  if (idx >= it->n_e) return;
+  const DevLevel L = it->L;
+  res_edge<NC>(L, it->z, it->U, it->eb, it->n_xe, it->n_e, idx);
+}
+
+template <int NC>
+__global__ void __launch_bounds__(128) kb_res_cells(BLaunch bl) {
+  BATCH_PROLOGUE(bl)
+  const DevLevel L = it->L;
+  if (idx >= L.n) return;
+  res_cell<NC>(L, it->eb, it->U, it->R, it->rn, it->n_xe, it->n_e, idx);
+}
+
+template <int NC, typename T>
+__global__ void __launch_bounds__(128) kb_jac_edges(BLaunch bl) {
+  BATCH_PROLOGUE(bl)
+  if (idx >= it->n_e) return;
+  const DevLevel L = it->L;
+  jac_edge<NC, T>(L, it->z, it->U, it->eb, it->blk, it->n_xe, it->n_e, idx);
+}
+
+template <int NC, typename T>
+__global__ void __launch_bounds__(128) kb_jac_cells(BLaunch bl) {
+  BATCH_PROLOGUE(bl)
+  const DevLevel L = it->L;
+  if (idx >= L.n) return;
+  jac_cell<NC, T>(L, it->eb, it->R, it->rn, it->blk, it->n_xe, it->n_e, idx);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) kb_newton_update(BLaunch bl, double tau, double h_eps) {
+  BATCH_PROLOGUE(bl)
+  if (idx >= it->L.n) return;
+  newton_update_cell<T>(it->L.n, it->L.nc, tau, h_eps, it->U, static_cast<const T*>(it->x), idx);
+}
+
+__global__ void __launch_bounds__(128) kb_average(BLaunch bl, const BItem* fine) {
+  BATCH_PROLOGUE(bl)
+  if (idx >= it->L.n) return;
+  const BItem* f = fine + p_;
+  average_cell(2, f->L.nx, f->L.ny, f->L.nc, f->U, it->U, idx);
+}
+
+__global__ void __launch_bounds__(128) kb_inject(BLaunch bl, const BItem* coarse) {
+  BATCH_PROLOGUE(bl)
+  if (idx >= it->L.n) return;
+  inject_cell(2, it->L.nx, it->L.ny, it->L.nc, coarse[p_].U, it->U, idx);
+}
+#undef BATCH_PROLOGUE
+
+// BLU-SGS half-sweep over a batch: step q updates diagonal q (forward) of
+// every masked problem that has one; the diagonals' cells are concatenated
+// in problem order and dealt to the warps, then the grid meets at the same
+// bounded barrier as the single-problem sweep.
+template <int NC, int NS, int GRP>
+__global__ void __launch_bounds__(128) kb_blusgs_sweep(const BItem* __restrict__ items,
+                                                       const int* __restrict__ mask, int B, int nsteps,
+                                                       int forward, int* sync, int* sticky_err,
+                                                       int spin_limit) {
+  __shared__ int s_go;
+  __shared__ int s_off[BATCH_MAX + 1];
+  __shared__ int s_cnt[BATCH_MAX], s_d[BATCH_MAX], s_ix0[BATCH_MAX];
+  const unsigned full = 0xffffffffu;
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
+  const int cpw = 32 / GRP;
+  for (int q = 0; q < nsteps; ++q) {
+    for (int p = threadIdx.x; p < B; p += blockDim.x) {
+      int cnt = 0, d = 0, ix0 = 0;
+      if (mask[p]) {
+        const int nx = items[p].L.nx, ny = items[p].L.ny, ndiag = nx + ny - 1;
+        if (q < ndiag) {
+          d = forward ? q : ndiag - 1 - q;
+          ix0 = d - (ny - 1) > 0 ? d - (ny - 1) : 0;
+          const int ix1 = d < nx - 1 ? d : nx - 1;
+          cnt = ix1 - ix0 + 1;
+        }
+      }
+      s_cnt[p] = cnt;
+      s_d[p] = d;
+      s_ix0[p] = ix0;
+    }
+    __syncthreads();
+    if (warp == 0) {   // exclusive prefix of the counts
+      const int per = (B + 31) / 32;
+      int loc = 0;
+      for (int k = 0; k < per; ++k) {
+        const int p = lane * per + k;
+        if (p < B) loc += s_cnt[p];
+      }
+      int inc = loc;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(full, inc, o);
+        if (lane >= o) inc += v;
+      }
+      int run = inc - loc;
+      for (int k = 0; k < per; ++k) {
+        const int p = lane * per + k;
+        if (p < B) {
+          s_off[p] = run;
+          run += s_cnt[p];
+        }
+      }
+      if (lane == 31) s_off[B] = inc;
+    }
+    __syncthreads();
+    const int total = s_off[B];
+    for (int c0 = gw * cpw; c0 < total; c0 += nw * cpw) {   // warp-uniform loop
+      const int flat = c0 + lane / GRP;
+      int p = 0, cell = 0, ncell = 0;
+      if (flat < total) {
+        int lo = 0, hi = B - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= flat) lo = mid;
+          else hi = mid - 1;
+        }
+        p = lo;
+        cell = flat - s_off[p];
+        ncell = s_cnt[p];
+      }
+      blusgs_group<NC, NS, GRP, true>(items[p].L, items[p].z, items[p].U, s_d[p], s_ix0[p], ncell, cell,
+                                      lane % GRP);
+    }
+    // grid barrier (as in k_blusgs_sweep)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&sync[0], 1);
+      const int target = (q + 1) * gridDim.x;
+      int ok = 0;
+      for (int it = 0; it < spin_limit; ++it) {
+        if (ld_acq(&sync[0]) >= target) { ok = 1; break; }
+        if (ld_acq(&sync[1])) break;
+        __nanosleep(20);
+      }
+      if (!ok) {
+        if (!ld_acq(&sync[1])) atomicOr(sticky_err, 1);
+        atomicExch(&sync[1], 1);
+      }
+      s_go = ok;
+    }
+    __syncthreads();
+    if (!s_go) return;
+  }
 }
 
 inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -873,6 +1072,58 @@ void launch_inject(int dim, int nxf, int nyf, int ncomp, const double* vc, doubl
   count_launches(1);
   const int ncells = nxf * (dim == 2 ? nyf : 1);
   k_inject<<<nblk(ncells, 256), 256, 0, st>>>(dim, nxf, nyf, ncomp, vc, vf);
+}
+
+// ---- batched launchers ----------------------------------------------------------
+
+void launch_b_residual(const BLaunch& edges, const BLaunch& cells, cudaStream_t st) {
+  count_launches(2);
+  if (edges.nblocks > 0) kb_res_edges<3><<<edges.nblocks, 128, 0, st>>>(edges);
+  if (cells.nblocks > 0) kb_res_cells<3><<<cells.nblocks, 128, 0, st>>>(cells);
+}
+
+void launch_b_jacobian(const BLaunch& edges, const BLaunch& cells, int fp32, cudaStream_t st) {
+  count_launches(2);
+  if (fp32) {
+    if (edges.nblocks > 0) kb_jac_edges<3, float><<<edges.nblocks, 128, 0, st>>>(edges);
+    if (cells.nblocks > 0) kb_jac_cells<3, float><<<cells.nblocks, 128, 0, st>>>(cells);
+  } else {
+    if (edges.nblocks > 0) kb_jac_edges<3, double><<<edges.nblocks, 128, 0, st>>>(edges);
+    if (cells.nblocks > 0) kb_jac_cells<3, double><<<cells.nblocks, 128, 0, st>>>(cells);
+  }
+}
+
+void launch_b_newton_update(const BLaunch& cells, double tau, double h_eps, int fp32, cudaStream_t st) {
+  count_launches(1);
+  if (cells.nblocks <= 0) return;
+  if (fp32) kb_newton_update<float><<<cells.nblocks, 128, 0, st>>>(cells, tau, h_eps);
+  else kb_newton_update<double><<<cells.nblocks, 128, 0, st>>>(cells, tau, h_eps);
+}
+
+void launch_b_average(const BLaunch& coarse, const BItem* fine_items, cudaStream_t st) {
+  count_launches(1);
+  if (coarse.nblocks > 0) kb_average<<<coarse.nblocks, 128, 0, st>>>(coarse, fine_items);
+}
+
+void launch_b_inject(const BLaunch& fine, const BItem* coarse_items, cudaStream_t st) {
+  count_launches(1);
+  if (fine.nblocks > 0) kb_inject<<<fine.nblocks, 128, 0, st>>>(fine, coarse_items);
+}
+
+void launch_b_blusgs_sweep(const BItem* items, const int* mask, int B, int nsteps, int forward, int blocks,
+                           int* sync, int* sticky_err, cudaStream_t st) {
+  count_launches(1);
+  cudaMemsetAsync(sync, 0, 2 * sizeof(int), st);
+  int b = B, ns = nsteps, fw = forward, spin = 1 << 22;
+  void* args[] = {(void*)&items, (void*)&mask, (void*)&b, (void*)&ns, (void*)&fw, (void*)&sync,
+                  (void*)&sticky_err, (void*)&spin};
+  cudaLaunchCooperativeKernel((const void*)kb_blusgs_sweep<3, 4, 16>, dim3(blocks), dim3(128), args, 0, st);
+}
+
+int b_blusgs_max_blocks_per_sm() {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_blusgs_sweep<3, 4, 16>, 128, 0);
+  return nb;
 }
 
 }  // namespace swnmg

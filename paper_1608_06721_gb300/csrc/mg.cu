@@ -18,11 +18,9 @@ template <typename T> __device__ __forceinline__ T tabs(T a) { return a < T(0) ?
 // 1e-14 max|D| marks a singular unknown (its reciprocal pivot is stored as 0,
 // so its correction is 0).
 template <int NC, typename T>
-__global__ void k_lu_factor(int nx, int ny, const T* __restrict__ blk, T* __restrict__ lu,
-                            int8_t* __restrict__ piv) {
+__device__ __forceinline__ void lu_factor_slot(int nx, int ny, const T* __restrict__ blk, T* __restrict__ lu,
+                                               int8_t* __restrict__ piv, long long slot) {
   const long long P = skew_slots(nx, ny);
-  const long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (slot >= P) return;
   // slot -> cell: lane k of strip t on skewed diagonal d is (d - k, 32 t + k)
   const int k = (int)(slot & 31);
   const long long line = slot >> 5;
@@ -74,6 +72,13 @@ __global__ void k_lu_factor(int nx, int ny, const T* __restrict__ blk, T* __rest
   }
 }
 
+template <int NC, typename T>
+__global__ void k_lu_factor(int nx, int ny, const T* __restrict__ blk, T* __restrict__ lu,
+                            int8_t* __restrict__ piv) {
+  const long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (slot < skew_slots(nx, ny)) lu_factor_slot<NC, T>(nx, ny, blk, lu, piv, slot);
+}
+
 // LU solve with the factors of one cell read from 9 values L[e*ls]
 template <int NC, typename T>
 __device__ __forceinline__ void lu_apply_v(const T* __restrict__ L, int ls, int8_t pv, const T r[NC],
@@ -100,10 +105,9 @@ __device__ __forceinline__ void lu_apply_v(const T* __restrict__ L, int ls, int8
 // children 00, 10, 01, 11; diagonal = children's diagonals plus the 8
 // couplings between children; W/E/S/N = the two couplings crossing that side.
 template <int NC, typename T>
-__global__ void k_galerkin(int dim, int nxf, int nyf, const T* __restrict__ bf, T* __restrict__ bc) {
+__device__ __forceinline__ void galerkin_cell(int dim, int nxf, int nyf, const T* __restrict__ bf,
+                                              T* __restrict__ bc, int I) {
   const int nxc = nxf / 2, nyc = dim == 2 ? nyf / 2 : 1, ncc = nxc * nyc;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= ncc) return;
   const int nyff = dim == 2 ? nyf : 1;
   const long long Pf = skew_slots(nxf, nyff), Pc = skew_slots(nxc, nyc);
   const int BS = NC * NC;
@@ -142,6 +146,12 @@ __global__ void k_galerkin(int dim, int nxf, int nyf, const T* __restrict__ bf, 
 #undef CB
 }
 
+template <int NC, typename T>
+__global__ void k_galerkin(int dim, int nxf, int nyf, const T* __restrict__ bf, T* __restrict__ bc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I < (nxf / 2) * (dim == 2 ? nyf / 2 : 1)) galerkin_cell<NC, T>(dim, nxf, nyf, bf, bc, I);
+}
+
 // linear residual of the fine system at cell i: r = b - D x_i - sum A x_j
 template <int NC, typename T>
 __device__ __forceinline__ void lin_resid(int dim, int nx, int ny, const T* __restrict__ blk,
@@ -174,11 +184,10 @@ __device__ __forceinline__ void lin_resid(int dim, int nx, int ny, const T* __re
 
 // coarse right-hand side = sum over children of (b - A x)  (eq. ProjectAR)
 template <int NC, typename T>
-__global__ void k_restrict(int dim, int nxf, int nyf, const T* __restrict__ blk,
-                           const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ bc) {
+__device__ __forceinline__ void restrict_cell(int dim, int nxf, int nyf, const T* __restrict__ blk,
+                                              const T* __restrict__ b, const T* __restrict__ x,
+                                              T* __restrict__ bc, int I) {
   const int nxc = nxf / 2, nyc = dim == 2 ? nyf / 2 : 1, ncc = nxc * nyc;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= ncc) return;
   const int Ix = I % nxc, Iy = I / nxc;
   const int ny = dim == 2 ? nyf : 1;
   int ch[4];
@@ -196,17 +205,29 @@ __global__ void k_restrict(int dim, int nxf, int nyf, const T* __restrict__ blk,
   for (int s = 0; s < NC; ++s) bc[(long long)s * ncc + I] = acc[s];
 }
 
+template <int NC, typename T>
+__global__ void k_restrict(int dim, int nxf, int nyf, const T* __restrict__ blk,
+                           const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ bc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I < (nxf / 2) * (dim == 2 ? nyf / 2 : 1)) restrict_cell<NC, T>(dim, nxf, nyf, blk, b, x, bc, I);
+}
+
 // x_j += x_I for every child j of I  (eq. correction, piecewise constant)
 template <typename T>
-__global__ void k_prolong(int dim, int nc, int nxf, int nyf, const T* __restrict__ xc,
-                          T* __restrict__ xf) {
+__device__ __forceinline__ void prolong_cell(int dim, int nc, int nxf, int nyf, const T* __restrict__ xc,
+                                             T* __restrict__ xf, int i) {
   const int nf = nxf * (dim == 2 ? nyf : 1);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nf) return;
   const int ix = i % nxf, iy = i / nxf, nxc = nxf / 2;
   const int ncc = nxc * (dim == 2 ? nyf / 2 : 1);
   const int I = (ix / 2) + nxc * (dim == 2 ? iy / 2 : 0);
   for (int s = 0; s < nc; ++s) xf[(long long)s * nf + i] = xf[(long long)s * nf + i] + xc[(long long)s * ncc + I];
+}
+
+template <typename T>
+__global__ void k_prolong(int dim, int nc, int nxf, int nyf, const T* __restrict__ xc,
+                          T* __restrict__ xf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nxf * (dim == 2 ? nyf : 1)) prolong_cell<T>(dim, nc, nxf, nyf, xc, xf, i);
 }
 
 // ---- block Gauss-Seidel sweep: strip-pipelined wavefront ---------------------
@@ -270,18 +291,19 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// default lines per staged chunk: the largest that fits twice in shared memory
 template <typename T> struct SgsChunk { static constexpr int S = sizeof(T) == 4 ? 16 : 8; };
 
 template <int NC, typename T>
 __host__ __device__ constexpr int sgs_entries() { return 4 * NC * NC + LU_E; }   // W, E, S, N blocks + LU
 
-template <int NC, typename T>
+template <int NC, typename T, int S>
 __host__ __device__ constexpr size_t sgs_stage_bytes() {
-  return (size_t)sgs_entries<NC, T>() * SgsChunk<T>::S * 32 * sizeof(T) + SgsChunk<T>::S * 32;
+  return (size_t)sgs_entries<NC, T>() * S * 32 * sizeof(T) + S * 32;
 }
 
-template <int NC, typename T>
-size_t sgs_smem_bytes() { return 128 + 2 * sgs_stage_bytes<NC, T>(); }
+template <int NC, typename T, int S>
+size_t sgs_smem_bytes() { return 128 + 2 * sgs_stage_bytes<NC, T, S>(); }
 
 // bounded wait of every lane for one chunk; warp-uniform result, false when
 // the bound expired for some lane
@@ -291,17 +313,19 @@ __device__ __forceinline__ bool chunk_wait(uint64_t* bar, unsigned parity, int l
   return __all_sync(0xffffffffu, ok) != 0;
 }
 
-template <int NC, typename T, bool FWD>
-__global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __restrict__ blk,
-                                                     const T* __restrict__ lu,
-                                                     const int8_t* __restrict__ piv,
-                                                     const T* __restrict__ b, T* x, int* sync,
-                                                     int* sticky_err, int nstrips, int spin_limit) {
-  constexpr int S = SgsChunk<T>::S;
+// One strip (processing index q of nstrips) of one sweep; lane 0 stages the
+// operator through the warp's two shared-memory buffers.  prog[q - 1] is the
+// previous strip's progress, prog[q] this strip's.  Returns false when a wait
+// ran out (the abort flag and the sticky error are then set).
+template <int NC, typename T, bool FWD, int S>
+__device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restrict__ blk,
+                                              const T* __restrict__ lu, const int8_t* __restrict__ piv,
+                                              const T* __restrict__ b, T* x, int* prog, int* abort_flag,
+                                              int* sticky_err, int q, int nstrips, int spin_limit,
+                                              unsigned char* smem, unsigned parity[2]) {
   constexpr int BS = NC * NC;
   constexpr int NOFF = 4 * BS, NE = NOFF + LU_E;
-  constexpr size_t STAGE = sgs_stage_bytes<NC, T>();
-  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr size_t STAGE = sgs_stage_bytes<NC, T, S>();
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   T* vals[2] = {reinterpret_cast<T*>(smem + 128), reinterpret_cast<T*>(smem + 128 + STAGE)};
   int8_t* pvs[2] = {reinterpret_cast<int8_t*>(smem + 128 + (size_t)NE * S * 32 * sizeof(T)),
@@ -309,24 +333,12 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
   const long long n = (long long)nx * ny, P = skew_slots(nx, ny);
-  if (lane == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
-    fence_proxy_async();
-  }
-  __syncwarp();
-  unsigned parity[2] = {0u, 0u};
-  // logical W, E, S, N -> physical block (1 W, 2 E, 3 S, 4 N) -> entry base in a stage
   const int oW = (FWD ? 0 : 1) * BS, oE = (FWD ? 1 : 0) * BS, oS = (FWD ? 2 : 3) * BS,
             oN = (FWD ? 3 : 2) * BS;
   const int lagk = FWD ? lane : 31 - lane;
   const int nsteps_full = nx + 31;
   const int wait_limit = spin_limit;
-  for (;;) {
-    int q = 0;
-    if (lane == 0) q = atomicAdd(&sync[0], 1);
-    q = __shfl_sync(FULL, q, 0);
-    if (q >= nstrips) return;
+  {
     const int ps = FWD ? q : nstrips - 1 - q;
     const long long line_base = (long long)ps * (nx + 31);
     // the strip's valid rows; in a forward sweep its last valid lane finishes
@@ -418,8 +430,8 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
             int p = 0, it = 0;
             do {
               if (lane == 0) {
-                p = ld_acquire(&sync[2 + q - 1]);
-                if (p < need && ld_acquire(&sync[1])) p = -1;
+                p = ld_acquire(&prog[q - 1]);
+                if (p < need && ld_acquire(abort_flag)) p = -1;
               }
               p = __shfl_sync(FULL, p, 0);
               if (p >= need || p < 0) break;
@@ -473,7 +485,7 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
         __syncwarp();
         if (lagk == 31 && act && q + 1 < nstrips && ((c + 1) % SGS_PUBLISH == 0 || c == nx - 1)) {
           __threadfence();
-          st_release(&sync[2 + q], c + 1);
+          st_release(&prog[q], c + 1);
         }
       }
       __syncwarp();
@@ -484,11 +496,44 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
     }
     if (failed) {
       // stop the other strips, then let this warp's copies land before leaving
-      if (lane == 0) st_release(&sync[1], 1);
+      if (lane == 0) st_release(abort_flag, 1);
       for (int st = 0; st < 2; ++st)
         if (inflight[st]) chunk_wait(&bar[st], parity[st], wait_limit);
-      return;
+      return false;
     }
+  }
+  return true;
+}
+
+// barriers of the warp's two staging buffers
+__device__ __forceinline__ void sgs_init_bars(unsigned char* smem) {
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    fence_proxy_async();
+  }
+  __syncwarp();
+}
+
+// one problem: strips claimed through the ticket sync[0]; sync[1] abort,
+// sync[2 + q] progress of the strip processed q-th
+template <int NC, typename T, bool FWD, int S>
+__global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __restrict__ blk,
+                                                  const T* __restrict__ lu, const int8_t* __restrict__ piv,
+                                                  const T* __restrict__ b, T* x, int* sync, int* sticky_err,
+                                                  int nstrips, int spin_limit) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  sgs_init_bars(smem);
+  unsigned parity[2] = {0u, 0u};
+  for (;;) {
+    int q = 0;
+    if (threadIdx.x == 0) q = atomicAdd(&sync[0], 1);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= nstrips) return;
+    if (!sgs_strip_run<NC, T, FWD, S>(nx, ny, blk, lu, piv, b, x, sync + 2, sync + 1, sticky_err, q, nstrips,
+                                      spin_limit, smem, parity))
+      return;
   }
 }
 
@@ -594,8 +639,8 @@ __global__ void k_coarse_exact(int nx, int ny, const T* __restrict__ blk, const 
 // (one CTA) and applied at every visit of the coarsest level.
 // aug: m x 2m working array (row-major), X: m x m column-major.
 template <int NC, typename T>
-__global__ void k_coarse_inverse(int nx, int ny, const T* __restrict__ blk, T* __restrict__ aug,
-                                 T* __restrict__ X, int* __restrict__ sing) {
+__device__ __forceinline__ void coarse_inverse_cta(int nx, int ny, const T* __restrict__ blk, T* __restrict__ aug,
+                                                   T* __restrict__ X, int* __restrict__ sing) {
   const int n = nx * ny, m = n * NC, w = 2 * m;
   const long long P = skew_slots(nx, ny);
   const int BS = NC * NC;
@@ -691,15 +736,26 @@ __global__ void k_coarse_inverse(int nx, int ny, const T* __restrict__ blk, T* _
   }
 }
 
+template <int NC, typename T>
+__global__ void k_coarse_inverse(int nx, int ny, const T* __restrict__ blk, T* __restrict__ aug,
+                                 T* __restrict__ X, int* __restrict__ sing) {
+  coarse_inverse_cta<NC, T>(nx, ny, blk, aug, X, sing);
+}
+
 // x = X b on the coarsest level (SoA vectors, cell-major unknowns)
 template <int NC, typename T>
-__global__ void k_coarse_apply(int n, const T* __restrict__ X, const T* __restrict__ b, T* __restrict__ x) {
+__device__ __forceinline__ void coarse_apply_row(int n, const T* __restrict__ X, const T* __restrict__ b,
+                                                 T* __restrict__ x, int u) {
   const int m = n * NC;
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= m) return;
   T acc = T(0);
   for (int jcol = 0; jcol < m; ++jcol) acc += X[(long long)jcol * m + u] * b[(long long)(jcol % NC) * n + jcol / NC];
   x[(long long)(u % NC) * n + u / NC] = acc;
+}
+
+template <int NC, typename T>
+__global__ void k_coarse_apply(int n, const T* __restrict__ X, const T* __restrict__ b, T* __restrict__ x) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n * NC) coarse_apply_row<NC, T>(n, X, b, x, u);
 }
 
 // ---- adjoint support ----------------------------------------------------------
@@ -804,6 +860,158 @@ __global__ void k_export(int nx, int ny, int nc, const T* __restrict__ blk, doub
       out[((long long)i * 5 + b) * BS + e] = (double)blk[((long long)b * BS + e) * P + si];
 }
 
+// ---- batched forms -------------------------------------------------------------
+// Same bodies as the single-problem kernels; problem from the block table.
+#define BATCH_PROLOGUE(bl)                                        \
+  const int p_ = batch_find((bl).bstart, (bl).B, blockIdx.x);     \
+  if (!(bl).mask[p_]) return;                                     \
+  const BItem* it = (bl).items + p_;                              \
+  const int idx = (blockIdx.x - (bl).bstart[p_]) * 128 + threadIdx.x;
+
+template <int NC, typename T>
+__global__ void __launch_bounds__(128) kb_lu_factor(BLaunch bl) {
+  BATCH_PROLOGUE(bl)
+  const int nx = it->L.nx, ny = it->L.ny;
+  if (idx < skew_slots(nx, ny))
+    lu_factor_slot<NC, T>(nx, ny, static_cast<const T*>(it->blk), static_cast<T*>(it->lu), it->piv, idx);
+}
+
+template <int NC, typename T>
+__global__ void __launch_bounds__(128) kb_galerkin(BLaunch bl, const BItem* fine) {
+  BATCH_PROLOGUE(bl)
+  if (idx >= it->L.n) return;
+  const BItem* f = fine + p_;
+  galerkin_cell<NC, T>(2, f->L.nx, f->L.ny, static_cast<const T*>(f->blk), static_cast<T*>(it->blk), idx);
+}
+
+template <int NC, typename T>
+__global__ void __launch_bounds__(128) kb_restrict(BLaunch bl, const BItem* fine) {
+  BATCH_PROLOGUE(bl)
+  if (idx >= it->L.n) return;
+  const BItem* f = fine + p_;
+  restrict_cell<NC, T>(2, f->L.nx, f->L.ny, static_cast<const T*>(f->blk), static_cast<const T*>(f->b),
+                       static_cast<const T*>(f->x), static_cast<T*>(it->b), idx);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) kb_prolong(BLaunch bl, const BItem* coarse) {
+  BATCH_PROLOGUE(bl)
+  if (idx >= it->L.n) return;
+  prolong_cell<T>(2, it->L.nc, it->L.nx, it->L.ny, static_cast<const T*>(coarse[p_].x), static_cast<T*>(it->x),
+                  idx);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) kb_fill_x(BLaunch bl) {
+  BATCH_PROLOGUE(bl)
+  const int n = it->L.n;
+  if (idx >= n) return;
+  T* x = static_cast<T*>(it->x);
+  for (int s = 0; s < it->L.nc; ++s) x[(long long)s * n + idx] = T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) kb_neg_residual(BLaunch bl) {
+  BATCH_PROLOGUE(bl)
+  const int n = it->L.n;
+  if (idx >= n) return;
+  T* b = static_cast<T*>(it->b);
+  for (int s = 0; s < it->L.nc; ++s)
+    b[(long long)s * n + idx] = static_cast<T>(-1.0 * it->R[(long long)s * n + idx]);
+}
+#undef BATCH_PROLOGUE
+
+// per-problem fixed-order sums of ||R_i||_1: the partial / final trees of
+// launch_sum with the problem's own partial count (blockIdx.y = problem)
+__device__ __forceinline__ int sum_partials(int n) {
+  int g = (n + 255) / 256;
+  return g > 1024 ? 1024 : (g < 1 ? 1 : g);
+}
+
+__global__ void kb_sum_partial(const BItem* items, const int* mask) {
+  const int p = blockIdx.y;
+  if (!mask[p]) return;
+  const int n = items[p].L.n, g = sum_partials(n);
+  if ((int)blockIdx.x >= g) return;
+  const double* v = items[p].rn;
+  __shared__ double sh[256];
+  double a = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += g * blockDim.x) a += v[i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) items[p].red[blockIdx.x] = sh[0];
+}
+
+__global__ void kb_sum_final(const BItem* items, const int* mask, double* out) {
+  const int p = blockIdx.x;
+  if (!mask[p]) return;
+  const int np = sum_partials(items[p].L.n);
+  const double* part = items[p].red;
+  __shared__ double sh[256];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) a += part[i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[p] = sh[0];
+}
+
+// SGS over a batch: warps claim (problem, strip) tickets in order (strip
+// index first), so a strip only ever waits for the previous strip of its own
+// problem, which a running warp already owns.  sync: [0] ticket, [1] abort,
+// [2 + strip0 + q] progress.
+template <int NC, typename T, bool FWD, int S>
+__global__ void __launch_bounds__(32, 1) kb_sgs_strip(const BItem* __restrict__ items,
+                                                      const int2* __restrict__ tickets, int ntickets,
+                                                      const int* __restrict__ mask, int* sync, int* sticky_err,
+                                                      int spin_limit) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  sgs_init_bars(smem);
+  unsigned parity[2] = {0u, 0u};
+  for (;;) {
+    int t = 0;
+    if (threadIdx.x == 0) t = atomicAdd(&sync[0], 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= ntickets) return;
+    const int2 tk = tickets[t];
+    if (!mask[tk.x]) continue;
+    const BItem* it = items + tk.x;
+    const int nx = it->L.nx, ny = it->L.ny;
+    if (!sgs_strip_run<NC, T, FWD, S>(nx, ny, static_cast<const T*>(it->blk), static_cast<const T*>(it->lu),
+                                      it->piv, static_cast<const T*>(it->b), static_cast<T*>(it->x),
+                                      sync + 2 + it->strip0, sync + 1, sticky_err, tk.y, (ny + 31) / 32,
+                                      spin_limit, smem, parity))
+      return;
+  }
+}
+
+template <int NC, typename T>
+__global__ void __launch_bounds__(1024) kb_coarse_inverse(const BItem* items, const int* mask) {
+  const int p = blockIdx.x;
+  if (!mask[p]) return;
+  const BItem* it = items + p;
+  coarse_inverse_cta<NC, T>(it->L.nx, it->L.ny, static_cast<const T*>(it->blk), static_cast<T*>(it->caug),
+                            static_cast<T*>(it->cinv), it->csing);
+}
+
+template <int NC, typename T>
+__global__ void __launch_bounds__(128) kb_coarse_apply(const BItem* items, const int* mask) {
+  const int p = blockIdx.y;
+  if (!mask[p]) return;
+  const BItem* it = items + p;
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < it->L.n * NC)
+    coarse_apply_row<NC, T>(it->L.n, static_cast<const T*>(it->cinv), static_cast<const T*>(it->b),
+                            static_cast<T*>(it->x), u);
+}
+
 }  // namespace
 
 // ---- launch wrappers ----------------------------------------------------------
@@ -862,15 +1070,16 @@ void launch_prolong(int dim, int nc, int nxf, int nyf, const void* xc, void* xf,
 template <int NC, typename T, bool F>
 static void sgs_launch(int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
                        const void* b, void* x, int* sync, int* sticky, cudaStream_t st) {
+  constexpr int S = SgsChunk<T>::S;
   const int nstrips = (ny + 31) / 32;
-  const size_t smem = sgs_smem_bytes<NC, T>();
+  const size_t smem = sgs_smem_bytes<NC, T, S>();
   static bool configured = false;   // per template instance
   if (!configured) {
-    cudaFuncSetAttribute(k_sgs_strip<NC, T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_sgs_strip<NC, T, F, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
   }
-  k_sgs_strip<NC, T, F><<<nstrips, 32, smem, st>>>(nx, ny, (const T*)blk, (const T*)lu, piv,
-                                                    (const T*)b, (T*)x, sync, sticky, nstrips, 1 << 22);
+  k_sgs_strip<NC, T, F, S><<<nstrips, 32, smem, st>>>(nx, ny, (const T*)blk, (const T*)lu, piv,
+                                                       (const T*)b, (T*)x, sync, sticky, nstrips, 1 << 22);
 }
 
 void launch_sgs_sweep(int nc, int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
@@ -974,6 +1183,113 @@ void launch_blocks_export(int nx, int ny, int nc, const void* blk, int fp32, dou
   const int n = nx * ny;
   if (fp32) k_export<float><<<nblk(n, 128), 128, 0, st>>>(nx, ny, nc, (const float*)blk, out);
   else k_export<double><<<nblk(n, 128), 128, 0, st>>>(nx, ny, nc, (const double*)blk, out);
+}
+
+// ---- batched launchers ----------------------------------------------------------
+
+void launch_b_sum(const BItem* items, const int* mask, int B, int max_n, double* out, cudaStream_t st) {
+  count_launches(2);
+  int gmax = nblk(max_n, 256);
+  gmax = gmax > 1024 ? 1024 : (gmax < 1 ? 1 : gmax);
+  kb_sum_partial<<<dim3(gmax, B), 256, 0, st>>>(items, mask);
+  kb_sum_final<<<B, 256, 0, st>>>(items, mask, out);
+}
+
+void launch_b_lu_factor(const BLaunch& slots, int fp32, cudaStream_t st) {
+  count_launches(1);
+  if (slots.nblocks <= 0) return;
+  if (fp32) kb_lu_factor<3, float><<<slots.nblocks, 128, 0, st>>>(slots);
+  else kb_lu_factor<3, double><<<slots.nblocks, 128, 0, st>>>(slots);
+}
+
+void launch_b_galerkin(const BLaunch& coarse, const BItem* fine_items, int fp32, cudaStream_t st) {
+  count_launches(1);
+  if (coarse.nblocks <= 0) return;
+  if (fp32) kb_galerkin<3, float><<<coarse.nblocks, 128, 0, st>>>(coarse, fine_items);
+  else kb_galerkin<3, double><<<coarse.nblocks, 128, 0, st>>>(coarse, fine_items);
+}
+
+void launch_b_restrict(const BLaunch& coarse, const BItem* fine_items, int fp32, cudaStream_t st) {
+  count_launches(1);
+  if (coarse.nblocks <= 0) return;
+  if (fp32) kb_restrict<3, float><<<coarse.nblocks, 128, 0, st>>>(coarse, fine_items);
+  else kb_restrict<3, double><<<coarse.nblocks, 128, 0, st>>>(coarse, fine_items);
+}
+
+void launch_b_prolong(const BLaunch& fine, const BItem* coarse_items, int fp32, cudaStream_t st) {
+  count_launches(1);
+  if (fine.nblocks <= 0) return;
+  if (fp32) kb_prolong<float><<<fine.nblocks, 128, 0, st>>>(fine, coarse_items);
+  else kb_prolong<double><<<fine.nblocks, 128, 0, st>>>(fine, coarse_items);
+}
+
+void launch_b_fill_x(const BLaunch& cells, int fp32, cudaStream_t st) {
+  count_launches(1);
+  if (cells.nblocks <= 0) return;
+  if (fp32) kb_fill_x<float><<<cells.nblocks, 128, 0, st>>>(cells);
+  else kb_fill_x<double><<<cells.nblocks, 128, 0, st>>>(cells);
+}
+
+void launch_b_neg_residual(const BLaunch& cells, int fp32, cudaStream_t st) {
+  count_launches(1);
+  if (cells.nblocks <= 0) return;
+  if (fp32) kb_neg_residual<float><<<cells.nblocks, 128, 0, st>>>(cells);
+  else kb_neg_residual<double><<<cells.nblocks, 128, 0, st>>>(cells);
+}
+
+template <typename T, bool F, int S>
+static void b_sgs_launch(const BItem* items, const int2* tickets, int ntickets, const int* mask, int* sync,
+                         int* sticky, cudaStream_t st) {
+  const size_t smem = sgs_smem_bytes<3, T, S>();
+  static int per_sm = 0;   // per template instance
+  static int nsm = 0;
+  if (per_sm == 0) {
+    cudaFuncSetAttribute(kb_sgs_strip<3, T, F, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_sgs_strip<3, T, F, S>, 32, smem);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (per_sm < 1) per_sm = 1;
+  }
+  // warps resident at once (each loops over tickets), never more than tickets
+  const int grid = ntickets < per_sm * nsm ? ntickets : per_sm * nsm;
+  kb_sgs_strip<3, T, F, S><<<grid, 32, smem, st>>>(items, tickets, ntickets, mask, sync, sticky, 1 << 22);
+}
+
+size_t b_sgs_smem_bytes(int fp32, int chunk) {
+  if (fp32) return chunk == 4 ? sgs_smem_bytes<3, float, 4>() : chunk == 8 ? sgs_smem_bytes<3, float, 8>()
+                                                                           : sgs_smem_bytes<3, float, 16>();
+  return chunk == 2 ? sgs_smem_bytes<3, double, 2>() : chunk == 4 ? sgs_smem_bytes<3, double, 4>()
+                                                                  : sgs_smem_bytes<3, double, 8>();
+}
+
+void launch_b_sgs_sweep(const BItem* items, const int2* tickets, int ntickets, int nslots, const int* mask,
+                        int forward, int fp32, int chunk, int* sync, int* sticky_err, cudaStream_t st) {
+  count_launches(1);
+  if (ntickets <= 0) return;
+  cudaMemsetAsync(sync, 0, sizeof(int) * (2 + nslots), st);
+#define BS_(T, F, S) b_sgs_launch<T, F, S>(items, tickets, ntickets, mask, sync, sticky_err, st)
+  if (fp32) {
+    if (forward) { if (chunk == 4) BS_(float, true, 4); else if (chunk == 8) BS_(float, true, 8); else BS_(float, true, 16); }
+    else { if (chunk == 4) BS_(float, false, 4); else if (chunk == 8) BS_(float, false, 8); else BS_(float, false, 16); }
+  } else {
+    if (forward) { if (chunk == 2) BS_(double, true, 2); else if (chunk == 4) BS_(double, true, 4); else BS_(double, true, 8); }
+    else { if (chunk == 2) BS_(double, false, 2); else if (chunk == 4) BS_(double, false, 4); else BS_(double, false, 8); }
+  }
+#undef BS_
+}
+
+void launch_b_coarse_inverse(const BItem* items, const int* mask, int B, int fp32, cudaStream_t st) {
+  count_launches(1);
+  if (fp32) kb_coarse_inverse<3, float><<<B, 1024, 0, st>>>(items, mask);
+  else kb_coarse_inverse<3, double><<<B, 1024, 0, st>>>(items, mask);
+}
+
+void launch_b_coarse_apply(const BItem* items, const int* mask, int B, int max_m, int fp32, cudaStream_t st) {
+  count_launches(1);
+  const dim3 g(nblk(max_m > 0 ? max_m : 1, 128), B);
+  if (fp32) kb_coarse_apply<3, float><<<g, 128, 0, st>>>(items, mask);
+  else kb_coarse_apply<3, double><<<g, 128, 0, st>>>(items, mask);
 }
 
 }  // namespace swnmg

@@ -81,11 +81,21 @@ def lib():
         L.swnmg_residual_noalloc.restype = C.c_int
         L.swnmg_adjoint.argtypes = [vp, vp, vp, vp, vp, dp, C.c_int32, C.c_double, C.POINTER(C.c_int32)]
         L.swnmg_level_cells.argtypes = [vp, C.c_int32]
+        L.swnmg_batch_create.argtypes = [C.POINTER(Problem), C.POINTER(C.c_int32), C.c_int32, C.POINTER(Params),
+                                         C.POINTER(vp), vp, C.POINTER(vp)]
+        L.swnmg_batch_destroy.argtypes = [vp]
+        L.swnmg_batch_last_error.argtypes = [vp]
+        L.swnmg_batch_last_error.restype = C.c_char_p
+        L.swnmg_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(Stats)]
+        L.swnmg_batch_set_graph.argtypes = [vp, C.c_int32]
+        L.swnmg_batch_tune.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.swnmg_batch_set_tuning.argtypes = [vp, C.POINTER(C.c_int32), C.c_int32]
         L.swnmg_level_cells.restype = C.c_int64
         for f in ("swnmg_default_params", "swnmg_create", "swnmg_destroy", "swnmg_set_params",
                   "swnmg_residual", "swnmg_jacobian", "swnmg_get_blocks", "swnmg_vcycle",
                   "swnmg_sgs_sweep", "swnmg_blusgs", "swnmg_solve", "swnmg_set_timing",
-                  "swnmg_get_timing", "swnmg_adjoint"):
+                  "swnmg_get_timing", "swnmg_adjoint", "swnmg_batch_create", "swnmg_batch_destroy",
+                  "swnmg_batch_solve", "swnmg_batch_set_graph", "swnmg_batch_tune", "swnmg_batch_set_tuning"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -245,6 +255,93 @@ class Solver:
         if check or rc != ERR_NOT_CONVERGED:
             self._check(rc)
         return lam, dRz, np.array(list(dRq)), cyc.value
+
+
+def _stats_dict(st, n_levels):
+    return {"status": st.status, "n_newton": st.n_newton, "n_vcycles": st.n_vcycles,
+            "blusgs_sweeps": list(st.blusgs_sweeps)[:n_levels + 1],
+            "init_res": st.init_res, "final_res": st.final_res,
+            "res_hist": list(st.res_hist)[:min(st.n_newton, HIST)],
+            "ms_step1": st.ms_step1, "ms_newton": st.ms_newton}
+
+
+class BatchSolver:
+    """Many independent 2D problems solved together (swnmg_batch_*).  Each
+    problem keeps its own grid, bed, boundary data and number of levels
+    (prob.params.n_levels); the other parameters are shared (``params``,
+    default the first problem's)."""
+
+    SGS_LEVELS = 13
+
+    def __init__(self, probs, params: W.Params | None = None, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("swnmg needs a CUDA device (no CPU fallback)")
+        self.L = lib()
+        self.probs = list(probs)
+        self.B = len(self.probs)
+        self.params = params or self.probs[0].params
+        self.stream = stream or torch.cuda.current_stream()
+        self.z = [torch.as_tensor(np.ascontiguousarray(p.z), dtype=torch.float64, device="cuda")
+                  for p in self.probs]
+        arr = (Problem * self.B)(*[make_problem(p) for p in self.probs])
+        nl = (C.c_int32 * self.B)(*[p.params.n_levels for p in self.probs])
+        zp = (C.c_void_p * self.B)(*[t.data_ptr() for t in self.z])
+        self._pr = make_params(self.params)
+        h = C.c_void_p()
+        rc = self.L.swnmg_batch_create(arr, nl, self.B, C.byref(self._pr), zp, C.c_void_p(self.stream.cuda_stream),
+                                       C.byref(h))
+        if rc != OK:
+            raise SwnmgError(rc, self.L.swnmg_batch_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise SwnmgError(rc, self.L.swnmg_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.swnmg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def states(self):
+        """Initial states of the problems as float64 CUDA tensors (3, n)."""
+        return [torch.as_tensor(np.ascontiguousarray(p.U0), dtype=torch.float64, device="cuda").contiguous()
+                for p in self.probs]
+
+    def _ptrs(self, Us):
+        if len(Us) != self.B:
+            raise ValueError("expected %d states" % self.B)
+        return (C.c_void_p * self.B)(*[_ptr(u).value for u in Us])
+
+    def solve(self, Us, check=False):
+        """Algorithm 1 on every problem in place; returns one counters dict each."""
+        st = (Stats * self.B)()
+        rc = self.L.swnmg_batch_solve(self.h, self._ptrs(Us), st)
+        if check:
+            self._check(rc)
+        elif rc not in (OK, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_DIVERGED):
+            self._check(rc)
+        return [_stats_dict(st[p], self.probs[p].params.n_levels) for p in range(self.B)]
+
+    def set_graph(self, enable=True):
+        self._check(self.L.swnmg_batch_set_graph(self.h, 1 if enable else 0))
+
+    def tune(self, Us):
+        """Autotuner; returns (SGS chunk per level, BLU-SGS grid blocks)."""
+        ch = (C.c_int32 * self.SGS_LEVELS)()
+        nb = C.c_int32(0)
+        self._check(self.L.swnmg_batch_tune(self.h, self._ptrs(Us), ch, C.byref(nb)))
+        return list(ch), nb.value
+
+    def set_tuning(self, chunks=None, blusgs_blocks=0):
+        ch = (C.c_int32 * self.SGS_LEVELS)(*chunks) if chunks is not None else None
+        self._check(self.L.swnmg_batch_set_tuning(self.h, ch, blusgs_blocks))
 
 
 def with_discharge(prob: W.Problem, q) -> W.Problem:

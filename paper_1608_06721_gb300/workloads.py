@@ -271,6 +271,27 @@ def channel_2d(seed: int = 301, nx: int = 1024, ny: int = 1024, n_bumps: int = 1
     return p
 
 
+def batch_channels(seed: int = 401, count: int = 64, sizes=(128, 256, 512, 1024), coarsest: int = 8,
+                   precision: int = PREC_MIXED) -> list:
+    """Batched workload: ``count`` independent channel problems.  A generator
+    seeded with ``seed`` draws, per problem in order, the grid n x n with n
+    uniform in ``sizes`` and the bump count uniform in 4..16; problem p then
+    follows channel_2d with seed 1000 seed + p (bumps, inflow hu ~ U[0.3,
+    1.5], the same dry redraw rule).  Levels: coarsest grid ``coarsest`` x
+    ``coarsest`` (log2(n / coarsest) levels); W-cycles, eps_p = 2, exact
+    coarsest solve, as for the single 1024 x 1024 workload."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for p in range(count):
+        n = int(rng.choice(np.asarray(sizes)))
+        nb = int(rng.integers(4, 17))
+        nl = int(round(np.log2(n // coarsest)))
+        pr = channel_2d(seed=1000 * seed + p, nx=n, ny=n, n_bumps=nb, q_range=(0.3, 1.5), n_levels=nl,
+                        precision=precision)
+        out.append(pr.with_params(gamma=2, eps_p=2.0, coarse_sweeps=0))
+    return out
+
+
 def transcritical_bump_2d(nx: int, ny: int, n_levels: int = 3) -> Problem:
     """Example 3.6: z = 0.2 - 0.05((x-10)^2 + y^2) inside radius 2 on
     [0,25]x[-5,5]; hu = 1.53 at x = 0, h = 0.52 at x = 25, reflective
