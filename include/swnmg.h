@@ -287,16 +287,17 @@ SWNMG_API swnmg_status swnmg_batch_solve(swnmg_batch* bt, double* const* U_dev, 
 SWNMG_API swnmg_status swnmg_batch_set_graph(swnmg_batch* bt, int32_t enable);
 
 /* Autotuner: times the candidate shared-memory staging depths of the SGS
- * sweep on every level and the candidate BLU-SGS grid sizes on this batch
- * (BLU-SGS on scratch copies of U_dev, which is not modified) and keeps the
- * fastest.  sgs_chunk (13 entries) and blusgs_blocks (nullable) receive the
+ * sweep and the candidate BLU-SGS grid sizes (a quarter of the SMs up to
+ * the co-resident limit) on every level of this batch (BLU-SGS on scratch
+ * copies of U_dev, which is not modified) and keeps the fastest per level.
+ * sgs_chunk and blusgs_blocks (13 entries each, nullable) receive the
  * choices.  Tuning changes speed only, never results.  Synchronises. */
 SWNMG_API swnmg_status swnmg_batch_tune(swnmg_batch* bt, double* const* U_dev, int32_t* sgs_chunk,
                                         int32_t* blusgs_blocks);
 
 /* Sets the tuning by hand: sgs_chunk (13 entries, each 4, 8 or 16 in MIXED
- * precision and 2, 4 or 8 in FP64; NULL keeps them), blusgs_blocks (<= 0
- * keeps it; otherwise at most the co-resident limit). */
+ * precision and 2, 4 or 8 in FP64; NULL keeps them), blusgs_blocks for
+ * every level (<= 0 keeps them; otherwise at most the co-resident limit). */
 SWNMG_API swnmg_status swnmg_batch_set_tuning(swnmg_batch* bt, const int32_t* sgs_chunk,
                                               int32_t blusgs_blocks);
 

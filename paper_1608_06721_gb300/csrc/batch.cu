@@ -66,7 +66,8 @@ struct swnmg_batch {
   int* h_sticky = nullptr;           // pinned
   // tuning
   int sgs_chunk[MAXL];
-  int blusgs_blocks = 0, blusgs_max = 0;
+  int blusgs_blocks[MAXL];
+  int blusgs_max = 0;
   // CUDA graph of the N_mg cycles
   bool use_graph = false;
   cudaGraphExec_t cyc_exec = nullptr;
@@ -172,7 +173,7 @@ swnmg_status residual_sums(swnmg_batch* b, int l, int slot, std::vector<double>&
 void blusgs(swnmg_batch* b, int l, int slot, int forward) {
   const int ns = steps_of(b, l, slot);
   if (ns == 0) return;
-  launch_b_blusgs_sweep(tab(b, l), mk(b, slot), b->B, ns, forward, b->blusgs_blocks, b->bl_sync, b->sticky,
+  launch_b_blusgs_sweep(tab(b, l), mk(b, slot), b->B, ns, forward, b->blusgs_blocks[l], b->bl_sync, b->sticky,
                         b->st);
 }
 
@@ -449,7 +450,7 @@ SWNMG_API swnmg_status swnmg_batch_create(const swnmg_problem* probs, const int3
     rc = bfail(b, SWNMG_ERR_CUDA, "BLU-SGS kernel cannot be resident");
     goto fail_out;
   }
-  b->blusgs_blocks = b->nsm;
+  for (int l = 0; l < MAXL; ++l) b->blusgs_blocks[l] = b->nsm;
   BTRY(cudaDeviceSynchronize());
 #undef BTRY
   *out = b;
@@ -483,7 +484,8 @@ SWNMG_API swnmg_status swnmg_batch_set_tuning(swnmg_batch* b, const int32_t* chu
   BCUDA(b, cudaStreamSynchronize(b->st));
   if (chunk)
     for (int l = 0; l < MAXL; ++l) b->sgs_chunk[l] = chunk[l];
-  if (blocks > 0) b->blusgs_blocks = blocks;
+  if (blocks > 0)
+    for (int l = 0; l < MAXL; ++l) b->blusgs_blocks[l] = blocks;
   if (b->cyc_exec) {   // the graph holds the old launch shapes
     cudaGraphExecDestroy(b->cyc_exec);
     b->cyc_exec = nullptr;
@@ -544,7 +546,8 @@ SWNMG_API swnmg_status swnmg_batch_tune(swnmg_batch* b, double* const* U, int32_
     b->sgs_chunk[l] = pick;
   }
   if ((s = check_sticky(b)) != SWNMG_OK) return s;
-  // BLU-SGS grid: one to all co-resident blocks per SM, on copies of U
+  // BLU-SGS grid per level, on copies of U averaged down the levels (the
+  // Step 1 states of levels >= 1 are rebuilt by every solve)
   for (int p = 0; p < b->B; ++p) {
     const size_t bytes = sizeof(double) * 3 * (size_t)b->h_items[p].L.n;
     cudaError_t e = cudaMalloc((void**)&scratch[p], bytes);
@@ -555,21 +558,25 @@ SWNMG_API swnmg_status swnmg_batch_tune(swnmg_batch* b, double* const* U, int32_
     }
   }
   if ((s = set_level0_state(b, scratch.data())) != SWNMG_OK) return s;
-  const int per_sm = b->blusgs_max / b->nsm;
-  float best = 1e30f;
-  int pick = b->blusgs_blocks;
-  for (int m = 1; m <= per_sm; m *= 2) {
-    b->blusgs_blocks = m * b->nsm;
-    blusgs(b, 0, M_ACT, 1);   // warm-up
-    cudaEventRecord(e0, b->st);
-    blusgs(b, 0, M_ACT, 1);
-    blusgs(b, 0, M_ACT, 0);
-    cudaEventRecord(e1, b->st);
-    cudaEventSynchronize(e1);
-    const float ms = time_ms(e0, e1);
-    if (ms < best) { best = ms; pick = b->blusgs_blocks; }
+  for (int l = 0; l < b->maxNL; ++l) launch_b_average(bl(b, l + 1, D_CELLS, M_DOWN + l), tab(b, l), b->st);
+  for (int l = 0; l <= b->maxNL; ++l) {
+    std::vector<int> cand;
+    for (int m = b->nsm / 4; m <= b->blusgs_max; m *= 2) cand.push_back(m);
+    float best = 1e30f;
+    int pick = b->blusgs_blocks[l];
+    for (int nb : cand) {
+      b->blusgs_blocks[l] = nb;
+      blusgs(b, l, M_HI + l, 1);   // warm-up
+      cudaEventRecord(e0, b->st);
+      blusgs(b, l, M_HI + l, 1);
+      blusgs(b, l, M_HI + l, 0);
+      cudaEventRecord(e1, b->st);
+      cudaEventSynchronize(e1);
+      const float ms = time_ms(e0, e1);
+      if (ms < best) { best = ms; pick = nb; }
+    }
+    b->blusgs_blocks[l] = pick;
   }
-  b->blusgs_blocks = pick;
   cudaError_t e = cudaStreamSynchronize(b->st);
   for (auto* q : scratch) if (q) cudaFree(q);
   cudaEventDestroy(e0);
@@ -583,7 +590,8 @@ SWNMG_API swnmg_status swnmg_batch_tune(swnmg_batch* b, double* const* U, int32_
   }
   if (chunk_out)
     for (int l = 0; l < MAXL; ++l) chunk_out[l] = b->sgs_chunk[l];
-  if (blocks_out) *blocks_out = b->blusgs_blocks;
+  if (blocks_out)
+    for (int l = 0; l < MAXL; ++l) blocks_out[l] = b->blusgs_blocks[l];
   return SWNMG_OK;
 }
 

@@ -333,11 +333,11 @@ class BatchSolver:
         self._check(self.L.swnmg_batch_set_graph(self.h, 1 if enable else 0))
 
     def tune(self, Us):
-        """Autotuner; returns (SGS chunk per level, BLU-SGS grid blocks)."""
+        """Autotuner; returns (SGS chunk per level, BLU-SGS grid blocks per level)."""
         ch = (C.c_int32 * self.SGS_LEVELS)()
-        nb = C.c_int32(0)
-        self._check(self.L.swnmg_batch_tune(self.h, self._ptrs(Us), ch, C.byref(nb)))
-        return list(ch), nb.value
+        nb = (C.c_int32 * self.SGS_LEVELS)()
+        self._check(self.L.swnmg_batch_tune(self.h, self._ptrs(Us), ch, nb))
+        return list(ch), list(nb)
 
     def set_tuning(self, chunks=None, blusgs_blocks=0):
         ch = (C.c_int32 * self.SGS_LEVELS)(*chunks) if chunks is not None else None

@@ -64,9 +64,9 @@ def test_batch_graph_and_tuning_do_not_change_results(swnmg):
     base = [u.clone() for u in U0]
     info0 = bt.solve(base)
     chunks, blocks = bt.tune(bt.states())
-    assert all(c in (4, 8, 16) for c in chunks) and blocks > 0
+    assert all(c in (4, 8, 16) for c in chunks) and min(blocks) > 0
     bt.set_graph(True)
-    for ch, nb in ((chunks, blocks), ([4] * 13, 0), ([8] * 13, 0)):
+    for ch, nb in ((chunks, 0), ([4] * 13, 38), ([8] * 13, max(blocks))):
         bt.set_tuning(ch, nb)
         Us = bt.states()
         infos = bt.solve(Us)
