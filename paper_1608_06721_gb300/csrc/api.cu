@@ -1,5 +1,6 @@
 // api.cu -- the C ABI (include/swnmg.h): context, operator hierarchy and the
 // host side of Algorithm 1 (NMGM) and Algorithm 0 (gamma-cycle).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <vector>
@@ -188,7 +189,7 @@ void sgs_half(swnmg_ctx* c, const Hier& H, int l, int forward) {
 void blusgs_half(swnmg_ctx* c, int l, double* U, int forward) {
   DevLevel L = dev_level(c, l);
   TimedScope ts(c, l == 0 ? SWNMG_T_BLUSGS : SWNMG_T_BLUSGS_COARSE, L.n);
-  launch_blusgs_sweep(L, c->lv[l].z, U, forward, c->sgs_sync, c->sticky, c->st);
+  launch_blusgs_sweep(L, c->lv[l].z, U, c->ghost, forward, c->sgs_sync, c->sticky, c->st);
 }
 
 // Algorithm 0 on level l of hierarchy H (lv[l].b, lv[l].x)
@@ -308,6 +309,7 @@ void free_ctx(swnmg_ctx* c) {
   if (c->derr) cudaFree(c->derr);
   if (c->sgs_sync) cudaFree(c->sgs_sync);
   if (c->sticky) cudaFree(c->sticky);
+  if (c->ghost) cudaFree(c->ghost);
   if (c->hbuf) cudaFreeHost(c->hbuf);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
@@ -422,6 +424,7 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
     ALLOC(c->derr, sizeof(int));
     ALLOC(c->sgs_sync, sizeof(int) * (2 + (v0.ny + 31) / 32 + 8));
     ALLOC(c->sticky, sizeof(int));
+    ALLOC(c->ghost, sizeof(double) * 4 * (size_t)std::max(v0.nx, v0.ny) * (c->nc + 1) * 3);
   }
   {
     const Level& vc = c->lv[c->nl];

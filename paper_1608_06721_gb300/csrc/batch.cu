@@ -374,6 +374,7 @@ SWNMG_API swnmg_status swnmg_batch_create(const swnmg_problem* probs, const int3
         it.rn = c->rn;
         it.eb = c->eb;
         it.red = c->red;
+        it.ghost = c->ghost;
         it.blk = v.blk;
         it.lu = v.lu;
         it.piv = v.piv;

@@ -71,6 +71,7 @@ struct BItem {
   int8_t* piv;
   void* b;
   void* x;
+  double* ghost;                // BLU-SGS ghost scratch (problem workspace)
   void* cinv;                   // coarsest level: guarded inverse and its scratch
   void* caug;
   int* csing;
@@ -114,7 +115,8 @@ void launch_residual(const DevLevel& L, const double* z, const double* U, double
                      double* edge_buf, cudaStream_t st);
 void launch_jacobian(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
                      double* edge_buf, void* blk, int fp32, cudaStream_t st);   // blk skewed
-void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forward, int* sync,
+// gbuf: 4 * max(nx, ny) * (nc + 1) * 3 doubles of ghost scratch
+void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
                          int* sticky_err, cudaStream_t st);
 void launch_newton_update(int n, int nc, double tau, double h_eps, double* U, const void* dU,
                           int dU_fp32, cudaStream_t st);

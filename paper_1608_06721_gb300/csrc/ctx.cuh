@@ -45,6 +45,7 @@ struct swnmg_ctx {
   void* caug = nullptr;     // its m x 2m elimination array
   int* csing = nullptr;
   int* derr = nullptr;
+  double* ghost = nullptr;  // BLU-SGS boundary ghost states (4 * max(nx, ny) * (nc + 1) * 3)
   int* sgs_sync = nullptr;  // ticket / abort / per-strip progress of the wavefront sweeps
   int* sticky = nullptr;    // set by a device wait that ran out of its bound
   double* hbuf = nullptr;   // pinned host scalars

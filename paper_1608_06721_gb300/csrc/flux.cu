@@ -421,51 +421,75 @@ __global__ void k_jac_cells(DevLevel L, const double* __restrict__ eb, double* _
 // ---- block solve with the same elimination as the reference definition -----
 // Gaussian elimination with partial pivoting (largest |entry|, lowest row on
 // ties); a pivot <= 1e-14 max|D| marks its unknown singular (correction 0).
+// Every index is a compile-time constant (row swaps and the permutation are
+// selections), so the block stays in registers; the arithmetic is the
+// elimination's, operation by operation.
 template <int NC>
-__device__ void small_solve(double m[NC * NC], const double b[NC], double x[NC]) {
+__device__ __forceinline__ void small_solve(double m[NC * NC], const double b[NC], double x[NC]) {
   double amax = 0.0;
+#pragma unroll
   for (int e = 0; e < NC * NC; ++e) {
     const double a = fabs(m[e]);
     if (a > amax) amax = a;
   }
   const double tiny = 1e-14 * amax;
-  int perm[NC], sing[NC];
-  for (int r = 0; r < NC; ++r) { perm[r] = r; sing[r] = 0; }
+  int perm[NC];
+  bool sing[NC];
+#pragma unroll
+  for (int r = 0; r < NC; ++r) { perm[r] = r; sing[r] = false; }
+#pragma unroll
   for (int col = 0; col < NC; ++col) {
     int p = col;
     double best = fabs(m[col * NC + col]);
+#pragma unroll
     for (int r = col + 1; r < NC; ++r) {
       const double a = fabs(m[r * NC + col]);
       if (a > best) { best = a; p = r; }
     }
-    if (p != col) {
-      for (int k = 0; k < NC; ++k) {
-        const double t = m[col * NC + k];
-        m[col * NC + k] = m[p * NC + k];
-        m[p * NC + k] = t;
+#pragma unroll
+    for (int r = col + 1; r < NC; ++r)
+      if (r == p) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          const double t = m[col * NC + k];
+          m[col * NC + k] = m[r * NC + k];
+          m[r * NC + k] = t;
+        }
+        const int t = perm[col]; perm[col] = perm[r]; perm[r] = t;
       }
-      const int t = perm[col]; perm[col] = perm[p]; perm[p] = t;
-    }
     if (!(best > tiny)) {
-      sing[col] = 1;
+      sing[col] = true;
+#pragma unroll
       for (int r = col + 1; r < NC; ++r) m[r * NC + col] = 0.0;
-      continue;
-    }
-    for (int r = col + 1; r < NC; ++r) {
-      const double l = m[r * NC + col] / m[col * NC + col];
-      m[r * NC + col] = l;
-      for (int k = col + 1; k < NC; ++k) m[r * NC + k] = m[r * NC + k] - l * m[col * NC + k];
+    } else {
+#pragma unroll
+      for (int r = col + 1; r < NC; ++r) {
+        const double l = m[r * NC + col] / m[col * NC + col];
+        m[r * NC + col] = l;
+#pragma unroll
+        for (int k = col + 1; k < NC; ++k) m[r * NC + k] = m[r * NC + k] - l * m[col * NC + k];
+      }
     }
   }
   double y[NC];
-  for (int r = 0; r < NC; ++r) y[r] = b[perm[r]];
+#pragma unroll
+  for (int r = 0; r < NC; ++r) {
+    double v = b[0];
+#pragma unroll
+    for (int k = 1; k < NC; ++k)
+      if (perm[r] == k) v = b[k];
+    y[r] = v;
+  }
+#pragma unroll
   for (int r = 0; r < NC; ++r)
+#pragma unroll
     for (int k = 0; k < r; ++k) y[r] = y[r] - m[r * NC + k] * y[k];
+#pragma unroll
   for (int r = NC - 1; r >= 0; --r) {
-    if (sing[r]) { x[r] = 0.0; continue; }
     double s = y[r];
+#pragma unroll
     for (int k = r + 1; k < NC; ++k) s = s - m[r * NC + k] * x[k];
-    x[r] = s / m[r * NC + r];
+    x[r] = sing[r] ? 0.0 : s / m[r * NC + r];
   }
 }
 
@@ -484,12 +508,63 @@ __device__ void small_solve(double m[NC * NC], const double b[NC], double x[NC])
 template <bool L2>
 __device__ __forceinline__ double ldU(const double* p) { return L2 ? __ldcg(p) : *p; }
 
+// The cell's primitive state along `axis` in perturbation p (p = k + 1 adds
+// eps to component k); rinv = 1/h of the unperturbed cell (0 when dry).
+// 1/h is recomputed only when the depth is the perturbed component.
+template <int NC>
+__device__ __forceinline__ Prim pert_prim(const DevLevel& L, const double c[NC], int p, double rinv, int axis) {
+  Prim me;
+  me.h = c[0];
+  const double qa = (NC == 2) ? c[1] : (axis == 0 ? c[1] : c[NC - 1]);
+  const double qb = (NC == 2) ? 0.0 : (axis == 0 ? c[NC - 1] : c[1]);
+  if (c[0] >= L.h_eps) {
+    const double r = (p == 1) ? 1.0 / c[0] : rinv;
+    me.u = qa * r;
+    me.v = qb * r;
+  } else {
+    me.u = 0.0;
+    me.v = 0.0;
+  }
+  return me;
+}
+
+// Ghost states of every boundary cell of a level for the base state and each
+// perturbation, before a BLU-SGS half-sweep: a cell's state does not change
+// until its own update, so its ghosts are the ones the sweep would compute
+// (the inflow ghost's cubic solve then leaves the per-diagonal critical
+// path).  gbuf[((side * glen + k) * NP + p) * 3 + {h, u, v}], k the position
+// along the side, glen = max(nx, ny).
+template <int NC, int NS>
+__device__ __forceinline__ void ghost_prologue(const DevLevel& L, const double* U, double* gbuf, int tid,
+                                               int nthreads) {
+  constexpr int NP = NC + 1;
+  const long long n = L.n;
+  const int glen = L.nx > L.ny ? L.nx : L.ny;
+  const int total = NS * glen * NP;
+  for (int t = tid; t < total; t += nthreads) {
+    const int p = t % NP, k = (t / NP) % glen, sd = t / (NP * glen);
+    if (k >= (sd < 2 ? L.ny : L.nx)) continue;
+    const int ix = sd == 0 ? 0 : (sd == 1 ? L.nx - 1 : k);
+    const int iy = sd < 2 ? k : (sd == 2 ? 0 : L.ny - 1);
+    const int i = ix + L.nx * iy;
+    double c[NC];
+    for (int s = 0; s < NC; ++s) c[s] = __ldcg(&U[s * n + i]);
+    const double rinv = c[0] >= L.h_eps ? 1.0 / c[0] : 0.0;
+    if (p > 0) c[p - 1] = c[p - 1] + L.eps;
+    const Prim gh = ghost_state(L, sd, pert_prim<NC>(L, c, p, rinv, sd >> 1));
+    gbuf[(long long)t * 3 + 0] = gh.h;
+    gbuf[(long long)t * 3 + 1] = gh.u;
+    gbuf[(long long)t * 3 + 2] = gh.v;
+  }
+}
+
 // One cell group of a BLU-SGS diagonal.  With L2 = true the state is read
 // through L2 only (the persistent sweep, where other SMs update it during the
 // launch).  All 32 lanes of the warp must call it together.
 template <int NC, int NS, int GRP, bool L2>
 __device__ __forceinline__ void blusgs_group(const DevLevel& L, const double* __restrict__ z,
-                                             double* U, int d, int ix0, int ncell, int cell, int g) {
+                                             double* U, const double* gbuf, int d, int ix0, int ncell,
+                                             int cell, int g) {
   constexpr int NP = NC + 1;                 // perturbations incl. the base
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -534,20 +609,19 @@ __device__ __forceinline__ void blusgs_group(const DevLevel& L, const double* __
     double c[NC];
     for (int s = 0; s < NC; ++s) c[s] = ci[s];
     if (p > 0) c[p - 1] = c[p - 1] + L.eps;
-    // the cell's velocities: 1/h only changes with the depth perturbation
-    Prim me;
-    me.h = c[0];
-    const double qa = (NC == 2) ? c[1] : (axis == 0 ? c[1] : c[NC - 1]);
-    const double qb = (NC == 2) ? 0.0 : (axis == 0 ? c[NC - 1] : c[1]);
-    if (c[0] >= L.h_eps) {
-      const double r = (p == 1) ? 1.0 / c[0] : rinv;
-      me.u = qa * r;
-      me.v = qb * r;
-    } else {
-      me.u = 0.0;
-      me.v = 0.0;
+    const Prim me = pert_prim<NC>(L, c, p, rinv, axis);
+    Prim other = nb;
+    if (j < 0) {
+      if (gbuf) {   // precomputed by ghost_prologue
+        const int glen = L.nx > L.ny ? L.nx : L.ny;
+        const long long t = ((long long)(sd * glen + (sd < 2 ? iy : ix)) * NP + p) * 3;
+        other.h = __ldcg(&gbuf[t]);
+        other.u = __ldcg(&gbuf[t + 1]);
+        other.v = __ldcg(&gbuf[t + 2]);
+      } else {
+        other = ghost_state(L, sd, me);
+      }
     }
-    Prim other = (j >= 0) ? nb : ghost_state(L, sd, me);
     const double zo = (j >= 0) ? zj : zi;
     const Prim a = upper ? me : other, b = upper ? other : me;
     const double za = upper ? zi : zo, zb = upper ? zo : zi;
@@ -602,43 +676,54 @@ __device__ __forceinline__ int ld_acq(const int* p) {
   return v;
 }
 
+// Bounded grid barrier number q + 1 (all blocks co-resident): false when the
+// wait ran out or another block gave up (the sticky error is then set).
+__device__ __forceinline__ bool grid_barrier(int* sync, int q, int* sticky_err, int spin_limit) {
+  __shared__ int s_go;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&sync[0], 1);
+    const int target = (q + 1) * gridDim.x;
+    int ok = 0;
+    for (int it = 0; it < spin_limit; ++it) {
+      if (ld_acq(&sync[0]) >= target) { ok = 1; break; }
+      if (ld_acq(&sync[1])) break;
+      __nanosleep(20);
+    }
+    if (!ok) {
+      if (!ld_acq(&sync[1])) atomicOr(sticky_err, 1);
+      atomicExch(&sync[1], 1);
+    }
+    s_go = ok;
+  }
+  __syncthreads();
+  return s_go != 0;
+}
+
+// gbuf: ghost scratch (ghost_prologue), 4 * max(nx, ny) * (NC + 1) * 3 doubles
 template <int NC, int NS, int GRP>
 __global__ void __launch_bounds__(128) k_blusgs_sweep(DevLevel L, const double* __restrict__ z,
-                                                      double* U, int forward, int* sync,
+                                                      double* U, double* gbuf, int forward, int* sync,
                                                       int* sticky_err, int spin_limit) {
-  __shared__ int s_go;
   const int ndiag = L.nx + L.ny - 1;
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
-  const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
+  // warp-major numbering: consecutive cell pairs go to different SMs first,
+  // so a short diagonal puts one warp per SM (GB300 issues about two FP64
+  // operations per clock per SM; four warps of one SM would queue on it)
+  const int gw = warp * gridDim.x + blockIdx.x, nw = gridDim.x * wpb;
   const int cpw = 32 / GRP;                     // cells per warp and round
+  ghost_prologue<NC, NS>(L, U, gbuf, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  if (!grid_barrier(sync, 0, sticky_err, spin_limit)) return;
   for (int q = 0; q < ndiag; ++q) {
     const int d = forward ? q : ndiag - 1 - q;
     const int ix0 = d - (L.ny - 1) > 0 ? d - (L.ny - 1) : 0;
     const int ix1 = d < L.nx - 1 ? d : L.nx - 1;
     const int ncell = ix1 - ix0 + 1;
     for (int c0 = gw * cpw; c0 < ncell; c0 += nw * cpw)   // warp-uniform loop
-      blusgs_group<NC, NS, GRP, true>(L, z, U, d, ix0, ncell, c0 + (threadIdx.x & 31) / GRP,
+      blusgs_group<NC, NS, GRP, true>(L, z, U, gbuf, d, ix0, ncell, c0 + (threadIdx.x & 31) / GRP,
                                       (threadIdx.x & 31) % GRP);
-    // grid barrier
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(&sync[0], 1);
-      const int target = (q + 1) * gridDim.x;
-      int ok = 0;
-      for (int it = 0; it < spin_limit; ++it) {
-        if (ld_acq(&sync[0]) >= target) { ok = 1; break; }
-        if (ld_acq(&sync[1])) break;
-        __nanosleep(20);
-      }
-      if (!ok) {
-        if (!ld_acq(&sync[1])) atomicOr(sticky_err, 1);
-        atomicExch(&sync[1], 1);
-      }
-      s_go = ok;
-    }
-    __syncthreads();
-    if (!s_go) return;
+    if (!grid_barrier(sync, q + 1, sticky_err, spin_limit)) return;
   }
 }
 
@@ -872,13 +957,20 @@ __global__ void __launch_bounds__(128) kb_blusgs_sweep(const BItem* __restrict__
                                                        const int* __restrict__ mask, int B, int nsteps,
                                                        int forward, int* sync, int* sticky_err,
                                                        int spin_limit) {
-  __shared__ int s_go;
   __shared__ int s_off[BATCH_MAX + 1];
   __shared__ int s_cnt[BATCH_MAX], s_d[BATCH_MAX], s_ix0[BATCH_MAX];
   const unsigned full = 0xffffffffu;
   const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
+  // warp-major numbering: consecutive cell pairs go to different SMs first,
+  // so a short diagonal puts one warp per SM (GB300 issues about two FP64
+  // operations per clock per SM; four warps of one SM would queue on it)
+  const int gw = warp * gridDim.x + blockIdx.x, nw = gridDim.x * wpb;
   const int cpw = 32 / GRP;
+  for (int p = 0; p < B; ++p)
+    if (mask[p])
+      ghost_prologue<NC, NS>(items[p].L, items[p].U, items[p].ghost, blockIdx.x * blockDim.x + threadIdx.x,
+                             gridDim.x * blockDim.x);
+  if (!grid_barrier(sync, 0, sticky_err, spin_limit)) return;
   for (int q = 0; q < nsteps; ++q) {
     for (int p = threadIdx.x; p < B; p += blockDim.x) {
       int cnt = 0, d = 0, ix0 = 0;
@@ -934,29 +1026,10 @@ __global__ void __launch_bounds__(128) kb_blusgs_sweep(const BItem* __restrict__
         cell = flat - s_off[p];
         ncell = s_cnt[p];
       }
-      blusgs_group<NC, NS, GRP, true>(items[p].L, items[p].z, items[p].U, s_d[p], s_ix0[p], ncell, cell,
-                                      lane % GRP);
+      blusgs_group<NC, NS, GRP, true>(items[p].L, items[p].z, items[p].U, items[p].ghost, s_d[p], s_ix0[p],
+                                      ncell, cell, lane % GRP);
     }
-    // grid barrier (as in k_blusgs_sweep)
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(&sync[0], 1);
-      const int target = (q + 1) * gridDim.x;
-      int ok = 0;
-      for (int it = 0; it < spin_limit; ++it) {
-        if (ld_acq(&sync[0]) >= target) { ok = 1; break; }
-        if (ld_acq(&sync[1])) break;
-        __nanosleep(20);
-      }
-      if (!ok) {
-        if (!ld_acq(&sync[1])) atomicOr(sticky_err, 1);
-        atomicExch(&sync[1], 1);
-      }
-      s_go = ok;
-    }
-    __syncthreads();
-    if (!s_go) return;
+    if (!grid_barrier(sync, q + 1, sticky_err, spin_limit)) return;
   }
 }
 
@@ -1009,7 +1082,7 @@ void launch_jacobian(const DevLevel& L, const double* z, const double* U, double
   }
 }
 
-void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forward, int* sync,
+void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
                          int* sticky_err, cudaStream_t st) {
   count_launches(1);
   static int nsm = 0;
@@ -1024,7 +1097,8 @@ void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, int forw
   int fw = forward;
   int spin = 1 << 22;
   DevLevel Lc = L;
-  void* args[] = {(void*)&Lc, (void*)&z, (void*)&U, (void*)&fw, (void*)&sync, (void*)&sticky_err, (void*)&spin};
+  void* args[] = {(void*)&Lc, (void*)&z, (void*)&U, (void*)&gbuf, (void*)&fw, (void*)&sync, (void*)&sticky_err,
+                  (void*)&spin};
   if (L.nc == 3)
     cudaLaunchCooperativeKernel((const void*)k_blusgs_sweep<3, 4, 16>, dim3(nsm), dim3(128), args, 0, st);
   else
