@@ -252,6 +252,7 @@ __global__ void k_prolong(int dim, int nc, int nxf, int nyf, const T* __restrict
 // returns; the other strips see the abort flag and return as well.
 // sync layout: [0] ticket, [1] abort, [2 .. 2+nstrips) progress.
 constexpr int SGS_PUBLISH = 4;
+constexpr int SGS_PREFETCH = 4;   // columns of b / old x values loaded ahead
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -394,12 +395,35 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
         for (int k = 0; k < NC; ++k) xn[k] = x[k * n + jj];
       }
     };
-    T sbuf[SGS_PUBLISH][NC];   // previous strip's last row, current group of columns
+    // prefetch ring: rb/re/rn[t] hold b, old east and old north values of the
+    // lane's column c + t (SGS_PREFETCH columns ahead, register-resident)
+    T rb[SGS_PREFETCH][NC], re[SGS_PREFETCH][NC], rn[SGS_PREFETCH][NC];
+#pragma unroll
+    for (int t = 0; t < SGS_PREFETCH; ++t)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) { rb[t][k] = T(0); re[t][k] = T(0); rn[t][k] = T(0); }
+#pragma unroll
+    for (int t = 0; t < SGS_PREFETCH; ++t)
+      if (rowok && t - lagk >= 0 && t - lagk < nx) load_cell(t - lagk, rb[t], re[t], rn[t]);
+    // the previous strip's last row for the lag-0 lane: the current group of
+    // SGS_PUBLISH columns (sc) and, once published, the next one (sn)
+    T sc[SGS_PUBLISH][NC], sn[SGS_PUBLISH][NC];
+#pragma unroll
     for (int t = 0; t < SGS_PUBLISH; ++t)
-      for (int k = 0; k < NC; ++k) sbuf[t][k] = T(0);
-    T cb[NC], cxe[NC], cxn[NC];
-    for (int k = 0; k < NC; ++k) { cb[k] = T(0); cxe[k] = T(0); cxn[k] = T(0); }
-    if (rowok && lagk == 0) load_cell(0, cb, cxe, cxn);
+#pragma unroll
+      for (int k = 0; k < NC; ++k) { sc[t][k] = T(0); sn[t][k] = T(0); }
+    bool have_next = false;
+    const int poller = FWD ? 0 : 31;   // the lag-0 lane
+    auto load_group = [&](int c0, T g[SGS_PUBLISH][NC]) {
+#pragma unroll
+      for (int t = 0; t < SGS_PUBLISH; ++t)
+        if (c0 + t < nx) {
+          const int pxt = FWD ? c0 + t : nx - 1 - (c0 + t);
+          const long long jj = (long long)pxt + (long long)nx * yS;
+#pragma unroll
+          for (int k = 0; k < NC; ++k) g[t][k] = __ldcg(&x[k * n + jj]);
+        }
+    };
     for (int j = 0; j < nchunks && !failed; ++j) {
       const int st = j & 1;
       if (!chunk_wait(&bar[st], parity[st], wait_limit)) {
@@ -416,77 +440,123 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
         const int line = FWD ? s - s0 : cnt - 1 - (s - s0);
         const int c = s - lagk;
         const bool act = rowok && c >= 0 && c < nx;
-        // prefetch the next step's cell data
-        T nb_[NC], nxe[NC], nxn[NC];
-        for (int k = 0; k < NC; ++k) { nb_[k] = T(0); nxe[k] = T(0); nxn[k] = T(0); }
-        if (rowok && c + 1 >= 0 && c + 1 < nx) load_cell(c + 1, nb_, nxe, nxn);
         T xS[NC];
+#pragma unroll
         for (int k = 0; k < NC; ++k)
           xS[k] = FWD ? __shfl_up_sync(FULL, res[k], 1) : __shfl_down_sync(FULL, res[k], 1);
         if (q > 0 && s < nx && (s & (SGS_PUBLISH - 1)) == 0) {
-          // the previous strip's last row, SGS_PUBLISH columns at a time
-          const int need = min(s + SGS_PUBLISH, nx);
-          if (known < need) {
-            int p = 0, it = 0;
-            do {
-              if (lane == 0) {
-                p = ld_acquire(&prog[q - 1]);
-                if (p < need && ld_acquire(abort_flag)) p = -1;
+          // group start of the lag-0 lane (column s): its south values
+          if (have_next) {
+#pragma unroll
+            for (int t = 0; t < SGS_PUBLISH; ++t)
+#pragma unroll
+              for (int k = 0; k < NC; ++k) sc[t][k] = sn[t][k];
+            have_next = false;
+          } else {
+            const int need = min(s + SGS_PUBLISH, nx);
+            if (known < need) {
+              int pg = 0, it = 0;
+              do {
+                if (lane == poller) {
+                  pg = ld_acquire(&prog[q - 1]);
+                  if (pg < need && ld_acquire(abort_flag)) pg = -1;
+                }
+                pg = __shfl_sync(FULL, pg, poller);
+                if (pg >= need || pg < 0) break;
+                __nanosleep(32);
+              } while (++it < spin_limit);
+              if (pg < need) {
+                if (lane == poller && pg >= 0) atomicOr(sticky_err, 1);
+                failed = true;
+                break;
               }
-              p = __shfl_sync(FULL, p, 0);
-              if (p >= need || p < 0) break;
-              __nanosleep(32);
-            } while (++it < spin_limit);
-            if (p < need) {
-              if (lane == 0 && p >= 0) atomicOr(sticky_err, 1);
-              failed = true;
-              break;
+              known = pg;
             }
-            known = p;
+            if (lane == poller && hasS) load_group(s, sc);
+          }
+          // the next group too, if the previous strip has already published it
+          const int need2 = min(s + 2 * SGS_PUBLISH, nx);
+          if (s + SGS_PUBLISH < nx) {
+            if (known < need2) {
+              int pg = 0;
+              if (lane == poller) pg = ld_acquire(&prog[q - 1]);
+              pg = __shfl_sync(FULL, pg, poller);
+              if (pg > known) known = pg;
+            }
+            if (known >= need2) {
+              if (lane == poller && hasS) load_group(s + SGS_PUBLISH, sn);
+              have_next = true;
+            }
           }
         }
         if (act) {
           const int px = FWD ? c : nx - 1 - c;
           const long long i = (long long)px + (long long)nx * y;
-          if (lagk == 0 && hasS) {   // south value from the previous strip (after acquire)
-            if ((c & (SGS_PUBLISH - 1)) == 0) {
-              for (int t = 0; t < SGS_PUBLISH; ++t)
-                if (c + t < nx) {
-                  const int pxt = FWD ? c + t : nx - 1 - (c + t);
-                  const long long jj = (long long)pxt + (long long)nx * yS;
-                  for (int k = 0; k < NC; ++k) sbuf[t][k] = __ldcg(&x[k * n + jj]);
-                }
-            }
-            for (int k = 0; k < NC; ++k) xS[k] = sbuf[c & (SGS_PUBLISH - 1)][k];
+          if (lagk == 0 && hasS) {   // south value from the previous strip
+#pragma unroll
+            for (int t = 0; t < SGS_PUBLISH; ++t)
+              if ((c & (SGS_PUBLISH - 1)) == t)
+#pragma unroll
+                for (int k = 0; k < NC; ++k) xS[k] = sc[t][k];
           }
           const T* Vl = V + line * 32 + lane;
           const int ES = S * 32;   // stride between entries in the stage
-          T r[NC];
-          for (int s2 = 0; s2 < NC; ++s2) r[s2] = cb[s2];
-          if (c > 0)
-            for (int s2 = 0; s2 < NC; ++s2)
-              for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oW + s2 * NC + k) * ES] * xprev[k];
-          if (c < nx - 1)
-            for (int s2 = 0; s2 < NC; ++s2)
-              for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oE + s2 * NC + k) * ES] * cxe[k];
-          if (hasS)
-            for (int s2 = 0; s2 < NC; ++s2)
-              for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oS + s2 * NC + k) * ES] * xS[k];
-          if (hasN)
-            for (int s2 = 0; s2 < NC; ++s2)
-              for (int k = 0; k < NC; ++k) r[s2] -= Vl[(oN + s2 * NC + k) * ES] * cxn[k];
+          // east and north terms first (prefetched values), then the west
+          // (this lane's previous result) and south (the lane below) terms
+          T r[NC], tW[NC], tS[NC];
+#pragma unroll
+          for (int s2 = 0; s2 < NC; ++s2) {
+            T a = rb[0][s2];
+            if (c < nx - 1)
+#pragma unroll
+              for (int k = 0; k < NC; ++k) a -= Vl[(oE + s2 * NC + k) * ES] * re[0][k];
+            if (hasN)
+#pragma unroll
+              for (int k = 0; k < NC; ++k) a -= Vl[(oN + s2 * NC + k) * ES] * rn[0][k];
+            r[s2] = a;
+          }
+#pragma unroll
+          for (int s2 = 0; s2 < NC; ++s2) {
+            T w = T(0), so = T(0);
+            if (c > 0)
+#pragma unroll
+              for (int k = 0; k < NC; ++k) w += Vl[(oW + s2 * NC + k) * ES] * xprev[k];
+            if (hasS)
+#pragma unroll
+              for (int k = 0; k < NC; ++k) so += Vl[(oS + s2 * NC + k) * ES] * xS[k];
+            tW[s2] = w;
+            tS[s2] = so;
+          }
+#pragma unroll
+          for (int s2 = 0; s2 < NC; ++s2) r[s2] = (r[s2] - tW[s2]) - tS[s2];
           lu_apply_v<NC, T>(Vl + (size_t)NOFF * ES, ES, PV[line * 32 + lane], r, res);
+#pragma unroll
           for (int k = 0; k < NC; ++k) {
             x[k * n + i] = res[k];
             xprev[k] = res[k];
           }
         }
-        for (int k = 0; k < NC; ++k) { cb[k] = nb_[k]; cxe[k] = nxe[k]; cxn[k] = nxn[k]; }
-        __syncwarp();
-        if (lagk == 31 && act && q + 1 < nstrips && ((c + 1) % SGS_PUBLISH == 0 || c == nx - 1)) {
-          __threadfence();
-          st_release(&prog[q], c + 1);
+        // advance the ring and fetch column c + SGS_PREFETCH
+#pragma unroll
+        for (int t = 0; t + 1 < SGS_PREFETCH; ++t)
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            rb[t][k] = rb[t + 1][k];
+            re[t][k] = re[t + 1][k];
+            rn[t][k] = rn[t + 1][k];
+          }
+        {
+          const int cf = c + SGS_PREFETCH;
+          T* tb = rb[SGS_PREFETCH - 1];
+          T* te = re[SGS_PREFETCH - 1];
+          T* tn = rn[SGS_PREFETCH - 1];
+#pragma unroll
+          for (int k = 0; k < NC; ++k) { tb[k] = T(0); te[k] = T(0); tn[k] = T(0); }
+          if (rowok && cf >= 0 && cf < nx) load_cell(cf, tb, te, tn);
         }
+        __syncwarp();
+        if (lagk == 31 && act && q + 1 < nstrips && ((c + 1) % SGS_PUBLISH == 0 || c == nx - 1))
+          st_release(&prog[q], c + 1);   // orders this lane's earlier stores and loads
       }
       __syncwarp();
       if (!failed && j + 2 < nchunks) {
