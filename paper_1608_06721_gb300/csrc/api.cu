@@ -197,7 +197,7 @@ swnmg_status coarse_solve(swnmg_ctx* c, const Hier& H, int l) {
   Level& v = H.lv[l];
   if (H.coarse_inverse) {
     TimedScope ts(c, SWNMG_T_COARSE_EXACT);
-    launch_coarse_apply(c->nc, v.n, H.cinv, v.b, v.x, H.fp32, c->st);
+    launch_coarse_apply(c->nc, v.nx, v.ny, H.cinv, v.b, v.x, H.fp32, c->st);
     LAUNCH_CHECK(c);
     return SWNMG_OK;
   }
@@ -233,7 +233,7 @@ swnmg_status mg_cycle(swnmg_ctx* c, const Hier& H, int l) {
   {
     TimedScope ts(c, SWNMG_T_TRANSFER);
     launch_restrict(c->prob.dim, c->nc, v.nx, v.ny, v.blk, v.b, v.x, w.b, H.fp32, c->st);
-    launch_fill(w.x, H.fp32, (long long)c->nc * w.n, c->st);
+    launch_fill(w.x, H.fp32, (long long)c->nc * skew_slots(w.nx, w.ny), c->st);
   }
   LAUNCH_CHECK(c);
   const int gam = (l == 0) ? 1 : c->prm.gamma;
@@ -411,8 +411,8 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
       rc = fail(c, SWNMG_ERR_CUDA, "memset of the operator arrays");
       goto fail_out;
     }
-    ALLOC(v.b, n * c->nc * c->wsz);
-    ALLOC(v.x, n * c->nc * c->wsz);
+    ALLOC(v.b, P * c->nc * c->wsz);   // multigrid vectors: strip-skewed like the operator
+    ALLOC(v.x, P * c->nc * c->wsz);
   }
   {
     const Level& v0 = c->lv[0];
@@ -535,15 +535,15 @@ SWNMG_API swnmg_status swnmg_vcycle(swnmg_ctx* c, const double* rhs, double* dU,
   if (!c || !rhs || !dU || ncycles < 0) return fail(c, SWNMG_ERR_ARG, "bad argument");
   Level& v = c->lv[0];
   const long long m = (long long)v.n * c->nc;
-  launch_convert(rhs, 0, v.b, c->fp32, m, 1.0, c->st);
-  launch_convert(dU, 0, v.x, c->fp32, m, 1.0, c->st);
+  launch_to_skew(rhs, 0, v.b, c->fp32, c->nc, v.nx, v.ny, 1.0, c->st);
+  launch_to_skew(dU, 0, v.x, c->fp32, c->nc, v.nx, v.ny, 1.0, c->st);
   LAUNCH_CHECK(c);
   const Hier H = fwd_hier(c);
   for (int k = 0; k < ncycles; ++k) {
     swnmg_status s = mg_cycle(c, H, 0);
     if (s != SWNMG_OK) return s;
   }
-  launch_convert(v.x, c->fp32, dU, 0, m, 1.0, c->st);
+  launch_from_skew(v.x, c->fp32, dU, 0, c->nc, v.nx, v.ny, 1.0, c->st);
   LAUNCH_CHECK(c);
   return check_sticky(c);
 }
@@ -553,11 +553,11 @@ SWNMG_API swnmg_status swnmg_sgs_sweep(swnmg_ctx* c, int32_t level, const double
   if (!c || !rhs || !x || level < 0 || level > c->nl) return fail(c, SWNMG_ERR_ARG, "bad argument");
   Level& v = c->lv[level];
   const long long m = (long long)v.n * c->nc;
-  launch_convert(rhs, 0, v.b, c->fp32, m, 1.0, c->st);
-  launch_convert(x, 0, v.x, c->fp32, m, 1.0, c->st);
+  launch_to_skew(rhs, 0, v.b, c->fp32, c->nc, v.nx, v.ny, 1.0, c->st);
+  launch_to_skew(x, 0, v.x, c->fp32, c->nc, v.nx, v.ny, 1.0, c->st);
   launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward ? 1 : 0, c->fp32,
                    c->sgs_sync, c->sticky, c->st);
-  launch_convert(v.x, c->fp32, x, 0, m, 1.0, c->st);
+  launch_from_skew(v.x, c->fp32, x, 0, c->nc, v.nx, v.ny, 1.0, c->st);
   LAUNCH_CHECK(c);
   return check_sticky(c);
 }
@@ -631,14 +631,14 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
     blusgs_half(c, 0, U, 0);
     LAUNCH_CHECK(c);
     if ((s = assemble(c, U)) != SWNMG_OK) return s;                // eq. NewtonREG
-    launch_convert(c->R, 0, v0.b, c->fp32, m, -1.0, c->st);        // b = -R
-    launch_fill(v0.x, c->fp32, m, c->st);
+    launch_to_skew(c->R, 0, v0.b, c->fp32, nc, v0.nx, v0.ny, -1.0, c->st);   // b = -R
+    launch_fill(v0.x, c->fp32, (long long)nc * skew_slots(v0.nx, v0.ny), c->st);
     LAUNCH_CHECK(c);
     for (int k = 0; k < c->prm.n_mg; ++k)                          // Step 2.2
       if ((s = mg_cycle(c, fwd_hier(c), 0)) != SWNMG_OK) return s;
     {
       TimedScope ts(c, SWNMG_T_UPDATE);                            // Step 2.3
-      launch_newton_update(v0.n, nc, c->prm.tau, c->prm.h_eps, U, v0.x, c->fp32, c->st);
+      launch_newton_update(v0.nx, v0.ny, nc, c->prm.tau, c->prm.h_eps, U, v0.x, c->fp32, c->st);
     }
     LAUNCH_CHECK(c);
     ++it;
@@ -685,8 +685,8 @@ swnmg_status adjoint_alloc(swnmg_ctx* c) {
     if (!v.blk) AALLOC(v.blk, P * 5 * bs * sizeof(double));
     if (!v.lu) AALLOC(v.lu, P * LU_E * sizeof(double));
     if (!v.piv) AALLOC(v.piv, P);
-    if (!v.b) AALLOC(v.b, (size_t)v.n * nc * sizeof(double));
-    if (!v.x) AALLOC(v.x, (size_t)v.n * nc * sizeof(double));
+    if (!v.b) AALLOC(v.b, P * nc * sizeof(double));
+    if (!v.x) AALLOC(v.x, P * nc * sizeof(double));
     CUDA_TRY(c, cudaMemset(v.blk, 0, P * 5 * bs * sizeof(double)));
     CUDA_TRY(c, cudaMemset(v.lu, 0, P * LU_E * sizeof(double)));
     CUDA_TRY(c, cudaMemset(v.piv, 0, P));
@@ -738,8 +738,8 @@ SWNMG_API swnmg_status swnmg_adjoint(swnmg_ctx* c, const double* U, const double
   const Hier H = adj_hier(c);
   build_hier(c, H);
   LAUNCH_CHECK(c);
-  launch_convert(g, 0, a0.b, 0, m, 1.0, c->st);
-  launch_fill(a0.x, 0, m, c->st);
+  launch_to_skew(g, 0, a0.b, 0, nc, a0.nx, a0.ny, 1.0, c->st);
+  launch_fill(a0.x, 0, (long long)nc * skew_slots(a0.nx, a0.ny), c->st);
   LAUNCH_CHECK(c);
   double gnorm = 0.0, rnorm = 0.0;
   if (rtol > 0) {
@@ -765,7 +765,7 @@ SWNMG_API swnmg_status swnmg_adjoint(swnmg_ctx* c, const double* U, const double
   }
   if (cycles_out) *cycles_out = k;
   if ((s = check_sticky(c)) != SWNMG_OK) return s;
-  launch_convert(a0.x, 0, lam, 0, m, 1.0, c->st);
+  launch_from_skew(a0.x, 0, lam, 0, nc, a0.nx, a0.ny, 1.0, c->st);
   // lambda^T dR/dz and lambda^T dR/dq (central differences of the edge terms)
   const double delta = 1e-6;
   launch_adjoint_z(L, c->lv[0].z, U, lam, delta, c->adj_cz, dRz, c->st);

@@ -1,7 +1,8 @@
 // Internal declarations shared by the CUDA translation units of libswnmg.
 //
 // Device data layout (SoA, x-fastest cell index i = ix + nx*iy):
-//   state U, residual R, vectors b/x : [c*n + i]  (row-major)
+//   state U, residual R               : [c*n + i]  (row-major)
+//   multigrid vectors b, x of a level : [c*P + spos(i)]  (strip-skewed, below)
 //   operator blocks of a level       : blk[(b*nc*nc + s*nc + k)*P + spos(i)]
 //        b = 0 diagonal (raw, with alpha||R_i||_1), 1 W, 2 E, 3 S, 4 N
 //   LU factors of the diagonal       : lu[e*P + spos(i)], e = 0..8 (LU layout below)
@@ -118,7 +119,8 @@ void launch_jacobian(const DevLevel& L, const double* z, const double* U, double
 // gbuf: 4 * max(nx, ny) * (nc + 1) * 3 doubles of ghost scratch
 void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
                          int* sticky_err, cudaStream_t st);
-void launch_newton_update(int n, int nc, double tau, double h_eps, double* U, const void* dU,
+// dU strip-skewed (a level-0 multigrid iterate)
+void launch_newton_update(int nx, int ny, int nc, double tau, double h_eps, double* U, const void* dU,
                           int dU_fp32, cudaStream_t st);
 void launch_adjoint_z(const DevLevel& L, const double* z, const double* U, const double* lam, double delta,
                       double* cz, double* dRz, cudaStream_t st);
@@ -159,7 +161,7 @@ void launch_coarse_exact(int nc, int nx, int ny, const void* blk, const void* b,
                          double* band, int* err, int fp32, cudaStream_t st);
 void launch_coarse_inverse(int nc, int nx, int ny, const void* blk, void* aug, void* X, int* sing,
                            int fp32, cudaStream_t st);
-void launch_coarse_apply(int nc, int n, const void* X, const void* b, void* x, int fp32,
+void launch_coarse_apply(int nc, int nx, int ny, const void* X, const void* b, void* x, int fp32,
                          cudaStream_t st);
 void launch_sum(const double* v, int n, double* partial, double* out, cudaStream_t st);
 void launch_transpose_blocks(int nc, int nx, int ny, const void* src, int src_fp32, double* dst,
@@ -170,6 +172,11 @@ void launch_abs_cells(int n, int nc, const double* v, double* out, cudaStream_t 
 void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n,
                     double scale, cudaStream_t st);
 void launch_fill(void* dst, int fp32, long long n, cudaStream_t st);
+// natural SoA (nc x nx*ny) <-> strip-skewed (nc x skew_slots) vectors, times scale
+void launch_to_skew(const void* src, int src_fp32, void* dst, int dst_fp32, int nc, int nx, int ny, double scale,
+                    cudaStream_t st);
+void launch_from_skew(const void* src, int src_fp32, void* dst, int dst_fp32, int nc, int nx, int ny, double scale,
+                      cudaStream_t st);
 void launch_blocks_export(int nx, int ny, int nc, const void* blk, int fp32, double* out,
                           cudaStream_t st);
 

@@ -815,12 +815,14 @@ __global__ void k_adj_q_cells(DevLevel Lp, DevLevel Lm, int side, const double* 
 
 // U += tau dU with the dry rules of Remark 2.5 (eq. NewtonREG-12)
 template <typename T>
-__device__ __forceinline__ void newton_update_cell(int n, int nc, double tau, double h_eps,
+__device__ __forceinline__ void newton_update_cell(int nx, int ny, int nc, double tau, double h_eps,
                                                    double* __restrict__ U, const T* __restrict__ dU, int i) {
+  // dU is a multigrid vector: strip-skewed, nc x skew_slots(nx, ny)
+  const long long n = (long long)nx * ny, P = skew_slots(nx, ny), si = skew_pos(i % nx, i / nx, nx);
   const double h0 = U[i];
   double v[3];
   for (int s = 0; s < nc; ++s) {
-    double d = static_cast<double>(dU[(long long)s * n + i]);
+    double d = static_cast<double>(dU[(long long)s * P + si]);
     if (s > 0 && h0 < h_eps) d = 0.0;
     v[s] = U[(long long)s * n + i] + tau * d;
   }
@@ -830,10 +832,10 @@ __device__ __forceinline__ void newton_update_cell(int n, int nc, double tau, do
 }
 
 template <typename T>
-__global__ void k_newton_update(int n, int nc, double tau, double h_eps, double* __restrict__ U,
+__global__ void k_newton_update(int nx, int ny, int nc, double tau, double h_eps, double* __restrict__ U,
                                 const T* __restrict__ dU) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) newton_update_cell<T>(n, nc, tau, h_eps, U, dU, i);
+  if (i < nx * ny) newton_update_cell<T>(nx, ny, nc, tau, h_eps, U, dU, i);
 }
 
 // coarse value = mean of the children (child order 00, 10, 01, 11)
@@ -931,7 +933,7 @@ template <typename T>
 __global__ void __launch_bounds__(128) kb_newton_update(BLaunch bl, double tau, double h_eps) {
   BATCH_PROLOGUE(bl)
   if (idx >= it->L.n) return;
-  newton_update_cell<T>(it->L.n, it->L.nc, tau, h_eps, it->U, static_cast<const T*>(it->x), idx);
+  newton_update_cell<T>(it->L.nx, it->L.ny, it->L.nc, tau, h_eps, it->U, static_cast<const T*>(it->x), idx);
 }
 
 __global__ void __launch_bounds__(128) kb_average(BLaunch bl, const BItem* fine) {
@@ -1125,13 +1127,14 @@ void launch_adjoint_q(const DevLevel& L, int side, const double* z, const double
   else k_adj_q_cells<2><<<nblk(L.n, 128), 128, 0, st>>>(Lp, Lm, side, z, U, lam, delta, out);
 }
 
-void launch_newton_update(int n, int nc, double tau, double h_eps, double* U, const void* dU,
+void launch_newton_update(int nx, int ny, int nc, double tau, double h_eps, double* U, const void* dU,
                           int dU_fp32, cudaStream_t st) {
   count_launches(1);
+  const int n = nx * ny;
   if (dU_fp32)
-    k_newton_update<float><<<nblk(n, 256), 256, 0, st>>>(n, nc, tau, h_eps, U, (const float*)dU);
+    k_newton_update<float><<<nblk(n, 256), 256, 0, st>>>(nx, ny, nc, tau, h_eps, U, (const float*)dU);
   else
-    k_newton_update<double><<<nblk(n, 256), 256, 0, st>>>(n, nc, tau, h_eps, U, (const double*)dU);
+    k_newton_update<double><<<nblk(n, 256), 256, 0, st>>>(nx, ny, nc, tau, h_eps, U, (const double*)dU);
 }
 
 void launch_average(int dim, int nxf, int nyf, int ncomp, const double* vf, double* vc,

@@ -161,21 +161,23 @@ __device__ __forceinline__ void lin_resid(int dim, int nx, int ny, const T* __re
   const int BS = NC * NC;
   const int ix = i % nx, iy = i / nx;
   const long long si = skew_pos(ix, iy, nx);
-  int nb[4] = {ix > 0 ? i - 1 : -1, ix < nx - 1 ? i + 1 : -1, iy > 0 ? i - nx : -1,
-               iy < ny - 1 ? i + nx : -1};
+  // neighbours' slots (b and x are strip-skewed like the operator)
+  const long long nb[4] = {ix > 0 ? skew_pos(ix - 1, iy, nx) : -1, ix < nx - 1 ? skew_pos(ix + 1, iy, nx) : -1,
+                           iy > 0 ? skew_pos(ix, iy - 1, nx) : -1, iy < ny - 1 ? skew_pos(ix, iy + 1, nx) : -1};
+  (void)n;
   T xi[NC];
-  for (int k = 0; k < NC; ++k) xi[k] = x[k * n + i];
+  for (int k = 0; k < NC; ++k) xi[k] = x[k * P + si];
   for (int s = 0; s < NC; ++s) {
-    T a = b[s * n + i];
+    T a = b[s * P + si];
     for (int k = 0; k < NC; ++k) a = a - blk[(long long)(s * NC + k) * P + si] * xi[k];
     r[s] = a;
   }
   const int nsd = dim == 2 ? 4 : 2;
   for (int side = 0; side < nsd; ++side) {
-    const int j = nb[side];
+    const long long j = nb[side];
     if (j < 0) continue;
     T xj[NC];
-    for (int k = 0; k < NC; ++k) xj[k] = x[k * n + j];
+    for (int k = 0; k < NC; ++k) xj[k] = x[k * P + j];
     for (int s = 0; s < NC; ++s)
       for (int k = 0; k < NC; ++k)
         r[s] = r[s] - blk[((long long)(1 + side) * BS + s * NC + k) * P + si] * xj[k];
@@ -202,7 +204,9 @@ __device__ __forceinline__ void restrict_cell(int dim, int nxf, int nyf, const T
     lin_resid<NC, T>(dim, nxf, ny, blk, b, x, ch[q], r);
     for (int s = 0; s < NC; ++s) acc[s] = q == 0 ? r[s] : acc[s] + r[s];
   }
-  for (int s = 0; s < NC; ++s) bc[(long long)s * ncc + I] = acc[s];
+  const long long Pc = skew_slots(nxc, nyc), sc = skew_pos(Ix, Iy, nxc);
+  (void)ncc;
+  for (int s = 0; s < NC; ++s) bc[(long long)s * Pc + sc] = acc[s];
 }
 
 template <int NC, typename T>
@@ -216,11 +220,11 @@ __global__ void k_restrict(int dim, int nxf, int nyf, const T* __restrict__ blk,
 template <typename T>
 __device__ __forceinline__ void prolong_cell(int dim, int nc, int nxf, int nyf, const T* __restrict__ xc,
                                              T* __restrict__ xf, int i) {
-  const int nf = nxf * (dim == 2 ? nyf : 1);
-  const int ix = i % nxf, iy = i / nxf, nxc = nxf / 2;
-  const int ncc = nxc * (dim == 2 ? nyf / 2 : 1);
-  const int I = (ix / 2) + nxc * (dim == 2 ? iy / 2 : 0);
-  for (int s = 0; s < nc; ++s) xf[(long long)s * nf + i] = xf[(long long)s * nf + i] + xc[(long long)s * ncc + I];
+  const int nyf1 = dim == 2 ? nyf : 1;
+  const int ix = i % nxf, iy = i / nxf, nxc = nxf / 2, nyc = dim == 2 ? nyf / 2 : 1;
+  const long long Pf = skew_slots(nxf, nyf1), Pc = skew_slots(nxc, nyc);
+  const long long sf = skew_pos(ix, iy, nxf), sc = skew_pos(ix / 2, dim == 2 ? iy / 2 : 0, nxc);
+  for (int s = 0; s < nc; ++s) xf[(long long)s * Pf + sf] = xf[(long long)s * Pf + sf] + xc[(long long)s * Pc + sc];
 }
 
 template <typename T>
@@ -296,7 +300,7 @@ __device__ __forceinline__ void fence_proxy_async() {
 template <typename T> struct SgsChunk { static constexpr int S = sizeof(T) == 4 ? 16 : 8; };
 
 template <int NC, typename T>
-__host__ __device__ constexpr int sgs_entries() { return 4 * NC * NC + LU_E; }   // W, E, S, N blocks + LU
+__host__ __device__ constexpr int sgs_entries() { return 4 * NC * NC + LU_E + 2 * NC; }   // W, E, S, N, LU, b, old x
 
 template <int NC, typename T, int S>
 __host__ __device__ constexpr size_t sgs_stage_bytes() {
@@ -325,7 +329,10 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
                                               int* sticky_err, int q, int nstrips, int spin_limit,
                                               unsigned char* smem, unsigned parity[2]) {
   constexpr int BS = NC * NC;
-  constexpr int NOFF = 4 * BS, NE = NOFF + LU_E;
+  constexpr int NOFF = 4 * BS;
+  constexpr int EB = NOFF + LU_E;         // stage entries: b, then the old x line
+  constexpr int EX = EB + NC;
+  constexpr int NE = EX + NC;
   constexpr size_t STAGE = sgs_stage_bytes<NC, T, S>();
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   T* vals[2] = {reinterpret_cast<T*>(smem + 128), reinterpret_cast<T*>(smem + 128 + STAGE)};
@@ -333,244 +340,244 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
                     reinterpret_cast<int8_t*>(smem + 128 + STAGE + (size_t)NE * S * 32 * sizeof(T))};
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
-  const long long n = (long long)nx * ny, P = skew_slots(nx, ny);
+  const long long P = skew_slots(nx, ny);
   const int oW = (FWD ? 0 : 1) * BS, oE = (FWD ? 1 : 0) * BS, oS = (FWD ? 2 : 3) * BS,
             oN = (FWD ? 3 : 2) * BS;
   const int lagk = FWD ? lane : 31 - lane;
   const int nsteps_full = nx + 31;
   const int wait_limit = spin_limit;
-  {
-    const int ps = FWD ? q : nstrips - 1 - q;
-    const long long line_base = (long long)ps * (nx + 31);
-    // the strip's valid rows; in a forward sweep its last valid lane finishes
-    // at step nx + rows - 2, in a backward sweep the leading lane is lane 31
-    // (lag 0) only when it is valid, so short strips keep the full skew there
-    const int rows = min(32, ny - ps * 32);
-    const int nsteps = FWD ? nx + rows - 1 : nsteps_full;
-    const int nchunks = (nsteps + S - 1) / S;
-    // lane 0 issues chunk j into stage st
-    auto issue = [&](int j, int st) {
-      const int s0 = j * S, cnt = min(S, nsteps - s0);
-      const int dlo = FWD ? s0 : nsteps_full - s0 - cnt;
-      const long long off = (line_base + dlo) * 32;
-      const unsigned vb = (unsigned)(cnt * 32 * sizeof(T));
-      fence_proxy_async();
-      mbar_expect_tx(&bar[st], vb * NE + (unsigned)(cnt * 32));
-      for (int e = 0; e < NOFF; ++e)
-        bulk_g2s(vals[st] + (size_t)e * S * 32, blk + (long long)(BS + e) * P + off, vb, &bar[st]);
-      for (int e = 0; e < LU_E; ++e)
-        bulk_g2s(vals[st] + (size_t)(NOFF + e) * S * 32, lu + (long long)e * P + off, vb, &bar[st]);
-      bulk_g2s(pvs[st], piv + off, (unsigned)(cnt * 32), &bar[st]);
-    };
-    bool inflight[2] = {false, false};
-    if (lane == 0) {
-      issue(0, 0);
-      if (nchunks > 1) issue(1, 1);
-    }
-    inflight[0] = true;
-    inflight[1] = nchunks > 1;
-    const int y = ps * 32 + lane;
-    const bool rowok = y < ny;
-    const int yS = FWD ? y - 1 : y + 1, yN = FWD ? y + 1 : y - 1;
-    const bool hasS = FWD ? (y > 0) : (y < ny - 1);
-    const bool hasN = FWD ? (y < ny - 1) : (y > 0);
-    int known = 0;
-    bool failed = false;
-    T xprev[NC], res[NC];
-    for (int k = 0; k < NC; ++k) { xprev[k] = T(0); res[k] = T(0); }
-    // right-hand side and the "old" east / north values of the lane's cell
-    // at logical column c, loaded one step ahead (they are written at step
-    // c + lagk + 2 at the earliest: by this lane, by the lane above, or by
-    // the next strip after this one has published column c + 2)
-    auto load_cell = [&](int c, T* bb, T* xe, T* xn) {
-      const int px = FWD ? c : nx - 1 - c;
-      const long long i = (long long)px + (long long)nx * y;
-      for (int k = 0; k < NC; ++k) bb[k] = b[k * n + i];
-      if (c < nx - 1) {
-        const long long jj = FWD ? i + 1 : i - 1;
-        for (int k = 0; k < NC; ++k) xe[k] = x[k * n + jj];
-      }
-      if (hasN) {
-        const long long jj = (long long)px + (long long)nx * yN;
-        for (int k = 0; k < NC; ++k) xn[k] = x[k * n + jj];
-      }
-    };
-    // prefetch ring: rb/re/rn[t] hold b, old east and old north values of the
-    // lane's column c + t (SGS_PREFETCH columns ahead, register-resident)
-    T rb[SGS_PREFETCH][NC], re[SGS_PREFETCH][NC], rn[SGS_PREFETCH][NC];
+  const int ps = FWD ? q : nstrips - 1 - q;
+  const long long line_base = (long long)ps * (nx + 31);
+  // the strip's valid rows; in a forward sweep its last valid lane finishes
+  // at step nx + rows - 2, in a backward sweep the leading lane is lane 31
+  // (lag 0) only when it is valid, so short strips keep the full skew there
+  const int rows = min(32, ny - ps * 32);
+  const int nsteps = FWD ? nx + rows - 1 : nsteps_full;
+  const int nchunks = (nsteps + S - 1) / S;
+  // The step on skewed diagonal d updates line d; its "old" east and north
+  // values are line d + 1 (forward) or d - 1 (backward): the same lane and
+  // the lane above (below).  Lane 0 stages chunk j (S lines) of the operator,
+  // LU factors, b and those old x lines into buffer st.  Old lines outside
+  // the strip are never used (they belong to the edge lanes' neighbours,
+  // which come from global memory) and are not copied.
+  auto issue = [&](int j, int st) {
+    const int s0 = j * S, cnt = min(S, nsteps - s0);
+    const int dlo = FWD ? s0 : nsteps_full - s0 - cnt;
+    const long long off = (line_base + dlo) * 32;
+    const unsigned vb = (unsigned)(cnt * 32 * sizeof(T));
+    const int xlo = dlo + (FWD ? 1 : -1);
+    const int xa = max(xlo, 0), xb = min(xlo + cnt, nsteps_full);
+    const unsigned xbytes = xb > xa ? (unsigned)((xb - xa) * 32 * sizeof(T)) : 0u;
+    fence_proxy_async();
+    mbar_expect_tx(&bar[st], vb * EX + xbytes * NC + (unsigned)(cnt * 32));
+    for (int e = 0; e < NOFF; ++e)
+      bulk_g2s(vals[st] + (size_t)e * S * 32, blk + (long long)(BS + e) * P + off, vb, &bar[st]);
+    for (int e = 0; e < LU_E; ++e)
+      bulk_g2s(vals[st] + (size_t)(NOFF + e) * S * 32, lu + (long long)e * P + off, vb, &bar[st]);
+    for (int k = 0; k < NC; ++k)
+      bulk_g2s(vals[st] + (size_t)(EB + k) * S * 32, b + (long long)k * P + off, vb, &bar[st]);
+    if (xbytes)
+      for (int k = 0; k < NC; ++k)
+        bulk_g2s(vals[st] + (size_t)(EX + k) * S * 32 + (size_t)(xa - xlo) * 32,
+                 x + (long long)k * P + (line_base + xa) * 32, xbytes, &bar[st]);
+    bulk_g2s(pvs[st], piv + off, (unsigned)(cnt * 32), &bar[st]);
+  };
+  bool inflight[2] = {false, false};
+  if (lane == 0) {
+    issue(0, 0);
+    if (nchunks > 1) issue(1, 1);
+  }
+  inflight[0] = true;
+  inflight[1] = nchunks > 1;
+  const int y = ps * 32 + lane;
+  const bool rowok = y < ny;
+  const int yS = FWD ? y - 1 : y + 1, yN = FWD ? y + 1 : y - 1;
+  const bool hasS = FWD ? (y > 0) : (y < ny - 1);
+  const bool hasN = FWD ? (y < ny - 1) : (y > 0);
+  // the lane whose north neighbour lies in the next strip (in processing order)
+  const bool nedge = FWD ? (lane == 31) : (lane == 0);
+  int known = 0;
+  bool failed = false;
+  T xprev[NC], res[NC];
 #pragma unroll
-    for (int t = 0; t < SGS_PREFETCH; ++t)
+  for (int k = 0; k < NC; ++k) { xprev[k] = T(0); res[k] = T(0); }
+  // old north values of the edge lane, SGS_PREFETCH columns ahead
+  T rn[SGS_PREFETCH][NC];
+  auto load_north = [&](int c, T* xn) {
+    const int px = FWD ? c : nx - 1 - c;
+    const long long jj = skew_pos(px, yN, nx);
 #pragma unroll
-      for (int k = 0; k < NC; ++k) { rb[t][k] = T(0); re[t][k] = T(0); rn[t][k] = T(0); }
+    for (int k = 0; k < NC; ++k) xn[k] = x[k * P + jj];
+  };
 #pragma unroll
-    for (int t = 0; t < SGS_PREFETCH; ++t)
-      if (rowok && t - lagk >= 0 && t - lagk < nx) load_cell(t - lagk, rb[t], re[t], rn[t]);
-    // the previous strip's last row for the lag-0 lane: the current group of
-    // SGS_PUBLISH columns (sc) and, once published, the next one (sn)
-    T sc[SGS_PUBLISH][NC], sn[SGS_PUBLISH][NC];
+  for (int t = 0; t < SGS_PREFETCH; ++t) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) rn[t][k] = T(0);
+    if (nedge && rowok && hasN && t - lagk >= 0 && t - lagk < nx) load_north(t - lagk, rn[t]);
+  }
+  // the previous strip's last row for the lag-0 lane: the current group of
+  // SGS_PUBLISH columns (sc) and, once published, the next one (sn)
+  T sc[SGS_PUBLISH][NC], sn[SGS_PUBLISH][NC];
+#pragma unroll
+  for (int t = 0; t < SGS_PUBLISH; ++t)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) { sc[t][k] = T(0); sn[t][k] = T(0); }
+  bool have_next = false;
+  const int poller = FWD ? 0 : 31;   // the lag-0 lane
+  auto load_group = [&](int c0, T g[SGS_PUBLISH][NC]) {
 #pragma unroll
     for (int t = 0; t < SGS_PUBLISH; ++t)
+      if (c0 + t < nx) {
+        const int pxt = FWD ? c0 + t : nx - 1 - (c0 + t);
+        const long long jj = skew_pos(pxt, yS, nx);
 #pragma unroll
-      for (int k = 0; k < NC; ++k) { sc[t][k] = T(0); sn[t][k] = T(0); }
-    bool have_next = false;
-    const int poller = FWD ? 0 : 31;   // the lag-0 lane
-    auto load_group = [&](int c0, T g[SGS_PUBLISH][NC]) {
-#pragma unroll
-      for (int t = 0; t < SGS_PUBLISH; ++t)
-        if (c0 + t < nx) {
-          const int pxt = FWD ? c0 + t : nx - 1 - (c0 + t);
-          const long long jj = (long long)pxt + (long long)nx * yS;
-#pragma unroll
-          for (int k = 0; k < NC; ++k) g[t][k] = __ldcg(&x[k * n + jj]);
-        }
-    };
-    for (int j = 0; j < nchunks && !failed; ++j) {
-      const int st = j & 1;
-      if (!chunk_wait(&bar[st], parity[st], wait_limit)) {
-        if (lane == 0) atomicOr(sticky_err, 1);
-        failed = true;
-        break;
+        for (int k = 0; k < NC; ++k) g[t][k] = __ldcg(&x[k * P + jj]);
       }
-      parity[st] ^= 1u;
-      inflight[st] = false;
-      const T* V = vals[st];
-      const int8_t* PV = pvs[st];
-      const int s0 = j * S, cnt = min(S, nsteps - s0);
-      for (int s = s0; s < s0 + cnt; ++s) {
-        const int line = FWD ? s - s0 : cnt - 1 - (s - s0);
-        const int c = s - lagk;
-        const bool act = rowok && c >= 0 && c < nx;
-        T xS[NC];
+  };
+  for (int j = 0; j < nchunks && !failed; ++j) {
+    const int st = j & 1;
+    if (!chunk_wait(&bar[st], parity[st], wait_limit)) {
+      if (lane == 0) atomicOr(sticky_err, 1);
+      failed = true;
+      break;
+    }
+    parity[st] ^= 1u;
+    inflight[st] = false;
+    const T* V = vals[st];
+    const int8_t* PV = pvs[st];
+    const int s0 = j * S, cnt = min(S, nsteps - s0);
+    const long long dbase = line_base + (FWD ? s0 : nsteps_full - s0 - cnt);
+    for (int s = s0; s < s0 + cnt; ++s) {
+      const int line = FWD ? s - s0 : cnt - 1 - (s - s0);
+      const int c = s - lagk;
+      const bool act = rowok && c >= 0 && c < nx;
+      T xS[NC];
 #pragma unroll
-        for (int k = 0; k < NC; ++k)
-          xS[k] = FWD ? __shfl_up_sync(FULL, res[k], 1) : __shfl_down_sync(FULL, res[k], 1);
-        if (q > 0 && s < nx && (s & (SGS_PUBLISH - 1)) == 0) {
-          // group start of the lag-0 lane (column s): its south values
-          if (have_next) {
+      for (int k = 0; k < NC; ++k)
+        xS[k] = FWD ? __shfl_up_sync(FULL, res[k], 1) : __shfl_down_sync(FULL, res[k], 1);
+      if (q > 0 && s < nx && (s & (SGS_PUBLISH - 1)) == 0) {
+        // group start of the lag-0 lane (column s): its south values
+        if (have_next) {
 #pragma unroll
-            for (int t = 0; t < SGS_PUBLISH; ++t)
+          for (int t = 0; t < SGS_PUBLISH; ++t)
 #pragma unroll
-              for (int k = 0; k < NC; ++k) sc[t][k] = sn[t][k];
-            have_next = false;
-          } else {
-            const int need = min(s + SGS_PUBLISH, nx);
-            if (known < need) {
-              int pg = 0, it = 0;
-              do {
-                if (lane == poller) {
-                  pg = ld_acquire(&prog[q - 1]);
-                  if (pg < need && ld_acquire(abort_flag)) pg = -1;
-                }
-                pg = __shfl_sync(FULL, pg, poller);
-                if (pg >= need || pg < 0) break;
-                __nanosleep(32);
-              } while (++it < spin_limit);
-              if (pg < need) {
-                if (lane == poller && pg >= 0) atomicOr(sticky_err, 1);
-                failed = true;
-                break;
+            for (int k = 0; k < NC; ++k) sc[t][k] = sn[t][k];
+          have_next = false;
+        } else {
+          const int need = min(s + SGS_PUBLISH, nx);
+          if (known < need) {
+            int pg = 0, it = 0;
+            do {
+              if (lane == poller) {
+                pg = ld_acquire(&prog[q - 1]);
+                if (pg < need && ld_acquire(abort_flag)) pg = -1;
               }
-              known = pg;
-            }
-            if (lane == poller && hasS) load_group(s, sc);
-          }
-          // the next group too, if the previous strip has already published it
-          const int need2 = min(s + 2 * SGS_PUBLISH, nx);
-          if (s + SGS_PUBLISH < nx) {
-            if (known < need2) {
-              int pg = 0;
-              if (lane == poller) pg = ld_acquire(&prog[q - 1]);
               pg = __shfl_sync(FULL, pg, poller);
-              if (pg > known) known = pg;
+              if (pg >= need || pg < 0) break;
+              __nanosleep(32);
+            } while (++it < spin_limit);
+            if (pg < need) {
+              if (lane == poller && pg >= 0) atomicOr(sticky_err, 1);
+              failed = true;
+              break;
             }
-            if (known >= need2) {
-              if (lane == poller && hasS) load_group(s + SGS_PUBLISH, sn);
-              have_next = true;
-            }
+            known = pg;
+          }
+          if (lane == poller && hasS) load_group(s, sc);
+        }
+        // the next group too, if the previous strip has already published it
+        const int need2 = min(s + 2 * SGS_PUBLISH, nx);
+        if (s + SGS_PUBLISH < nx) {
+          if (known < need2) {
+            int pg = 0;
+            if (lane == poller) pg = ld_acquire(&prog[q - 1]);
+            pg = __shfl_sync(FULL, pg, poller);
+            if (pg > known) known = pg;
+          }
+          if (known >= need2) {
+            if (lane == poller && hasS) load_group(s + SGS_PUBLISH, sn);
+            have_next = true;
           }
         }
-        if (act) {
-          const int px = FWD ? c : nx - 1 - c;
-          const long long i = (long long)px + (long long)nx * y;
-          if (lagk == 0 && hasS) {   // south value from the previous strip
+      }
+      if (act) {
+        if (lagk == 0 && hasS) {   // south value from the previous strip
 #pragma unroll
-            for (int t = 0; t < SGS_PUBLISH; ++t)
-              if ((c & (SGS_PUBLISH - 1)) == t)
+          for (int t = 0; t < SGS_PUBLISH; ++t)
+            if ((c & (SGS_PUBLISH - 1)) == t)
 #pragma unroll
-                for (int k = 0; k < NC; ++k) xS[k] = sc[t][k];
-          }
-          const T* Vl = V + line * 32 + lane;
-          const int ES = S * 32;   // stride between entries in the stage
-          // east and north terms first (prefetched values), then the west
-          // (this lane's previous result) and south (the lane below) terms
-          T r[NC], tW[NC], tS[NC];
-#pragma unroll
-          for (int s2 = 0; s2 < NC; ++s2) {
-            T a = rb[0][s2];
-            if (c < nx - 1)
-#pragma unroll
-              for (int k = 0; k < NC; ++k) a -= Vl[(oE + s2 * NC + k) * ES] * re[0][k];
-            if (hasN)
-#pragma unroll
-              for (int k = 0; k < NC; ++k) a -= Vl[(oN + s2 * NC + k) * ES] * rn[0][k];
-            r[s2] = a;
-          }
-#pragma unroll
-          for (int s2 = 0; s2 < NC; ++s2) {
-            T w = T(0), so = T(0);
-            if (c > 0)
-#pragma unroll
-              for (int k = 0; k < NC; ++k) w += Vl[(oW + s2 * NC + k) * ES] * xprev[k];
-            if (hasS)
-#pragma unroll
-              for (int k = 0; k < NC; ++k) so += Vl[(oS + s2 * NC + k) * ES] * xS[k];
-            tW[s2] = w;
-            tS[s2] = so;
-          }
-#pragma unroll
-          for (int s2 = 0; s2 < NC; ++s2) r[s2] = (r[s2] - tW[s2]) - tS[s2];
-          lu_apply_v<NC, T>(Vl + (size_t)NOFF * ES, ES, PV[line * 32 + lane], r, res);
-#pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            x[k * n + i] = res[k];
-            xprev[k] = res[k];
-          }
+              for (int k = 0; k < NC; ++k) xS[k] = sc[t][k];
         }
-        // advance the ring and fetch column c + SGS_PREFETCH
+        const T* Vl = V + line * 32 + lane;
+        const int ES = S * 32;   // stride between entries in the stage
+        T xe[NC], xn[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          xe[k] = Vl[(EX + k) * ES];
+          xn[k] = nedge ? rn[0][k] : Vl[(EX + k) * ES + (FWD ? 1 : -1)];
+        }
+        // east and north terms first (old values), then the west (this
+        // lane's previous result) and south (the lane below) terms
+        T r[NC], tW[NC], tS[NC];
+#pragma unroll
+        for (int s2 = 0; s2 < NC; ++s2) {
+          T a = Vl[(EB + s2) * ES];
+          if (c < nx - 1)
+#pragma unroll
+            for (int k = 0; k < NC; ++k) a -= Vl[(oE + s2 * NC + k) * ES] * xe[k];
+          if (hasN)
+#pragma unroll
+            for (int k = 0; k < NC; ++k) a -= Vl[(oN + s2 * NC + k) * ES] * xn[k];
+          r[s2] = a;
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < NC; ++s2) {
+          T w = T(0), so = T(0);
+          if (c > 0)
+#pragma unroll
+            for (int k = 0; k < NC; ++k) w += Vl[(oW + s2 * NC + k) * ES] * xprev[k];
+          if (hasS)
+#pragma unroll
+            for (int k = 0; k < NC; ++k) so += Vl[(oS + s2 * NC + k) * ES] * xS[k];
+          tW[s2] = w;
+          tS[s2] = so;
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < NC; ++s2) r[s2] = (r[s2] - tW[s2]) - tS[s2];
+        lu_apply_v<NC, T>(Vl + (size_t)NOFF * ES, ES, PV[line * 32 + lane], r, res);
+        const long long slot = (dbase + line) * 32 + lane;   // coalesced: one line per step
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          x[k * P + slot] = res[k];
+          xprev[k] = res[k];
+        }
+      }
+      if (nedge) {   // advance the edge lane's ring, fetch column c + SGS_PREFETCH
 #pragma unroll
         for (int t = 0; t + 1 < SGS_PREFETCH; ++t)
 #pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            rb[t][k] = rb[t + 1][k];
-            re[t][k] = re[t + 1][k];
-            rn[t][k] = rn[t + 1][k];
-          }
-        {
-          const int cf = c + SGS_PREFETCH;
-          T* tb = rb[SGS_PREFETCH - 1];
-          T* te = re[SGS_PREFETCH - 1];
-          T* tn = rn[SGS_PREFETCH - 1];
+          for (int k = 0; k < NC; ++k) rn[t][k] = rn[t + 1][k];
+        const int cf = c + SGS_PREFETCH;
 #pragma unroll
-          for (int k = 0; k < NC; ++k) { tb[k] = T(0); te[k] = T(0); tn[k] = T(0); }
-          if (rowok && cf >= 0 && cf < nx) load_cell(cf, tb, te, tn);
-        }
-        __syncwarp();
-        if (lagk == 31 && act && q + 1 < nstrips && ((c + 1) % SGS_PUBLISH == 0 || c == nx - 1))
-          st_release(&prog[q], c + 1);   // orders this lane's earlier stores and loads
+        for (int k = 0; k < NC; ++k) rn[SGS_PREFETCH - 1][k] = T(0);
+        if (rowok && hasN && cf >= 0 && cf < nx) load_north(cf, rn[SGS_PREFETCH - 1]);
       }
       __syncwarp();
-      if (!failed && j + 2 < nchunks) {
-        if (lane == 0) issue(j + 2, st);
-        inflight[st] = true;
-      }
+      if (lagk == 31 && act && q + 1 < nstrips && ((c + 1) % SGS_PUBLISH == 0 || c == nx - 1))
+        st_release(&prog[q], c + 1);   // orders this lane's earlier stores and loads
     }
-    if (failed) {
-      // stop the other strips, then let this warp's copies land before leaving
-      if (lane == 0) st_release(abort_flag, 1);
-      for (int st = 0; st < 2; ++st)
-        if (inflight[st]) chunk_wait(&bar[st], parity[st], wait_limit);
-      return false;
+    __syncwarp();
+    if (!failed && j + 2 < nchunks) {
+      if (lane == 0) issue(j + 2, st);
+      inflight[st] = true;
     }
+  }
+  if (failed) {
+    // stop the other strips, then let this warp's copies land before leaving
+    if (lane == 0) st_release(abort_flag, 1);
+    for (int st = 0; st < 2; ++st)
+      if (inflight[st]) chunk_wait(&bar[st], parity[st], wait_limit);
+    return false;
   }
   return true;
 }
@@ -631,7 +638,7 @@ __global__ void k_coarse_exact(int nx, int ny, const T* __restrict__ blk, const 
     int nb[4] = {ix > 0 ? i - 1 : -1, ix < nx - 1 ? i + 1 : -1, iy > 0 ? i - nx : -1,
                  iy < ny - 1 ? i + nx : -1};
     for (int s = 0; s < NC; ++s) {
-      rhs[i * NC + s] = (double)b[(long long)s * n + i];
+      rhs[i * NC + s] = (double)b[(long long)s * P + si];
       sing[i * NC + s] = 0;
       for (int k = 0; k < NC; ++k) AB(i * NC + s, i * NC + k) = (double)blk[(long long)(s * NC + k) * P + si];
       for (int side = 0; side < 4; ++side) {
@@ -694,7 +701,10 @@ __global__ void k_coarse_exact(int nx, int ny, const T* __restrict__ blk, const 
       }
       rhs[r] = v;   // rhs now holds the solution from r on
     }
-    for (int r = 0; r < m; ++r) x[(long long)(r % NC) * n + r / NC] = (T)rhs[r];
+    for (int r = 0; r < m; ++r) {
+      const int cell = r / NC;
+      x[(long long)(r % NC) * P + skew_pos(cell % nx, cell / nx, nx)] = (T)rhs[r];
+    }
     if (err) *err = 0;
   }
 }
@@ -814,18 +824,30 @@ __global__ void k_coarse_inverse(int nx, int ny, const T* __restrict__ blk, T* _
 
 // x = X b on the coarsest level (SoA vectors, cell-major unknowns)
 template <int NC, typename T>
-__device__ __forceinline__ void coarse_apply_row(int n, const T* __restrict__ X, const T* __restrict__ b,
-                                                 T* __restrict__ x, int u) {
-  const int m = n * NC;
+__device__ __forceinline__ void coarse_apply_block(int nx, int ny, const T* __restrict__ X,
+                                                   const T* __restrict__ b, T* __restrict__ x) {
+  // b gathered once per block into unknown order (m <= 384), then one row per thread
+  __shared__ __align__(16) unsigned char sraw[384 * sizeof(T)];
+  T* sb = reinterpret_cast<T*>(sraw);
+  const int n = nx * ny, m = n * NC;
+  const long long P = skew_slots(nx, ny);
+  for (int u = threadIdx.x; u < m; u += blockDim.x) {
+    const int cell = u / NC;
+    sb[u] = b[(long long)(u % NC) * P + skew_pos(cell % nx, cell / nx, nx)];
+  }
+  __syncthreads();
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= m) return;
   T acc = T(0);
-  for (int jcol = 0; jcol < m; ++jcol) acc += X[(long long)jcol * m + u] * b[(long long)(jcol % NC) * n + jcol / NC];
-  x[(long long)(u % NC) * n + u / NC] = acc;
+  for (int jcol = 0; jcol < m; ++jcol) acc += X[(long long)jcol * m + u] * sb[jcol];
+  const int cell = u / NC;
+  x[(long long)(u % NC) * P + skew_pos(cell % nx, cell / nx, nx)] = acc;
 }
 
 template <int NC, typename T>
-__global__ void k_coarse_apply(int n, const T* __restrict__ X, const T* __restrict__ b, T* __restrict__ x) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u < n * NC) coarse_apply_row<NC, T>(n, X, b, x, u);
+__global__ void k_coarse_apply(int nx, int ny, const T* __restrict__ X, const T* __restrict__ b,
+                               T* __restrict__ x) {
+  coarse_apply_block<NC, T>(nx, ny, X, b, x);
 }
 
 // ---- adjoint support ----------------------------------------------------------
@@ -911,6 +933,25 @@ __global__ void k_convert(const S* __restrict__ s, D* __restrict__ d, long long 
     d[i] = static_cast<D>(scale * static_cast<double>(s[i]));
 }
 
+// natural SoA vector (nc x n) <-> strip-skewed vector (nc x P), scaled
+template <typename S, typename D>
+__global__ void k_to_skew(const S* __restrict__ s, D* __restrict__ d, int nc, int nx, int ny, double scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = nx * ny;
+  if (i >= n) return;
+  const long long P = skew_slots(nx, ny), si = skew_pos(i % nx, i / nx, nx);
+  for (int k = 0; k < nc; ++k) d[k * P + si] = static_cast<D>(scale * static_cast<double>(s[(long long)k * n + i]));
+}
+
+template <typename S, typename D>
+__global__ void k_from_skew(const S* __restrict__ s, D* __restrict__ d, int nc, int nx, int ny, double scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = nx * ny;
+  if (i >= n) return;
+  const long long P = skew_slots(nx, ny), si = skew_pos(i % nx, i / nx, nx);
+  for (int k = 0; k < nc; ++k) d[(long long)k * n + i] = static_cast<D>(scale * static_cast<double>(s[k * P + si]));
+}
+
 template <typename T>
 __global__ void k_fill0(T* __restrict__ d, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -977,7 +1018,8 @@ __global__ void __launch_bounds__(128) kb_fill_x(BLaunch bl) {
   const int n = it->L.n;
   if (idx >= n) return;
   T* x = static_cast<T*>(it->x);
-  for (int s = 0; s < it->L.nc; ++s) x[(long long)s * n + idx] = T(0);
+  const long long P = skew_slots(it->L.nx, it->L.ny), si = skew_pos(idx % it->L.nx, idx / it->L.nx, it->L.nx);
+  for (int s = 0; s < it->L.nc; ++s) x[(long long)s * P + si] = T(0);
 }
 
 template <typename T>
@@ -986,8 +1028,9 @@ __global__ void __launch_bounds__(128) kb_neg_residual(BLaunch bl) {
   const int n = it->L.n;
   if (idx >= n) return;
   T* b = static_cast<T*>(it->b);
+  const long long P = skew_slots(it->L.nx, it->L.ny), si = skew_pos(idx % it->L.nx, idx / it->L.nx, it->L.nx);
   for (int s = 0; s < it->L.nc; ++s)
-    b[(long long)s * n + idx] = static_cast<T>(-1.0 * it->R[(long long)s * n + idx]);
+    b[(long long)s * P + si] = static_cast<T>(-1.0 * it->R[(long long)s * n + idx]);
 }
 #undef BATCH_PROLOGUE
 
@@ -1076,10 +1119,9 @@ __global__ void __launch_bounds__(128) kb_coarse_apply(const BItem* items, const
   const int p = blockIdx.y;
   if (!mask[p]) return;
   const BItem* it = items + p;
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u < it->L.n * NC)
-    coarse_apply_row<NC, T>(it->L.n, static_cast<const T*>(it->cinv), static_cast<const T*>(it->b),
-                            static_cast<T*>(it->x), u);
+  if ((int)(blockIdx.x * blockDim.x) >= it->L.n * NC) return;   // whole block idle
+  coarse_apply_block<NC, T>(it->L.nx, it->L.ny, static_cast<const T*>(it->cinv), static_cast<const T*>(it->b),
+                            static_cast<T*>(it->x));
 }
 
 }  // namespace
@@ -1187,10 +1229,11 @@ void launch_coarse_inverse(int nc, int nx, int ny, const void* blk, void* aug, v
 #undef CI
 }
 
-void launch_coarse_apply(int nc, int n, const void* X, const void* b, void* x, int fp32, cudaStream_t st) {
+void launch_coarse_apply(int nc, int nx, int ny, const void* X, const void* b, void* x, int fp32,
+                         cudaStream_t st) {
   count_launches(1);
-  const int m = n * nc;
-#define CA(NC, T) k_coarse_apply<NC, T><<<nblk(m, 128), 128, 0, st>>>(n, (const T*)X, (const T*)b, (T*)x)
+  const int m = nx * ny * nc;
+#define CA(NC, T) k_coarse_apply<NC, T><<<nblk(m, 128), 128, 0, st>>>(nx, ny, (const T*)X, (const T*)b, (T*)x)
   if (nc == 3) { if (fp32) CA(3, float); else CA(3, double); }
   else { if (fp32) CA(2, float); else CA(2, double); }
 #undef CA
@@ -1238,6 +1281,26 @@ void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long
   else if (src_fp32) k_convert<float, double><<<g, 256, 0, st>>>((const float*)src, (double*)dst, n, scale);
   else if (dst_fp32) k_convert<double, float><<<g, 256, 0, st>>>((const double*)src, (float*)dst, n, scale);
   else k_convert<double, double><<<g, 256, 0, st>>>((const double*)src, (double*)dst, n, scale);
+}
+
+void launch_to_skew(const void* src, int src_fp32, void* dst, int dst_fp32, int nc, int nx, int ny, double scale,
+                    cudaStream_t st) {
+  count_launches(1);
+  const int g = nblk((long long)nx * ny, 256);
+  if (src_fp32 && dst_fp32) k_to_skew<float, float><<<g, 256, 0, st>>>((const float*)src, (float*)dst, nc, nx, ny, scale);
+  else if (src_fp32) k_to_skew<float, double><<<g, 256, 0, st>>>((const float*)src, (double*)dst, nc, nx, ny, scale);
+  else if (dst_fp32) k_to_skew<double, float><<<g, 256, 0, st>>>((const double*)src, (float*)dst, nc, nx, ny, scale);
+  else k_to_skew<double, double><<<g, 256, 0, st>>>((const double*)src, (double*)dst, nc, nx, ny, scale);
+}
+
+void launch_from_skew(const void* src, int src_fp32, void* dst, int dst_fp32, int nc, int nx, int ny, double scale,
+                      cudaStream_t st) {
+  count_launches(1);
+  const int g = nblk((long long)nx * ny, 256);
+  if (src_fp32 && dst_fp32) k_from_skew<float, float><<<g, 256, 0, st>>>((const float*)src, (float*)dst, nc, nx, ny, scale);
+  else if (src_fp32) k_from_skew<float, double><<<g, 256, 0, st>>>((const float*)src, (double*)dst, nc, nx, ny, scale);
+  else if (dst_fp32) k_from_skew<double, float><<<g, 256, 0, st>>>((const double*)src, (float*)dst, nc, nx, ny, scale);
+  else k_from_skew<double, double><<<g, 256, 0, st>>>((const double*)src, (double*)dst, nc, nx, ny, scale);
 }
 
 void launch_fill(void* dst, int fp32, long long n, cudaStream_t st) {
