@@ -151,6 +151,41 @@ def algorithmic(cls, p, fp32):
     return None, None
 
 
+# ---------------------------------------------------------------- ranks
+
+def rank_env():
+    """(world, rank, local rank) from the torchrun environment (1, 0, 0 alone)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, world, device):
+    """Largest x over the ranks of the default process group (x alone when world == 1)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world, device):
+    """Sum of x over the ranks (x alone when world == 1)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard(items, rank, world):
+    """The independent problems a rank solves: every world-th one from rank."""
+    return list(items)[rank::world]
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def run_gpu(args):
@@ -159,9 +194,7 @@ def run_gpu(args):
     import torch.distributed as dist
     from paper_1608_06721_gb300 import swnmg, workloads as W
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -170,13 +203,6 @@ def run_gpu(args):
     def barrier():
         if world > 1:
             dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     p = workload(W.PREC_MIXED, args.nx, args.nx)
     stream = torch.cuda.current_stream()
@@ -218,7 +244,7 @@ def run_gpu(args):
     launches = swnmg.lib().swnmg_launch_count() - n0
     timing = S.get_timing()
     S.set_timing(False)
-    total_ms = max_over_ranks(total_ms)
+    total_ms = max_over_ranks(total_ms, world, dev)
     value = world * p.n * cycles / (total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
 
@@ -288,7 +314,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_cycles += info["n_vcycles"]
-    e2e_ms = max_over_ranks(e2e_ms)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
     e2e = {"value": world * p.n * e2e_cycles / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": int(hU0.numel() * 8), "d2h_bytes_per_step": int(hU.numel() * 8),
            "ms_per_step": e2e_ms / max(1, args.e2e_steps)}
@@ -317,13 +343,22 @@ def run_batch(args):
     swnmg_batch_solve per step, autotuned, N_mg cycles replayed from a CUDA
     graph.  value = converged problems per second; beside it cell*cycles/s
     over all problems and, with --sequential, the same problems solved one by
-    one through the single-problem API."""
+    one through the single-problem API.  Under torchrun the problems are
+    dealt to the ranks (every N-th from the rank's index), each rank solving
+    its share as one batch on its GPU: no data-path collective, and value =
+    all ranks' converged problems / the slowest rank's time."""
     import numpy as np
     import torch
+    import torch.distributed as dist
     from paper_1608_06721_gb300 import swnmg, workloads as W
 
-    torch.cuda.set_device(0)
-    probs = W.batch_channels(seed=401, count=args.batch_count)
+    world, rank, local = rank_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    all_probs = W.batch_channels(seed=401, count=args.batch_count)
+    probs = shard(all_probs, rank, world)
     stream = torch.cuda.current_stream()
     bt = swnmg.BatchSolver(probs, stream=stream)
     U0 = bt.states()
@@ -342,8 +377,10 @@ def run_batch(args):
         one()
     torch.cuda.synchronize()
     n0 = swnmg.lib().swnmg_launch_count()
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(local)
     clocks.start()
+    if world > 1:
+        dist.barrier()
     total_ms, infos = 0.0, None
     for _ in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -352,31 +389,34 @@ def run_batch(args):
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
+    if world > 1:
+        dist.barrier()
     clk = clocks.stop()
     launches = swnmg.lib().swnmg_launch_count() - n0
-    ms = total_ms / args.steps
-    ok = [i["status"] == 0 for i in infos]
-    cells = sum(p.n for p in probs)
-    cc = sum(i["n_vcycles"] * p.n for i, p in zip(infos, probs))
+    ms = max_over_ranks(total_ms / args.steps, world, dev)
+    ok = sum_over_ranks(sum(i["status"] == 0 for i in infos), world, dev)
+    cells = sum(p.n for p in all_probs)
+    cc = sum_over_ranks(sum(i["n_vcycles"] * p.n for i, p in zip(infos, probs)), world, dev)
     status_names = {0: "ok", 3: "not_converged", 4: "nonfinite", 5: "diverged"}
     by = {}
     for i, p in zip(infos, probs):
         k = status_names.get(i["status"], str(i["status"]))
         by.setdefault(k, []).append(p.nx)
     out = {"metric": "batched steady solves/s (64 seeded channels 128^2..1024^2, mixed precision)",
-           "value": sum(ok) / (ms * 1e-3), "unit": "converged solves/s", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "value": ok / (ms * 1e-3), "unit": "converged solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
            "vs_baseline": None, "dtype": "f64+f32 (FP32 multigrid, FP64 residual/update)",
            "data": "synthetic (seeded Gaussian-bump topography)",
            "config": {"workload": "%d channel problems, sizes %s, seed 401, W-cycle, eps_p=2, exact 8x8 coarsest"
-                                  % (len(probs), sorted(set(p.nx for p in probs))),
-                      "cells": cells, "l2": "working set %.1f GB > L2" % (cells * 3 * 8 * 12 / 1e9)},
-           "cell_cycles_per_s": cc / (ms * 1e-3), "converged": int(sum(ok)), "problems": len(probs),
-           "status_by_size": {k: sorted(v) for k, v in by.items()},
-           "max_newton_steps": max(i["n_newton"] for i in infos),
-           "tuning": {"sgs_chunk": chunks, "blusgs_blocks": blocks, "seconds": tune_s},
+                                  % (len(all_probs), sorted(set(p.nx for p in all_probs))),
+                      "cells": cells, "parallelism": "problems dealt to %d rank(s)" % world,
+                      "l2": "working set %.1f GB > L2" % (cells * 3 * 8 * 12 / 1e9)},
+           "cell_cycles_per_s": cc / (ms * 1e-3), "converged": int(ok), "problems": len(all_probs),
+           "status_by_size_rank0": {k: sorted(v) for k, v in by.items()},
+           "max_newton_steps_rank0": max(i["n_newton"] for i in infos),
+           "tuning_rank0": {"sgs_chunk": chunks, "blusgs_blocks": blocks, "seconds": tune_s},
            "gpu_launches": int(launches), "clocks": clk}
-    if args.sequential:
+    if args.sequential and world == 1:
         tot, cyc, okn = 0.0, 0, 0
         for p in probs:
             S = swnmg.Solver(p, stream=stream)
@@ -392,7 +432,10 @@ def run_batch(args):
             S.close()
         out["sequential_single"] = {"ms": tot, "converged_solves_per_s": okn / (tot * 1e-3),
                                     "cell_cycles_per_s": cyc / (tot * 1e-3), "speedup_batched": tot / ms}
-    print(json.dumps(out), flush=True)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 # ---------------------------------------------------------------- CPU oracle
