@@ -534,7 +534,6 @@ SWNMG_API swnmg_status swnmg_get_blocks(swnmg_ctx* c, int32_t level, double* hos
 SWNMG_API swnmg_status swnmg_vcycle(swnmg_ctx* c, const double* rhs, double* dU, int32_t ncycles) {
   if (!c || !rhs || !dU || ncycles < 0) return fail(c, SWNMG_ERR_ARG, "bad argument");
   Level& v = c->lv[0];
-  const long long m = (long long)v.n * c->nc;
   launch_to_skew(rhs, 0, v.b, c->fp32, c->nc, v.nx, v.ny, 1.0, c->st);
   launch_to_skew(dU, 0, v.x, c->fp32, c->nc, v.nx, v.ny, 1.0, c->st);
   LAUNCH_CHECK(c);
@@ -552,7 +551,6 @@ SWNMG_API swnmg_status swnmg_sgs_sweep(swnmg_ctx* c, int32_t level, const double
                                        int32_t forward) {
   if (!c || !rhs || !x || level < 0 || level > c->nl) return fail(c, SWNMG_ERR_ARG, "bad argument");
   Level& v = c->lv[level];
-  const long long m = (long long)v.n * c->nc;
   launch_to_skew(rhs, 0, v.b, c->fp32, c->nc, v.nx, v.ny, 1.0, c->st);
   launch_to_skew(x, 0, v.x, c->fp32, c->nc, v.nx, v.ny, 1.0, c->st);
   launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward ? 1 : 0, c->fp32,
@@ -617,8 +615,6 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
   auto t1 = clk::now();
   // Steps 2-3: Newton multigrid iteration
   Level& v0 = c->lv[0];
-  const long long m = (long long)v0.n * nc;
-  const DevLevel L0 = dev_level(c, 0);
   double res;
   if ((s = level_residual_sum(c, 0, U, &res)) != SWNMG_OK) return s;
   st->init_res = res;
@@ -727,7 +723,6 @@ SWNMG_API swnmg_status swnmg_adjoint(swnmg_ctx* c, const double* U, const double
   const int nc = c->nc;
   const DevLevel L = dev_level(c, 0);
   Level& a0 = c->alv[0];
-  const long long m = (long long)a0.n * nc;
   // J at U* in FP64, then J^T in the strip-skewed layout and its hierarchy
   {
     TimedScope ts(c, SWNMG_T_JACOBIAN, L.n);

@@ -107,7 +107,7 @@ __device__ __forceinline__ void lu_apply_v(const T* __restrict__ L, int ls, int8
 template <int NC, typename T>
 __device__ __forceinline__ void galerkin_cell(int dim, int nxf, int nyf, const T* __restrict__ bf,
                                               T* __restrict__ bc, int I) {
-  const int nxc = nxf / 2, nyc = dim == 2 ? nyf / 2 : 1, ncc = nxc * nyc;
+  const int nxc = nxf / 2, nyc = dim == 2 ? nyf / 2 : 1;
   const int nyff = dim == 2 ? nyf : 1;
   const long long Pf = skew_slots(nxf, nyff), Pc = skew_slots(nxc, nyc);
   const int BS = NC * NC;
