@@ -34,7 +34,7 @@ class Cfg(C.Structure):
                 ("tol", C.c_double),
                 ("n_levels", C.c_int), ("n_mg", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("gamma", C.c_int), ("coarse_sweeps", C.c_int), ("max_newton", C.c_int),
-                ("max_blusgs", C.c_int), ("init_mode", C.c_int)]
+                ("max_blusgs", C.c_int), ("init_mode", C.c_int), ("eps_f", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -101,7 +101,7 @@ def make_cfg(prob, **over) -> Cfg:
         c.bc[s].kind, c.bc[s].h, c.bc[s].q, c.bc[s].ut = b.kind, b.h, b.q, b.ut
     for f in ("flux", "llf_wetdry", "alpha", "fd_eps", "tau", "h_eps", "eps_r", "eps_p", "tol",
               "n_levels", "n_mg", "nu1", "nu2", "gamma", "coarse_sweeps", "max_newton",
-              "max_blusgs", "init_mode"):
+              "max_blusgs", "init_mode", "eps_f"):
         setattr(c, f, getattr(prm, f))
     return c
 

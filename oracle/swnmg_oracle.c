@@ -36,7 +36,7 @@
 /* ---- configuration (mirrors the C-ABI structs field for field) ---------- */
 enum { BC_WALL_REFLECT = 0, BC_WALL_SLIP = 1, BC_INFLOW_DISCHARGE = 2,
        BC_OUTFLOW_DEPTH = 3, BC_SUPER_INFLOW = 4, BC_SUPER_OUTFLOW = 5 };
-enum { FLUX_HLL = 0, FLUX_HLLC = 1, FLUX_LLF = 2 };
+enum { FLUX_HLL = 0, FLUX_HLLC = 1, FLUX_LLF = 2, FLUX_ROE = 3 };
 enum { INIT_CASCADE = 0, INIT_NONE = 1 };
 enum { ST_OK = 0, ST_ARG = 1, ST_NOT_CONVERGED = 3, ST_NONFINITE = 4, ST_DIVERGED = 5 };
 
@@ -49,6 +49,7 @@ typedef struct {
   int flux, llf_wetdry;
   double alpha, fd_eps, tau, h_eps, eps_r, eps_p, tol;
   int n_levels, n_mg, nu1, nu2, gamma, coarse_sweeps, max_newton, max_blusgs, init_mode;
+  double eps_f;                       /* Harten's entropy-fix width of the Roe flux */
 } orc_cfg;
 
 #define ORC_HIST 512
@@ -162,6 +163,47 @@ static void flux_llf(const orc_cfg* c, double hl, double ul, double vl,
     F[k] = ((FL[k] + FR[k]) - smax * (UR[k] - UL[k])) * 0.5;
 }
 
+/* Harten's entropy fix of the Roe flux (Remark 2.2): |x| replaced by
+ * x^2/(4 eps_f) + eps_f when |x| < 2 eps_f. */
+static double harten_q(double x, double ef) {
+  double a = fabs(x);
+  return (a < 2.0 * ef) ? (x * x) / (4.0 * ef) + ef : a;
+}
+
+/* Roe flux with Harten's entropy fix, eq. ROEflux.  The Roe matrix of the
+ * shallow water equations: mean depth h^ = (h- + h+)/2 and sqrt(h)-weighted
+ * velocities u^, v^, c^ = sqrt(g h^); eigenvalues u^ - c^, u^, u^ + c^ with
+ * right eigenvectors (1, u^ - c^, v^), (0, 0, 1), (1, u^ + c^, v^); the wave
+ * strengths chi_k solve U+ - U- = sum chi_k r_k.  In 1D the middle wave has
+ * zero strength (no tangential momentum), which leaves the m = 2 form.  Both
+ * depths zero: zero flux. */
+static void flux_roe(const orc_cfg* c, double hl, double ul, double vl,
+                     double hr, double ur, double vr, double F[3]) {
+  double g = c->g, half_g = 0.5 * c->g, ef = c->eps_f;
+  if (hl == 0.0 && hr == 0.0) { F[0] = F[1] = F[2] = 0.0; return; }
+  double sl = sqrt(hl), sr = sqrt(hr);
+  double rs = 1.0 / (sl + sr);
+  double uh = (sl * ul + sr * ur) * rs;
+  double vh = (sl * vl + sr * vr) * rs;
+  double ch = sqrt(g * ((hl + hr) * 0.5));
+  double FL[3], FR[3];
+  phys_flux(half_g, hl, ul, vl, FL);
+  phys_flux(half_g, hr, ur, vr, FR);
+  double dh = hr - hl, dq = hr * ur - hl * ul, dp = hr * vr - hl * vl;
+  double l1 = uh - ch, l3 = uh + ch;
+  double r2c = 1.0 / (2.0 * ch);
+  double a1 = (l3 * dh - dq) * r2c;   /* chi_1 */
+  double a3 = (dq - l1 * dh) * r2c;   /* chi_3 */
+  double a2 = dp - vh * dh;           /* chi_2 */
+  double w1 = harten_q(l1, ef) * a1, w2 = harten_q(uh, ef) * a2, w3 = harten_q(l3, ef) * a3;
+  double D0 = w1 + w3;
+  double D1 = w1 * l1 + w3 * l3;
+  double D2 = (w1 * vh + w2) + w3 * vh;
+  F[0] = ((FL[0] + FR[0]) - D0) * 0.5;
+  F[1] = ((FL[1] + FR[1]) - D1) * 0.5;
+  F[2] = ((FL[2] + FR[2]) - D2) * 0.5;
+}
+
 /* One edge, eq. totalFlux with the hydrostatic reconstruction of section 2.1.
  * Inputs are the two cell states in the edge frame (depth, normal velocity,
  * tangential velocity, bed), the left one being the cell on the lower-index
@@ -174,6 +216,7 @@ static void edge_eval(const orc_cfg* c, double hL, double uL, double vL, double 
   double hl = (tl > 0.0) ? tl : 0.0, hr = (tr > 0.0) ? tr : 0.0;
   double F[3];
   if (c->flux == FLUX_LLF) flux_llf(c, hl, uL, vL, hr, uR, vR, F);
+  else if (c->flux == FLUX_ROE) flux_roe(c, hl, uL, vL, hr, uR, vR, F);
   else flux_hll(c, hl, uL, vL, hr, uR, vR, c->flux == FLUX_HLLC, F);
   double half_g = 0.5 * c->g;
   out[0] = F[0]; out[1] = F[1]; out[2] = F[2];
@@ -387,6 +430,7 @@ static void lu_solve(int n, const blu* f, const double* b, double* x) {
 static int check_cfg(const orc_cfg* c) {
   if (!c || (c->dim != 1 && c->dim != 2) || c->nx < 1 || (c->dim == 2 && c->ny < 1)) return ST_ARG;
   if (c->n_levels < 0 || c->n_levels > 12) return ST_ARG;
+  if (c->flux < 0 || c->flux > FLUX_ROE || (c->flux == FLUX_ROE && !(c->eps_f > 0.0))) return ST_ARG;
   int m = 1 << c->n_levels;
   if (c->nx % m) return ST_ARG;
   if (c->dim == 2 && c->ny % m) return ST_ARG;

@@ -35,6 +35,7 @@ BC_SUPER_OUTFLOW = 5
 FLUX_HLL = 0
 FLUX_HLLC = 1
 FLUX_LLF = 2
+FLUX_ROE = 3       # Roe with Harten's entropy fix (Remark 2.2)
 
 INIT_CASCADE = 0   # Algorithm 1, Step 1
 INIT_NONE = 1      # warm start from the given state
@@ -75,6 +76,7 @@ class Params:
     max_blusgs: int = 1000
     init_mode: int = INIT_CASCADE
     precision: int = PREC_FP64
+    eps_f: float = 0.4          # Harten's entropy-fix width (Roe flux)
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)

@@ -1,0 +1,99 @@
+"""Pins of the oracle's Roe flux with Harten's entropy fix (Remark 2.2,
+eq. ROEflux): consistency, the Roe property (upwinding of supersonic states
+follows from A^(U+ - U-) = F(U+) - F(U-) only when the averages and the
+eigen-decomposition are right), the continuity of Harten's Q, mirror
+symmetry, dry states, the lake at rest, and Table 3.1's Roe rows (Newton
+steps of the V-cycle N_L = 3 and the spectral radius of the block SGS
+iteration at the steady state)."""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_1608_06721_gb300 import workloads as W
+from tests import dense
+from tests.golden import tables
+
+G = 9.81
+PAPER = tables.load()
+
+
+def _oracle(dim=2, eps_f=0.4):
+    if dim == 2:
+        p = W.channel_2d(nx=8, ny=8, n_levels=1, redraw=False).with_params(flux=W.FLUX_ROE, eps_f=eps_f)
+    else:
+        p = W.smooth_subcritical_1d(8, flux=W.FLUX_ROE).with_params(n_levels=0, eps_f=eps_f)
+    return Oracle(p)
+
+
+def _phys(h, u, v):
+    q = h * u
+    return np.array([q, q * u + 0.5 * G * h * h, q * v])
+
+
+def test_consistency():
+    o = _oracle()
+    for h, u, v in [(1.0, 0.3, -0.2), (0.05, -2.0, 1.0), (3.0, 0.0, 0.0)]:
+        out = o.edge_flux(h, u, v, 0.0, h, u, v, 0.0)
+        np.testing.assert_allclose(out[:3], _phys(h, u, v), rtol=1e-14, atol=1e-15)
+        assert out[3] == out[4] == (0.5 * G) * (h * h)
+
+
+def test_roe_property_upwinds_supersonic_states():
+    """All eigenvalues beyond 2 eps_f: Q = |lambda| and the Roe flux is the
+    upwind physical flux exactly when sum lambda_k chi_k r_k = F(U+) - F(U-)."""
+    o = _oracle()
+    hl, ul, vl, hr, ur, vr = 0.5, 6.0, 0.7, 0.8, 7.5, -0.4      # u - c > 0.8 on both sides
+    out = o.edge_flux(hl, ul, vl, 0.0, hr, ur, vr, 0.0)
+    np.testing.assert_allclose(out[:3], _phys(hl, ul, vl), rtol=1e-13)
+    out = o.edge_flux(hl, -ul, vl, 0.0, hr, -ur, vr, 0.0)
+    np.testing.assert_allclose(out[:3], _phys(hr, -ur, vr), rtol=1e-13)
+
+
+def test_harten_fix_is_continuous_and_dissipative_at_sonic_points():
+    o = _oracle()
+    # left state with u - c crossing 0: the flux is continuous in u
+    h = 1.0
+    c = np.sqrt(G * h)
+    f = [o.edge_flux(h, c + d, 0.0, 0.0, 0.9, c + d, 0.0, 0.0)[:3] for d in (-1e-9, 0.0, 1e-9)]
+    assert np.abs(f[0] - f[1]).max() < 1e-7 and np.abs(f[2] - f[1]).max() < 1e-7
+    # at the sonic point the eps_f dissipation acts on the jump
+    lo = _oracle(eps_f=1e-12).edge_flux(1.0, c, 0.0, 0.0, 0.9, c, 0.0, 0.0)[:3]
+    hi = _oracle(eps_f=0.4).edge_flux(1.0, c, 0.0, 0.0, 0.9, c, 0.0, 0.0)[:3]
+    assert abs(hi[0] - lo[0]) > 1e-3
+
+
+def test_mirror_symmetry():
+    o = _oracle()
+    a = o.edge_flux(0.7, 0.4, 0.1, 0.0, 1.1, -0.2, 0.3, 0.0)
+    b = o.edge_flux(1.1, 0.2, 0.3, 0.0, 0.7, -0.4, 0.1, 0.0)
+    np.testing.assert_allclose([a[0], a[1], a[2]], [-b[0], b[1], -b[2]], rtol=1e-13, atol=1e-15)
+    assert a[3] == b[4] and a[4] == b[3]
+
+
+def test_dry_states():
+    o = _oracle()
+    assert np.all(o.edge_flux(0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0)[:3] == 0.0)
+    out = o.edge_flux(0.0, 0.0, 0.0, 0.0, 0.5, -0.3, 0.0, 0.0)
+    assert np.isfinite(out).all() and out[0] < 0.0      # water flows into the dry side
+
+
+def test_lake_at_rest_is_preserved():
+    p = W.lake_at_rest_2d(n=64, flux=W.FLUX_ROE)
+    R, rn = Oracle(p).residual(p.U0)
+    assert np.abs(R).max() <= 1e-13
+
+
+def test_paper_newton_counts_table31_roe():
+    for n, ref in zip((64, 128, 256), PAPER["t31_roe_V_NL3_Nstep"]):
+        U, info = Oracle(W.smooth_subcritical_1d(n, flux=W.FLUX_ROE)).solve()
+        assert info["status"] == 0 and abs(info["n_newton"] - ref) <= 1
+
+
+@pytest.mark.parametrize("k,n", [(0, 64), (1, 128)])
+def test_paper_spectral_radius_table31_roe(k, n):
+    p = W.smooth_subcritical_1d(n, flux=W.FLUX_ROE)
+    o = Oracle(p)
+    U, info = o.solve()
+    R, rn, blk = o.jacobian(U)
+    rho = dense.sgs_iteration_radius(dense.assemble(blk, p.nx, 1), p.ncomp)
+    assert abs(rho - PAPER["t31_roe_rho"][k]) <= 5e-4, rho
