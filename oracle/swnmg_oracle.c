@@ -35,7 +35,7 @@
 
 /* ---- configuration (mirrors the C-ABI structs field for field) ---------- */
 enum { BC_WALL_REFLECT = 0, BC_WALL_SLIP = 1, BC_INFLOW_DISCHARGE = 2,
-       BC_OUTFLOW_DEPTH = 3, BC_SUPER_INFLOW = 4, BC_SUPER_OUTFLOW = 5 };
+       BC_OUTFLOW_DEPTH = 3, BC_SUPER_INFLOW = 4, BC_SUPER_OUTFLOW = 5, BC_AUTO_FROUDE = 6 };
 enum { FLUX_HLL = 0, FLUX_HLLC = 1, FLUX_LLF = 2, FLUX_ROE = 3 };
 enum { INIT_CASCADE = 0, INIT_NONE = 1 };
 enum { ST_OK = 0, ST_ARG = 1, ST_NOT_CONVERGED = 3, ST_NONFINITE = 4, ST_DIVERGED = 5 };
@@ -257,7 +257,16 @@ static double inflow_celerity(double g, double RI, double qn) {
 static void ghost(const orc_cfg* c, const orc_bc* b, double sigma, double hI, double uI,
                   double vI, double* hg, double* ug, double* vg) {
   double g = c->g;
-  switch (b->kind) {
+  int kind = b->kind;
+  if (kind == BC_AUTO_FROUDE) {
+    /* Remark 2.3's choice by the interior's local Froude number |u|/sqrt(g h)
+     * (compared as |u|^2 >= g h: supercritical, a dry cell included) and the
+     * sign of the outward normal velocity (u_n < 0: inflow) */
+    int super = (uI * uI + vI * vI) >= g * hI;
+    int in = (sigma * uI) < 0.0;
+    kind = super ? (in ? BC_SUPER_INFLOW : BC_SUPER_OUTFLOW) : (in ? BC_INFLOW_DISCHARGE : BC_OUTFLOW_DEPTH);
+  }
+  switch (kind) {
     case BC_WALL_SLIP: *hg = hI; *ug = 0.0; *vg = vI; break;
     case BC_INFLOW_DISCHARGE: {
       double qn = sigma * b->q;

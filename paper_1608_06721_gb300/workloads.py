@@ -30,6 +30,7 @@ BC_INFLOW_DISCHARGE = 2
 BC_OUTFLOW_DEPTH = 3
 BC_SUPER_INFLOW = 4
 BC_SUPER_OUTFLOW = 5
+BC_AUTO_FROUDE = 6      # Remark 2.3 switch by the local Froude number
 
 # numerical fluxes (Remark 2.2)
 FLUX_HLL = 0
