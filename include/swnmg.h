@@ -50,11 +50,14 @@ enum {
   SWNMG_BC_INFLOW_DISCHARGE = 2, /* subcritical inflow: discharge q and u_tau prescribed */
   SWNMG_BC_OUTFLOW_DEPTH = 3,    /* subcritical outflow: depth h prescribed */
   SWNMG_BC_SUPER_INFLOW = 4,     /* supercritical inflow: h, q, u_tau prescribed */
-  SWNMG_BC_SUPER_OUTFLOW = 5     /* supercritical outflow: ghost = interior */
+  SWNMG_BC_SUPER_OUTFLOW = 5,    /* supercritical outflow: ghost = interior */
+  SWNMG_BC_AUTO_FROUDE = 6       /* open boundary: one of kinds 2-5 chosen per evaluation by the
+                                    interior's Froude number (|u|^2 >= g h: supercritical) and the
+                                    sign of its outward normal velocity (< 0: inflow); uses h, q, ut */
 };
 
 /* numerical fluxes, Remark 2.2 */
-enum { SWNMG_FLUX_HLL = 0, SWNMG_FLUX_HLLC = 1, SWNMG_FLUX_LLF = 2 };
+enum { SWNMG_FLUX_HLL = 0, SWNMG_FLUX_HLLC = 1, SWNMG_FLUX_LLF = 2, SWNMG_FLUX_ROE = 3 };
 enum { SWNMG_INIT_CASCADE = 0, SWNMG_INIT_NONE = 1 };   /* Algorithm 1 Step 1, or warm start */
 enum { SWNMG_PREC_FP64 = 0, SWNMG_PREC_MIXED = 1 };     /* MIXED: FP32 multigrid inner solve */
 
@@ -74,7 +77,8 @@ typedef struct {
 
 /* Solver parameters; swnmg_default_params gives the paper's values
  * (Section 3 preamble): alpha = 3, fd_eps = 1e-8, tau = 1, h_eps = 1e-6,
- * eps_r = 0.03, eps_p = 0.2, N_mg = 2 (1D) / 3 (2D), N_L = 3, V-cycle.
+ * eps_r = 0.03, eps_p = 0.2, N_mg = 2 (1D) / 3 (2D), N_L = 3, V-cycle,
+ * eps_f = 0.4 (Roe flux, Remark 2.2).
  *   llf_wetdry    1: add eps_r sqrt(g max h) to the LLF speed on every edge
  *   tol           stop when sum_i ||R_i||_1 < tol (Step 3)
  *   nu1, nu2      symmetric block-SGS sweeps before/after the coarse correction
@@ -87,6 +91,7 @@ typedef struct {
   double alpha, fd_eps, tau, h_eps, eps_r, eps_p, tol;
   int32_t n_levels, n_mg, nu1, nu2, gamma, coarse_sweeps, max_newton, max_blusgs,
       init_mode, precision;
+  double eps_f;   /* Harten's entropy-fix width of the Roe flux (paper: 0.4) */
 } swnmg_params;
 
 #define SWNMG_HIST 512

@@ -91,6 +91,7 @@ DevLevel dev_level(const swnmg_ctx* c, int l) {
   L.eps_r = c->prm.eps_r;
   L.alpha = c->prm.alpha;
   L.eps = c->prm.fd_eps;
+  L.eps_f = c->prm.eps_f;
   L.reps = 1.0 / c->prm.fd_eps;
   for (int s = 0; s < 4; ++s) {
     L.bc[s].kind = c->prob.bc[s].kind;
@@ -102,7 +103,8 @@ DevLevel dev_level(const swnmg_ctx* c, int l) {
 }
 
 swnmg_status check_params(const swnmg_problem* p, const swnmg_params* q) {
-  if (q->flux < 0 || q->flux > 2) return SWNMG_ERR_ARG;
+  if (q->flux < 0 || q->flux > 3) return SWNMG_ERR_ARG;
+  if (q->flux == SWNMG_FLUX_ROE && !(q->eps_f > 0)) return SWNMG_ERR_ARG;
   if (p->dim == 1 && q->flux == SWNMG_FLUX_HLLC) return SWNMG_ERR_ARG;
   if (!(q->fd_eps > 0) || !(q->h_eps > 0) || q->alpha < 0) return SWNMG_ERR_ARG;
   if (q->n_levels < 0 || q->n_levels > 12 || q->n_mg < 0 || q->nu1 < 0 || q->nu2 < 0) return SWNMG_ERR_ARG;
@@ -341,6 +343,7 @@ SWNMG_API swnmg_status swnmg_default_params(int32_t dim, swnmg_params* o) {
   o->max_blusgs = 1000;
   o->init_mode = SWNMG_INIT_CASCADE;
   o->precision = SWNMG_PREC_FP64;
+  o->eps_f = 0.4;
   return SWNMG_OK;
 }
 
@@ -361,7 +364,7 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
   if ((long long)p->nx * (p->dim == 2 ? p->ny : 1) > (1LL << 28))
     return fail(nullptr, SWNMG_ERR_ARG, "more than 2^28 cells");
   for (int s = 0; s < 4; ++s)
-    if (p->bc[s].kind < 0 || p->bc[s].kind > 5) return fail(nullptr, SWNMG_ERR_ARG, "bad boundary kind");
+    if (p->bc[s].kind < 0 || p->bc[s].kind > 6) return fail(nullptr, SWNMG_ERR_ARG, "bad boundary kind");
   if (check_params(p, q) != SWNMG_OK)
     return fail(nullptr, SWNMG_ERR_ARG, "bad parameters or mesh not divisible by 2^n_levels");
   int dev = -1;

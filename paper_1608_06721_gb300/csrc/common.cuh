@@ -24,8 +24,9 @@
 namespace swnmg {
 
 // boundary kinds / fluxes (same numbering as the public header)
-enum { BC_REFLECT = 0, BC_SLIP = 1, BC_INFLOW = 2, BC_OUTFLOW = 3, BC_SUPER_IN = 4, BC_SUPER_OUT = 5 };
-enum { FX_HLL = 0, FX_HLLC = 1, FX_LLF = 2 };
+enum { BC_REFLECT = 0, BC_SLIP = 1, BC_INFLOW = 2, BC_OUTFLOW = 3, BC_SUPER_IN = 4, BC_SUPER_OUT = 5,
+       BC_AUTO = 6 };
+enum { FX_HLL = 0, FX_HLLC = 1, FX_LLF = 2, FX_ROE = 3 };
 
 struct DevBC { int kind; double h, q, ut; };
 
@@ -36,6 +37,7 @@ struct DevLevel {
   double ex, ey;          // |x-edge| (W/E sides), |y-edge| (S/N sides); 1D: 1, 0
   int flux, llf_wetdry;
   double g, half_g, h_eps, eps_r, alpha, eps, reps;   // reps = 1/eps
+  double eps_f;           // Harten's entropy-fix width (Roe flux)
   DevBC bc[4];            // W, E, S, N
 };
 

@@ -33,10 +33,18 @@ __device__ __forceinline__ Prim to_prim(double h, double qa, double qb, double h
   return p;
 }
 
+// Harten's entropy fix (Remark 2.2): |x|, or x^2/(4 eps_f) + eps_f below 2 eps_f
+__device__ __forceinline__ double harten_q(double x, double ef) {
+  const double a = fabs(x);
+  return (a < 2.0 * ef) ? (x * x) / (4.0 * ef) + ef : a;
+}
+
 // Numerical flux of Remark 2.2 between reconstructed states (hl, ul, vl) and
 // (hr, ur, vr): HLL (eq. HLLflux) with the wet/dry wave speeds, HLLC's contact
-// choice for the tangential flux, or LLF (eq. LLFflux) with the optional
-// wet/dry speed increase.  Both depths zero: zero flux.
+// choice for the tangential flux, LLF (eq. LLFflux) with the optional wet/dry
+// speed increase, or Roe with Harten's entropy fix (eq. ROEflux: mean depth,
+// sqrt(h)-weighted velocities, waves u - c, u, u + c).  Both depths zero:
+// zero flux.
 __device__ void num_flux(const DevLevel& L, double hl, double ul, double vl, double hr, double ur,
                          double vr, double F[3]) {
   if (hl == 0.0 && hr == 0.0) {
@@ -49,6 +57,27 @@ __device__ void num_flux(const DevLevel& L, double hl, double ul, double vl, dou
   const double FL0 = ql, FL1 = ql * ul + hg * (hl * hl), FL2 = ql * vl;
   const double FR0 = qr, FR1 = qr * ur + hg * (hr * hr), FR2 = qr * vr;
   const double dU0 = hr - hl, dU1 = qr - ql, dU2 = hr * vr - hl * vl;   // U+ - U-
+  if (L.flux == FX_ROE) {
+    const double ef = L.eps_f;
+    const double sl = sqrt(hl), sr = sqrt(hr);
+    const double rs = 1.0 / (sl + sr);
+    const double uh = (sl * ul + sr * ur) * rs;
+    const double vh = (sl * vl + sr * vr) * rs;
+    const double ch = sqrt(g * ((hl + hr) * 0.5));
+    const double l1 = uh - ch, l3 = uh + ch;
+    const double r2c = 1.0 / (2.0 * ch);
+    const double a1 = (l3 * dU0 - dU1) * r2c;   // wave strengths
+    const double a3 = (dU1 - l1 * dU0) * r2c;
+    const double a2 = dU2 - vh * dU0;
+    const double w1 = harten_q(l1, ef) * a1, w2 = harten_q(uh, ef) * a2, w3 = harten_q(l3, ef) * a3;
+    const double D0 = w1 + w3;
+    const double D1 = w1 * l1 + w3 * l3;
+    const double D2 = (w1 * vh + w2) + w3 * vh;
+    F[0] = ((FL0 + FR0) - D0) * 0.5;
+    F[1] = ((FL1 + FR1) - D1) * 0.5;
+    F[2] = ((FL2 + FR2) - D2) * 0.5;
+    return;
+  }
   if (L.flux == FX_LLF) {
     double smax = dmax(fabs(ul) + cl, fabs(ur) + cr);
     // sqrt(g max(h-, h+)) equals max(sqrt(g h-), sqrt(g h+)) bit for bit:
@@ -119,7 +148,15 @@ __device__ Prim ghost_state(const DevLevel& L, int side, Prim I) {
   const double sigma = (side & 1) ? 1.0 : -1.0;
   const double g = L.g;
   Prim o;
-  switch (bc.kind) {
+  int kind = bc.kind;
+  if (kind == BC_AUTO) {
+    // Remark 2.3's choice by the interior's local Froude number (|u|^2 >= g h:
+    // supercritical, a dry cell included) and the sign of the outward u_n
+    const bool super = (I.u * I.u + I.v * I.v) >= g * I.h;
+    const bool in = (sigma * I.u) < 0.0;
+    kind = super ? (in ? BC_SUPER_IN : BC_SUPER_OUT) : (in ? BC_INFLOW : BC_OUTFLOW);
+  }
+  switch (kind) {
     case BC_SLIP: o.h = I.h; o.u = 0.0; o.v = I.v; break;
     case BC_INFLOW: {
       const double qn = sigma * bc.q;

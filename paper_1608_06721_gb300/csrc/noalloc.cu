@@ -69,9 +69,10 @@ SWNMG_API swnmg_status swnmg_residual_noalloc(const swnmg_problem* p, const swnm
       !(p->x1 > p->x0) || (p->dim == 2 && !(p->y1 > p->y0)))
     return noalloc_fail(SWNMG_ERR_ARG, "residual_noalloc: bad mesh or gravity");
   for (int s = 0; s < 4; ++s)
-    if (p->bc[s].kind < 0 || p->bc[s].kind > 5)
+    if (p->bc[s].kind < 0 || p->bc[s].kind > 6)
       return noalloc_fail(SWNMG_ERR_ARG, "residual_noalloc: bad boundary kind");
-  if (q->flux < 0 || q->flux > 2 || (p->dim == 1 && q->flux == SWNMG_FLUX_HLLC) || !(q->h_eps > 0))
+  if (q->flux < 0 || q->flux > 3 || (p->dim == 1 && q->flux == SWNMG_FLUX_HLLC) || !(q->h_eps > 0) ||
+      (q->flux == SWNMG_FLUX_ROE && !(q->eps_f > 0)))
     return noalloc_fail(SWNMG_ERR_ARG, "residual_noalloc: bad flux parameters");
   const int nc = p->dim == 2 ? 3 : 2;
   const int ny = p->dim == 2 ? p->ny : 1;
@@ -113,6 +114,7 @@ SWNMG_API swnmg_status swnmg_residual_noalloc(const swnmg_problem* p, const swnm
   L.alpha = q->alpha;
   L.eps = q->fd_eps;
   L.reps = 1.0 / q->fd_eps;
+  L.eps_f = q->eps_f;
   for (int k = 0; k < 4; ++k) {
     L.bc[k].kind = p->bc[k].kind;
     L.bc[k].h = p->bc[k].h;

@@ -35,6 +35,7 @@ def test_default_params_are_the_papers():
     assert p1["alpha"] == 3.0 and p1["fd_eps"] == 1e-8 and p1["tau"] == 1.0 and p1["h_eps"] == 1e-6
     assert p1["n_mg"] == 2 and p2["n_mg"] == 3 and p1["n_levels"] == 3 and p1["eps_p"] == 0.2
     assert p2["eps_r"] == 0.03 and p2["flux"] == 1 and p1["flux"] == 0
+    assert p1["eps_f"] == 0.4 and p2["eps_f"] == 0.4
 
 
 def test_struct_layouts_match_header():
@@ -42,5 +43,5 @@ def test_struct_layouts_match_header():
     from paper_1608_06721_gb300 import swnmg
     assert C.sizeof(swnmg._BC) == 32
     assert C.sizeof(swnmg.Problem) == 3 * 4 + 4 + 5 * 8 + 4 * 32
-    assert C.sizeof(swnmg.Params) == 2 * 4 + 7 * 8 + 10 * 4
+    assert C.sizeof(swnmg.Params) == 2 * 4 + 7 * 8 + 10 * 4 + 8
     assert C.sizeof(swnmg.Stats) == 3 * 4 + 16 * 4 + 4 + 2 * 8 + 512 * 8 + 2 * 8

@@ -27,6 +27,20 @@ def swnmg():
     return S
 
 
+def _auto_state(p):
+    """A random state whose west and east columns also hold shallow, fast
+    cells (|u|^2 >= g h) moving in and out, so that all four regimes of the
+    Froude-number boundary are evaluated."""
+    U = W.random_state(p, 10, wet_frac=0.5)
+    for row in range(p.ny):
+        for col, sgn in ((0, 1.0), (p.nx - 1, -1.0)):
+            if row % 4 in (1, 2):
+                i = col + p.nx * row
+                U[0, i] = 0.05
+                U[1, i] = (sgn if row % 4 == 1 else -sgn) * 0.5
+    return U
+
+
 def _cases():
     """(name, problem, state generator) covering 1D/2D, every flux, ragged
     tile tails, wet/dry fronts and all boundary kinds of the workloads."""
@@ -49,6 +63,21 @@ def _cases():
     # multiple of the wavefront's 4-column publication group
     p = W.channel_2d(nx=66, ny=70, n_levels=1, redraw=False)
     out.append(("channel_66x70", p, lambda p: W.random_state(p, 7, wet_frac=0.5)))
+    # Roe flux with Harten's entropy fix, 1D and 2D (wet/dry)
+    p = W.smooth_subcritical_1d(128, flux=W.FLUX_ROE)
+    out.append(("ex31_128_roe", p, lambda p: W.random_state(p, 8)))
+    p = W.channel_2d(nx=64, ny=48, n_levels=2, redraw=False).with_params(flux=W.FLUX_ROE, llf_wetdry=0)
+    out.append(("channel_64x48_roe", p, lambda p: W.random_state(p, 9, wet_frac=0.5)))
+    # open boundaries chosen by the local Froude number (random states reach
+    # the sub- and supercritical, inflow and outflow branches)
+    p = W.channel_2d(nx=64, ny=32, n_levels=2, redraw=False)
+    p.bc[0] = W.BC(W.BC_AUTO_FROUDE, h=0.6, q=p.bc[0].q, ut=0.1)
+    p.bc[1] = W.BC(W.BC_AUTO_FROUDE, h=0.6, q=0.4)
+    out.append(("channel_64x32_auto", p, _auto_state))
+    p = W.subcritical_bump_1d(n=200)
+    p.bc[0] = W.BC(W.BC_AUTO_FROUDE, h=2.0, q=p.bc[0].q)
+    p.bc[1] = W.BC(W.BC_AUTO_FROUDE, h=2.0, q=p.bc[0].q)
+    out.append(("bump1d_200_auto", p, lambda p: W.random_state(p, 11)))
     return out
 
 
@@ -150,6 +179,8 @@ SOLVES = [
     ("channel_128x32", W.channel_2d(nx=128, ny=32, n_levels=2)),
     ("hill_64x32", W.hill_wetdry_2d(64, 32)),
     ("ex36_64x32", W.transcritical_bump_2d(64, 32)),
+    ("ex31_256_roe", W.smooth_subcritical_1d(256, flux=W.FLUX_ROE)),
+    ("ex36_48x24_roe", W.transcritical_bump_2d(48, 24).with_params(flux=W.FLUX_ROE)),
 ]
 
 
