@@ -34,7 +34,8 @@ class Cfg(C.Structure):
                 ("tol", C.c_double),
                 ("n_levels", C.c_int), ("n_mg", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("gamma", C.c_int), ("coarse_sweeps", C.c_int), ("max_newton", C.c_int),
-                ("max_blusgs", C.c_int), ("init_mode", C.c_int), ("eps_f", C.c_double)]
+                ("max_blusgs", C.c_int), ("init_mode", C.c_int), ("eps_f", C.c_double),
+                ("t_ka", C.c_double), ("t_omb", C.c_double), ("t_src", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -82,6 +83,7 @@ def lib():
         _lib.orc_level_cells.argtypes = [cfgp, C.c_int]
         _lib.orc_transpose_blocks.argtypes = [cfgp, C.c_int, P, P]
         _lib.orc_adjoint.argtypes = [cfgp, P, P, P, P, P, P, C.c_int]
+        _lib.orc_time_step.argtypes = [cfgp, P, P, C.c_double, C.c_double, C.POINTER(Stats)]
     return _lib
 
 
@@ -243,6 +245,16 @@ class Oracle:
         self.L.orc_adjoint(C.byref(self.cfg), _p(np.ascontiguousarray(z, dtype=np.float64)), _p(U), _p(g),
                            _p(lam), _p(dRz), _p(dRq), ncycles)
         return lam, dRz, dRq
+
+    def time_step(self, U, dt, beta=0.0):
+        """Remark 2.6: U^{n+1} from U^n = U (returns a new array and the counters)."""
+        U = np.array(U, dtype=np.float64, copy=True)
+        st = Stats()
+        self.L.orc_time_step(C.byref(self.cfg), _p(np.ascontiguousarray(self.prob.z, dtype=np.float64)), _p(U),
+                             float(dt), float(beta), C.byref(st))
+        info = {"status": st.status, "n_newton": st.n_newton, "final_res": st.final_res,
+                "res_hist": list(st.res_hist)[:min(st.n_newton, HIST)]}
+        return U, info
 
     def solve(self, U0=None):
         U = np.array(self.prob.U0 if U0 is None else U0, dtype=np.float64, copy=True)

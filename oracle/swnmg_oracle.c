@@ -50,6 +50,11 @@ typedef struct {
   double alpha, fd_eps, tau, h_eps, eps_r, eps_p, tol;
   int n_levels, n_mg, nu1, nu2, gamma, coarse_sweeps, max_newton, max_blusgs, init_mode;
   double eps_f;                       /* Harten's entropy-fix width of the Roe flux */
+  /* implicit time step (Remark 2.6), active when t_ka > 0: the level-0
+   * residual becomes (1 - beta) R(U) + |K_i|/dt U - t_src with
+   * t_src = |K_i|/dt U^n - beta R(U^n), t_ka = |K_i|/dt, t_omb = 1 - beta */
+  double t_ka, t_omb;
+  const double* t_src;
 } orc_cfg;
 
 #define ORC_HIST 512
@@ -345,6 +350,15 @@ static double l1norm(const double* r, int nc) {
   return s;
 }
 
+/* Remark 2.6: the time-step residual of cell i on level 0 from its flux sum R */
+static void time_residual(const orc_cfg* c, const lvl* L, const double* U, int i, double R[3]) {
+  int nc = ncomp(c), n = L->n;
+  for (int s = 0; s < nc; ++s)
+    R[s] = (c->t_omb * R[s] + c->t_ka * U[s * n + i]) - c->t_src[s * n + i];
+}
+
+static int time_mode(const orc_cfg* c, const lvl* L) { return c->t_ka > 0.0 && L->nx == c->nx; }
+
 /* eq. Res: R_i = sum_e |e| F_hat(...), edges in the order W, E, S, N */
 static void cell_residual(const orc_cfg* c, const lvl* L, const double* z, const double* U,
                           int i, double R[3]) {
@@ -355,6 +369,7 @@ static void cell_residual(const orc_cfg* c, const lvl* L, const double* z, const
     cell_G(c, L, z, U, i, side, -1, 0, 0.0, G);
     for (int s = 0; s < nc; ++s) R[s] = R[s] + len * G[s];
   }
+  if (time_mode(c, L)) time_residual(c, L, U, i, R);
 }
 
 /* eq. NumerDiff plus eq. NewtonREG: the diagonal block
@@ -384,6 +399,12 @@ static void cell_jacobian(const orc_cfg* c, const lvl* L, const double* z, const
         for (int s = 0; s < nc; ++s) offd[side * 9 + s * nc + k] = len * ((Gp[s] - Gb[s]) * reps);
       }
     }
+  }
+  if (time_mode(c, L)) {   /* d/dU of (1 - beta) R + |K|/dt U: scaled blocks, |K|/dt on the diagonal */
+    time_residual(c, L, U, i, R);
+    for (int e = 0; e < nc * nc; ++e) D[e] = c->t_omb * D[e];
+    for (int s = 0; s < nc; ++s) D[s * nc + s] = D[s * nc + s] + c->t_ka;
+    if (offd) for (int e = 0; e < 36; ++e) offd[e] = c->t_omb * offd[e];
   }
   *rn = l1norm(R, nc);
   for (int s = 0; s < nc; ++s) D[s * nc + s] = D[s * nc + s] + c->alpha * (*rn);
@@ -1035,4 +1056,33 @@ int orc_adjoint(const orc_cfg* c, const double* z, const double* U, const double
   adjoint_vjp(c, &L, z, U, lam, dRz, dRq);
   free(R); free(blk); free(blkT);
   return ST_OK;
+}
+
+/* ---- Remark 2.6: one implicit (beta = 0) or semi-implicit time step -------
+ * |K_i| (U^{n+1} - U^n)/dt + beta R(U^n) + (1 - beta) R(U^{n+1}) = 0 solved by
+ * Steps 2-3 of Algorithm 1 from U^{n+1} = U^n (no Step 1); the Jacobian is
+ * |K_i|/dt I + (1 - beta) J, regularised by alpha ||R_i||_1 of the time-step
+ * residual.  U holds U^n on entry and U^{n+1} on return. */
+int orc_time_step(const orc_cfg* c, const double* z, double* U, double dt, double beta, orc_stats* st) {
+  if (check_cfg(c) || !(dt > 0.0) || !(beta >= 0.0 && beta < 1.0)) return ST_ARG;
+  lvl L = level_geom(c, 0);
+  int nc = ncomp(c), n = L.n;
+  double dx = (c->x1 - c->x0) / c->nx;
+  double area = (c->dim == 2) ? dx * ((c->y1 - c->y0) / c->ny) : dx;
+  double ka = area / dt;
+  orc_cfg cs = *c;
+  cs.t_ka = 0.0;
+  double* Rn = (double*)malloc(sizeof(double) * (size_t)n * nc);
+  double* S = (double*)malloc(sizeof(double) * (size_t)n * nc);
+  orc_residual(&cs, 0, z, U, Rn, NULL);
+  for (int e = 0; e < n * nc; ++e) S[e] = ka * U[e] - beta * Rn[e];
+  orc_cfg ct = *c;
+  ct.t_ka = ka;
+  ct.t_omb = 1.0 - beta;
+  ct.t_src = S;
+  ct.init_mode = INIT_NONE;
+  int status = orc_solve(&ct, z, U, st);
+  free(Rn);
+  free(S);
+  return status;
 }
