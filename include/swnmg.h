@@ -166,6 +166,21 @@ SWNMG_API swnmg_status swnmg_blusgs(swnmg_ctx* ctx, double* U_dev, int32_t level
  * Returns SWNMG_OK on convergence (sum ||R_i||_1 < tol). */
 SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* ctx, double* U_dev, swnmg_stats* st);
 
+/* One implicit (beta = 0) or semi-implicit (0 < beta < 1) time step of the
+ * time-dependent equations, Remark 2.6:
+ *   |K_i| (U^{n+1} - U^n)/dt + beta R(U^n) + (1 - beta) R(U^{n+1}) = 0,
+ * with |K_i| the cell measure (the remark's displayed equation leaves it out
+ * of the time difference; the finite-volume form has it).  The nonlinear
+ * system is solved by Steps 2-3 of Algorithm 1 from U^{n+1} = U^n (no Step 1):
+ * BLU-SGS and the multigrid work on the step's residual and its Jacobian
+ * |K_i|/dt I + (1 - beta) J, regularised by alpha ||R_i||_1 of the step's
+ * residual; the stop test is sum_i ||R_i||_1 < tol on that residual.
+ *   U_dev  (ncomp*n) U^n on entry, U^{n+1} on return
+ *   dt > 0, 0 <= beta < 1; st (nullable) as for swnmg_solve
+ * Returns as swnmg_solve.  The context's other entry points stay steady. */
+SWNMG_API swnmg_status swnmg_time_step(swnmg_ctx* ctx, double* U_dev, double dt, double beta,
+                                       swnmg_stats* st);
+
 /* Kernel classes timed by swnmg_set_timing (CUDA events on the context's
  * stream around each launch of that class). */
 enum {

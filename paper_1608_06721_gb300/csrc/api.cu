@@ -92,6 +92,9 @@ DevLevel dev_level(const swnmg_ctx* c, int l) {
   L.alpha = c->prm.alpha;
   L.eps = c->prm.fd_eps;
   L.eps_f = c->prm.eps_f;
+  L.t_ka = (l == 0 && c->t_on) ? c->t_ka : 0.0;   // implicit time step (Remark 2.6)
+  L.t_omb = c->t_omb;
+  L.t_src = c->t_src;
   L.reps = 1.0 / c->prm.fd_eps;
   for (int s = 0; s < 4; ++s) {
     L.bc[s].kind = c->prob.bc[s].kind;
@@ -312,6 +315,7 @@ void free_ctx(swnmg_ctx* c) {
   if (c->sgs_sync) cudaFree(c->sgs_sync);
   if (c->sticky) cudaFree(c->sticky);
   if (c->ghost) cudaFree(c->ghost);
+  if (c->t_src) cudaFree(c->t_src);
   if (c->hbuf) cudaFreeHost(c->hbuf);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
@@ -658,6 +662,31 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
   st->ms_newton = std::chrono::duration<double, std::milli>(t2 - t1).count();
   if (status != SWNMG_OK) return fail(c, status, "after " + std::to_string(it) + " Newton steps");
   return SWNMG_OK;
+}
+
+SWNMG_API swnmg_status swnmg_time_step(swnmg_ctx* c, double* U, double dt, double beta, swnmg_stats* st) {
+  if (!c || !U) return fail(c, SWNMG_ERR_ARG, "null pointer");
+  if (!(dt > 0) || !(beta >= 0 && beta < 1)) return fail(c, SWNMG_ERR_ARG, "need dt > 0 and 0 <= beta < 1");
+  const Level& v0 = c->lv[0];
+  const long long m = (long long)v0.n * c->nc;
+  if (!c->t_src) CUDA_TRY(c, cudaMalloc((void**)&c->t_src, sizeof(double) * m));
+  const double dx = (c->prob.x1 - c->prob.x0) / c->prob.nx;
+  const double area = c->prob.dim == 2 ? dx * ((c->prob.y1 - c->prob.y0) / c->prob.ny) : dx;
+  const double ka = area / dt;
+  c->t_on = false;
+  const DevLevel L = dev_level(c, 0);
+  launch_residual(L, v0.z, U, c->R, c->rn, c->eb, c->st);   // R(U^n)
+  launch_time_source(m, ka, beta, U, c->R, c->t_src, c->st);
+  LAUNCH_CHECK(c);
+  c->t_on = true;
+  c->t_ka = ka;
+  c->t_omb = 1.0 - beta;
+  const int32_t im = c->prm.init_mode;
+  c->prm.init_mode = SWNMG_INIT_NONE;
+  const swnmg_status s = swnmg_solve(c, U, st);
+  c->prm.init_mode = im;
+  c->t_on = false;
+  return s;
 }
 
 namespace {

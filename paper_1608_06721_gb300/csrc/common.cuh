@@ -38,6 +38,11 @@ struct DevLevel {
   int flux, llf_wetdry;
   double g, half_g, h_eps, eps_r, alpha, eps, reps;   // reps = 1/eps
   double eps_f;           // Harten's entropy-fix width (Roe flux)
+  // implicit time step (Remark 2.6), active when t_ka > 0 (level 0 only): the
+  // residual becomes (1 - beta) R(U) + |K|/dt U - t_src, t_src = |K|/dt U^n -
+  // beta R(U^n) (nc x n), t_ka = |K|/dt, t_omb = 1 - beta
+  double t_ka, t_omb;
+  const double* t_src;
   DevBC bc[4];            // W, E, S, N
 };
 
@@ -130,6 +135,9 @@ void launch_adjoint_q(const DevLevel& L, int side, const double* z, const double
                       double delta, double* out, cudaStream_t st);
 void launch_average(int dim, int nxf, int nyf, int ncomp, const double* vf, double* vc,
                     cudaStream_t st);
+// t_src = ka U^n - beta R(U^n) over m values (the time step's fixed part)
+void launch_time_source(long long m, double ka, double beta, const double* U, const double* R, double* src,
+                        cudaStream_t st);
 void launch_inject(int dim, int nxf, int nyf, int ncomp, const double* vc, double* vf,
                    cudaStream_t st);
 

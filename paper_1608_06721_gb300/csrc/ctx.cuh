@@ -46,6 +46,10 @@ struct swnmg_ctx {
   int* csing = nullptr;
   int* derr = nullptr;
   double* ghost = nullptr;  // BLU-SGS boundary ghost states (4 * max(nx, ny) * (nc + 1) * 3)
+  // implicit time step (Remark 2.6): on during swnmg_time_step only
+  bool t_on = false;
+  double t_ka = 0.0, t_omb = 1.0;
+  double* t_src = nullptr;  // |K|/dt U^n - beta R(U^n), nc x n
   int* sgs_sync = nullptr;  // ticket / abort / per-strip progress of the wavefront sweeps
   int* sticky = nullptr;    // set by a device wait that ran out of its bound
   double* hbuf = nullptr;   // pinned host scalars

@@ -297,6 +297,19 @@ __device__ __forceinline__ void cell_edges(const DevLevel& L, int i, int n_xe, i
 // R_i = sum over W, E, S, N of |e| G (eq. Res), ||R_i||_1
 // (a non-finite cell state makes ||R_i||_1 NaN, so that the sums report it:
 // the reconstruction's max(0, .) would otherwise hide a NaN depth)
+// Remark 2.6: an off-diagonal Jacobian entry of a time step is (1 - beta) x
+__device__ __forceinline__ double time_scale(const DevLevel& L, double v) {
+  return L.t_ka > 0.0 ? L.t_omb * v : v;
+}
+
+// Remark 2.6: the time-step residual of cell i from its flux sum r
+template <int NC>
+__device__ __forceinline__ void time_residual(const DevLevel& L, const double* __restrict__ U, int i,
+                                              double r[NC]) {
+  const long long n = L.n;
+  for (int s = 0; s < NC; ++s) r[s] = (L.t_omb * r[s] + L.t_ka * U[s * n + i]) - L.t_src[s * n + i];
+}
+
 template <int NC>
 __device__ __forceinline__ void res_cell(const DevLevel& L, const double* __restrict__ eb,
                                          const double* __restrict__ U, double* __restrict__ R,
@@ -313,8 +326,9 @@ __device__ __forceinline__ void res_cell(const DevLevel& L, const double* __rest
       a = a + L.ey * eb[s * (long long)n_e + eN];
     }
     r[s] = a;
-    R[s * (long long)L.n + i] = a;
   }
+  if (L.t_ka > 0.0) time_residual<NC>(L, U, i, r);
+  for (int s = 0; s < NC; ++s) R[s * (long long)L.n + i] = r[s];
   double m = fabs(r[0]) + fabs(r[1]);
   if (NC == 3) m = m + fabs(r[NC - 1]);
   bool fin = true;
@@ -369,7 +383,7 @@ __device__ __forceinline__ void jac_edge(const DevLevel& L, const double* __rest
       for (int s = 0; s < NC; ++s) {
         eb[(f_dLL + s * NC + k) * ne + e] = len * ((GL[s] - GLb[s]) * L.reps);
         if (iR >= 0) st<T>(blk, ((long long)(bR * NC * NC + s * NC + k)) * P + sR,
-                           len * ((GR[s] - GRb[s]) * L.reps));
+                           time_scale(L, len * ((GR[s] - GRb[s]) * L.reps)));
       }
     } else {
       for (int s = 0; s < NC; ++s) {
@@ -388,7 +402,7 @@ __device__ __forceinline__ void jac_edge(const DevLevel& L, const double* __rest
       for (int s = 0; s < NC; ++s) {
         eb[(f_dRR + s * NC + k) * ne + e] = len * ((GR[s] - GRb[s]) * L.reps);
         if (iL >= 0) st<T>(blk, ((long long)(bL * NC * NC + s * NC + k)) * P + sL,
-                           len * ((GL[s] - GLb[s]) * L.reps));
+                           time_scale(L, len * ((GL[s] - GLb[s]) * L.reps)));
       }
     } else {
       for (int s = 0; s < NC; ++s) {
@@ -410,8 +424,9 @@ __global__ void k_jac_edges(DevLevel L, const double* __restrict__ z, const doub
 // residual and its norm.  1D cells have only W and E.
 template <int NC, typename T>
 __device__ __forceinline__ void jac_cell(const DevLevel& L, const double* __restrict__ eb,
-                                         double* __restrict__ R, double* __restrict__ rn,
-                                         void* __restrict__ blk, int n_xe, int n_e, int i) {
+                                         const double* __restrict__ U, double* __restrict__ R,
+                                         double* __restrict__ rn, void* __restrict__ blk, int n_xe, int n_e,
+                                         int i) {
   int eW, eE, eS, eN;
   cell_edges(L, i, n_xe, eW, eE, eS, eN);
   const long long ne = n_e, n = L.n, P = skew_slots(L.nx, L.ny);
@@ -426,8 +441,10 @@ __device__ __forceinline__ void jac_cell(const DevLevel& L, const double* __rest
       a = a + L.ey * eb[s * ne + eN];
     }
     r[s] = a;
-    R[s * n + i] = a;
   }
+  const bool tm = L.t_ka > 0.0;   // time step: scaled blocks, |K|/dt on the diagonal
+  if (tm) time_residual<NC>(L, U, i, r);
+  for (int s = 0; s < NC; ++s) R[s * n + i] = r[s];
   double m = fabs(r[0]) + fabs(r[1]);
   if (NC == 3) m = m + fabs(r[NC - 1]);
   if (rn) rn[i] = m;
@@ -443,16 +460,21 @@ __device__ __forceinline__ void jac_cell(const DevLevel& L, const double* __rest
         d = d + eb[(f_dRR + f) * ne + eS];
         d = d + eb[(f_dLL + f) * ne + eN];
       }
+      if (tm) {
+        d = L.t_omb * d;
+        if (s == k) d = d + L.t_ka;
+      }
       if (s == k) d = d + am;
       st<T>(blk, (long long)f * P + si, d);
     }
 }
 
 template <int NC, typename T>
-__global__ void k_jac_cells(DevLevel L, const double* __restrict__ eb, double* __restrict__ R,
-                            double* __restrict__ rn, void* __restrict__ blk, int n_xe, int n_e) {
+__global__ void k_jac_cells(DevLevel L, const double* __restrict__ eb, const double* __restrict__ U,
+                            double* __restrict__ R, double* __restrict__ rn, void* __restrict__ blk, int n_xe,
+                            int n_e) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < L.n) jac_cell<NC, T>(L, eb, R, rn, blk, n_xe, n_e, i);
+  if (i < L.n) jac_cell<NC, T>(L, eb, U, R, rn, blk, n_xe, n_e, i);
 }
 
 // ---- block solve with the same elimination as the reference definition -----
@@ -686,6 +708,11 @@ __device__ __forceinline__ void blusgs_group(const DevLevel& L, const double* __
         else D[s * NC + (pp - 1)] = D[s * NC + (pp - 1)] + w;
       }
   if (!cell_ok || g != 0) return;
+  if (L.t_ka > 0.0) {   // time step (Remark 2.6): the step's residual and diagonal block
+    for (int s = 0; s < NC; ++s) Rs[s] = (L.t_omb * Rs[s] + L.t_ka * ci[s]) - L.t_src[s * n + i];
+    for (int e = 0; e < NC * NC; ++e) D[e] = L.t_omb * D[e];
+    for (int s = 0; s < NC; ++s) D[s * NC + s] = D[s * NC + s] + L.t_ka;
+  }
   double m = fabs(Rs[0]) + fabs(Rs[1]);
   if (NC == 3) m = m + fabs(Rs[NC - 1]);
   const double am = L.alpha * m;
@@ -875,6 +902,13 @@ __global__ void k_newton_update(int nx, int ny, int nc, double tau, double h_eps
   if (i < nx * ny) newton_update_cell<T>(nx, ny, nc, tau, h_eps, U, dU, i);
 }
 
+// t_src = ka U^n - beta R(U^n) (Remark 2.6)
+__global__ void k_time_source(long long m, double ka, double beta, const double* __restrict__ U,
+                              const double* __restrict__ R, double* __restrict__ src) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e < m) src[e] = ka * U[e] - beta * R[e];
+}
+
 // coarse value = mean of the children (child order 00, 10, 01, 11)
 __device__ __forceinline__ void average_cell(int dim, int nxf, int nyf, int ncomp, const double* __restrict__ vf,
                                              double* __restrict__ vc, int I) {
@@ -963,7 +997,7 @@ __global__ void __launch_bounds__(128) kb_jac_cells(BLaunch bl) {
   BATCH_PROLOGUE(bl)
   const DevLevel L = it->L;
   if (idx >= L.n) return;
-  jac_cell<NC, T>(L, it->eb, it->R, it->rn, it->blk, it->n_xe, it->n_e, idx);
+  jac_cell<NC, T>(L, it->eb, it->U, it->R, it->rn, it->blk, it->n_xe, it->n_e, idx);
 }
 
 template <typename T>
@@ -1105,18 +1139,18 @@ void launch_jacobian(const DevLevel& L, const double* z, const double* U, double
   if (L.nc == 3) {
     if (fp32) {
       k_jac_edges<3, float><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, blk, n_xe, n_e);
-      k_jac_cells<3, float><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, R, rn, blk, n_xe, n_e);
+      k_jac_cells<3, float><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, U, R, rn, blk, n_xe, n_e);
     } else {
       k_jac_edges<3, double><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, blk, n_xe, n_e);
-      k_jac_cells<3, double><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, R, rn, blk, n_xe, n_e);
+      k_jac_cells<3, double><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, U, R, rn, blk, n_xe, n_e);
     }
   } else {
     if (fp32) {
       k_jac_edges<2, float><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, blk, n_xe, n_e);
-      k_jac_cells<2, float><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, R, rn, blk, n_xe, n_e);
+      k_jac_cells<2, float><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, U, R, rn, blk, n_xe, n_e);
     } else {
       k_jac_edges<2, double><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, blk, n_xe, n_e);
-      k_jac_cells<2, double><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, R, rn, blk, n_xe, n_e);
+      k_jac_cells<2, double><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, U, R, rn, blk, n_xe, n_e);
     }
   }
 }
@@ -1172,6 +1206,12 @@ void launch_newton_update(int nx, int ny, int nc, double tau, double h_eps, doub
     k_newton_update<float><<<nblk(n, 256), 256, 0, st>>>(nx, ny, nc, tau, h_eps, U, (const float*)dU);
   else
     k_newton_update<double><<<nblk(n, 256), 256, 0, st>>>(nx, ny, nc, tau, h_eps, U, (const double*)dU);
+}
+
+void launch_time_source(long long m, double ka, double beta, const double* U, const double* R, double* src,
+                        cudaStream_t st) {
+  count_launches(1);
+  k_time_source<<<nblk(m, 256), 256, 0, st>>>(m, ka, beta, U, R, src);
 }
 
 void launch_average(int dim, int nxf, int nyf, int ncomp, const double* vf, double* vc,

@@ -115,6 +115,9 @@ SWNMG_API swnmg_status swnmg_residual_noalloc(const swnmg_problem* p, const swnm
   L.eps = q->fd_eps;
   L.reps = 1.0 / q->fd_eps;
   L.eps_f = q->eps_f;
+  L.t_ka = 0.0;   // steady residual
+  L.t_omb = 1.0;
+  L.t_src = nullptr;
   for (int k = 0; k < 4; ++k) {
     L.bc[k].kind = p->bc[k].kind;
     L.bc[k].h = p->bc[k].h;

@@ -81,6 +81,7 @@ def lib():
         L.swnmg_residual_noalloc.argtypes = [C.POINTER(Problem), C.POINTER(Params), vp, vp, vp, vp, vp, vp]
         L.swnmg_residual_noalloc.restype = C.c_int
         L.swnmg_adjoint.argtypes = [vp, vp, vp, vp, vp, dp, C.c_int32, C.c_double, C.POINTER(C.c_int32)]
+        L.swnmg_time_step.argtypes = [vp, vp, C.c_double, C.c_double, C.POINTER(Stats)]
         L.swnmg_level_cells.argtypes = [vp, C.c_int32]
         L.swnmg_batch_create.argtypes = [C.POINTER(Problem), C.POINTER(C.c_int32), C.c_int32, C.POINTER(Params),
                                          C.POINTER(vp), vp, C.POINTER(vp)]
@@ -95,7 +96,8 @@ def lib():
         for f in ("swnmg_default_params", "swnmg_create", "swnmg_destroy", "swnmg_set_params",
                   "swnmg_residual", "swnmg_jacobian", "swnmg_get_blocks", "swnmg_vcycle",
                   "swnmg_sgs_sweep", "swnmg_blusgs", "swnmg_solve", "swnmg_set_timing",
-                  "swnmg_get_timing", "swnmg_adjoint", "swnmg_batch_create", "swnmg_batch_destroy",
+                  "swnmg_get_timing", "swnmg_adjoint", "swnmg_time_step", "swnmg_batch_create",
+                  "swnmg_batch_destroy",
                   "swnmg_batch_solve", "swnmg_batch_set_graph", "swnmg_batch_tune", "swnmg_batch_set_tuning"):
             getattr(L, f).restype = C.c_int
         _lib = L
@@ -241,6 +243,16 @@ class Solver:
                 "init_res": st.init_res, "final_res": st.final_res,
                 "res_hist": list(st.res_hist)[:min(st.n_newton, HIST)],
                 "ms_step1": st.ms_step1, "ms_newton": st.ms_newton}
+
+    def time_step(self, U, dt, beta=0.0, check=False):
+        """Remark 2.6: U (U^n) becomes U^{n+1} in place; returns the counters."""
+        st = Stats()
+        rc = self.L.swnmg_time_step(self.h, _ptr(U), float(dt), float(beta), C.byref(st))
+        if check:
+            self._check(rc)
+        elif rc not in (OK, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_DIVERGED):
+            self._check(rc)
+        return _stats_dict(st, self.params.n_levels)
 
     def adjoint(self, U, g, max_cycles=100, rtol=1e-12, check=True):
         """swnmg_adjoint: lambda with J(U)^T lambda = g by multigrid cycles on the
