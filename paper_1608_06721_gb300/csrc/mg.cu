@@ -79,26 +79,69 @@ __global__ void k_lu_factor(int nx, int ny, const T* __restrict__ blk, T* __rest
   if (slot < skew_slots(nx, ny)) lu_factor_slot<NC, T>(nx, ny, blk, lu, piv, slot);
 }
 
+// explicit fused multiply-add: the smoother's rounding does not depend on how
+// the compiler contracts a given call site
+template <typename T> __device__ __forceinline__ T tfma(T a, T b, T c);
+template <> __device__ __forceinline__ float tfma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double tfma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename T> __device__ __forceinline__ T pick3(const T* r, int p) {
+  return p == 0 ? r[0] : (p == 1 ? r[1] : r[2]);
+}
+
 // LU solve with the factors of one cell read from 9 values L[e*ls]
 template <int NC, typename T>
 __device__ __forceinline__ void lu_apply_v(const T* __restrict__ L, int ls, int8_t pv, const T r[NC],
                                            T x[NC]) {
   const int p0 = pv % 3, p1 = (pv / 3) % 3, p2 = pv / 9;
   if (NC == 3) {
-    T y0 = r[p0], y1 = r[p1 % NC], y2 = r[p2 % NC];
-    y1 = y1 - L[0 * ls] * y0;
-    y2 = y2 - L[1 * ls] * y0 - L[2 * ls] * y1;
+    const T y0 = pick3(r, p0);
+    const T y1 = tfma(-L[0 * ls], y0, pick3(r, p1));
+    const T y2 = tfma(-L[2 * ls], y1, tfma(-L[1 * ls], y0, pick3(r, p2)));
     const T x2 = y2 * L[8 * ls];
-    const T x1 = (y1 - L[5 * ls] * x2) * L[7 * ls];
-    const T x0 = (y0 - L[3 * ls] * x1 - L[4 * ls] * x2) * L[6 * ls];
+    const T x1 = tfma(-L[5 * ls], x2, y1) * L[7 * ls];
+    const T x0 = tfma(-L[4 * ls], x2, tfma(-L[3 * ls], x1, y0)) * L[6 * ls];
     x[0] = x0; x[1 % NC] = x1; x[2 % NC] = x2;
   } else {
-    T y0 = r[p0], y1 = r[p1 % NC];
-    y1 = y1 - L[0 * ls] * y0;
+    const T y0 = p0 == 0 ? r[0] : r[1 % NC];
+    const T y1 = tfma(-L[0 * ls], y0, p1 == 0 ? r[0] : r[1 % NC]);
     const T x1 = y1 * L[7 * ls];
-    const T x0 = (y0 - L[3 * ls] * x1) * L[6 * ls];
+    const T x0 = tfma(-L[3 * ls], x1, y0) * L[6 * ls];
     x[0] = x0; x[1 % NC] = x1;
   }
+}
+
+// One block Gauss-Seidel cell update, x_i = D_i^-1 (b_i - A_W x_W - A_E x_E -
+// A_S x_S - A_N x_N) in logical directions (the sweep's own west / south are
+// the new values): the old east and north terms first, then the new west and
+// south terms.  A* point at a block's entry (s, k) = A*[(s NC + k) * es]; lu
+// at the 9 LU values (stride es).  Explicit FMAs fix its rounding wherever it
+// is inlined.
+template <int NC, typename T>
+__device__ __forceinline__ void sgs_cell(const T* AW, const T* AE, const T* AS, const T* AN, int es,
+                                         const T* lu, int8_t pv, const T bb[NC], bool hW, const T xw[NC],
+                                         bool hE, const T xe[NC], bool hS, const T xs[NC], bool hN,
+                                         const T xn[NC], T res[NC]) {
+  T r[NC];
+#pragma unroll
+  for (int s2 = 0; s2 < NC; ++s2) {
+    T a = bb[s2];
+    if (hE)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) a = tfma(-AE[(s2 * NC + k) * es], xe[k], a);
+    if (hN)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) a = tfma(-AN[(s2 * NC + k) * es], xn[k], a);
+    T w = T(0), so = T(0);
+    if (hW)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) w = tfma(AW[(s2 * NC + k) * es], xw[k], w);
+    if (hS)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) so = tfma(AS[(s2 * NC + k) * es], xs[k], so);
+    r[s2] = (a - w) - so;
+  }
+  lu_apply_v<NC, T>(lu, es, pv, r, res);
 }
 
 // ---- Galerkin coarse operator: A_{IJ,l+1} = sum_{i in I} sum_{j in J} A_ij ---
@@ -516,35 +559,11 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
           xe[k] = Vl[(EX + k) * ES];
           xn[k] = nedge ? rn[0][k] : Vl[(EX + k) * ES + (FWD ? 1 : -1)];
         }
-        // east and north terms first (old values), then the west (this
-        // lane's previous result) and south (the lane below) terms
-        T r[NC], tW[NC], tS[NC];
+        T bb[NC];
 #pragma unroll
-        for (int s2 = 0; s2 < NC; ++s2) {
-          T a = Vl[(EB + s2) * ES];
-          if (c < nx - 1)
-#pragma unroll
-            for (int k = 0; k < NC; ++k) a -= Vl[(oE + s2 * NC + k) * ES] * xe[k];
-          if (hasN)
-#pragma unroll
-            for (int k = 0; k < NC; ++k) a -= Vl[(oN + s2 * NC + k) * ES] * xn[k];
-          r[s2] = a;
-        }
-#pragma unroll
-        for (int s2 = 0; s2 < NC; ++s2) {
-          T w = T(0), so = T(0);
-          if (c > 0)
-#pragma unroll
-            for (int k = 0; k < NC; ++k) w += Vl[(oW + s2 * NC + k) * ES] * xprev[k];
-          if (hasS)
-#pragma unroll
-            for (int k = 0; k < NC; ++k) so += Vl[(oS + s2 * NC + k) * ES] * xS[k];
-          tW[s2] = w;
-          tS[s2] = so;
-        }
-#pragma unroll
-        for (int s2 = 0; s2 < NC; ++s2) r[s2] = (r[s2] - tW[s2]) - tS[s2];
-        lu_apply_v<NC, T>(Vl + (size_t)NOFF * ES, ES, PV[line * 32 + lane], r, res);
+        for (int k = 0; k < NC; ++k) bb[k] = Vl[(EB + k) * ES];
+        sgs_cell<NC, T>(Vl + oW * ES, Vl + oE * ES, Vl + oS * ES, Vl + oN * ES, ES, Vl + (size_t)NOFF * ES,
+                        PV[line * 32 + lane], bb, c > 0, xprev, c < nx - 1, xe, hasS, xS, hasN, xn, res);
         const long long slot = (dbase + line) * 32 + lane;   // coalesced: one line per step
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
