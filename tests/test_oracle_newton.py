@@ -151,3 +151,23 @@ def test_paper_spectral_radius_table31(k, n):
 
 def test_paper_spectral_radius_table32():
     assert abs(_steady_rho(W.transcritical_1d(64, 1)) - PAPER["t32_hll_rho"][0]) <= 5e-3
+
+
+@pytest.mark.parametrize("flux,key", [(W.FLUX_HLL, "hll"), (W.FLUX_LLF, "llf"), (W.FLUX_ROE, "roe")])
+def test_paper_table33_shock(flux, key):
+    """Table 3.3 (Example 3.2 (II), transcritical flow with a hydraulic jump):
+    V-cycle (N_L = 3) Newton steps within one at N = 64, 128 and the block
+    SGS spectral radius at the steady state (N = 64 within 1e-4: measured
+    0.39174 / 0.92514 / 0.25370; N = 128 within 1e-3)."""
+    for k, n in enumerate((64, 128)):
+        p = W.transcritical_1d(n, 2, flux=flux)
+        if flux == W.FLUX_LLF:
+            p = p.with_params(llf_wetdry=0)
+        o = Oracle(p)
+        U, info = o.solve()
+        assert info["status"] == 0
+        assert abs(info["n_newton"] - PAPER["t33_%s_V_NL3_Nstep" % key][k]) <= 1
+        R, rn, blk = o.jacobian(U)
+        rho = dense.sgs_iteration_radius(dense.assemble(blk, p.nx, 1), p.ncomp)
+        assert abs(rho - PAPER["t33_%s_rho" % key][k]) <= (1e-4 if n == 64 else 1e-3), rho
+
