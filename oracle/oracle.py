@@ -35,7 +35,8 @@ class Cfg(C.Structure):
                 ("n_levels", C.c_int), ("n_mg", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("gamma", C.c_int), ("coarse_sweeps", C.c_int), ("max_newton", C.c_int),
                 ("max_blusgs", C.c_int), ("init_mode", C.c_int), ("eps_f", C.c_double),
-                ("t_ka", C.c_double), ("t_omb", C.c_double), ("t_src", C.c_void_p)]
+                ("t_ka", C.c_double), ("t_omb", C.c_double), ("t_src", C.c_void_p),
+                ("mesh_x", C.c_void_p), ("mesh_y", C.c_void_p), ("t_kai", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -81,6 +82,7 @@ def lib():
         _lib.orc_average.argtypes = [cfgp, C.c_int, C.c_int, P, P]
         _lib.orc_solve.argtypes = [cfgp, P, P, C.POINTER(Stats)]
         _lib.orc_level_cells.argtypes = [cfgp, C.c_int]
+        _lib.orc_cell_areas.argtypes = [cfgp, C.c_int, P]
         _lib.orc_transpose_blocks.argtypes = [cfgp, C.c_int, P, P]
         _lib.orc_adjoint.argtypes = [cfgp, P, P, P, P, P, P, C.c_int]
         _lib.orc_time_step.argtypes = [cfgp, P, P, C.c_double, C.c_double, C.POINTER(Stats)]
@@ -93,9 +95,17 @@ def _p(a):
 
 
 def make_cfg(prob, **over) -> Cfg:
-    """Oracle configuration from a workloads.Problem (+ parameter overrides)."""
+    """Oracle configuration from a workloads.Problem (+ parameter overrides).
+    A curvilinear problem's vertex arrays are referenced, not copied: the
+    configuration keeps them alive as ``_mesh``."""
     prm = prob.params.replace(**over) if over else prob.params
     c = Cfg()
+    if getattr(prob, "mesh_x", None) is not None:
+        mx = np.ascontiguousarray(prob.mesh_x, dtype=np.float64)
+        my = np.ascontiguousarray(prob.mesh_y, dtype=np.float64)
+        assert mx.shape == my.shape == (prob.ny + 1, prob.nx + 1)
+        c._mesh = (mx, my)
+        c.mesh_x, c.mesh_y = mx.ctypes.data, my.ctypes.data
     c.dim, c.nx, c.ny = prob.dim, prob.nx, (prob.ny if prob.dim == 2 else 1)
     c.x0, c.x1, c.y0, c.y1, c.g = prob.x0, prob.x1, prob.y0, prob.y1, prob.g
     for s in range(4):
@@ -122,6 +132,12 @@ class Oracle:
 
     def ncells(self, level=0):
         return self.L.orc_level_cells(C.byref(self.cfg), level)
+
+    def areas(self, level=0):
+        """|K_i| of the cells of a curvilinear mesh's level."""
+        out = np.zeros(self.ncells(level))
+        assert self.L.orc_cell_areas(C.byref(self.cfg), level, _p(out)) == 0
+        return out
 
     def z_levels(self):
         zs = [np.ascontiguousarray(self.prob.z, dtype=np.float64)]

@@ -16,6 +16,8 @@
  *
  * Layouts (shared with the library's interface, not its code):
  *   cell index      i = ix + nx*iy (x fastest)
+ *   mesh            uniform Cartesian, or (2D) structured curvilinear with
+ *                   vertex (a, b) at (mesh_x, mesh_y)[a + (nx+1)*b]
  *   state / vectors SoA: comp c of cell i at v[c*n + i]; 1D: (h, hu), 2D: (h, hu, hv)
  *   blocks          blk[((i*5 + b)*nc + s)*nc + k], b = 0 diag, 1 W, 2 E, 3 S, 4 N;
  *                   block b maps the neighbour's unknown k to equation s of cell i.
@@ -27,7 +29,10 @@
  *
  * Parity status: pinned by tests/test_oracle_*.py (lake at rest, Bernoulli
  * closed form, flux properties, dense-matrix restatements of Algorithm 0,
- * central-difference Jacobian, the paper's Newton counts and spectral radii).
+ * central-difference Jacobian, the paper's Newton counts and spectral radii;
+ * on curvilinear meshes: the Cartesian special case, rotation invariance,
+ * free-stream preservation, and the oblique-jump plateau heights of
+ * Example 3.4).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -55,6 +60,14 @@ typedef struct {
    * t_src = |K_i|/dt U^n - beta R(U^n), t_ka = |K_i|/dt, t_omb = 1 - beta */
   double t_ka, t_omb;
   const double* t_src;
+  /* structured curvilinear quadrilateral mesh (2D; both NULL: the uniform
+   * Cartesian mesh of [x0,x1] x [y0,y1]).  Vertex (a, b), 0 <= a <= nx,
+   * 0 <= b <= ny, lies at (mesh_x, mesh_y)[a + (nx + 1) b]; cell (ix, iy) has
+   * the corners (ix, iy), (ix+1, iy), (ix+1, iy+1), (ix, iy+1).  The coarse
+   * mesh of level l is that of every 2^l-th vertex. */
+  const double* mesh_x;
+  const double* mesh_y;
+  const double* t_kai;                /* per-cell |K_i|/dt of a time step on such a mesh */
 } orc_cfg;
 
 #define ORC_HIST 512
@@ -65,12 +78,22 @@ typedef struct {
   double res_hist[ORC_HIST];          /* sum ||R_i||_1 after Newton step n+1 */
 } orc_stats;
 
-typedef struct { int nx, ny, n; double ex, ey; } lvl;   /* ex = |x-edge|, ey = |y-edge| */
+typedef struct {
+  int nx, ny, n;
+  double ex, ey;                      /* Cartesian: ex = |x-edge|, ey = |y-edge| */
+  const double* vx;                   /* curvilinear: the finest vertices, NULL otherwise */
+  const double* vy;
+  int vrow, vstep;                    /* vertex row length (nx + 1) and 2^l */
+} lvl;
 
 static int ncomp(const orc_cfg* c) { return c->dim == 2 ? 3 : 2; }
 
 static lvl level_geom(const orc_cfg* c, int l) {
   lvl L;
+  L.vx = L.vy = NULL;
+  L.vrow = c->nx + 1;
+  L.vstep = 1 << l;
+  if (c->dim == 2 && c->mesh_x && c->mesh_y) { L.vx = c->mesh_x; L.vy = c->mesh_y; }
   L.nx = c->nx >> l;
   L.ny = (c->dim == 2) ? (c->ny >> l) : 1;
   L.n = L.nx * L.ny;
@@ -95,6 +118,52 @@ static int nbr(const lvl* L, int i, int side) {
     case 2: return iy > 0 ? i - L->nx : -1;
     default: return iy < L->ny - 1 ? i + L->nx : -1;
   }
+}
+
+/* ---- structured curvilinear meshes (Examples 3.4, 3.5) --------------------
+ * Every quantity of eq. totalFlux that depends on the mesh -- |e_ij|, n_ij and
+ * |K_i| -- is taken from the straight segments between a cell's four
+ * vertices. */
+static int curvilinear(const lvl* L) { return L->vx != NULL; }
+
+static void vertex(const lvl* L, int a, int b, double* x, double* y) {
+  size_t k = (size_t)a * L->vstep + (size_t)L->vrow * ((size_t)b * L->vstep);
+  *x = L->vx[k];
+  *y = L->vy[k];
+}
+
+/* Edge `side` (0 W, 1 E, 2 S, 3 N) of cell i: its length |e| and its unit
+ * normal n, oriented from the lower-index cell to the higher-index one (the
+ * +i direction on W/E edges, +j on S/N edges, as on the Cartesian mesh).
+ * t = the edge's vertex difference, from (a, b) to (a, b+1) on W/E edges and
+ * from (a, b) to (a+1, b) on S/N edges; n is t turned by -90 degrees on W/E
+ * edges and by +90 degrees on S/N edges. */
+static void edge_frame(const lvl* L, int i, int side, double* len, double* nx, double* ny) {
+  int ix = i % L->nx, iy = i / L->nx;
+  int a0 = ix, b0 = iy, a1, b1;
+  if (side < 2) { a0 = ix + (side & 1); a1 = a0; b1 = iy + 1; }
+  else { b0 = iy + (side & 1); b1 = b0; a1 = ix + 1; }
+  double xa, ya, xb, yb;
+  vertex(L, a0, b0, &xa, &ya);
+  vertex(L, a1, b1, &xb, &yb);
+  double tx = xb - xa, ty = yb - ya;
+  double l = sqrt(tx * tx + ty * ty);
+  *len = l;
+  if (side < 2) { *nx = ty / l; *ny = -tx / l; }
+  else { *nx = -ty / l; *ny = tx / l; }
+}
+
+/* |K_i| of the quadrilateral (shoelace form: half the cross product of its
+ * diagonals); positive for a mesh whose i and j directions are
+ * counter-clockwise */
+static double cell_area(const lvl* L, int i) {
+  int ix = i % L->nx, iy = i / L->nx;
+  double x00, y00, x10, y10, x11, y11, x01, y01;
+  vertex(L, ix, iy, &x00, &y00);
+  vertex(L, ix + 1, iy, &x10, &y10);
+  vertex(L, ix + 1, iy + 1, &x11, &y11);
+  vertex(L, ix, iy + 1, &x01, &y01);
+  return 0.5 * ((x11 - x00) * (y01 - y10) - (x01 - x10) * (y11 - y00));
 }
 
 static double mn(double a, double b) { return (a < b) ? a : b; }
@@ -308,8 +377,12 @@ static void load_state(const double* U, int n, int nc, int idx, int pc, int pk, 
 /* G received by cell i from its edge `side`, in global components; the state
  * of cell pc (i or its neighbour) has component pk perturbed by eps.  The
  * edge is always evaluated with its lower-index cell on the left. */
+static void cell_G_curv(const orc_cfg* c, const lvl* L, const double* z, const double* U, int i,
+                        int side, int pc, int pk, double eps, double G[3]);
+
 static void cell_G(const orc_cfg* c, const lvl* L, const double* z, const double* U, int i,
                    int side, int pc, int pk, double eps, double G[3]) {
+  if (curvilinear(L)) { cell_G_curv(c, L, z, U, i, side, pc, pk, eps, G); return; }
   int nc = ncomp(c), n = L->n;
   int axis = side >> 1, upper = side & 1;
   int j = nbr(L, i, side);
@@ -341,8 +414,57 @@ static void cell_G(const orc_cfg* c, const lvl* L, const double* z, const double
   else { G[0] = Ge[0]; G[1] = Ge[2]; G[2] = Ge[1]; }
 }
 
+/* cell_G on a curvilinear mesh.  The states are taken to the edge frame
+ * (h, u_n, u_tau) with u_n = u.n and u_tau = u.tau, tau being n turned by
+ * +90 degrees on W/E edges and by -90 degrees on S/N edges (so that on a
+ * Cartesian mesh the frame is the one above: u_tau is v on W/E edges and u
+ * on S/N edges; a boundary's discharge q is along n and its u_tau along tau).
+ * The flux is taken back to global components, F_n = F_1 n + F_2 tau, and the
+ * source term of eq. totalFlux, g/2 h_{e,-}^2 (n^x, n^y), is subtracted there. */
+static void cell_G_curv(const orc_cfg* c, const lvl* L, const double* z, const double* U, int i,
+                        int side, int pc, int pk, double eps, double G[3]) {
+  int n = L->n, upper = side & 1;
+  int j = nbr(L, i, side);
+  double len, nx, ny;
+  edge_frame(L, i, side, &len, &nx, &ny);
+  double tx = (side < 2) ? -ny : ny, ty = (side < 2) ? nx : -nx;
+  double qi[3], u, v, hi, ui, vi, hj, uj, vj, zj;
+  load_state(U, n, 3, i, pc, pk, eps, qi);
+  hi = qi[0];
+  vels(hi, qi[1], qi[2], c->h_eps, &u, &v);
+  ui = u * nx + v * ny;
+  vi = u * tx + v * ty;
+  if (j >= 0) {
+    double qj[3];
+    load_state(U, n, 3, j, pc, pk, eps, qj);
+    hj = qj[0];
+    vels(hj, qj[1], qj[2], c->h_eps, &u, &v);
+    uj = u * nx + v * ny;
+    vj = u * tx + v * ty;
+    zj = z[j];
+  } else {
+    ghost(c, &c->bc[side], upper ? 1.0 : -1.0, hi, ui, vi, &hj, &uj, &vj);
+    zj = z[i];                                  /* ghost bed = interior bed */
+  }
+  double o[5];
+  if (upper) edge_eval(c, hi, ui, vi, z[i], hj, uj, vj, zj, o);
+  else edge_eval(c, hj, uj, vj, zj, hi, ui, vi, z[i], o);
+  double fx = o[1] * nx + o[2] * tx, fy = o[1] * ny + o[2] * ty;
+  double s = upper ? o[3] : o[4];
+  double G0 = o[0], G1 = fx - s * nx, G2 = fy - s * ny;
+  if (upper) { G[0] = G0; G[1] = G1; G[2] = G2; }
+  else { G[0] = -G0; G[1] = -G1; G[2] = -G2; }
+}
+
 static int nsides(const orc_cfg* c) { return c->dim == 2 ? 4 : 2; }
-static double side_len(const lvl* L, int side) { return side < 2 ? L->ex : L->ey; }
+
+/* |e| of edge `side` of cell i */
+static double edge_len(const lvl* L, int i, int side) {
+  if (!curvilinear(L)) return side < 2 ? L->ex : L->ey;
+  double len, nx, ny;
+  edge_frame(L, i, side, &len, &nx, &ny);
+  return len;
+}
 
 static double l1norm(const double* r, int nc) {
   double s = fabs(r[0]) + fabs(r[1]);
@@ -350,11 +472,14 @@ static double l1norm(const double* r, int nc) {
   return s;
 }
 
+/* |K_i|/dt of a time step: one value on the uniform mesh, per cell on a curvilinear one */
+static double time_ka(const orc_cfg* c, int i) { return c->t_kai ? c->t_kai[i] : c->t_ka; }
+
 /* Remark 2.6: the time-step residual of cell i on level 0 from its flux sum R */
 static void time_residual(const orc_cfg* c, const lvl* L, const double* U, int i, double R[3]) {
   int nc = ncomp(c), n = L->n;
   for (int s = 0; s < nc; ++s)
-    R[s] = (c->t_omb * R[s] + c->t_ka * U[s * n + i]) - c->t_src[s * n + i];
+    R[s] = (c->t_omb * R[s] + time_ka(c, i) * U[s * n + i]) - c->t_src[s * n + i];
 }
 
 static int time_mode(const orc_cfg* c, const lvl* L) { return c->t_ka > 0.0 && L->nx == c->nx; }
@@ -365,7 +490,7 @@ static void cell_residual(const orc_cfg* c, const lvl* L, const double* z, const
   int nc = ncomp(c);
   R[0] = R[1] = R[2] = 0.0;
   for (int side = 0; side < nsides(c); ++side) {
-    double G[3], len = side_len(L, side);
+    double G[3], len = edge_len(L, i, side);
     cell_G(c, L, z, U, i, side, -1, 0, 0.0, G);
     for (int s = 0; s < nc; ++s) R[s] = R[s] + len * G[s];
   }
@@ -385,7 +510,7 @@ static void cell_jacobian(const orc_cfg* c, const lvl* L, const double* z, const
   if (offd) for (int e = 0; e < 36; ++e) offd[e] = 0.0;
   R[0] = R[1] = R[2] = 0.0;
   for (int side = 0; side < nsides(c); ++side) {
-    double len = side_len(L, side), Gb[3], Gp[3];
+    double len = edge_len(L, i, side), Gb[3], Gp[3];
     cell_G(c, L, z, U, i, side, -1, 0, 0.0, Gb);
     for (int s = 0; s < nc; ++s) R[s] = R[s] + len * Gb[s];
     for (int k = 0; k < nc; ++k) {
@@ -403,7 +528,7 @@ static void cell_jacobian(const orc_cfg* c, const lvl* L, const double* z, const
   if (time_mode(c, L)) {   /* d/dU of (1 - beta) R + |K|/dt U: scaled blocks, |K|/dt on the diagonal */
     time_residual(c, L, U, i, R);
     for (int e = 0; e < nc * nc; ++e) D[e] = c->t_omb * D[e];
-    for (int s = 0; s < nc; ++s) D[s * nc + s] = D[s * nc + s] + c->t_ka;
+    for (int s = 0; s < nc; ++s) D[s * nc + s] = D[s * nc + s] + time_ka(c, i);
     if (offd) for (int e = 0; e < 36; ++e) offd[e] = c->t_omb * offd[e];
   }
   *rn = l1norm(R, nc);
@@ -464,10 +589,29 @@ static int check_cfg(const orc_cfg* c) {
   int m = 1 << c->n_levels;
   if (c->nx % m) return ST_ARG;
   if (c->dim == 2 && c->ny % m) return ST_ARG;
+  if ((c->mesh_x != NULL) != (c->mesh_y != NULL)) return ST_ARG;
+  if (c->mesh_x) {                    /* every level's cells positive and their edges non-degenerate */
+    if (c->dim != 2) return ST_ARG;
+    for (int l = 0; l <= c->n_levels; ++l) {
+      lvl L = level_geom(c, l);
+      for (int i = 0; i < L.n; ++i) {
+        if (!(cell_area(&L, i) > 0.0)) return ST_ARG;
+        for (int side = 0; side < 4; ++side) if (!(edge_len(&L, i, side) > 0.0)) return ST_ARG;
+      }
+    }
+  }
   return ST_OK;
 }
 
 int orc_level_cells(const orc_cfg* c, int l) { lvl L = level_geom(c, l); return L.n; }
+
+/* |K_i| of every cell of level l (curvilinear meshes; ST_ARG otherwise) */
+int orc_cell_areas(const orc_cfg* c, int l, double* out) {
+  lvl L = level_geom(c, l);
+  if (!curvilinear(&L)) return ST_ARG;
+  for (int i = 0; i < L.n; ++i) out[i] = cell_area(&L, i);
+  return ST_OK;
+}
 
 int orc_residual(const orc_cfg* c, int l, const double* z, const double* U, double* R, double* rn) {
   lvl L = level_geom(c, l);
@@ -841,12 +985,25 @@ int orc_blusgs(const orc_cfg* c, int l, const double* z, double* U, int nsweeps)
   return ST_OK;
 }
 
-/* average the children of every coarse cell (child order), for z and U */
+/* average the children of every coarse cell (child order), for z and U: the
+ * cell average over the coarse cell (Algorithm 1, Step 1) from the children's
+ * averages.  On a curvilinear mesh the children are weighted by their areas,
+ * sum_q |K_q| v_q / sum_q |K_q|. */
 int orc_average(const orc_cfg* c, int l, int ncomp_v, const double* vf, double* vc) {
   lvl Lf = level_geom(c, l), Lc = level_geom(c, l + 1);
   double w = (c->dim == 2) ? 0.25 : 0.5;
   for (int I = 0; I < Lc.n; ++I) {
     int ch[4], m = children(c, &Lf, &Lc, I, ch);
+    if (curvilinear(&Lf)) {
+      double ar[4], tot = 0.0;
+      for (int q = 0; q < m; ++q) { ar[q] = cell_area(&Lf, ch[q]); tot = tot + ar[q]; }
+      for (int s = 0; s < ncomp_v; ++s) {
+        double a = 0.0;
+        for (int q = 0; q < m; ++q) a = a + ar[q] * vf[s * Lf.n + ch[q]];
+        vc[s * Lc.n + I] = a / tot;
+      }
+      continue;
+    }
     for (int s = 0; s < ncomp_v; ++s) {
       double a = vf[s * Lf.n + ch[0]];
       for (int q = 1; q < m; ++q) a = a + vf[s * Lf.n + ch[q]];
@@ -1002,7 +1159,7 @@ static void adjoint_vjp(const orc_cfg* c, const lvl* L, const double* z, const d
     zp[j] = z[j] + d;
     zm[j] = z[j] - d;
     for (int side = 0; side < nsides(c); ++side) {
-      double len = side_len(L, side), Gm[3], Gp[3];
+      double len = edge_len(L, j, side), Gm[3], Gp[3];
       cell_G(c, L, zm, U, j, side, -1, 0, 0.0, Gm);          /* the cell itself */
       cell_G(c, L, zp, U, j, side, -1, 0, 0.0, Gp);
       for (int s = 0; s < nc; ++s) acc = acc + lam[s * n + j] * (len * ((Gp[s] - Gm[s]) * r2d));
@@ -1025,10 +1182,10 @@ static void adjoint_vjp(const orc_cfg* c, const lvl* L, const double* z, const d
     orc_cfg cp = *c, cm = *c;
     cp.bc[side].q = c->bc[side].q + d;
     cm.bc[side].q = c->bc[side].q - d;
-    double acc = 0.0, len = side_len(L, side);
+    double acc = 0.0;
     for (int i = 0; i < n; ++i) {
       if (nbr(L, i, side) >= 0) continue;
-      double Gm[3], Gp[3];
+      double Gm[3], Gp[3], len = edge_len(L, i, side);
       cell_G(&cm, L, z, U, i, side, -1, 0, 0.0, Gm);
       cell_G(&cp, L, z, U, i, side, -1, 0, 0.0, Gp);
       for (int s = 0; s < nc; ++s) acc = acc + lam[s * n + i] * (len * ((Gp[s] - Gm[s]) * r2d));
@@ -1072,17 +1229,25 @@ int orc_time_step(const orc_cfg* c, const double* z, double* U, double dt, doubl
   double ka = area / dt;
   orc_cfg cs = *c;
   cs.t_ka = 0.0;
+  cs.t_kai = NULL;
   double* Rn = (double*)malloc(sizeof(double) * (size_t)n * nc);
   double* S = (double*)malloc(sizeof(double) * (size_t)n * nc);
+  double* kai = NULL;
+  if (curvilinear(&L)) {              /* |K_i|/dt per cell */
+    kai = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int i = 0; i < n; ++i) kai[i] = cell_area(&L, i) / dt;
+  }
   orc_residual(&cs, 0, z, U, Rn, NULL);
-  for (int e = 0; e < n * nc; ++e) S[e] = ka * U[e] - beta * Rn[e];
+  for (int e = 0; e < n * nc; ++e) S[e] = (kai ? kai[e % n] : ka) * U[e] - beta * Rn[e];
   orc_cfg ct = *c;
-  ct.t_ka = ka;
+  ct.t_ka = kai ? 1.0 : ka;           /* > 0: time mode; the values come from t_kai */
+  ct.t_kai = kai;
   ct.t_omb = 1.0 - beta;
   ct.t_src = S;
   ct.init_mode = INIT_NONE;
   int status = orc_solve(&ct, z, U, st);
   free(Rn);
   free(S);
+  free(kai);
   return status;
 }

@@ -115,6 +115,9 @@ class SwnmgError(RuntimeError):
 
 
 def make_problem(p: W.Problem) -> Problem:
+    if getattr(p, "mesh_x", None) is not None:
+        raise NotImplementedError("the CUDA library solves on uniform Cartesian meshes only; "
+                                  "problem %r has a curvilinear mesh" % p.name)
     s = Problem()
     s.dim, s.nx, s.ny = p.dim, p.nx, (p.ny if p.dim == 2 else 1)
     s.x0, s.x1, s.y0, s.y1, s.g = p.x0, p.x1, p.y0, p.y1, p.g

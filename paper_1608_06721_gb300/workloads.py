@@ -99,6 +99,11 @@ class Problem:
     params: Params
     g: float = G
     meta: dict = field(default_factory=dict)
+    # structured curvilinear quadrilateral mesh (2D only): vertex (a, b),
+    # 0 <= a <= nx, 0 <= b <= ny, at (mesh_x[b, a], mesh_y[b, a]); None: the
+    # uniform Cartesian mesh of [x0, x1] x [y0, y1]
+    mesh_x: np.ndarray | None = None
+    mesh_y: np.ndarray | None = None
 
     @property
     def ncomp(self) -> int:
@@ -109,6 +114,10 @@ class Problem:
         return self.nx * (self.ny if self.dim == 2 else 1)
 
     def centres(self):
+        if self.mesh_x is not None:           # mean of the four corners
+            X = 0.25 * (self.mesh_x[:-1, :-1] + self.mesh_x[:-1, 1:] + self.mesh_x[1:, :-1] + self.mesh_x[1:, 1:])
+            Y = 0.25 * (self.mesh_y[:-1, :-1] + self.mesh_y[:-1, 1:] + self.mesh_y[1:, :-1] + self.mesh_y[1:, 1:])
+            return X.ravel(), Y.ravel()
         dx = (self.x1 - self.x0) / self.nx
         xc = self.x0 + (np.arange(self.nx) + 0.5) * dx
         if self.dim == 1:
@@ -325,6 +334,87 @@ def hill_wetdry_2d(nx: int, ny: int, n_levels: int = 3) -> Problem:
     p.bc[0] = BC(BC_INFLOW_DISCHARGE, q=0.1)
     p.bc[1] = BC(BC_OUTFLOW_DEPTH, h=0.2)
     return p
+
+
+# ------------------------------------------------------ curvilinear meshes
+
+def cartesian_vertices(p: Problem):
+    """Vertex arrays (ny+1, nx+1) of a 2D problem's uniform mesh."""
+    xs = p.x0 + (p.x1 - p.x0) * (np.arange(p.nx + 1) / p.nx)
+    ys = p.y0 + (p.y1 - p.y0) * (np.arange(p.ny + 1) / p.ny)
+    X, Y = np.meshgrid(xs, ys)
+    return X, Y
+
+
+def with_mesh(p: Problem, X, Y) -> Problem:
+    """The problem on the structured mesh with vertices (X, Y), each (ny+1, nx+1)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    assert p.dim == 2 and X.shape == Y.shape == (p.ny + 1, p.nx + 1)
+    return dataclasses.replace(p, mesh_x=X, mesh_y=Y)
+
+
+def _channel_mesh(nx: int, ny: int, length: float, half_width):
+    """Vertices of a channel symmetric about y = 0: vertical mesh lines at
+    x_a = length a/nx, each split into ny equal parts between -w(x_a) and
+    w(x_a), w = half_width(x)."""
+    xs = length * (np.arange(nx + 1) / nx)
+    w = half_width(xs)
+    frac = np.arange(ny + 1) / ny
+    X = np.broadcast_to(xs, (ny + 1, nx + 1)).copy()
+    Y = (2.0 * frac[:, None] - 1.0) * w[None, :]
+    return X, Y
+
+
+def constricted_channel(kind: str = "I", nx: int = 72, ny: int = 40, n_levels: int = 3,
+                        flux: int = FLUX_HLLC) -> Problem:
+    """Example 3.4: a flat channel of width 40 (y in [-20, 20]) and length 90,
+    constricted symmetrically from x = 10 on at the angle 5 degrees to the end
+    (channel I), or at 15 degrees up to x = 30 and straight after it (channel
+    II).  Supercritical inflow h = 1, v = 0, Froude number 2.5 at x = 0,
+    supercritical outflow at x = 90, slip walls; HLLC, V-cycle, N_L = 3,
+    eps_p = 200.  The mesh's kinks (x = 10, 30) lie on vertices of every level
+    when nx is a multiple of 9 * 2^N_L."""
+    ang = np.deg2rad(5.0 if kind == "I" else 15.0)
+    x_end = 90.0 if kind == "I" else 30.0
+
+    def half_width(x):
+        return 20.0 - (np.clip(x, 10.0, x_end) - 10.0) * np.tan(ang)
+
+    X, Y = _channel_mesh(nx, ny, 90.0, half_width)
+    u_in = 2.5 * np.sqrt(G * 1.0)
+    n = nx * ny
+    bc = [BC(BC_SUPER_INFLOW, h=1.0, q=u_in, ut=0.0), BC(BC_SUPER_OUTFLOW),
+          BC(BC_WALL_SLIP), BC(BC_WALL_SLIP)]
+    U0 = np.stack([np.ones(n), np.full(n, u_in), np.zeros(n)])
+    p = Problem("ex34_" + kind, 2, nx, ny, 0.0, 90.0, -20.0, 20.0, np.zeros(n), U0, bc,
+                Params(flux=flux, n_levels=n_levels, n_mg=3, eps_p=200.0, tol=1e-9),
+                meta={"angle_deg": 5.0 if kind == "I" else 15.0, "froude_in": 2.5})
+    return with_mesh(p, X, Y)
+
+
+def hubbard_channel(froude: float, nx: int = 96, ny: int = 32, w_min: float = 0.9, h0: float = 1.0,
+                    n_levels: int = 3, flux: int = FLUX_HLLC) -> Problem:
+    """Example 3.5: a flat channel of length 3 and width
+    W(x) = 1 - (1 - W_min) cos^2(pi (x - 1.5)) for |x - 1.5| <= 0.5, else 1,
+    symmetric about y = 0.  Both open ends choose their condition by the local
+    Froude number (Remark 2.3) with hu = h0 F_in sqrt(g h0), hv = 0 and
+    h = h0 as the prescribed data; slip walls; initial state the inflow
+    state; HLLC, V-cycle."""
+    def half_width(x):
+        s = x - 1.5
+        return 0.5 * np.where(np.abs(s) <= 0.5, 1.0 - (1.0 - w_min) * np.cos(np.pi * s) ** 2, 1.0)
+
+    X, Y = _channel_mesh(nx, ny, 3.0, half_width)
+    q = h0 * froude * np.sqrt(G * h0)
+    n = nx * ny
+    bc = [BC(BC_AUTO_FROUDE, h=h0, q=q, ut=0.0), BC(BC_AUTO_FROUDE, h=h0, q=q, ut=0.0),
+          BC(BC_WALL_SLIP), BC(BC_WALL_SLIP)]
+    U0 = np.stack([np.full(n, h0), np.full(n, q), np.zeros(n)])
+    p = Problem("ex35_F%g" % froude, 2, nx, ny, 0.0, 3.0, -0.5, 0.5, np.zeros(n), U0, bc,
+                Params(flux=flux, n_levels=n_levels, n_mg=3),
+                meta={"froude_in": froude, "w_min": w_min})
+    return with_mesh(p, X, Y)
 
 
 def random_state(p: Problem, seed: int, wet_frac: float = 1.0, u_scale: float = 0.3):

@@ -1,0 +1,370 @@
+"""Pins of the oracle on structured curvilinear quadrilateral meshes
+(eq. totalFlux with general |e_ij| and n_ij; Examples 3.4 and 3.5):
+
+* the uniform mesh given as vertices goes through the curvilinear code and
+  reproduces the Cartesian path bit for bit (residual, Jacobian, solve, time
+  step, adjoint) -- the Cartesian path being pinned by the paper's tables;
+* a rotated mesh gives the rotated residual and steady state;
+* a uniform flow on a warped mesh has zero residual (the discrete metric
+  identity sum_e |e| n_e = 0 and the frame transforms), a lake at rest with
+  dry islands stays at rest, a closed basin keeps sum |K_i| h_i over time
+  steps;
+* cell areas add up to the channel's polygon area on every level;
+* Example 3.4: the plateau heights behind the oblique jumps approach both the
+  values the paper prints (1.25 and 1.5271) and the closed form of the
+  oblique hydraulic jump (mass and normal momentum balanced across the jump,
+  tangential velocity continuous); channel II's jumps meet near (33, 0) and
+  take more Newton steps;
+* Example 3.5: the five flow patterns the paper lists for F_in = 0.5 ... 2,
+  mirror symmetry, and Case 2 needing the most Newton steps."""
+import copy
+
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+
+from oracle.oracle import Oracle
+from paper_1608_06721_gb300 import workloads as W
+from tests.golden import tables
+
+G = W.G
+PAPER = tables.load()
+
+
+def _cartesian_as_mesh(p):
+    X, Y = W.cartesian_vertices(p)
+    return W.with_mesh(p, X, Y)
+
+
+def _all_kinds(nx=16, ny=16):
+    """channel_2d on [0,4]x[0,1] (vertex coordinates exact in binary) with every
+    boundary kind: Froude-switching ends, supercritical inflow from the south,
+    a slip wall on the north."""
+    p = W.channel_2d(nx=nx, ny=ny, n_levels=2, redraw=False)
+    p = copy.deepcopy(p)
+    p.bc[0] = W.BC(W.BC_AUTO_FROUDE, h=0.6, q=0.9, ut=0.05)
+    p.bc[1] = W.BC(W.BC_AUTO_FROUDE, h=0.6, q=0.9, ut=0.0)
+    p.bc[2] = W.BC(W.BC_SUPER_INFLOW, h=0.3, q=0.02, ut=0.1)
+    p.bc[3] = W.BC(W.BC_WALL_SLIP)
+    return p
+
+
+@pytest.mark.parametrize("make", [lambda: W.channel_2d(nx=16, ny=16, n_levels=2, redraw=False), _all_kinds],
+                         ids=["channel", "all_kinds"])
+@pytest.mark.parametrize("flux", [W.FLUX_HLLC, W.FLUX_LLF, W.FLUX_ROE])
+def test_uniform_mesh_as_vertices_is_the_cartesian_path(make, flux):
+    p = make().with_params(flux=flux)
+    q = _cartesian_as_mesh(p)
+    oc, om = Oracle(p), Oracle(q)
+    U = W.random_state(p, 7)
+    assert np.array_equal(oc.residual(U)[0], om.residual(U)[0])
+    assert np.array_equal(oc.jacobian(U)[2], om.jacobian(U)[2])
+    for l in (1, 2):
+        assert np.array_equal(oc.z_levels()[l], om.z_levels()[l])
+        assert np.array_equal(oc.residual(oc.average(0, U) if l == 1 else oc.average(1, oc.average(0, U)),
+                                          level=l, z=oc.z_levels()[l])[0],
+                              om.residual(om.average(0, U) if l == 1 else om.average(1, om.average(0, U)),
+                                          level=l, z=om.z_levels()[l])[0])
+    if make is _all_kinds:
+        return
+    Uc, ic = oc.solve()
+    Um, im = om.solve()
+    assert ic["status"] == im["status"] == 0 and ic["n_newton"] == im["n_newton"]
+    assert np.array_equal(Uc, Um)
+    Vc, _ = oc.time_step(Uc + 0.01 * (Uc[0] > 0.1), dt=0.01, beta=0.5)
+    Vm, _ = om.time_step(Uc + 0.01 * (Uc[0] > 0.1), dt=0.01, beta=0.5)
+    assert np.array_equal(Vc, Vm)
+    g = np.random.default_rng(3).standard_normal(Uc.shape)
+    for a, b in zip(oc.adjoint(Uc, g), om.adjoint(Uc, g)):
+        assert np.array_equal(a, b)
+
+
+def _rot(theta):
+    c, s = np.cos(theta), np.sin(theta)
+    return np.array([[c, -s], [s, c]])
+
+
+def _rotate_state(U, Q):
+    V = U.copy()
+    V[1:] = Q @ U[1:]
+    return V
+
+
+@pytest.mark.parametrize("flux", [W.FLUX_HLLC, W.FLUX_LLF, W.FLUX_ROE])
+def test_rotated_mesh_gives_the_rotated_residual(flux):
+    """Every boundary datum is given in the edge frame (q along n, u_tau along
+    tau), so rotating the mesh about any point rotates R and the steady
+    state; an error in n, tau or the back transform breaks this."""
+    p = W.channel_2d(nx=16, ny=16, n_levels=2, redraw=False).with_params(flux=flux)
+    X, Y = W.cartesian_vertices(p)
+    theta = 0.37
+    Q = _rot(theta)
+    Xr = Q[0, 0] * (X - 1.0) + Q[0, 1] * (Y + 2.0)
+    Yr = Q[1, 0] * (X - 1.0) + Q[1, 1] * (Y + 2.0)
+    o, orot = Oracle(_cartesian_as_mesh(p)), Oracle(W.with_mesh(p, Xr, Yr))
+    U = W.random_state(p, 11)
+    R = o.residual(U)[0]
+    Rr = orot.residual(_rotate_state(U, Q))[0]
+    scale = np.abs(R).max()
+    assert np.abs(Rr - _rotate_state(R, Q)).max() <= 1e-13 * scale
+    Us, info = o.solve()
+    Ur, infor = orot.solve(_rotate_state(p.U0, Q))
+    assert info["status"] == infor["status"] == 0 and abs(info["n_newton"] - infor["n_newton"]) <= 1
+    assert np.abs(Ur - _rotate_state(Us, Q)).max() <= 1e-9 * np.abs(Us).max()
+
+
+def _warped(nx=24, ny=16, amp=0.25):
+    """A smoothly warped mesh of [0,3]x[0,2]: interior vertices displaced by
+    amp cell widths along sine modes, boundaries curved too."""
+    xs = 3.0 * np.arange(nx + 1) / nx
+    ys = 2.0 * np.arange(ny + 1) / ny
+    X, Y = np.meshgrid(xs, ys)
+    dx, dy = 3.0 / nx, 2.0 / ny
+    Xw = X + amp * dx * np.sin(np.pi * Y) * np.sin(2 * np.pi * X / 3.0)
+    Yw = Y + amp * dy * np.sin(2 * np.pi * X / 3.0 + 0.5) * np.cos(0.5 * np.pi * Y)
+    return Xw, Yw
+
+
+def _warped_problem(bc, flux, nx=24, ny=16, z=None, U0=None):
+    n = nx * ny
+    p = W.Problem("warped", 2, nx, ny, 0.0, 3.0, 0.0, 2.0, np.zeros(n) if z is None else z,
+                  np.zeros((3, n)) if U0 is None else U0, bc,
+                  W.Params(flux=flux, n_levels=2, n_mg=3, llf_wetdry=1 if flux == W.FLUX_LLF else 0))
+    X, Y = _warped(nx, ny)
+    return W.with_mesh(p, X, Y)
+
+
+@pytest.mark.parametrize("flux", [W.FLUX_HLLC, W.FLUX_LLF, W.FLUX_ROE, W.FLUX_HLL])
+def test_uniform_flow_on_a_warped_mesh_has_zero_residual(flux):
+    p = _warped_problem([W.BC(W.BC_SUPER_OUTFLOW) for _ in range(4)], flux)
+    o = Oracle(p)
+    assert (o.areas() > 0).all() and (o.areas(1) > 0).all()
+    h, u, v = 0.8, 0.5, -0.3
+    U = np.stack([np.full(p.n, h), np.full(p.n, h * u), np.full(p.n, h * v)])
+    R = o.residual(U)[0]
+    flux_scale = h * u * u + 0.5 * G * h * h
+    assert np.abs(R).max() <= 1e-13 * flux_scale * 0.15
+
+
+def _bumps_on_warped(nx=24, ny=16):
+    p = _warped_problem(W._walls(), W.FLUX_LLF, nx, ny)
+    Xc, Yc = p.centres()
+    z = (W.gaussian_bumps(Xc, Yc, [0.7, 0.35], [0.25, 0.3], [1.0, 2.1], [0.8, 1.3]))
+    h = np.maximum(0.5 - z, 0.0)
+    p.z = z
+    p.U0 = np.stack([h, np.zeros_like(h), np.zeros_like(h)])
+    return p
+
+
+@pytest.mark.parametrize("flux", [W.FLUX_HLLC, W.FLUX_LLF, W.FLUX_ROE, W.FLUX_HLL])
+def test_lake_at_rest_with_dry_islands_on_a_warped_mesh(flux):
+    p = _bumps_on_warped().with_params(flux=flux)
+    assert (p.U0[0] == 0).sum() >= 4
+    R, rn = Oracle(p).residual(p.U0)
+    assert np.abs(R).max() <= 1e-13
+
+
+def test_closed_basin_keeps_its_volume_over_time_steps():
+    """|K_i| (U^{n+1} - U^n)/dt + ... = 0 with per-cell areas: the volume
+    sum_i |K_i| h_i is kept by every step (a single |K|/dt for all cells
+    would keep sum_i h_i instead, which changes here)."""
+    p = _bumps_on_warped()
+    o = Oracle(p)
+    K = o.areas()
+    U = p.U0.copy()
+    U[0] = U[0] + 0.02 * (U[0] > 0) * np.random.default_rng(5).random(p.n)
+    vol0, mass0 = np.dot(K, U[0]), U[0].sum()
+    for beta in (0.0, 0.5):
+        V = U.copy()
+        for _ in range(3):
+            V, info = o.time_step(V, dt=0.01, beta=beta)
+            assert info["status"] == 0
+        assert abs(np.dot(K, V[0]) - vol0) <= 1e-11 * vol0
+        assert abs(V[0].sum() - mass0) > 1e-8 * mass0
+
+
+def test_cell_areas_add_up_to_the_channel_area():
+    """Channel I is a polygon: 90 x 40 less two triangles of legs 80 and
+    80 tan 5 degrees; its kinks lie on vertices of every level, so every
+    level covers it exactly and each coarse cell is the union of its
+    children."""
+    p = W.constricted_channel("I", 72, 40)
+    o = Oracle(p)
+    exact = 90.0 * 40.0 - 80.0 * 80.0 * np.tan(np.deg2rad(5.0))
+    for l in range(4):
+        K = o.areas(l)
+        assert (K > 0).all()
+        assert abs(K.sum() - exact) <= 1e-12 * exact
+        if l:
+            f = o.areas(l - 1).reshape(p.ny >> (l - 1), p.nx >> (l - 1))
+            kids = f[0::2, 0::2] + f[0::2, 1::2] + f[1::2, 0::2] + f[1::2, 1::2]
+            np.testing.assert_allclose(kids.ravel(), K, rtol=1e-13)
+    # Example 3.5's curved walls: the width integrates to 3 - (1 - W_min)/2
+    q = W.hubbard_channel(0.5, 96, 32)
+    assert abs(Oracle(q).areas().sum() - (3.0 - 0.1 / 2)) <= 2e-5
+
+
+def test_cuda_library_refuses_curvilinear_meshes():
+    from paper_1608_06721_gb300 import swnmg
+    with pytest.raises(NotImplementedError):
+        swnmg.make_problem(W.constricted_channel("I", 72, 40))
+
+
+# ---------------------------------------------------------------- Example 3.4
+
+def _oblique_jump(F1, theta):
+    """Weak oblique hydraulic jump turning a flow of Froude number F1 by the
+    wall angle theta: the jump's angle beta to the upstream flow, the depth
+    ratio h2/h1 and the downstream Froude number.  Normal to the jump it is a
+    1D hydraulic jump of Froude number F1 sin(beta) (h2/h1 =
+    (sqrt(1 + 8 F1^2 sin^2 beta) - 1)/2); the tangential velocity is
+    continuous, and the normal velocity drops by h1/h2 (mass), so
+    tan(beta - theta) = (h1/h2) tan(beta)."""
+    def ratio(b):
+        return 0.5 * (np.sqrt(1.0 + 8.0 * (F1 * np.sin(b)) ** 2) - 1.0)
+
+    def turn(b):
+        return b - np.arctan(np.tan(b) / ratio(b))
+
+    b0 = np.arcsin(1.0 / F1)                        # the Mach angle: no turn
+    bs = np.linspace(b0, 0.5 * np.pi, 4001)[1:-1]
+    bmax = bs[np.argmax(turn(bs))]                  # the weak branch lies below it
+    b = brentq(lambda x: turn(x) - theta, b0 + 1e-12, bmax)
+    r = ratio(b)
+    vt, vn2 = F1 * np.cos(b), F1 * np.sin(b) / r    # in units of sqrt(g h1)
+    return b, r, np.hypot(vt, vn2) / np.sqrt(r)
+
+
+def test_oblique_jump_closed_form_reproduces_the_paper():
+    """The closed form alone gives the paper's plateau heights (the paper
+    computes them numerically on 576 x 320 cells)."""
+    th = np.deg2rad(5.0)
+    b, r2, F2 = _oblique_jump(2.5, th)
+    _, r3, _ = _oblique_jump(F2, th)
+    h2, h3 = PAPER["ex34_plateau_h"]
+    assert abs(r2 - h2) <= 2e-4 and abs(r2 * r3 - h3) <= 3e-4
+
+
+def _channel_I(nx, ny):
+    p = W.constricted_channel("I", nx, ny)
+    U, info = Oracle(p).solve()
+    assert info["status"] == 0
+    return p, U, info
+
+
+def _plateaus(p, U, margin=3.0):
+    """Median depth behind the incident jump (region 2, away from the jumps and
+    the wall by margin) and the depth on the centreline behind the reflected
+    jumps (region 3, 60 <= x <= 70), located with the closed-form angles."""
+    th = np.deg2rad(5.0)
+    b, r2, F2 = _oblique_jump(2.5, th)
+    b3, _, _ = _oblique_jump(F2, th)
+    x_axis = 10.0 + 20.0 / np.tan(b)                 # the incident jump meets the axis
+    X, Y = p.centres()
+    ay, h = np.abs(Y), U[0]
+    wall = 20.0 - (np.clip(X, 10.0, 90.0) - 10.0) * np.tan(th)
+    incident = 20.0 - (X - 10.0) * np.tan(b)
+    reflected = (X - x_axis) * np.tan(b3 - th)
+    r2m = (X > 20.0) & (ay > incident + margin) & (ay < wall - margin) & (ay > reflected + margin)
+    centre = (ay < 0.5 * 40.0 / p.ny + 1e-9) & (X >= 60.0) & (X <= 70.0)
+    return np.median(h[r2m]), np.median(h[centre])
+
+
+def test_example34_plateau_heights():
+    """Channel I: on 72 x 40 (the paper's coarsest mesh), 144 x 80 and
+    288 x 160 cells the two plateaus approach the closed form and the
+    paper's values, monotonically."""
+    th = np.deg2rad(5.0)
+    _, r2, F2 = _oblique_jump(2.5, th)
+    _, r3, _ = _oblique_jump(F2, th)
+    h2p, h3p = PAPER["ex34_plateau_h"]
+    err = []
+    for nx, ny in ((72, 40), (144, 80), (288, 160)):
+        p, U, info = _channel_I(nx, ny)
+        assert info["n_newton"] <= 15
+        h2, h3 = _plateaus(p, U)
+        err.append((abs(h2 - r2), abs(h3 - r2 * r3)))
+    assert err[0][0] > err[1][0] > err[2][0] and err[0][1] > err[1][1] > err[2][1], err
+    h2, h3 = _plateaus(p, U)
+    assert abs(h2 - h2p) <= 1e-3 and abs(h2 - r2) <= 1e-3, h2
+    assert abs(h3 - h3p) <= 1e-3 and abs(h3 - r2 * r3) <= 1e-3, h3
+
+
+def test_example34_channel_II():
+    """Channel II (15 degrees from x = 10 to 30): the incident jumps meet on
+    the axis near x = 33 (the paper's figure; 34.2 by the closed form), the
+    first plateau approaches the closed form 1.807, and the solve takes more
+    Newton steps than channel I on the same mesh."""
+    th = np.deg2rad(15.0)
+    b, r2, _ = _oblique_jump(2.5, th)
+    x_axis = 10.0 + 20.0 / np.tan(b)
+    assert abs(x_axis - 33.0) < 1.5
+    p = W.constricted_channel("II", 144, 80)
+    U, info = Oracle(p).solve()
+    assert info["status"] == 0
+    _, _, info_I = _channel_I(144, 80)
+    assert info["n_newton"] > info_I["n_newton"]
+    X, Y = p.centres()
+    ay, h = np.abs(Y), U[0]
+    wall = 20.0 - (np.clip(X, 10.0, 30.0) - 10.0) * np.tan(th)
+    region = (X > 12.0) & (X < 28.0) & (ay > 20.0 - (X - 10.0) * np.tan(b) + 2.0) & (ay < wall - 2.0)
+    assert abs(np.median(h[region]) - r2) <= 0.01
+    # the depth on the axis first passes half-way to the plateau within a
+    # few cells of where the jumps meet
+    on_axis = ay < 0.5 * 40.0 / p.ny + 1e-9
+    xs, ha = X[on_axis], h[on_axis]
+    order = np.argsort(xs)
+    xs, ha = xs[order], ha[order]
+    x_jump = xs[np.argmax(ha > 0.5 * (1.0 + r2))]
+    assert abs(x_jump - x_axis) <= 2.5, x_jump
+
+
+# ---------------------------------------------------------------- Example 3.5
+
+def _froude(U):
+    h, hu, hv = U
+    return np.hypot(hu / h, hv / h) / np.sqrt(G * h)
+
+
+def _hubbard(F, nx=96, ny=32):
+    p = W.hubbard_channel(F, nx=nx, ny=ny)
+    U, info = Oracle(p).solve()
+    assert info["status"] == 0, (F, info["status"])
+    h = U[0].reshape(ny, nx)
+    assert np.abs(h - h[::-1]).max() <= 1e-10          # mirror symmetry about y = 0
+    return p, U, info
+
+
+def test_example35_flow_patterns():
+    """The five cases of Example 3.5 (W_min = 0.9, h0 = 1) on 96 x 32 cells:
+    1) subcritical everywhere; 2) subcritical at both ends with a supercritical
+    part past the throat; 3) subcritical at the inflow (the constriction chokes
+    the F_in = 1.2 stream and the inflow boundary switches), supercritical at
+    the outflow; 4) supercritical at both ends; 5) supercritical everywhere.
+    Case 2 takes the most Newton steps."""
+    steps = {}
+    for F in (0.5, 0.67, 1.2, 1.7, 2.0):
+        p, U, info = _hubbard(F)
+        Fr = _froude(U).reshape(p.ny, p.nx)
+        inflow, outflow = Fr[:, 0], Fr[:, -1]
+        steps[F] = info["n_newton"]
+        if F == 0.5:
+            assert Fr.max() < 1.0
+        elif F == 0.67:
+            assert inflow.max() < 1.0 and outflow.max() < 1.0 and Fr.max() > 1.0
+        elif F == 1.2:
+            assert inflow.max() < 1.0 and outflow.min() > 1.0
+        elif F == 1.7:
+            assert inflow.min() > 1.0 and outflow.min() > 1.0
+        else:
+            assert Fr.min() > 1.0
+    assert steps[0.67] == max(steps.values()) and list(steps.values()).count(steps[0.67]) == 1, steps
+
+
+def test_example35_case4_subcritical_pocket():
+    """Case 4 (F_in = 1.7) has a subcritical pocket inside the constriction
+    (1 < x < 2); it appears once the mesh resolves it (192 x 64 cells)."""
+    p, U, info = _hubbard(1.7, 192, 64)
+    X, _ = p.centres()
+    sub = _froude(U) < 1.0
+    assert sub.sum() > 0 and X[sub].min() > 1.0 and X[sub].max() < 2.0
