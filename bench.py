@@ -135,9 +135,13 @@ TRAFFIC_PER_CELL = {"blusgs": 36.2, "blusgs_coarse": 36.2, "sgs_fine": 217.9, "s
 
 def algorithmic(cls, p, fp32):
     """(bound, algorithmic units per cell) of a kernel class: bytes for the
-    block-SGS smoother, FP64 operations for the flux kernels (counts per cell
-    derived in the design doc).  Multiplied by the cells the timed launches
-    processed, as reported by the library."""
+    block-SGS smoother, FP64 operations for the flux kernels.  One edge
+    evaluation (reconstruction, two reciprocals, two square roots, the flux
+    and the sources) is about 53 FP64 operations; a cell owns about 2.5 edge
+    evaluations in the residual (130), 7 per edge in the FD Jacobian (1035),
+    and a BLU-SGS cell update makes 16 plus a 3x3 elimination (1020).
+    Multiplied by the cells the timed launches processed, as reported by the
+    library."""
     nc = p.ncomp
     w = 4 if fp32 else 8
     if cls in ("sgs_fine", "sgs_coarse"):
