@@ -129,8 +129,13 @@ FP64_OPS_PEAK = 152 * 2 * 2.07e9
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per cell of one
 # launch, from ncu captures of one BLU-SGS and one SGS half-sweep of the
 # 512 x 512 channel; a launch's traffic grows with the cells it processes, so
-# it is scaled to the timed launches by their cell counts
+# it is scaled to the timed launches by their cell counts.  Both kernels
+# changed after those captures (the Roe flux, the Froude-number boundary and
+# the time-step term entered the BLU-SGS cell update; the SGS cell update
+# became one explicit-FMA function), so `traffic` is null until the next
+# capture, and the captured figure is kept as `traffic_previous_build`.
 TRAFFIC_PER_CELL = {"blusgs": 36.2, "blusgs_coarse": 36.2, "sgs_fine": 217.9, "sgs_coarse": 217.9}
+TRAFFIC_CURRENT = False
 
 
 def algorithmic(cls, p, fp32):
@@ -260,18 +265,20 @@ def run_gpu(args):
         avg_ms = timing[dom][0] / timing[dom][1]
         units = per_cell * timing[dom][2] / timing[dom][1]    # per launch
         cells_per_launch = timing[dom][2] / timing[dom][1]
-        traffic = TRAFFIC_PER_CELL[dom] * cells_per_launch if dom in TRAFFIC_PER_CELL else None
+        captured = TRAFFIC_PER_CELL[dom] * cells_per_launch if dom in TRAFFIC_PER_CELL else None
+        traffic = captured if TRAFFIC_CURRENT else None
         if bound == "hbm":
             pk, src = peaks()
             ach = units / (avg_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk, "unit": "GB/s",
-                    "frac": ach / pk, "traffic": traffic, "peak_source": src,
-                    "units_per_launch": units, "avg_launch_ms": avg_ms}
+                    "frac": ach / pk, "traffic": traffic, "traffic_previous_build": captured,
+                    "peak_source": src, "units_per_launch": units, "avg_launch_ms": avg_ms}
         else:
             ach = units / (avg_ms * 1e-3) / 1e12
             pk = FP64_OPS_PEAK / 1e12
             roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": pk,
                     "unit": "TFLOP/s (FP64 ops, no FMA)", "frac": ach / pk, "traffic": traffic,
+                    "traffic_previous_build": captured,
                     "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz",
                     "units_per_launch": units, "avg_launch_ms": avg_ms}
     total_dev = sum(v[0] for v in timing.values())
