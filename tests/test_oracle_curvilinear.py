@@ -8,7 +8,8 @@
 * a uniform flow on a warped mesh has zero residual (the discrete metric
   identity sum_e |e| n_e = 0 and the frame transforms), a lake at rest with
   dry islands stays at rest, a closed basin keeps sum |K_i| h_i over time
-  steps;
+  steps, and its time steps converge at first (backward Euler) and second
+  (Crank-Nicolson) order;
 * cell areas add up to the channel's polygon area on every level;
 * Example 3.4: the plateau heights behind the oblique jumps approach both the
   values the paper prints (1.25 and 1.5271) and the closed form of the
@@ -181,6 +182,29 @@ def test_closed_basin_keeps_its_volume_over_time_steps():
             assert info["status"] == 0
         assert abs(np.dot(K, V[0]) - vol0) <= 1e-11 * vol0
         assert abs(V[0].sum() - mass0) > 1e-8 * mass0
+
+
+@pytest.mark.parametrize("beta,order", [(0.0, 1), (0.5, 2)])
+def test_time_accuracy_order_on_a_warped_mesh(beta, order):
+    """Remark 2.6 with |K_i|/dt per cell on the warped closed basin: over a
+    fixed time the error against 128 Crank-Nicolson steps falls at first
+    order for backward Euler and at second order for Crank-Nicolson."""
+    p = _bumps_on_warped()
+    o = Oracle(p)
+    U0 = p.U0.copy()
+    U0[0] = U0[0] + 0.02 * (U0[0] > 0) * np.random.default_rng(5).random(p.n)
+    T = 0.04
+
+    def run(nsteps, b):
+        U = U0.copy()
+        for _ in range(nsteps):
+            U, info = o.time_step(U, dt=T / nsteps, beta=b)
+            assert info["status"] == 0
+        return U
+
+    ref = run(128, 0.5)
+    e1, e2 = np.abs(run(8, beta) - ref).max(), np.abs(run(16, beta) - ref).max()
+    assert abs(np.log2(e1 / e2) - order) < 0.3, (e1, e2)
 
 
 def test_cell_areas_add_up_to_the_channel_area():
