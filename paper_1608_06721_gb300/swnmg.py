@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import workloads as W
-from .build import LIB, build
+from .build import build
 
 HIST = 512
 

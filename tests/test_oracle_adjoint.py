@@ -5,7 +5,6 @@ lambda^T dR/dq against central differences of the residual map, and the
 gradient of a gauge loss against central differences with re-solved steady
 states (implicit function theorem)."""
 import numpy as np
-import pytest
 
 from oracle.oracle import Oracle
 from paper_1608_06721_gb300 import workloads as W

@@ -6,7 +6,6 @@ step is the steady solve, a small backward-Euler step differs from the
 forward-Euler step by O(dt^2), and over a fixed time backward Euler
 (beta = 0) converges at first order and Crank-Nicolson (beta = 1/2) at
 second order."""
-import copy
 
 import numpy as np
 import pytest

@@ -7,7 +7,6 @@ import json
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
