@@ -385,6 +385,20 @@ def test_example35_flow_patterns():
     assert steps[0.67] == max(steps.values()) and list(steps.values()).count(steps[0.67]) == 1, steps
 
 
+def test_example35_newton_steps_against_the_inflow_froude_number():
+    """The paper's histogram of Example 3.5 (384 x 128 cells): NMGM needs more
+    Newton steps when F_in is below 0.3 or equal to 0.7.  On 96 x 32 cells:
+    every F_in <= 0.25 takes more steps than any F_in in 0.4 ... 0.6, and
+    F_in = 0.7 takes the most between 0.3 and 1.2."""
+    steps = {}
+    for F in (0.1, 0.2, 0.25, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 1.0, 1.2):
+        U, info = Oracle(W.hubbard_channel(F)).solve()
+        assert info["status"] == 0, F
+        steps[F] = info["n_newton"]
+    assert min(steps[F] for F in (0.1, 0.2, 0.25)) > max(steps[F] for F in (0.4, 0.5, 0.6)), steps
+    assert steps[0.7] > max(steps[F] for F in (0.3, 0.4, 0.5, 0.6, 0.8, 1.0, 1.2)), steps
+
+
 def test_example35_case4_subcritical_pocket():
     """Case 4 (F_in = 1.7) has a subcritical pocket inside the constriction
     (1 < x < 2); it appears once the mesh resolves it (192 x 64 cells)."""
