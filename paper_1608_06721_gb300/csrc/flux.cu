@@ -696,17 +696,30 @@ __device__ __forceinline__ void blusgs_group(const DevLevel& L, const double* __
     const double gb = __shfl_sync(full, G[s], src0);
     v[s] = (p == 0) ? len * G[s] : len * ((G[s] - gb) * L.reps);
   }
-  // gather on the group's first lane in side order
+  // Sum over the sides, lane-parallel: lane g < NC*NP of the group owns
+  // entry (s, pp) = (g / NP, g % NP) and adds the sides' values in the order
+  // W, E, S, N (the same additions, in the same order, as one lane summing
+  // every entry), then the group's first lane collects the NC*NP sums.
+  const int es = g / NP < NC ? g / NP : 0, ep = g % NP;
+  double acc = 0.0;
+  for (int q = 0; q < NS; ++q) {
+    double w = 0.0;
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      const double t = __shfl_sync(full, v[s], gbase + q * NP + ep);
+      if (s == es) w = t;
+    }
+    acc = acc + w;
+  }
   double Rs[NC], D[NC * NC];
-  for (int s = 0; s < NC; ++s) Rs[s] = 0.0;
-  for (int e = 0; e < NC * NC; ++e) D[e] = 0.0;
-  for (int q = 0; q < NS; ++q)
-    for (int pp = 0; pp < NP; ++pp)
-      for (int s = 0; s < NC; ++s) {
-        const double w = __shfl_sync(full, v[s], gbase + q * NP + pp);
-        if (pp == 0) Rs[s] = Rs[s] + w;
-        else D[s * NC + (pp - 1)] = D[s * NC + (pp - 1)] + w;
-      }
+#pragma unroll
+  for (int s = 0; s < NC; ++s)
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) {
+      const double t = __shfl_sync(full, acc, gbase + s * NP + pp);
+      if (pp == 0) Rs[s] = t;
+      else D[s * NC + (pp - 1)] = t;
+    }
   if (!cell_ok || g != 0) return;
   if (L.t_ka > 0.0) {   // time step (Remark 2.6): the step's residual and diagonal block
     for (int s = 0; s < NC; ++s) Rs[s] = (L.t_omb * Rs[s] + L.t_ka * ci[s]) - L.t_src[s * n + i];
