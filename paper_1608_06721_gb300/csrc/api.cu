@@ -194,7 +194,7 @@ void sgs_half(swnmg_ctx* c, const Hier& H, int l, int forward) {
 void blusgs_half(swnmg_ctx* c, int l, double* U, int forward) {
   DevLevel L = dev_level(c, l);
   TimedScope ts(c, l == 0 ? SWNMG_T_BLUSGS : SWNMG_T_BLUSGS_COARSE, L.n);
-  launch_blusgs_sweep(L, c->lv[l].z, U, c->ghost, forward, c->sgs_sync, c->sticky, c->st);
+  launch_blusgs_strip(L, c->lv[l].z, U, c->ghost, forward, c->blu_sync, c->sticky, c->st);
 }
 
 // Algorithm 0 on level l of hierarchy H (lv[l].b, lv[l].x)
@@ -313,6 +313,7 @@ void free_ctx(swnmg_ctx* c) {
   if (c->csing) cudaFree(c->csing);
   if (c->derr) cudaFree(c->derr);
   if (c->sgs_sync) cudaFree(c->sgs_sync);
+  if (c->blu_sync) cudaFree(c->blu_sync);
   if (c->sticky) cudaFree(c->sticky);
   if (c->ghost) cudaFree(c->ghost);
   if (c->t_src) cudaFree(c->t_src);
@@ -430,6 +431,7 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
     ALLOC(c->red, 1032 * sizeof(double));
     ALLOC(c->derr, sizeof(int));
     ALLOC(c->sgs_sync, sizeof(int) * (2 + (v0.ny + 31) / 32 + 8));
+    ALLOC(c->blu_sync, sizeof(int) * (2 + (v0.ny + 1) / 2 + 8));   // 2-row strips
     ALLOC(c->sticky, sizeof(int));
     ALLOC(c->ghost, sizeof(double) * 4 * (size_t)std::max(v0.nx, v0.ny) * (c->nc + 1) * 3);
   }

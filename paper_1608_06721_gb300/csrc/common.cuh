@@ -124,6 +124,8 @@ void launch_residual(const DevLevel& L, const double* z, const double* U, double
 void launch_jacobian(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
                      double* edge_buf, void* blk, int fp32, cudaStream_t st);   // blk skewed
 // gbuf: 4 * max(nx, ny) * (nc + 1) * 3 doubles of ghost scratch
+void launch_blusgs_strip(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
+                         int* sticky_err, cudaStream_t st);
 void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
                          int* sticky_err, cudaStream_t st);
 // dU strip-skewed (a level-0 multigrid iterate)

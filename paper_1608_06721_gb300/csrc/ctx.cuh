@@ -51,6 +51,7 @@ struct swnmg_ctx {
   double t_ka = 0.0, t_omb = 1.0;
   double* t_src = nullptr;  // |K|/dt U^n - beta R(U^n), nc x n
   int* sgs_sync = nullptr;  // ticket / abort / per-strip progress of the wavefront sweeps
+  int* blu_sync = nullptr;  // ticket / abort / per-strip progress of the BLU-SGS strip sweep
   int* sticky = nullptr;    // set by a device wait that ran out of its bound
   double* hbuf = nullptr;   // pinned host scalars
   bool coarse_exact = false;

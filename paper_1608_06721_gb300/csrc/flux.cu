@@ -804,6 +804,96 @@ __global__ void __launch_bounds__(128) k_blusgs_sweep(DevLevel L, const double* 
   }
 }
 
+// ---- BLU-SGS: strip-pipelined half-sweep ------------------------------------
+// The same cell updates as k_blusgs_sweep, ordered by point-to-point waits
+// instead of a grid barrier per anti-diagonal.  Strip q holds R = 32 / GRP
+// consecutive rows, counted from the sweep's first row (the bottom row
+// forward, the top row backward), and columns are counted from the sweep's
+// first column.  At step t the strip's warp updates row r at column t - r,
+// so the cells of a step lie on one anti-diagonal.  A cell's neighbours
+// before it in the sweep order are then new values: inside the strip they
+// were updated at step t - 1 by this warp, and the first row's neighbour is
+// in the last row of strip q - 1, which this strip waits for (bounded) until
+// that row has passed column t.  Its neighbours after it in the sweep order
+// are still old values: they are updated later by this warp, or by strip
+// q + 1, which waits for this strip's last row.  The lane that wrote the
+// last row's cell publishes the progress with a release store after it (in
+// a forward step that cell is cell 0, in a backward step the last cell).
+// Strips are claimed in order through an atomic ticket, so a strip only
+// waits for one that a running warp owns.  The ghosts come from
+// k_ghost_prologue, launched before.
+// sync: [0] ticket, [1] abort, [2 + q] columns completed by strip q's last row.
+__device__ __forceinline__ void st_rel(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int NC, int NS>
+__global__ void __launch_bounds__(128) k_ghost_prologue(DevLevel L, const double* __restrict__ U,
+                                                        double* gbuf) {
+  ghost_prologue<NC, NS>(L, U, gbuf, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+template <int NC, int NS, int GRP>
+__global__ void __launch_bounds__(32) k_blusgs_strip(DevLevel L, const double* __restrict__ z, double* U,
+                                                     const double* gbuf, int forward, int* sync,
+                                                     int* sticky_err, int spin_limit) {
+  constexpr int R = 32 / GRP;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int nstrips = (L.ny + R - 1) / R;
+  int* prog = sync + 2;
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(&sync[0], 1);
+    q = __shfl_sync(full, q, 0);
+    if (q >= nstrips) return;
+    const int rows = (L.ny - q * R < R) ? L.ny - q * R : R;
+    const int nsteps = L.nx + rows - 1;
+    int known = 0;
+    for (int t = 0; t < nsteps; ++t) {
+      if (q > 0 && t < L.nx && known < t + 1) {   // the previous strip's last row at column t
+        int pg = 0, it = 0;
+        do {
+          if (lane == 0) {
+            pg = ld_acq(&prog[q - 1]);
+            if (pg < t + 1 && ld_acq(&sync[1])) pg = -1;
+          }
+          pg = __shfl_sync(full, pg, 0);
+          if (pg >= t + 1 || pg < 0) break;
+          __nanosleep(32);
+        } while (++it < spin_limit);
+        if (pg < t + 1) {
+          if (lane == 0) {
+            if (pg >= 0) atomicOr(sticky_err, 1);
+            atomicExch(&sync[1], 1);
+          }
+          return;
+        }
+        known = pg;
+      }
+      __syncwarp();   // lane 0's acquire before the other lanes' loads of that row
+      const int c_lo = t - rows + 1 > 0 ? t - rows + 1 : 0;
+      const int c_hi = t < L.nx - 1 ? t : L.nx - 1;
+      const int ncell = c_hi - c_lo + 1;
+      int d, ix0;
+      if (forward) {   // ix = c, iy = qR + (t - c)
+        d = q * R + t;
+        ix0 = c_lo;
+      } else {         // ix = nx-1-c, iy = ny-1-qR-(t - c)
+        d = (L.nx - 1) + (L.ny - 1) - (q * R + t);
+        ix0 = L.nx - 1 - c_hi;
+      }
+      blusgs_group<NC, NS, GRP, true>(L, z, U, gbuf, d, ix0, ncell, lane / GRP, lane % GRP);
+      __syncwarp();
+      const int done = t - rows + 2;                  // columns completed by the last row
+      if (q + 1 < nstrips && done >= 1 && done <= L.nx) {
+        const int rel = forward ? 0 : (ncell - 1) * GRP;
+        if (lane == rel) st_rel(&prog[q], done);
+      }
+    }
+  }
+}
+
 // ---- adjoint: lambda^T dR/dz and lambda^T dR/dq --------------------------------
 // Central differences (step delta) of the edge terms with respect to the bed of
 // either cell, contracted with lambda of both cells: cz[e] for the left cell's
@@ -1165,6 +1255,35 @@ void launch_jacobian(const DevLevel& L, const double* z, const double* U, double
       k_jac_edges<2, double><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, blk, n_xe, n_e);
       k_jac_cells<2, double><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, U, R, rn, blk, n_xe, n_e);
     }
+  }
+}
+
+// strip-pipelined half-sweep: ghosts, then one warp per strip in flight;
+// sync holds 2 + ceil(ny / R) ints, R = 2 (2D) or 4 (1D) rows per strip
+void launch_blusgs_strip(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
+                         int* sticky_err, cudaStream_t st) {
+  count_launches(2);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int R = L.nc == 3 ? 2 : 4;
+  const int nstrips = (L.ny + R - 1) / R;
+  cudaMemsetAsync(sync, 0, (2 + nstrips) * sizeof(int), st);
+  const int glen = L.nx > L.ny ? L.nx : L.ny;
+  const int gthreads = 4 * glen * (L.nc + 1);
+  const int gblocks = (gthreads + 127) / 128;
+  // at most 16 warps per SM: more strips than that queue on the ticket
+  const int grid = nstrips < 16 * nsm ? nstrips : 16 * nsm;
+  const int spin = 1 << 22;
+  if (L.nc == 3) {
+    k_ghost_prologue<3, 4><<<gblocks, 128, 0, st>>>(L, U, gbuf);
+    k_blusgs_strip<3, 4, 16><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
+  } else {
+    k_ghost_prologue<2, 2><<<gblocks, 128, 0, st>>>(L, U, gbuf);
+    k_blusgs_strip<2, 2, 8><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
   }
 }
 
