@@ -6,7 +6,6 @@ checks the lexicographic sweep's dependencies (Algorithm 1, BLU-SGS): every
 cell is updated exactly once, its neighbours before it in the sweep order are
 already updated, the ones after it are not, and the lane that publishes a
 strip's progress is the lane that wrote the published cell."""
-import itertools
 import random
 
 import pytest
