@@ -124,6 +124,25 @@ SWNMG_API const char* swnmg_last_error(const swnmg_ctx* ctx);
  * not change (SWNMG_ERR_ARG otherwise). */
 SWNMG_API swnmg_status swnmg_set_params(swnmg_ctx* ctx, const swnmg_params* prm);
 
+/* Puts a 2D context on a structured curvilinear quadrilateral mesh (the
+ * meshes of Examples 3.4 and 3.5): eq. totalFlux with each edge's own length
+ * |e_ij| and unit normal n_ij, and each cell's own area |K_i|.
+ * vx_host, vy_host: (nx+1)*(ny+1) vertex coordinates each, vertex (a, b) at
+ * index a + (nx+1)*b, copied; cell (ix, iy) has the corners (ix, iy),
+ * (ix+1, iy), (ix+1, iy+1), (ix, iy+1), counter-clockwise.  Level l uses every
+ * 2^l-th vertex.  Edges are the straight segments between vertices, the
+ * normal points from the lower-index cell to the higher-index one, and the
+ * edge frame's tangent is the normal turned by +90 degrees on W/E edges and
+ * by -90 degrees on S/N edges, so that a boundary's q is the discharge along
+ * that normal and its ut the velocity along that tangent.  Step 1 averages
+ * the children by area, and swnmg_time_step uses |K_i|/dt per cell.  Call
+ * it after swnmg_create, before solving; calling it again replaces the mesh.
+ * SWNMG_ERR_ARG for a 1D context, a null pointer, or a mesh with a
+ * zero-length edge or a cell of non-positive area on any level (the context
+ * then stays on its uniform mesh).  swnmg_adjoint then returns SWNMG_ERR_ARG
+ * (built for uniform meshes only).  Synchronises the stream. */
+SWNMG_API swnmg_status swnmg_set_mesh(swnmg_ctx* ctx, const double* vx_host, const double* vy_host);
+
 /* eq. Res on the finest mesh: R_dev (ncomp*n) = R(U_dev); rnorm_dev (n,
  * nullable) = ||R_i||_1; l1_host (nullable) = sum_i ||R_i||_1 (this one
  * synchronises the stream). */

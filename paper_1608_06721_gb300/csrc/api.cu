@@ -96,6 +96,11 @@ DevLevel dev_level(const swnmg_ctx* c, int l) {
   L.t_omb = c->t_omb;
   L.t_src = c->t_src;
   L.reps = 1.0 / c->prm.fd_eps;
+  if (c->curv) {
+    L.geo = c->lv[l].geo;
+    L.area = c->lv[l].area;
+    L.t_kai = (l == 0 && c->t_on) ? c->kai : nullptr;
+  }
   for (int s = 0; s < 4; ++s) {
     L.bc[s].kind = c->prob.bc[s].kind;
     L.bc[s].h = c->prob.bc[s].h;
@@ -302,7 +307,11 @@ void free_ctx(swnmg_ctx* c) {
     if (v.piv) cudaFree(v.piv);
     if (v.b) cudaFree(v.b);
     if (v.x) cudaFree(v.x);
+    if (v.geo) cudaFree(v.geo);
+    if (v.area) cudaFree(v.area);
   }
+  if (c->mesh) cudaFree(c->mesh);
+  if (c->kai) cudaFree(c->kai);
   if (c->R) cudaFree(c->R);
   if (c->rn) cudaFree(c->rn);
   if (c->eb) cudaFree(c->eb);
@@ -504,6 +513,48 @@ SWNMG_API swnmg_status swnmg_set_params(swnmg_ctx* c, const swnmg_params* q) {
   return SWNMG_OK;
 }
 
+SWNMG_API swnmg_status swnmg_set_mesh(swnmg_ctx* c, const double* vx, const double* vy) {
+  if (!c || !vx || !vy) return fail(c, SWNMG_ERR_ARG, "null pointer");
+  if (c->prob.dim != 2) return fail(c, SWNMG_ERR_ARG, "curvilinear meshes are two-dimensional");
+  const int nx = c->prob.nx, ny = c->prob.ny;
+  const size_t nv = (size_t)(nx + 1) * (ny + 1);
+  if (!c->mesh) {
+    CUDA_TRY(c, cudaMalloc((void**)&c->mesh, 2 * nv * sizeof(double)));
+    CUDA_TRY(c, cudaMalloc((void**)&c->kai, (size_t)c->lv[0].n * sizeof(double)));
+    for (int l = 0; l <= c->nl; ++l) {
+      Level& v = c->lv[l];
+      const size_t ne = (size_t)(v.nx + 1) * v.ny + (size_t)v.nx * (v.ny + 1);
+      CUDA_TRY(c, cudaMalloc((void**)&v.geo, 3 * ne * sizeof(double)));
+      CUDA_TRY(c, cudaMalloc((void**)&v.area, (size_t)v.n * sizeof(double)));
+    }
+  }
+  c->curv = false;
+  CUDA_TRY(c, cudaMemcpyAsync(c->mesh, vx, nv * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->mesh + nv, vy, nv * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(c, cudaMemsetAsync(c->derr, 0, sizeof(int), c->st));
+  for (int l = 0; l <= c->nl; ++l) {
+    Level& v = c->lv[l];
+    launch_mesh_level(v.nx, v.ny, nx + 1, 1 << l, c->mesh, c->mesh + nv, v.geo, v.area, c->derr, c->st);
+  }
+  LAUNCH_CHECK(c);
+  int bad = 0;
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  CUDA_TRY(c, cudaMemcpy(&bad, c->derr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (bad) {   // back to the uniform mesh's coarse beds (a replaced mesh may have changed them)
+    for (int l = 0; l < c->nl; ++l)
+      launch_average(2, c->lv[l].nx, c->lv[l].ny, 1, c->lv[l].z, c->lv[l + 1].z, c->st);
+    LAUNCH_CHECK(c);
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return fail(c, SWNMG_ERR_ARG, "degenerate mesh: an edge of zero length or a cell of non-positive area");
+  }
+  c->curv = true;
+  for (int l = 0; l < c->nl; ++l)   // coarse beds: the children weighted by their areas
+    launch_average_area(c->lv[l].nx, c->lv[l].ny, 1, c->lv[l].area, c->lv[l].z, c->lv[l + 1].z, c->st);
+  LAUNCH_CHECK(c);
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SWNMG_OK;
+}
+
 SWNMG_API swnmg_status swnmg_residual(swnmg_ctx* c, const double* U, double* R, double* rn,
                                       double* l1_host) {
   if (!c || !U || !R) return fail(c, SWNMG_ERR_ARG, "null pointer");
@@ -596,7 +647,10 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
   if (c->prm.init_mode == SWNMG_INIT_CASCADE && NL > 0) {
     const double* src = U;
     for (int l = 0; l < NL; ++l) {
-      launch_average(c->prob.dim, c->lv[l].nx, c->lv[l].ny, nc, src, c->lv[l + 1].U, c->st);
+      if (c->curv)   // the children weighted by their areas
+        launch_average_area(c->lv[l].nx, c->lv[l].ny, nc, c->lv[l].area, src, c->lv[l + 1].U, c->st);
+      else
+        launch_average(c->prob.dim, c->lv[l].nx, c->lv[l].ny, nc, src, c->lv[l + 1].U, c->st);
       src = c->lv[l + 1].U;
     }
     LAUNCH_CHECK(c);
@@ -678,10 +732,15 @@ SWNMG_API swnmg_status swnmg_time_step(swnmg_ctx* c, double* U, double dt, doubl
   c->t_on = false;
   const DevLevel L = dev_level(c, 0);
   launch_residual(L, v0.z, U, c->R, c->rn, c->eb, c->st);   // R(U^n)
-  launch_time_source(m, ka, beta, U, c->R, c->t_src, c->st);
+  if (c->curv) {   // |K_i|/dt per cell
+    launch_time_ka(v0.n, v0.area, dt, c->kai, c->st);
+    launch_time_source_cells(m, v0.n, c->kai, beta, U, c->R, c->t_src, c->st);
+  } else {
+    launch_time_source(m, ka, beta, U, c->R, c->t_src, c->st);
+  }
   LAUNCH_CHECK(c);
   c->t_on = true;
-  c->t_ka = ka;
+  c->t_ka = c->curv ? 1.0 : ka;   // > 0 switches the time step on; a curvilinear mesh reads kai
   c->t_omb = 1.0 - beta;
   const int32_t im = c->prm.init_mode;
   c->prm.init_mode = SWNMG_INIT_NONE;
@@ -751,6 +810,7 @@ SWNMG_API swnmg_status swnmg_adjoint(swnmg_ctx* c, const double* U, const double
                                      int32_t* cycles_out) {
   if (!c || !U || !g || !lam || !dRz || max_cycles < 1) return fail(c, SWNMG_ERR_ARG, "bad argument");
   if (!(rtol == rtol)) return fail(c, SWNMG_ERR_ARG, "rtol is NaN");
+  if (c->curv) return fail(c, SWNMG_ERR_ARG, "the adjoint is built for uniform meshes only");
   if (cycles_out) *cycles_out = 0;
   swnmg_status s = adjoint_alloc(c);
   if (s != SWNMG_OK) return s;

@@ -44,6 +44,13 @@ struct DevLevel {
   double t_ka, t_omb;
   const double* t_src;
   DevBC bc[4];            // W, E, S, N
+  // structured curvilinear mesh (2D; NULL: the uniform mesh above).  geo per
+  // edge e (x-edges first): |e| at geo[e], the unit normal (from the
+  // lower-index cell to the higher-index one) at geo[n_e + e], geo[2 n_e + e];
+  // area |K_i| per cell; t_kai |K_i|/dt per cell during a time step.
+  const double* geo = nullptr;
+  const double* area = nullptr;
+  const double* t_kai = nullptr;
 };
 
 // LU layout of a block (n = 2 or 3), partial pivoting, guard for singular
@@ -135,6 +142,14 @@ void launch_adjoint_z(const DevLevel& L, const double* z, const double* U, const
                       double* cz, double* dRz, cudaStream_t st);
 void launch_adjoint_q(const DevLevel& L, int side, const double* z, const double* U, const double* lam,
                       double delta, double* out, cudaStream_t st);
+// curvilinear meshes (Examples 3.4, 3.5)
+void launch_average_area(int nxf, int nyf, int ncomp, const double* area_f, const double* vf, double* vc,
+                         cudaStream_t st);
+void launch_time_source_cells(long long m, long long n, const double* kai, double beta, const double* U,
+                              const double* R, double* src, cudaStream_t st);
+void launch_mesh_level(int nx, int ny, int vrow, int step, const double* vx, const double* vy, double* geo,
+                       double* area, int* bad, cudaStream_t st);
+void launch_time_ka(int n, const double* area, double dt, double* kai, cudaStream_t st);
 void launch_average(int dim, int nxf, int nyf, int ncomp, const double* vf, double* vc,
                     cudaStream_t st);
 // t_src = ka U^n - beta R(U^n) over m values (the time step's fixed part)
