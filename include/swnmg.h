@@ -59,7 +59,11 @@ enum {
 /* numerical fluxes, Remark 2.2 */
 enum { SWNMG_FLUX_HLL = 0, SWNMG_FLUX_HLLC = 1, SWNMG_FLUX_LLF = 2, SWNMG_FLUX_ROE = 3 };
 enum { SWNMG_INIT_CASCADE = 0, SWNMG_INIT_NONE = 1 };   /* Algorithm 1 Step 1, or warm start */
-enum { SWNMG_PREC_FP64 = 0, SWNMG_PREC_MIXED = 1 };     /* MIXED: FP32 multigrid inner solve */
+/* MIXED: FP32 multigrid inner solve.  MIXED_STEP1: MIXED, and Step 1's
+ * BLU-SGS sweeps on the coarse levels (l >= 1) in FP32 (finite-difference
+ * step 2^-12, singular-pivot guard 1e-6 max|D|; the state stays FP64).
+ * Batches take MIXED_STEP1 as MIXED. */
+enum { SWNMG_PREC_FP64 = 0, SWNMG_PREC_MIXED = 1, SWNMG_PREC_MIXED_STEP1 = 2 };
 
 /* Boundary data of one side.  q is the discharge along the +axis direction
  * (hu on the W/E sides, hv on S/N), so an inflow through the west side has

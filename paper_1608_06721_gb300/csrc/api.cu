@@ -117,7 +117,8 @@ swnmg_status check_params(const swnmg_problem* p, const swnmg_params* q) {
   if (!(q->fd_eps > 0) || !(q->h_eps > 0) || q->alpha < 0) return SWNMG_ERR_ARG;
   if (q->n_levels < 0 || q->n_levels > 12 || q->n_mg < 0 || q->nu1 < 0 || q->nu2 < 0) return SWNMG_ERR_ARG;
   if (q->gamma < 1 || q->gamma > 2 || q->max_newton < 0 || q->max_blusgs < 0) return SWNMG_ERR_ARG;
-  if (q->precision != SWNMG_PREC_FP64 && q->precision != SWNMG_PREC_MIXED) return SWNMG_ERR_ARG;
+  if (q->precision != SWNMG_PREC_FP64 && q->precision != SWNMG_PREC_MIXED && q->precision != SWNMG_PREC_MIXED_STEP1)
+    return SWNMG_ERR_ARG;
   if (q->init_mode != SWNMG_INIT_CASCADE && q->init_mode != SWNMG_INIT_NONE) return SWNMG_ERR_ARG;
   const int m = 1 << q->n_levels;
   if (p->nx % m) return SWNMG_ERR_ARG;
@@ -199,7 +200,11 @@ void sgs_half(swnmg_ctx* c, const Hier& H, int l, int forward) {
 void blusgs_half(swnmg_ctx* c, int l, double* U, int forward) {
   DevLevel L = dev_level(c, l);
   TimedScope ts(c, l == 0 ? SWNMG_T_BLUSGS : SWNMG_T_BLUSGS_COARSE, L.n);
-  launch_blusgs_strip(L, c->lv[l].z, U, c->ghost, forward, c->blu_sync, c->sticky, c->st);
+  if (l >= 1 && c->prm.precision == SWNMG_PREC_MIXED_STEP1)   // Step 1's coarse levels in FP32
+    launch_blusgs32_strip(L, c->lv[l].z, U, reinterpret_cast<float*>(c->ghost), forward, c->blu_sync, c->sticky,
+                          c->st);
+  else
+    launch_blusgs_strip(L, c->lv[l].z, U, c->ghost, forward, c->blu_sync, c->sticky, c->st);
 }
 
 // Algorithm 0 on level l of hierarchy H (lv[l].b, lv[l].x)
@@ -389,7 +394,7 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
   c->prm = *q;
   c->nc = p->dim == 2 ? 3 : 2;
   c->nl = q->n_levels;
-  c->fp32 = q->precision == SWNMG_PREC_MIXED;
+  c->fp32 = q->precision != SWNMG_PREC_FP64;
   c->wsz = c->fp32 ? 4 : 8;
   c->st = (cudaStream_t)stream;
   const double dx = (p->x1 - p->x0) / p->nx;

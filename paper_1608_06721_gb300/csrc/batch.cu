@@ -308,7 +308,7 @@ SWNMG_API swnmg_status swnmg_batch_create(const swnmg_problem* probs, const int3
   swnmg_batch* b = new swnmg_batch();
   b->B = B;
   b->prm = *prm;
-  b->fp32 = prm->precision == SWNMG_PREC_MIXED;
+  b->fp32 = prm->precision != SWNMG_PREC_FP64;   // MIXED_STEP1 runs as MIXED in a batch
   b->user_st = (cudaStream_t)stream;
   swnmg_status rc = SWNMG_OK;
   int dev = 0;

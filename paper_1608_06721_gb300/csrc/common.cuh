@@ -131,6 +131,9 @@ void launch_residual(const DevLevel& L, const double* z, const double* U, double
 void launch_jacobian(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
                      double* edge_buf, void* blk, int fp32, cudaStream_t st);   // blk skewed
 // gbuf: 4 * max(nx, ny) * (nc + 1) * 3 doubles of ghost scratch
+// FP32 BLU-SGS half-sweep (blusgs32.cu): Step 1 under SWNMG_PREC_MIXED_STEP1
+void launch_blusgs32_strip(const DevLevel& L, const double* z, double* U, float* gbuf, int forward, int* sync,
+                           int* sticky_err, cudaStream_t st);
 void launch_blusgs_strip(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
                          int* sticky_err, cudaStream_t st);
 void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
