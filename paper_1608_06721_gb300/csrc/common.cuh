@@ -92,6 +92,7 @@ struct BItem {
   int* csing;
   int n_xe, n_e;                // x-edges, all edges
   int strip0;                   // first SGS progress slot of this problem
+  int bstrip0;                  // first BLU-SGS strip progress slot of this problem
   int has;                      // the problem has this level
 };
 
@@ -171,6 +172,10 @@ void launch_b_average(const BLaunch& coarse, const BItem* fine_items, cudaStream
 void launch_b_inject(const BLaunch& fine, const BItem* coarse_items, cudaStream_t st);
 // one half-sweep over every masked problem's level; nsteps = max diagonals,
 // blocks = cooperative grid size, sync: [0] arrivals, [1] abort (zeroed here)
+// batched strip-pipelined BLU-SGS half-sweep: (problem, strip) tickets in
+// claim order (strip index first), grid warps at most
+void launch_b_blusgs_strip(const BItem* items, const int2* tickets, int ntickets, int nslots, const int* mask,
+                           int B, int forward, int grid, int* sync, int* sticky_err, cudaStream_t st);
 void launch_b_blusgs_sweep(const BItem* items, const int* mask, int B, int nsteps, int forward, int blocks,
                            int* sync, int* sticky_err, cudaStream_t st);
 int b_blusgs_max_blocks_per_sm();

@@ -1645,6 +1645,104 @@ void launch_b_inject(const BLaunch& fine, const BItem* coarse_items, cudaStream_
   if (fine.nblocks > 0) kb_inject<<<fine.nblocks, 128, 0, st>>>(fine, coarse_items);
 }
 
+// Batched strip-pipelined BLU-SGS: the schedule of k_blusgs_strip, one
+// (problem, strip) ticket at a time; problems outside the mask are skipped
+// whole.  Tickets list strip 0 of every problem first, then strip 1, ..., so
+// a strip only waits for one that a running warp owns.  sync: [0] ticket,
+// [1] abort, [2 + bstrip0(p) + q] columns completed by strip q's last row.
+template <int NC, int NS>
+__global__ void __launch_bounds__(128) kb_ghost_prologue(const BItem* __restrict__ items,
+                                                         const int* __restrict__ mask, int B) {
+  for (int p = 0; p < B; ++p)
+    if (mask[p])
+      ghost_prologue<NC, NS>(items[p].L, items[p].U, items[p].ghost, blockIdx.x * blockDim.x + threadIdx.x,
+                             gridDim.x * blockDim.x);
+}
+
+template <int NC, int NS, int GRP>
+__global__ void __launch_bounds__(32) kb_blusgs_strip(const BItem* __restrict__ items,
+                                                      const int2* __restrict__ tickets, int ntickets,
+                                                      const int* __restrict__ mask, int forward, int* sync,
+                                                      int* sticky_err, int spin_limit) {
+  constexpr int R = 32 / GRP;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int tid = 0;
+    if (lane == 0) tid = atomicAdd(&sync[0], 1);
+    tid = __shfl_sync(full, tid, 0);
+    if (tid >= ntickets) return;
+    const int2 tk = tickets[tid];
+    const int p = tk.x, q = tk.y;
+    if (!mask[p]) continue;
+    const BItem& it = items[p];
+    const DevLevel L = it.L;
+    const int nstrips = (L.ny + R - 1) / R;
+    int* prog = sync + 2 + it.bstrip0;
+    const int rows = (L.ny - q * R < R) ? L.ny - q * R : R;
+    const int nsteps = L.nx + rows - 1;
+    int known = 0;
+    for (int t = 0; t < nsteps; ++t) {
+      if (q > 0 && t < L.nx && known < t + 1) {
+        int pg = 0, n_it = 0;
+        do {
+          if (lane == 0) {
+            pg = ld_acq(&prog[q - 1]);
+            if (pg < t + 1 && ld_acq(&sync[1])) pg = -1;
+          }
+          pg = __shfl_sync(full, pg, 0);
+          if (pg >= t + 1 || pg < 0) break;
+          __nanosleep(32);
+        } while (++n_it < spin_limit);
+        if (pg < t + 1) {
+          if (lane == 0) {
+            if (pg >= 0) atomicOr(sticky_err, 1);
+            atomicExch(&sync[1], 1);
+          }
+          return;
+        }
+        known = pg;
+      }
+      __syncwarp();
+      const int c_lo = t - rows + 1 > 0 ? t - rows + 1 : 0;
+      const int c_hi = t < L.nx - 1 ? t : L.nx - 1;
+      const int ncell = c_hi - c_lo + 1;
+      int d, ix0;
+      if (forward) {
+        d = q * R + t;
+        ix0 = c_lo;
+      } else {
+        d = (L.nx - 1) + (L.ny - 1) - (q * R + t);
+        ix0 = L.nx - 1 - c_hi;
+      }
+      blusgs_group<NC, NS, GRP, true>(L, it.z, it.U, it.ghost, d, ix0, ncell, lane / GRP, lane % GRP);
+      __syncwarp();
+      const int done = t - rows + 2;
+      if (q + 1 < nstrips && done >= 1 && done <= L.nx) {
+        const int rel = forward ? 0 : (ncell - 1) * GRP;
+        if (lane == rel) st_rel(&prog[q], done);
+      }
+    }
+  }
+}
+
+void launch_b_blusgs_strip(const BItem* items, const int2* tickets, int ntickets, int nslots, const int* mask,
+                           int B, int forward, int grid, int* sync, int* sticky_err, cudaStream_t st) {
+  if (ntickets <= 0) return;
+  count_launches(2);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  cudaMemsetAsync(sync, 0, (2 + nslots) * sizeof(int), st);
+  kb_ghost_prologue<3, 4><<<4 * nsm, 128, 0, st>>>(items, mask, B);
+  const int g = grid < ntickets ? grid : ntickets;
+  kb_blusgs_strip<3, 4, 16><<<g > 0 ? g : 1, 32, 0, st>>>(items, tickets, ntickets, mask, forward, sync, sticky_err,
+                                                         1 << 22);
+}
+
 void launch_b_blusgs_sweep(const BItem* items, const int* mask, int B, int nsteps, int forward, int blocks,
                            int* sync, int* sticky_err, cudaStream_t st) {
   count_launches(1);
