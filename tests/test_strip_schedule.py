@@ -89,3 +89,66 @@ def test_strip_schedule_keeps_sweep_order(nx, ny, forward):
         check(nx, ny, 2, 16, forward, seed)        # 2D: 16 lanes per cell, 2 rows per strip
         if ny == 1:
             check(nx, ny, 4, 8, forward, seed)     # 1D: 8 lanes per cell
+
+
+def _batch_tickets(sizes, R):
+    """(problem, strip) tickets in claim order: strip index first, then problem."""
+    out = []
+    for q in range(max((ny + R - 1) // R for _, ny in sizes)):
+        for p, (_, ny) in enumerate(sizes):
+            if q < (ny + R - 1) // R:
+                out.append((p, q))
+    return out
+
+
+def _run_batch(sizes, R, warps, rng):
+    """G warps claim tickets in order and run their strips step by step in a
+    random interleaving; a warp whose strip waits on the previous strip of
+    its problem stays put.  Returns False on a deadlock."""
+    tickets = _batch_tickets(sizes, R)
+    nxt = 0
+    prog = {}
+    state = [None] * warps            # (p, q, t) of the strip a warp holds
+    done_cells = {p: set() for p in range(len(sizes))}
+    while True:
+        for w in range(warps):
+            if state[w] is None and nxt < len(tickets):
+                p, q = tickets[nxt]
+                nxt += 1
+                state[w] = (p, q, 0)
+        live = [w for w in range(warps) if state[w] is not None]
+        if not live:
+            break
+        movable = []
+        for w in live:
+            p, q, t = state[w]
+            nx, ny = sizes[p]
+            if q > 0 and t < nx and prog.get((p, q - 1), 0) < t + 1:
+                continue
+            movable.append(w)
+        if not movable:
+            return False
+        w = rng.choice(movable)
+        p, q, t = state[w]
+        nx, ny = sizes[p]
+        rows = min(R, ny - q * R)
+        for r in range(rows):
+            c = t - r
+            if 0 <= c < nx:
+                done_cells[p].add((c, q * R + r))
+        dn = t - rows + 2
+        if 1 <= dn <= nx:
+            prog[(p, q)] = dn
+        t += 1
+        state[w] = None if t == nx + rows - 1 else (p, q, t)
+    return all(len(done_cells[p]) == nx * ny for p, (nx, ny) in enumerate(sizes))
+
+
+@pytest.mark.parametrize("warps", [1, 2, 3, 7])
+def test_batch_tickets_never_deadlock(warps):
+    """Batched strips: with any number of resident warps, every problem of a
+    mixed-size batch completes (a strip waits only for an earlier ticket)."""
+    rng = random.Random(warps)
+    for trial in range(20):
+        sizes = [(rng.randint(1, 9), rng.randint(1, 9)) for _ in range(rng.randint(1, 5))]
+        assert _run_batch(sizes, 2, warps, rng), sizes
