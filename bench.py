@@ -50,7 +50,9 @@ def config_dict(p, flush):
     prm = p.params
     return {"workload": "2D partial-dry channel %dx%d (LLF, W-cycle N_L=%d exact coarsest, N_mg=%d, eps_p=%g, seed 301)"
             % (p.nx, p.ny, prm.n_levels, prm.n_mg, prm.eps_p),
-            "cells": p.n, "precision": "mixed FP32 multigrid / FP64 residual+update",
+            "cells": p.n,
+            "precision": ("mixed FP32 multigrid and FP32 Step 1 BLU-SGS / FP64 residual+update"
+                          if prm.precision == 2 else "mixed FP32 multigrid / FP64 residual+update"),
             "l2": flush, "tol": prm.tol}
 
 
@@ -213,7 +215,7 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
-    p = workload(W.PREC_MIXED, args.nx, args.nx)
+    p = workload(W.PREC_MIXED_STEP1 if args.step1_fp32 else W.PREC_MIXED, args.nx, args.nx)
     stream = torch.cuda.current_stream()
     S = swnmg.Solver(p, stream=stream)
     U0 = torch.as_tensor(p.U0, dtype=torch.float64, device=dev).contiguous()
@@ -506,6 +508,8 @@ def main():
     ap.add_argument("--workload", default="channel1024", choices=["channel1024", "batch"])
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--sequential", action="store_true")
+    ap.add_argument("--step1-fp32", action="store_true",
+                    help="Step 1's coarse-level BLU-SGS in FP32 (precision MIXED_STEP1)")
     args = ap.parse_args()
     globals()["LEVELS"] = args.levels
     if args.impl == "reference":

@@ -59,7 +59,11 @@ enum {
 /* numerical fluxes, Remark 2.2 */
 enum { SWNMG_FLUX_HLL = 0, SWNMG_FLUX_HLLC = 1, SWNMG_FLUX_LLF = 2, SWNMG_FLUX_ROE = 3 };
 enum { SWNMG_INIT_CASCADE = 0, SWNMG_INIT_NONE = 1 };   /* Algorithm 1 Step 1, or warm start */
-enum { SWNMG_PREC_FP64 = 0, SWNMG_PREC_MIXED = 1 };     /* MIXED: FP32 multigrid inner solve */
+/* MIXED: FP32 multigrid inner solve.  MIXED_STEP1: MIXED, and Step 1's
+ * BLU-SGS sweeps on the coarse levels (l >= 1) in FP32 (finite-difference
+ * step 2^-12, singular-pivot guard 1e-6 max|D|; the state stays FP64).
+ * Batches take MIXED_STEP1 as MIXED. */
+enum { SWNMG_PREC_FP64 = 0, SWNMG_PREC_MIXED = 1, SWNMG_PREC_MIXED_STEP1 = 2 };
 
 /* Boundary data of one side.  q is the discharge along the +axis direction
  * (hu on the W/E sides, hv on S/N), so an inflow through the west side has
@@ -123,6 +127,25 @@ SWNMG_API const char* swnmg_last_error(const swnmg_ctx* ctx);
 /* Replaces the parameters; n_levels, precision and dim-dependent sizes must
  * not change (SWNMG_ERR_ARG otherwise). */
 SWNMG_API swnmg_status swnmg_set_params(swnmg_ctx* ctx, const swnmg_params* prm);
+
+/* Puts a 2D context on a structured curvilinear quadrilateral mesh (the
+ * meshes of Examples 3.4 and 3.5): eq. totalFlux with each edge's own length
+ * |e_ij| and unit normal n_ij, and each cell's own area |K_i|.
+ * vx_host, vy_host: (nx+1)*(ny+1) vertex coordinates each, vertex (a, b) at
+ * index a + (nx+1)*b, copied; cell (ix, iy) has the corners (ix, iy),
+ * (ix+1, iy), (ix+1, iy+1), (ix, iy+1), counter-clockwise.  Level l uses every
+ * 2^l-th vertex.  Edges are the straight segments between vertices, the
+ * normal points from the lower-index cell to the higher-index one, and the
+ * edge frame's tangent is the normal turned by +90 degrees on W/E edges and
+ * by -90 degrees on S/N edges, so that a boundary's q is the discharge along
+ * that normal and its ut the velocity along that tangent.  Step 1 averages
+ * the children by area, and swnmg_time_step uses |K_i|/dt per cell.  Call
+ * it after swnmg_create, before solving; calling it again replaces the mesh.
+ * SWNMG_ERR_ARG for a 1D context, a null pointer, or a mesh with a
+ * zero-length edge or a cell of non-positive area on any level (the context
+ * then stays on its uniform mesh).  swnmg_adjoint then returns SWNMG_ERR_ARG
+ * (built for uniform meshes only).  Synchronises the stream. */
+SWNMG_API swnmg_status swnmg_set_mesh(swnmg_ctx* ctx, const double* vx_host, const double* vy_host);
 
 /* eq. Res on the finest mesh: R_dev (ncomp*n) = R(U_dev); rnorm_dev (n,
  * nullable) = ||R_i||_1; l1_host (nullable) = sum_i ||R_i||_1 (this one

@@ -24,6 +24,7 @@ UNITS = {
     "api.cu": [],
     "noalloc.cu": [],
     "batch.cu": [],
+    "blusgs32.cu": [],
 }
 
 

@@ -96,6 +96,11 @@ DevLevel dev_level(const swnmg_ctx* c, int l) {
   L.t_omb = c->t_omb;
   L.t_src = c->t_src;
   L.reps = 1.0 / c->prm.fd_eps;
+  if (c->curv) {
+    L.geo = c->lv[l].geo;
+    L.area = c->lv[l].area;
+    L.t_kai = (l == 0 && c->t_on) ? c->kai : nullptr;
+  }
   for (int s = 0; s < 4; ++s) {
     L.bc[s].kind = c->prob.bc[s].kind;
     L.bc[s].h = c->prob.bc[s].h;
@@ -112,7 +117,8 @@ swnmg_status check_params(const swnmg_problem* p, const swnmg_params* q) {
   if (!(q->fd_eps > 0) || !(q->h_eps > 0) || q->alpha < 0) return SWNMG_ERR_ARG;
   if (q->n_levels < 0 || q->n_levels > 12 || q->n_mg < 0 || q->nu1 < 0 || q->nu2 < 0) return SWNMG_ERR_ARG;
   if (q->gamma < 1 || q->gamma > 2 || q->max_newton < 0 || q->max_blusgs < 0) return SWNMG_ERR_ARG;
-  if (q->precision != SWNMG_PREC_FP64 && q->precision != SWNMG_PREC_MIXED) return SWNMG_ERR_ARG;
+  if (q->precision != SWNMG_PREC_FP64 && q->precision != SWNMG_PREC_MIXED && q->precision != SWNMG_PREC_MIXED_STEP1)
+    return SWNMG_ERR_ARG;
   if (q->init_mode != SWNMG_INIT_CASCADE && q->init_mode != SWNMG_INIT_NONE) return SWNMG_ERR_ARG;
   const int m = 1 << q->n_levels;
   if (p->nx % m) return SWNMG_ERR_ARG;
@@ -194,7 +200,11 @@ void sgs_half(swnmg_ctx* c, const Hier& H, int l, int forward) {
 void blusgs_half(swnmg_ctx* c, int l, double* U, int forward) {
   DevLevel L = dev_level(c, l);
   TimedScope ts(c, l == 0 ? SWNMG_T_BLUSGS : SWNMG_T_BLUSGS_COARSE, L.n);
-  launch_blusgs_sweep(L, c->lv[l].z, U, c->ghost, forward, c->sgs_sync, c->sticky, c->st);
+  if (l >= 1 && c->prm.precision == SWNMG_PREC_MIXED_STEP1)   // Step 1's coarse levels in FP32
+    launch_blusgs32_strip(L, c->lv[l].z, U, reinterpret_cast<float*>(c->ghost), forward, c->blu_sync, c->sticky,
+                          c->st);
+  else
+    launch_blusgs_strip(L, c->lv[l].z, U, c->ghost, forward, c->blu_sync, c->sticky, c->st);
 }
 
 // Algorithm 0 on level l of hierarchy H (lv[l].b, lv[l].x)
@@ -302,7 +312,11 @@ void free_ctx(swnmg_ctx* c) {
     if (v.piv) cudaFree(v.piv);
     if (v.b) cudaFree(v.b);
     if (v.x) cudaFree(v.x);
+    if (v.geo) cudaFree(v.geo);
+    if (v.area) cudaFree(v.area);
   }
+  if (c->mesh) cudaFree(c->mesh);
+  if (c->kai) cudaFree(c->kai);
   if (c->R) cudaFree(c->R);
   if (c->rn) cudaFree(c->rn);
   if (c->eb) cudaFree(c->eb);
@@ -313,6 +327,7 @@ void free_ctx(swnmg_ctx* c) {
   if (c->csing) cudaFree(c->csing);
   if (c->derr) cudaFree(c->derr);
   if (c->sgs_sync) cudaFree(c->sgs_sync);
+  if (c->blu_sync) cudaFree(c->blu_sync);
   if (c->sticky) cudaFree(c->sticky);
   if (c->ghost) cudaFree(c->ghost);
   if (c->t_src) cudaFree(c->t_src);
@@ -379,7 +394,7 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
   c->prm = *q;
   c->nc = p->dim == 2 ? 3 : 2;
   c->nl = q->n_levels;
-  c->fp32 = q->precision == SWNMG_PREC_MIXED;
+  c->fp32 = q->precision != SWNMG_PREC_FP64;
   c->wsz = c->fp32 ? 4 : 8;
   c->st = (cudaStream_t)stream;
   const double dx = (p->x1 - p->x0) / p->nx;
@@ -430,6 +445,7 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
     ALLOC(c->red, 1032 * sizeof(double));
     ALLOC(c->derr, sizeof(int));
     ALLOC(c->sgs_sync, sizeof(int) * (2 + (v0.ny + 31) / 32 + 8));
+    ALLOC(c->blu_sync, sizeof(int) * (2 + (v0.ny + 1) / 2 + 8));   // 2-row strips
     ALLOC(c->sticky, sizeof(int));
     ALLOC(c->ghost, sizeof(double) * 4 * (size_t)std::max(v0.nx, v0.ny) * (c->nc + 1) * 3);
   }
@@ -499,6 +515,48 @@ SWNMG_API swnmg_status swnmg_set_params(swnmg_ctx* c, const swnmg_params* q) {
   const bool exact = (c->prob.dim == 1) || (q->coarse_sweeps <= 0);
   if (exact != c->coarse_exact) return fail(c, SWNMG_ERR_ARG, "coarse-solve kind is fixed at create");
   c->prm = *q;
+  return SWNMG_OK;
+}
+
+SWNMG_API swnmg_status swnmg_set_mesh(swnmg_ctx* c, const double* vx, const double* vy) {
+  if (!c || !vx || !vy) return fail(c, SWNMG_ERR_ARG, "null pointer");
+  if (c->prob.dim != 2) return fail(c, SWNMG_ERR_ARG, "curvilinear meshes are two-dimensional");
+  const int nx = c->prob.nx, ny = c->prob.ny;
+  const size_t nv = (size_t)(nx + 1) * (ny + 1);
+  if (!c->mesh) {
+    CUDA_TRY(c, cudaMalloc((void**)&c->mesh, 2 * nv * sizeof(double)));
+    CUDA_TRY(c, cudaMalloc((void**)&c->kai, (size_t)c->lv[0].n * sizeof(double)));
+    for (int l = 0; l <= c->nl; ++l) {
+      Level& v = c->lv[l];
+      const size_t ne = (size_t)(v.nx + 1) * v.ny + (size_t)v.nx * (v.ny + 1);
+      CUDA_TRY(c, cudaMalloc((void**)&v.geo, 3 * ne * sizeof(double)));
+      CUDA_TRY(c, cudaMalloc((void**)&v.area, (size_t)v.n * sizeof(double)));
+    }
+  }
+  c->curv = false;
+  CUDA_TRY(c, cudaMemcpyAsync(c->mesh, vx, nv * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->mesh + nv, vy, nv * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(c, cudaMemsetAsync(c->derr, 0, sizeof(int), c->st));
+  for (int l = 0; l <= c->nl; ++l) {
+    Level& v = c->lv[l];
+    launch_mesh_level(v.nx, v.ny, nx + 1, 1 << l, c->mesh, c->mesh + nv, v.geo, v.area, c->derr, c->st);
+  }
+  LAUNCH_CHECK(c);
+  int bad = 0;
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  CUDA_TRY(c, cudaMemcpy(&bad, c->derr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (bad) {   // back to the uniform mesh's coarse beds (a replaced mesh may have changed them)
+    for (int l = 0; l < c->nl; ++l)
+      launch_average(2, c->lv[l].nx, c->lv[l].ny, 1, c->lv[l].z, c->lv[l + 1].z, c->st);
+    LAUNCH_CHECK(c);
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return fail(c, SWNMG_ERR_ARG, "degenerate mesh: an edge of zero length or a cell of non-positive area");
+  }
+  c->curv = true;
+  for (int l = 0; l < c->nl; ++l)   // coarse beds: the children weighted by their areas
+    launch_average_area(c->lv[l].nx, c->lv[l].ny, 1, c->lv[l].area, c->lv[l].z, c->lv[l + 1].z, c->st);
+  LAUNCH_CHECK(c);
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
   return SWNMG_OK;
 }
 
@@ -594,7 +652,10 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
   if (c->prm.init_mode == SWNMG_INIT_CASCADE && NL > 0) {
     const double* src = U;
     for (int l = 0; l < NL; ++l) {
-      launch_average(c->prob.dim, c->lv[l].nx, c->lv[l].ny, nc, src, c->lv[l + 1].U, c->st);
+      if (c->curv)   // the children weighted by their areas
+        launch_average_area(c->lv[l].nx, c->lv[l].ny, nc, c->lv[l].area, src, c->lv[l + 1].U, c->st);
+      else
+        launch_average(c->prob.dim, c->lv[l].nx, c->lv[l].ny, nc, src, c->lv[l + 1].U, c->st);
       src = c->lv[l + 1].U;
     }
     LAUNCH_CHECK(c);
@@ -676,10 +737,15 @@ SWNMG_API swnmg_status swnmg_time_step(swnmg_ctx* c, double* U, double dt, doubl
   c->t_on = false;
   const DevLevel L = dev_level(c, 0);
   launch_residual(L, v0.z, U, c->R, c->rn, c->eb, c->st);   // R(U^n)
-  launch_time_source(m, ka, beta, U, c->R, c->t_src, c->st);
+  if (c->curv) {   // |K_i|/dt per cell
+    launch_time_ka(v0.n, v0.area, dt, c->kai, c->st);
+    launch_time_source_cells(m, v0.n, c->kai, beta, U, c->R, c->t_src, c->st);
+  } else {
+    launch_time_source(m, ka, beta, U, c->R, c->t_src, c->st);
+  }
   LAUNCH_CHECK(c);
   c->t_on = true;
-  c->t_ka = ka;
+  c->t_ka = c->curv ? 1.0 : ka;   // > 0 switches the time step on; a curvilinear mesh reads kai
   c->t_omb = 1.0 - beta;
   const int32_t im = c->prm.init_mode;
   c->prm.init_mode = SWNMG_INIT_NONE;
@@ -749,6 +815,7 @@ SWNMG_API swnmg_status swnmg_adjoint(swnmg_ctx* c, const double* U, const double
                                      int32_t* cycles_out) {
   if (!c || !U || !g || !lam || !dRz || max_cycles < 1) return fail(c, SWNMG_ERR_ARG, "bad argument");
   if (!(rtol == rtol)) return fail(c, SWNMG_ERR_ARG, "rtol is NaN");
+  if (c->curv) return fail(c, SWNMG_ERR_ARG, "the adjoint is built for uniform meshes only");
   if (cycles_out) *cycles_out = 0;
   swnmg_status s = adjoint_alloc(c);
   if (s != SWNMG_OK) return s;

@@ -56,6 +56,9 @@ struct swnmg_batch {
   std::vector<int> h_bstart;
   int2* tickets = nullptr;           // per level, concatenated
   std::vector<int> tick_off, tick_cnt, nslots, max_m, max_n, max_steps;
+  int2* btickets = nullptr;          // BLU-SGS (problem, 2-row strip) tickets, per level, concatenated
+  std::vector<int> btick_off, btick_cnt, nbslots;
+  int* blu_sync = nullptr;           // ticket / abort / progress of the BLU-SGS strips
   int* mask = nullptr;               // [M_COUNT][B]
   int* h_mask = nullptr;             // pinned
   double* sums = nullptr;
@@ -170,11 +173,13 @@ swnmg_status residual_sums(swnmg_batch* b, int l, int slot, std::vector<double>&
   return SWNMG_OK;
 }
 
+// a half-sweep of every problem in mask slot: the strip-pipelined kernel,
+// its grid capped at four warps per tuned BLU-SGS block
 void blusgs(swnmg_batch* b, int l, int slot, int forward) {
   const int ns = steps_of(b, l, slot);
   if (ns == 0) return;
-  launch_b_blusgs_sweep(tab(b, l), mk(b, slot), b->B, ns, forward, b->blusgs_blocks[l], b->bl_sync, b->sticky,
-                        b->st);
+  launch_b_blusgs_strip(tab(b, l), b->btickets + b->btick_off[l], b->btick_cnt[l], b->nbslots[l], mk(b, slot),
+                        b->B, forward, 4 * b->blusgs_blocks[l], b->blu_sync, b->sticky, b->st);
 }
 
 void sgs(swnmg_batch* b, int l, int slot, int forward) {
@@ -271,6 +276,8 @@ void free_batch(swnmg_batch* b) {
   if (b->items) cudaFree(b->items);
   if (b->bstart) cudaFree(b->bstart);
   if (b->tickets) cudaFree(b->tickets);
+  if (b->btickets) cudaFree(b->btickets);
+  if (b->blu_sync) cudaFree(b->blu_sync);
   if (b->mask) cudaFree(b->mask);
   if (b->sums) cudaFree(b->sums);
   if (b->sgs_sync) cudaFree(b->sgs_sync);
@@ -308,7 +315,7 @@ SWNMG_API swnmg_status swnmg_batch_create(const swnmg_problem* probs, const int3
   swnmg_batch* b = new swnmg_batch();
   b->B = B;
   b->prm = *prm;
-  b->fp32 = prm->precision == SWNMG_PREC_MIXED;
+  b->fp32 = prm->precision != SWNMG_PREC_FP64;   // MIXED_STEP1 runs as MIXED in a batch
   b->user_st = (cudaStream_t)stream;
   swnmg_status rc = SWNMG_OK;
   int dev = 0;
@@ -356,11 +363,14 @@ SWNMG_API swnmg_status swnmg_batch_create(const swnmg_problem* probs, const int3
     b->tick_off.assign(MAXL, 0);
     b->tick_cnt.assign(MAXL, 0);
     b->nslots.assign(MAXL, 0);
+    b->btick_off.assign(MAXL, 0);
+    b->btick_cnt.assign(MAXL, 0);
+    b->nbslots.assign(MAXL, 0);
     b->max_m.assign(MAXL, 0);
     b->max_n.assign(MAXL, 0);
-    std::vector<int2> tk;
+    std::vector<int2> tk, btk;
     for (int l = 0; l < MAXL; ++l) {
-      int slot0 = 0, maxs = 0;
+      int slot0 = 0, maxs = 0, bslot0 = 0, bmaxs = 0;
       for (int p = 0; p < B; ++p) {
         BItem& it = b->h_items[(size_t)l * B + p];
         memset(&it, 0, sizeof it);
@@ -389,13 +399,17 @@ SWNMG_API swnmg_status swnmg_batch_create(const swnmg_problem* probs, const int3
         it.n_xe = (v.nx + 1) * v.ny;
         it.n_e = it.n_xe + v.nx * (v.ny + 1);
         it.strip0 = slot0;
+        it.bstrip0 = bslot0;
         it.has = 1;
         const int ns = (v.ny + 31) / 32;
         slot0 += ns;
+        bslot0 += (v.ny + 1) / 2;
+        bmaxs = std::max(bmaxs, (v.ny + 1) / 2);
         maxs = std::max(maxs, ns);
         b->max_n[l] = std::max(b->max_n[l], v.n);
       }
       b->nslots[l] = slot0;
+      b->nbslots[l] = bslot0;
       // block tables
       for (int d = 0; d < ND; ++d) {
         int* bs = &b->h_bstart[((size_t)l * ND + d) * (B + 1)];
@@ -417,12 +431,24 @@ SWNMG_API swnmg_status swnmg_batch_create(const swnmg_problem* probs, const int3
           if (it.has && q < (it.L.ny + 31) / 32) tk.push_back(make_int2(p, q));
         }
       b->tick_cnt[l] = (int)tk.size() - b->tick_off[l];
+      // BLU-SGS strip tickets (2 rows): strip index first, then problem
+      b->btick_off[l] = (int)btk.size();
+      for (int q = 0; q < bmaxs; ++q)
+        for (int p = 0; p < B; ++p) {
+          const BItem& it = b->h_items[(size_t)l * B + p];
+          if (it.has && q < (it.L.ny + 1) / 2) btk.push_back(make_int2(p, q));
+        }
+      b->btick_cnt[l] = (int)btk.size() - b->btick_off[l];
     }
     int maxslots = 0;
     for (int l = 0; l < MAXL; ++l) maxslots = std::max(maxslots, b->nslots[l]);
     BTRY(cudaMalloc((void**)&b->items, sizeof(BItem) * b->h_items.size()));
     BTRY(cudaMalloc((void**)&b->bstart, sizeof(int) * b->h_bstart.size()));
     BTRY(cudaMalloc((void**)&b->tickets, sizeof(int2) * std::max<size_t>(tk.size(), 1)));
+    BTRY(cudaMalloc((void**)&b->btickets, sizeof(int2) * std::max<size_t>(btk.size(), 1)));
+    int maxbslots = 0;
+    for (int l = 0; l < MAXL; ++l) maxbslots = std::max(maxbslots, b->nbslots[l]);
+    BTRY(cudaMalloc((void**)&b->blu_sync, sizeof(int) * (2 + maxbslots + 8)));
     BTRY(cudaMalloc((void**)&b->mask, sizeof(int) * (size_t)M_COUNT * B));
     BTRY(cudaMalloc((void**)&b->sums, sizeof(double) * B));
     BTRY(cudaMalloc((void**)&b->sgs_sync, sizeof(int) * (2 + maxslots + 8)));
@@ -435,6 +461,8 @@ SWNMG_API swnmg_status swnmg_batch_create(const swnmg_problem* probs, const int3
     BTRY(cudaMemcpy(b->bstart, b->h_bstart.data(), sizeof(int) * b->h_bstart.size(), cudaMemcpyHostToDevice));
     if (!tk.empty())
       BTRY(cudaMemcpy(b->tickets, tk.data(), sizeof(int2) * tk.size(), cudaMemcpyHostToDevice));
+    if (!btk.empty())
+      BTRY(cudaMemcpy(b->btickets, btk.data(), sizeof(int2) * btk.size(), cudaMemcpyHostToDevice));
     BTRY(cudaMemset(b->sticky, 0, sizeof(int)));
     memset(b->h_mask, 0, sizeof(int) * (size_t)M_COUNT * B);
     for (int p = 0; p < B; ++p)

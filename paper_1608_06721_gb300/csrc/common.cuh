@@ -44,6 +44,13 @@ struct DevLevel {
   double t_ka, t_omb;
   const double* t_src;
   DevBC bc[4];            // W, E, S, N
+  // structured curvilinear mesh (2D; NULL: the uniform mesh above).  geo per
+  // edge e (x-edges first): |e| at geo[e], the unit normal (from the
+  // lower-index cell to the higher-index one) at geo[n_e + e], geo[2 n_e + e];
+  // area |K_i| per cell; t_kai |K_i|/dt per cell during a time step.
+  const double* geo = nullptr;
+  const double* area = nullptr;
+  const double* t_kai = nullptr;
 };
 
 // LU layout of a block (n = 2 or 3), partial pivoting, guard for singular
@@ -85,6 +92,7 @@ struct BItem {
   int* csing;
   int n_xe, n_e;                // x-edges, all edges
   int strip0;                   // first SGS progress slot of this problem
+  int bstrip0;                  // first BLU-SGS strip progress slot of this problem
   int has;                      // the problem has this level
 };
 
@@ -124,6 +132,11 @@ void launch_residual(const DevLevel& L, const double* z, const double* U, double
 void launch_jacobian(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
                      double* edge_buf, void* blk, int fp32, cudaStream_t st);   // blk skewed
 // gbuf: 4 * max(nx, ny) * (nc + 1) * 3 doubles of ghost scratch
+// FP32 BLU-SGS half-sweep (blusgs32.cu): Step 1 under SWNMG_PREC_MIXED_STEP1
+void launch_blusgs32_strip(const DevLevel& L, const double* z, double* U, float* gbuf, int forward, int* sync,
+                           int* sticky_err, cudaStream_t st);
+void launch_blusgs_strip(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
+                         int* sticky_err, cudaStream_t st);
 void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
                          int* sticky_err, cudaStream_t st);
 // dU strip-skewed (a level-0 multigrid iterate)
@@ -133,6 +146,14 @@ void launch_adjoint_z(const DevLevel& L, const double* z, const double* U, const
                       double* cz, double* dRz, cudaStream_t st);
 void launch_adjoint_q(const DevLevel& L, int side, const double* z, const double* U, const double* lam,
                       double delta, double* out, cudaStream_t st);
+// curvilinear meshes (Examples 3.4, 3.5)
+void launch_average_area(int nxf, int nyf, int ncomp, const double* area_f, const double* vf, double* vc,
+                         cudaStream_t st);
+void launch_time_source_cells(long long m, long long n, const double* kai, double beta, const double* U,
+                              const double* R, double* src, cudaStream_t st);
+void launch_mesh_level(int nx, int ny, int vrow, int step, const double* vx, const double* vy, double* geo,
+                       double* area, int* bad, cudaStream_t st);
+void launch_time_ka(int n, const double* area, double dt, double* kai, cudaStream_t st);
 void launch_average(int dim, int nxf, int nyf, int ncomp, const double* vf, double* vc,
                     cudaStream_t st);
 // t_src = ka U^n - beta R(U^n) over m values (the time step's fixed part)
@@ -151,6 +172,10 @@ void launch_b_average(const BLaunch& coarse, const BItem* fine_items, cudaStream
 void launch_b_inject(const BLaunch& fine, const BItem* coarse_items, cudaStream_t st);
 // one half-sweep over every masked problem's level; nsteps = max diagonals,
 // blocks = cooperative grid size, sync: [0] arrivals, [1] abort (zeroed here)
+// batched strip-pipelined BLU-SGS half-sweep: (problem, strip) tickets in
+// claim order (strip index first), grid warps at most
+void launch_b_blusgs_strip(const BItem* items, const int2* tickets, int ntickets, int nslots, const int* mask,
+                           int B, int forward, int grid, int* sync, int* sticky_err, cudaStream_t st);
 void launch_b_blusgs_sweep(const BItem* items, const int* mask, int B, int nsteps, int forward, int blocks,
                            int* sync, int* sticky_err, cudaStream_t st);
 int b_blusgs_max_blocks_per_sm();

@@ -22,6 +22,8 @@ struct Level {
   int8_t* piv = nullptr;
   void* b = nullptr;        // right-hand side of A x = b
   void* x = nullptr;        // iterate
+  double* geo = nullptr;    // curvilinear mesh: per edge |e|, n^x, n^y (3 x n_e)
+  double* area = nullptr;   // curvilinear mesh: |K_i|
 };
 
 // DevLevel of level l of ctx (api.cu)
@@ -50,7 +52,13 @@ struct swnmg_ctx {
   bool t_on = false;
   double t_ka = 0.0, t_omb = 1.0;
   double* t_src = nullptr;  // |K|/dt U^n - beta R(U^n), nc x n
+  // structured curvilinear mesh (swnmg_set_mesh): finest vertices x then y,
+  // (nx + 1)(ny + 1) each; per-cell |K_i|/dt of a time step
+  bool curv = false;
+  double* mesh = nullptr;
+  double* kai = nullptr;
   int* sgs_sync = nullptr;  // ticket / abort / per-strip progress of the wavefront sweeps
+  int* blu_sync = nullptr;  // ticket / abort / per-strip progress of the BLU-SGS strip sweep
   int* sticky = nullptr;    // set by a device wait that ran out of its bound
   double* hbuf = nullptr;   // pinned host scalars
   bool coarse_exact = false;

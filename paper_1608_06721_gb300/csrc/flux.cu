@@ -204,28 +204,87 @@ __device__ __forceinline__ void edge_G(const double o[5], int axis, double GL[NC
   }
 }
 
+// ---- structured curvilinear meshes (Examples 3.4, 3.5) ----------------------
+// The edge frame is (n, tau): n from L.geo, tau = n turned by +90 degrees on
+// x-edges and by -90 degrees on y-edges, so that on a uniform mesh it is the
+// frame above (tau-velocity v on x-edges, u on y-edges; a boundary's q is
+// along n, its u_tau along tau).  States go to the frame as u_n = u n^x +
+// v n^y, u_tau = u tau^x + v tau^y; the flux comes back as F_1 n + F_2 tau,
+// and the source term g/2 h_{e,-}^2 (n^x, n^y) is subtracted there.
+struct Frame { double nx, ny, tx, ty; };
+
+__device__ __forceinline__ long long level_edges(const DevLevel& L) {
+  return (long long)(L.nx + 1) * L.ny + (L.dim == 2 ? (long long)L.nx * (L.ny + 1) : 0);
+}
+
+__device__ __forceinline__ Frame edge_frame(const DevLevel& L, long long e, int axis) {
+  const long long ne = level_edges(L);
+  Frame f;
+  f.nx = L.geo[ne + e];
+  f.ny = L.geo[2 * ne + e];
+  if (axis == 0) { f.tx = -f.ny; f.ty = f.nx; }
+  else { f.tx = f.ny; f.ty = -f.nx; }
+  return f;
+}
+
+// global primitive (h, u, v) -> (h, u_n, u_tau)
+__device__ __forceinline__ Prim to_frame(Prim g, const Frame& f) {
+  Prim p;
+  p.h = g.h;
+  p.u = g.u * f.nx + g.v * f.ny;
+  p.v = g.u * f.tx + g.v * f.ty;
+  return p;
+}
+
+// G of the left and right cell in global components on a curvilinear mesh
+__device__ __forceinline__ void edge_G_frame(const double o[5], const Frame& f, double GL[3], double GR[3]) {
+  const double fx = o[1] * f.nx + o[2] * f.tx, fy = o[1] * f.ny + o[2] * f.ty;
+  GL[0] = o[0];
+  GL[1] = fx - o[3] * f.nx;
+  GL[2] = fy - o[3] * f.ny;
+  GR[0] = -o[0];
+  GR[1] = -(fx - o[4] * f.nx);
+  GR[2] = -(fy - o[4] * f.ny);
+}
+
+// a cell's primitive state in the edge's frame (fr: curvilinear, else the axis frame)
+template <int NC>
+__device__ __forceinline__ Prim prim_edge(const DevLevel& L, const double* c, int axis, const Frame* fr) {
+  if constexpr (NC == 3) {
+    if (fr) return to_frame(to_prim(c[0], c[1], c[2], L.h_eps), *fr);
+  }
+  return prim_axis<NC>(L, c, axis);
+}
+
 // One edge with conserved states cL / cR (NULL = boundary, ghost computed
-// from the other side); returns G of both cells.
+// from the other side); returns G of both cells.  fr: the edge's frame on a
+// curvilinear mesh, NULL on the uniform one.
 template <int NC>
 __device__ __forceinline__ void eval_edge_states(const DevLevel& L, int axis, const double* cL,
                                                  double zL, const double* cR, double zR,
-                                                 double GL[NC], double GR[NC]) {
+                                                 double GL[NC], double GR[NC], const Frame* fr = nullptr) {
   Prim a, b;
   double za = zL, zb = zR;
   if (cL && cR) {
-    a = prim_axis<NC>(L, cL, axis);
-    b = prim_axis<NC>(L, cR, axis);
+    a = prim_edge<NC>(L, cL, axis, fr);
+    b = prim_edge<NC>(L, cR, axis, fr);
   } else if (cR) {
-    b = prim_axis<NC>(L, cR, axis);
+    b = prim_edge<NC>(L, cR, axis, fr);
     a = ghost_state(L, 2 * axis, b);
     za = zR;
   } else {
-    a = prim_axis<NC>(L, cL, axis);
+    a = prim_edge<NC>(L, cL, axis, fr);
     b = ghost_state(L, 2 * axis + 1, a);
     zb = zL;
   }
   double o[5];
   edge_eval(L, a, za, b, zb, o);
+  if constexpr (NC == 3) {
+    if (fr) {
+      edge_G_frame(o, *fr, GL, GR);
+      return;
+    }
+  }
   edge_G<NC>(o, axis, GL, GR);
 }
 
@@ -237,14 +296,26 @@ __device__ __forceinline__ void edge_cells(const DevLevel& L, int e, int n_xe, i
     axis = 0;
     iL = ie > 0 ? (ie - 1) + L.nx * iy : -1;
     iR = ie < L.nx ? ie + L.nx * iy : -1;
-    len = L.ex;
+    len = L.geo ? L.geo[e] : L.ex;
   } else {
     const int f = e - n_xe, ix = f % L.nx, je = f / L.nx;
     axis = 1;
     iL = je > 0 ? ix + L.nx * (je - 1) : -1;
     iR = je < L.ny ? ix + L.nx * je : -1;
-    len = L.ey;
+    len = L.geo ? L.geo[e] : L.ey;
   }
+}
+
+// the frame of edge e on a curvilinear mesh (fr filled, returned), else NULL
+template <int NC>
+__device__ __forceinline__ const Frame* frame_of(const DevLevel& L, int e, int axis, Frame& fr) {
+  if constexpr (NC == 3) {
+    if (L.geo) {
+      fr = edge_frame(L, e, axis);
+      return &fr;
+    }
+  }
+  return nullptr;
 }
 
 template <int NC>
@@ -269,8 +340,10 @@ __device__ __forceinline__ void res_edge(const DevLevel& L, const double* __rest
   double cL[NC], cR[NC], GL[NC], GR[NC];
   if (iL >= 0) load_c<NC>(U, L.n, iL, cL);
   if (iR >= 0) load_c<NC>(U, L.n, iR, cR);
+  Frame fr;
+  const Frame* pf = frame_of<NC>(L, e, axis, fr);
   eval_edge_states<NC>(L, axis, iL >= 0 ? cL : nullptr, iL >= 0 ? z[iL] : 0.0,
-                       iR >= 0 ? cR : nullptr, iR >= 0 ? z[iR] : 0.0, GL, GR);
+                       iR >= 0 ? cR : nullptr, iR >= 0 ? z[iR] : 0.0, GL, GR, pf);
   for (int s = 0; s < NC; ++s) {
     eb[s * (long long)n_e + e] = GL[s];
     eb[(NC + s) * (long long)n_e + e] = GR[s];
@@ -302,12 +375,20 @@ __device__ __forceinline__ double time_scale(const DevLevel& L, double v) {
   return L.t_ka > 0.0 ? L.t_omb * v : v;
 }
 
+// |K_i|/dt of a time step: one value on the uniform mesh, per cell on a curvilinear one
+__device__ __forceinline__ double tka(const DevLevel& L, long long i) { return L.t_kai ? L.t_kai[i] : L.t_ka; }
+
+// |e| of a cell's W/E (x) or S/N (y) edge e
+__device__ __forceinline__ double elen(const DevLevel& L, int e, int axis) {
+  return L.geo ? L.geo[e] : (axis == 0 ? L.ex : L.ey);
+}
+
 // Remark 2.6: the time-step residual of cell i from its flux sum r
 template <int NC>
 __device__ __forceinline__ void time_residual(const DevLevel& L, const double* __restrict__ U, int i,
                                               double r[NC]) {
   const long long n = L.n;
-  for (int s = 0; s < NC; ++s) r[s] = (L.t_omb * r[s] + L.t_ka * U[s * n + i]) - L.t_src[s * n + i];
+  for (int s = 0; s < NC; ++s) r[s] = (L.t_omb * r[s] + tka(L, i) * U[s * n + i]) - L.t_src[s * n + i];
 }
 
 template <int NC>
@@ -316,14 +397,16 @@ __device__ __forceinline__ void res_cell(const DevLevel& L, const double* __rest
                                          double* __restrict__ rn, int n_xe, int n_e, int i) {
   int eW, eE, eS, eN;
   cell_edges(L, i, n_xe, eW, eE, eS, eN);
+  const double lW = elen(L, eW, 0), lE = elen(L, eE, 0);
+  const double lS = L.dim == 2 ? elen(L, eS, 1) : 0.0, lN = L.dim == 2 ? elen(L, eN, 1) : 0.0;
   double r[NC];
   for (int s = 0; s < NC; ++s) {
     double a = 0.0;
-    a = a + L.ex * eb[(NC + s) * (long long)n_e + eW];
-    a = a + L.ex * eb[s * (long long)n_e + eE];
+    a = a + lW * eb[(NC + s) * (long long)n_e + eW];
+    a = a + lE * eb[s * (long long)n_e + eE];
     if (L.dim == 2) {
-      a = a + L.ey * eb[(NC + s) * (long long)n_e + eS];
-      a = a + L.ey * eb[s * (long long)n_e + eN];
+      a = a + lS * eb[(NC + s) * (long long)n_e + eS];
+      a = a + lN * eb[s * (long long)n_e + eN];
     }
     r[s] = a;
   }
@@ -365,7 +448,9 @@ __device__ __forceinline__ void jac_edge(const DevLevel& L, const double* __rest
   const double zL = iL >= 0 ? z[iL] : 0.0, zR = iR >= 0 ? z[iR] : 0.0;
   const double* pL = iL >= 0 ? cL : nullptr;
   const double* pR = iR >= 0 ? cR : nullptr;
-  eval_edge_states<NC>(L, axis, pL, zL, pR, zR, GLb, GRb);
+  Frame fr;
+  const Frame* pf = frame_of<NC>(L, e, axis, fr);
+  eval_edge_states<NC>(L, axis, pL, zL, pR, zR, GLb, GRb, pf);
   for (int s = 0; s < NC; ++s) {
     eb[s * ne + e] = GLb[s];
     eb[(NC + s) * ne + e] = GRb[s];
@@ -379,7 +464,7 @@ __device__ __forceinline__ void jac_edge(const DevLevel& L, const double* __rest
       double c[NC];
       for (int s = 0; s < NC; ++s) c[s] = cL[s];
       c[k] = c[k] + L.eps;
-      eval_edge_states<NC>(L, axis, c, zL, pR, zR, GL, GR);
+      eval_edge_states<NC>(L, axis, c, zL, pR, zR, GL, GR, pf);
       for (int s = 0; s < NC; ++s) {
         eb[(f_dLL + s * NC + k) * ne + e] = len * ((GL[s] - GLb[s]) * L.reps);
         if (iR >= 0) st<T>(blk, ((long long)(bR * NC * NC + s * NC + k)) * P + sR,
@@ -398,7 +483,7 @@ __device__ __forceinline__ void jac_edge(const DevLevel& L, const double* __rest
       double c[NC];
       for (int s = 0; s < NC; ++s) c[s] = cR[s];
       c[k] = c[k] + L.eps;
-      eval_edge_states<NC>(L, axis, pL, zL, c, zR, GL, GR);
+      eval_edge_states<NC>(L, axis, pL, zL, c, zR, GL, GR, pf);
       for (int s = 0; s < NC; ++s) {
         eb[(f_dRR + s * NC + k) * ne + e] = len * ((GR[s] - GRb[s]) * L.reps);
         if (iL >= 0) st<T>(blk, ((long long)(bL * NC * NC + s * NC + k)) * P + sL,
@@ -431,14 +516,16 @@ __device__ __forceinline__ void jac_cell(const DevLevel& L, const double* __rest
   cell_edges(L, i, n_xe, eW, eE, eS, eN);
   const long long ne = n_e, n = L.n, P = skew_slots(L.nx, L.ny);
   const long long si = skew_pos(i % L.nx, i / L.nx, L.nx);
+  const double lW = elen(L, eW, 0), lE = elen(L, eE, 0);
+  const double lS = L.dim == 2 ? elen(L, eS, 1) : 0.0, lN = L.dim == 2 ? elen(L, eN, 1) : 0.0;
   double r[NC];
   for (int s = 0; s < NC; ++s) {
     double a = 0.0;
-    a = a + L.ex * eb[(NC + s) * ne + eW];
-    a = a + L.ex * eb[s * ne + eE];
+    a = a + lW * eb[(NC + s) * ne + eW];
+    a = a + lE * eb[s * ne + eE];
     if (L.dim == 2) {
-      a = a + L.ey * eb[(NC + s) * ne + eS];
-      a = a + L.ey * eb[s * ne + eN];
+      a = a + lS * eb[(NC + s) * ne + eS];
+      a = a + lN * eb[s * ne + eN];
     }
     r[s] = a;
   }
@@ -462,7 +549,7 @@ __device__ __forceinline__ void jac_cell(const DevLevel& L, const double* __rest
       }
       if (tm) {
         d = L.t_omb * d;
-        if (s == k) d = d + L.t_ka;
+        if (s == k) d = d + tka(L, i);
       }
       if (s == k) d = d + am;
       st<T>(blk, (long long)f * P + si, d);
@@ -571,7 +658,23 @@ __device__ __forceinline__ double ldU(const double* p) { return L2 ? __ldcg(p) :
 // eps to component k); rinv = 1/h of the unperturbed cell (0 when dry).
 // 1/h is recomputed only when the depth is the perturbed component.
 template <int NC>
-__device__ __forceinline__ Prim pert_prim(const DevLevel& L, const double c[NC], int p, double rinv, int axis) {
+__device__ __forceinline__ Prim pert_prim(const DevLevel& L, const double c[NC], int p, double rinv, int axis,
+                                          const Frame* fr = nullptr) {
+  if constexpr (NC == 3) {
+    if (fr) {   // curvilinear: global velocities, then the edge frame
+      Prim gl;
+      gl.h = c[0];
+      if (c[0] >= L.h_eps) {
+        const double r = (p == 1) ? 1.0 / c[0] : rinv;
+        gl.u = c[1] * r;
+        gl.v = c[2] * r;
+      } else {
+        gl.u = 0.0;
+        gl.v = 0.0;
+      }
+      return to_frame(gl, *fr);
+    }
+  }
   Prim me;
   me.h = c[0];
   const double qa = (NC == 2) ? c[1] : (axis == 0 ? c[1] : c[NC - 1]);
@@ -585,6 +688,17 @@ __device__ __forceinline__ Prim pert_prim(const DevLevel& L, const double c[NC],
     me.v = 0.0;
   }
   return me;
+}
+
+// edge of side sd (0 W, 1 E, 2 S, 3 N) of cell (ix, iy), in edge_cells' numbering
+__device__ __forceinline__ int side_edge(const DevLevel& L, int ix, int iy, int sd) {
+  const int n_xe = (L.nx + 1) * L.ny;
+  switch (sd) {
+    case 0: return ix + (L.nx + 1) * iy;
+    case 1: return ix + 1 + (L.nx + 1) * iy;
+    case 2: return n_xe + ix + L.nx * iy;
+    default: return n_xe + ix + L.nx * (iy + 1);
+  }
 }
 
 // Ghost states of every boundary cell of a level for the base state and each
@@ -610,7 +724,9 @@ __device__ __forceinline__ void ghost_prologue(const DevLevel& L, const double* 
     for (int s = 0; s < NC; ++s) c[s] = __ldcg(&U[s * n + i]);
     const double rinv = c[0] >= L.h_eps ? 1.0 / c[0] : 0.0;
     if (p > 0) c[p - 1] = c[p - 1] + L.eps;
-    const Prim gh = ghost_state(L, sd, pert_prim<NC>(L, c, p, rinv, sd >> 1));
+    Frame fr;
+    const Frame* pf = frame_of<NC>(L, side_edge(L, ix, iy, sd), sd >> 1, fr);
+    const Prim gh = ghost_state(L, sd, pert_prim<NC>(L, c, p, rinv, sd >> 1, pf));
     gbuf[(long long)t * 3 + 0] = gh.h;
     gbuf[(long long)t * 3 + 1] = gh.u;
     gbuf[(long long)t * 3 + 2] = gh.v;
@@ -646,6 +762,9 @@ __device__ __forceinline__ void blusgs_group(const DevLevel& L, const double* __
   double ci[NC];
   for (int s = 0; s < NC; ++s) ci[s] = act ? ldU<L2>(&U[s * n + i]) : 0.0;
   const double zi = act ? z[i] : 0.0, zj = (j >= 0) ? z[j] : zi;
+  const int eidx = L.dim == 2 ? side_edge(L, ix, iy, sd) : 0;   // a valid edge on every lane
+  Frame fr;
+  const Frame* pf = frame_of<NC>(L, eidx, axis, fr);
   // base lane: 1/h_i and the neighbour's primitive state
   double rinv = 0.0;
   Prim nb{0.0, 0.0, 0.0};
@@ -654,7 +773,7 @@ __device__ __forceinline__ void blusgs_group(const DevLevel& L, const double* __
     if (j >= 0) {
       double cj[NC];
       for (int s = 0; s < NC; ++s) cj[s] = ldU<L2>(&U[s * n + j]);
-      nb = prim_axis<NC>(L, cj, axis);
+      nb = prim_edge<NC>(L, cj, axis, pf);
     }
   }
   const int src0 = gbase + sd * NP;          // the side's p = 0 lane
@@ -668,7 +787,7 @@ __device__ __forceinline__ void blusgs_group(const DevLevel& L, const double* __
     double c[NC];
     for (int s = 0; s < NC; ++s) c[s] = ci[s];
     if (p > 0) c[p - 1] = c[p - 1] + L.eps;
-    const Prim me = pert_prim<NC>(L, c, p, rinv, axis);
+    const Prim me = pert_prim<NC>(L, c, p, rinv, axis, pf);
     Prim other = nb;
     if (j < 0) {
       if (gbuf) {   // precomputed by ghost_prologue
@@ -686,32 +805,53 @@ __device__ __forceinline__ void blusgs_group(const DevLevel& L, const double* __
     const double za = upper ? zi : zo, zb = upper ? zo : zi;
     double o[5], GL[NC], GR[NC];
     edge_eval(L, a, za, b, zb, o);
-    edge_G<NC>(o, axis, GL, GR);
+    bool done = false;
+    if constexpr (NC == 3) {
+      if (pf) {
+        edge_G_frame(o, *pf, GL, GR);
+        done = true;
+      }
+    }
+    if (!done) edge_G<NC>(o, axis, GL, GR);
     for (int s = 0; s < NC; ++s) G[s] = upper ? GL[s] : GR[s];
   }
   // p = 0 lanes hold |e| G; p = k+1 lanes column k of |e| dG/dU_i
-  const double len = axis == 0 ? L.ex : L.ey;
+  const double len = L.dim == 2 ? elen(L, eidx, axis) : L.ex;
   double v[NC];
   for (int s = 0; s < NC; ++s) {
     const double gb = __shfl_sync(full, G[s], src0);
     v[s] = (p == 0) ? len * G[s] : len * ((G[s] - gb) * L.reps);
   }
-  // gather on the group's first lane in side order
+  // Sum over the sides, lane-parallel: lane g < NC*NP of the group owns
+  // entry (s, pp) = (g / NP, g % NP) and adds the sides' values in the order
+  // W, E, S, N (the same additions, in the same order, as one lane summing
+  // every entry), then the group's first lane collects the NC*NP sums.
+  const int es = g / NP < NC ? g / NP : 0, ep = g % NP;
+  double acc = 0.0;
+  for (int q = 0; q < NS; ++q) {
+    double w = 0.0;
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      const double t = __shfl_sync(full, v[s], gbase + q * NP + ep);
+      if (s == es) w = t;
+    }
+    acc = acc + w;
+  }
   double Rs[NC], D[NC * NC];
-  for (int s = 0; s < NC; ++s) Rs[s] = 0.0;
-  for (int e = 0; e < NC * NC; ++e) D[e] = 0.0;
-  for (int q = 0; q < NS; ++q)
-    for (int pp = 0; pp < NP; ++pp)
-      for (int s = 0; s < NC; ++s) {
-        const double w = __shfl_sync(full, v[s], gbase + q * NP + pp);
-        if (pp == 0) Rs[s] = Rs[s] + w;
-        else D[s * NC + (pp - 1)] = D[s * NC + (pp - 1)] + w;
-      }
+#pragma unroll
+  for (int s = 0; s < NC; ++s)
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) {
+      const double t = __shfl_sync(full, acc, gbase + s * NP + pp);
+      if (pp == 0) Rs[s] = t;
+      else D[s * NC + (pp - 1)] = t;
+    }
   if (!cell_ok || g != 0) return;
   if (L.t_ka > 0.0) {   // time step (Remark 2.6): the step's residual and diagonal block
-    for (int s = 0; s < NC; ++s) Rs[s] = (L.t_omb * Rs[s] + L.t_ka * ci[s]) - L.t_src[s * n + i];
+    const double ka = tka(L, i);
+    for (int s = 0; s < NC; ++s) Rs[s] = (L.t_omb * Rs[s] + ka * ci[s]) - L.t_src[s * n + i];
     for (int e = 0; e < NC * NC; ++e) D[e] = L.t_omb * D[e];
-    for (int s = 0; s < NC; ++s) D[s * NC + s] = D[s * NC + s] + L.t_ka;
+    for (int s = 0; s < NC; ++s) D[s * NC + s] = D[s * NC + s] + ka;
   }
   double m = fabs(Rs[0]) + fabs(Rs[1]);
   if (NC == 3) m = m + fabs(Rs[NC - 1]);
@@ -788,6 +928,96 @@ __global__ void __launch_bounds__(128) k_blusgs_sweep(DevLevel L, const double* 
       blusgs_group<NC, NS, GRP, true>(L, z, U, gbuf, d, ix0, ncell, c0 + (threadIdx.x & 31) / GRP,
                                       (threadIdx.x & 31) % GRP);
     if (!grid_barrier(sync, q + 1, sticky_err, spin_limit)) return;
+  }
+}
+
+// ---- BLU-SGS: strip-pipelined half-sweep ------------------------------------
+// The same cell updates as k_blusgs_sweep, ordered by point-to-point waits
+// instead of a grid barrier per anti-diagonal.  Strip q holds R = 32 / GRP
+// consecutive rows, counted from the sweep's first row (the bottom row
+// forward, the top row backward), and columns are counted from the sweep's
+// first column.  At step t the strip's warp updates row r at column t - r,
+// so the cells of a step lie on one anti-diagonal.  A cell's neighbours
+// before it in the sweep order are then new values: inside the strip they
+// were updated at step t - 1 by this warp, and the first row's neighbour is
+// in the last row of strip q - 1, which this strip waits for (bounded) until
+// that row has passed column t.  Its neighbours after it in the sweep order
+// are still old values: they are updated later by this warp, or by strip
+// q + 1, which waits for this strip's last row.  The lane that wrote the
+// last row's cell publishes the progress with a release store after it (in
+// a forward step that cell is cell 0, in a backward step the last cell).
+// Strips are claimed in order through an atomic ticket, so a strip only
+// waits for one that a running warp owns.  The ghosts come from
+// k_ghost_prologue, launched before.
+// sync: [0] ticket, [1] abort, [2 + q] columns completed by strip q's last row.
+__device__ __forceinline__ void st_rel(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int NC, int NS>
+__global__ void __launch_bounds__(128) k_ghost_prologue(DevLevel L, const double* __restrict__ U,
+                                                        double* gbuf) {
+  ghost_prologue<NC, NS>(L, U, gbuf, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+template <int NC, int NS, int GRP>
+__global__ void __launch_bounds__(32) k_blusgs_strip(DevLevel L, const double* __restrict__ z, double* U,
+                                                     const double* gbuf, int forward, int* sync,
+                                                     int* sticky_err, int spin_limit) {
+  constexpr int R = 32 / GRP;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int nstrips = (L.ny + R - 1) / R;
+  int* prog = sync + 2;
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(&sync[0], 1);
+    q = __shfl_sync(full, q, 0);
+    if (q >= nstrips) return;
+    const int rows = (L.ny - q * R < R) ? L.ny - q * R : R;
+    const int nsteps = L.nx + rows - 1;
+    int known = 0;
+    for (int t = 0; t < nsteps; ++t) {
+      if (q > 0 && t < L.nx && known < t + 1) {   // the previous strip's last row at column t
+        int pg = 0, it = 0;
+        do {
+          if (lane == 0) {
+            pg = ld_acq(&prog[q - 1]);
+            if (pg < t + 1 && ld_acq(&sync[1])) pg = -1;
+          }
+          pg = __shfl_sync(full, pg, 0);
+          if (pg >= t + 1 || pg < 0) break;
+          __nanosleep(32);
+        } while (++it < spin_limit);
+        if (pg < t + 1) {
+          if (lane == 0) {
+            if (pg >= 0) atomicOr(sticky_err, 1);
+            atomicExch(&sync[1], 1);
+          }
+          return;
+        }
+        known = pg;
+      }
+      __syncwarp();   // lane 0's acquire before the other lanes' loads of that row
+      const int c_lo = t - rows + 1 > 0 ? t - rows + 1 : 0;
+      const int c_hi = t < L.nx - 1 ? t : L.nx - 1;
+      const int ncell = c_hi - c_lo + 1;
+      int d, ix0;
+      if (forward) {   // ix = c, iy = qR + (t - c)
+        d = q * R + t;
+        ix0 = c_lo;
+      } else {         // ix = nx-1-c, iy = ny-1-qR-(t - c)
+        d = (L.nx - 1) + (L.ny - 1) - (q * R + t);
+        ix0 = L.nx - 1 - c_hi;
+      }
+      blusgs_group<NC, NS, GRP, true>(L, z, U, gbuf, d, ix0, ncell, lane / GRP, lane % GRP);
+      __syncwarp();
+      const int done = t - rows + 2;                  // columns completed by the last row
+      if (q + 1 < nstrips && done >= 1 && done <= L.nx) {
+        const int rel = forward ? 0 : (ncell - 1) * GRP;
+        if (lane == rel) st_rel(&prog[q], done);
+      }
+    }
   }
 }
 
@@ -939,6 +1169,102 @@ __global__ void k_average(int dim, int nxf, int nyf, int ncomp, const double* __
   const int nc_cells = (nxf / 2) * (dim == 2 ? nyf / 2 : 1);
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I < nc_cells) average_cell(dim, nxf, nyf, ncomp, vf, vc, I);
+}
+
+// curvilinear mesh: the children weighted by their areas (the cell average
+// over their union), sum_q |K_q| v_q / sum_q |K_q|, children in the order 00,
+// 10, 01, 11
+__global__ void k_average_area(int nxf, int nyf, int ncomp, const double* __restrict__ area_f,
+                               const double* __restrict__ vf, double* __restrict__ vc) {
+  const int nxc = nxf / 2, nc_cells = nxc * (nyf / 2);
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc_cells) return;
+  const long long nf = (long long)nxf * nyf;
+  const int f = 2 * (I % nxc) + nxf * 2 * (I / nxc);
+  const int ch[4] = {f, f + 1, f + nxf, f + nxf + 1};
+  double ar[4], tot = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    ar[q] = area_f[ch[q]];
+    tot = tot + ar[q];
+  }
+  for (int s = 0; s < ncomp; ++s) {
+    double a = 0.0;
+    for (int q = 0; q < 4; ++q) a = a + ar[q] * vf[s * nf + ch[q]];
+    vc[(long long)s * nc_cells + I] = a / tot;
+  }
+}
+
+// time step on a curvilinear mesh: t_src = |K_i|/dt U^n - beta R(U^n), per cell
+__global__ void k_time_source_cells(long long m, long long n, const double* __restrict__ kai, double beta,
+                                    const double* __restrict__ U, const double* __restrict__ R,
+                                    double* __restrict__ src) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e < m) src[e] = kai[e % n] * U[e] - beta * R[e];
+}
+
+// ---- curvilinear mesh geometry --------------------------------------------------
+// Level l of a mesh with vertex (a, b) at (vx, vy)[a + vrow b] is the mesh of
+// every step-th vertex, step = 2^l.  Edge e (x-edges first, edge_cells'
+// numbering) runs from vertex (a, b) to (a, b + 1) (x-edges) or to (a + 1, b)
+// (y-edges); with t their difference, |e| = sqrt(t.t) and n is t turned by
+// -90 degrees (x-edges) or +90 degrees (y-edges), divided by |e|.  |K_i| is
+// half the cross product of the quadrilateral's diagonals.  A degenerate edge
+// or a cell of non-positive area sets *bad.
+__device__ __forceinline__ void mesh_vertex(const double* vx, const double* vy, int vrow, int step, int a, int b,
+                                            double& x, double& y) {
+  const long long k = (long long)a * step + (long long)vrow * ((long long)b * step);
+  x = vx[k];
+  y = vy[k];
+}
+
+__global__ void k_edge_geometry(int nx, int ny, int vrow, int step, const double* __restrict__ vx,
+                                const double* __restrict__ vy, double* __restrict__ geo, int* bad) {
+  const long long n_xe = (long long)(nx + 1) * ny, ne = n_xe + (long long)nx * (ny + 1);
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const bool xe = e < n_xe;
+  int a0, b0, a1, b1;
+  if (xe) {
+    a0 = (int)(e % (nx + 1));
+    b0 = (int)(e / (nx + 1));
+    a1 = a0;
+    b1 = b0 + 1;
+  } else {
+    const long long f = e - n_xe;
+    a0 = (int)(f % nx);
+    b0 = (int)(f / nx);
+    a1 = a0 + 1;
+    b1 = b0;
+  }
+  double xa, ya, xb, yb;
+  mesh_vertex(vx, vy, vrow, step, a0, b0, xa, ya);
+  mesh_vertex(vx, vy, vrow, step, a1, b1, xb, yb);
+  const double tx = xb - xa, ty = yb - ya;
+  const double l = sqrt(tx * tx + ty * ty);
+  geo[e] = l;
+  geo[ne + e] = xe ? ty / l : -ty / l;
+  geo[2 * ne + e] = xe ? -tx / l : tx / l;
+  if (!(l > 0.0)) atomicOr(bad, 1);
+}
+
+__global__ void k_cell_area(int nx, int ny, int vrow, int step, const double* __restrict__ vx,
+                            const double* __restrict__ vy, double* __restrict__ area, int* bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx * ny) return;
+  const int ix = i % nx, iy = i / nx;
+  double x00, y00, x10, y10, x11, y11, x01, y01;
+  mesh_vertex(vx, vy, vrow, step, ix, iy, x00, y00);
+  mesh_vertex(vx, vy, vrow, step, ix + 1, iy, x10, y10);
+  mesh_vertex(vx, vy, vrow, step, ix + 1, iy + 1, x11, y11);
+  mesh_vertex(vx, vy, vrow, step, ix, iy + 1, x01, y01);
+  const double a = 0.5 * ((x11 - x00) * (y01 - y10) - (x01 - x10) * (y11 - y00));
+  area[i] = a;
+  if (!(a > 0.0)) atomicOr(bad, 1);
+}
+
+__global__ void k_time_ka(int n, const double* __restrict__ area, double dt, double* __restrict__ kai) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) kai[i] = area[i] / dt;
 }
 
 // piecewise-constant injection of a coarse solution (Algorithm 1, Step 1)
@@ -1155,6 +1481,35 @@ void launch_jacobian(const DevLevel& L, const double* z, const double* U, double
   }
 }
 
+// strip-pipelined half-sweep: ghosts, then one warp per strip in flight;
+// sync holds 2 + ceil(ny / R) ints, R = 2 (2D) or 4 (1D) rows per strip
+void launch_blusgs_strip(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
+                         int* sticky_err, cudaStream_t st) {
+  count_launches(2);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int R = L.nc == 3 ? 2 : 4;
+  const int nstrips = (L.ny + R - 1) / R;
+  cudaMemsetAsync(sync, 0, (2 + nstrips) * sizeof(int), st);
+  const int glen = L.nx > L.ny ? L.nx : L.ny;
+  const int gthreads = 4 * glen * (L.nc + 1);
+  const int gblocks = (gthreads + 127) / 128;
+  // at most 16 warps per SM: more strips than that queue on the ticket
+  const int grid = nstrips < 16 * nsm ? nstrips : 16 * nsm;
+  const int spin = 1 << 22;
+  if (L.nc == 3) {
+    k_ghost_prologue<3, 4><<<gblocks, 128, 0, st>>>(L, U, gbuf);
+    k_blusgs_strip<3, 4, 16><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
+  } else {
+    k_ghost_prologue<2, 2><<<gblocks, 128, 0, st>>>(L, U, gbuf);
+    k_blusgs_strip<2, 2, 8><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
+  }
+}
+
 void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
                          int* sticky_err, cudaStream_t st) {
   count_launches(1);
@@ -1214,6 +1569,32 @@ void launch_time_source(long long m, double ka, double beta, const double* U, co
   k_time_source<<<nblk(m, 256), 256, 0, st>>>(m, ka, beta, U, R, src);
 }
 
+void launch_average_area(int nxf, int nyf, int ncomp, const double* area_f, const double* vf, double* vc,
+                         cudaStream_t st) {
+  count_launches(1);
+  const int ncells = (nxf / 2) * (nyf / 2);
+  k_average_area<<<nblk(ncells, 256), 256, 0, st>>>(nxf, nyf, ncomp, area_f, vf, vc);
+}
+
+void launch_time_source_cells(long long m, long long n, const double* kai, double beta, const double* U,
+                              const double* R, double* src, cudaStream_t st) {
+  count_launches(1);
+  k_time_source_cells<<<nblk(m, 256), 256, 0, st>>>(m, n, kai, beta, U, R, src);
+}
+
+void launch_mesh_level(int nx, int ny, int vrow, int step, const double* vx, const double* vy, double* geo,
+                       double* area, int* bad, cudaStream_t st) {
+  count_launches(2);
+  const long long ne = (long long)(nx + 1) * ny + (long long)nx * (ny + 1);
+  k_edge_geometry<<<nblk(ne, 256), 256, 0, st>>>(nx, ny, vrow, step, vx, vy, geo, bad);
+  k_cell_area<<<nblk((long long)nx * ny, 256), 256, 0, st>>>(nx, ny, vrow, step, vx, vy, area, bad);
+}
+
+void launch_time_ka(int n, const double* area, double dt, double* kai, cudaStream_t st) {
+  count_launches(1);
+  k_time_ka<<<nblk(n, 256), 256, 0, st>>>(n, area, dt, kai);
+}
+
 void launch_average(int dim, int nxf, int nyf, int ncomp, const double* vf, double* vc,
                     cudaStream_t st) {
   count_launches(1);
@@ -1262,6 +1643,104 @@ void launch_b_average(const BLaunch& coarse, const BItem* fine_items, cudaStream
 void launch_b_inject(const BLaunch& fine, const BItem* coarse_items, cudaStream_t st) {
   count_launches(1);
   if (fine.nblocks > 0) kb_inject<<<fine.nblocks, 128, 0, st>>>(fine, coarse_items);
+}
+
+// Batched strip-pipelined BLU-SGS: the schedule of k_blusgs_strip, one
+// (problem, strip) ticket at a time; problems outside the mask are skipped
+// whole.  Tickets list strip 0 of every problem first, then strip 1, ..., so
+// a strip only waits for one that a running warp owns.  sync: [0] ticket,
+// [1] abort, [2 + bstrip0(p) + q] columns completed by strip q's last row.
+template <int NC, int NS>
+__global__ void __launch_bounds__(128) kb_ghost_prologue(const BItem* __restrict__ items,
+                                                         const int* __restrict__ mask, int B) {
+  for (int p = 0; p < B; ++p)
+    if (mask[p])
+      ghost_prologue<NC, NS>(items[p].L, items[p].U, items[p].ghost, blockIdx.x * blockDim.x + threadIdx.x,
+                             gridDim.x * blockDim.x);
+}
+
+template <int NC, int NS, int GRP>
+__global__ void __launch_bounds__(32) kb_blusgs_strip(const BItem* __restrict__ items,
+                                                      const int2* __restrict__ tickets, int ntickets,
+                                                      const int* __restrict__ mask, int forward, int* sync,
+                                                      int* sticky_err, int spin_limit) {
+  constexpr int R = 32 / GRP;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int tid = 0;
+    if (lane == 0) tid = atomicAdd(&sync[0], 1);
+    tid = __shfl_sync(full, tid, 0);
+    if (tid >= ntickets) return;
+    const int2 tk = tickets[tid];
+    const int p = tk.x, q = tk.y;
+    if (!mask[p]) continue;
+    const BItem& it = items[p];
+    const DevLevel L = it.L;
+    const int nstrips = (L.ny + R - 1) / R;
+    int* prog = sync + 2 + it.bstrip0;
+    const int rows = (L.ny - q * R < R) ? L.ny - q * R : R;
+    const int nsteps = L.nx + rows - 1;
+    int known = 0;
+    for (int t = 0; t < nsteps; ++t) {
+      if (q > 0 && t < L.nx && known < t + 1) {
+        int pg = 0, n_it = 0;
+        do {
+          if (lane == 0) {
+            pg = ld_acq(&prog[q - 1]);
+            if (pg < t + 1 && ld_acq(&sync[1])) pg = -1;
+          }
+          pg = __shfl_sync(full, pg, 0);
+          if (pg >= t + 1 || pg < 0) break;
+          __nanosleep(32);
+        } while (++n_it < spin_limit);
+        if (pg < t + 1) {
+          if (lane == 0) {
+            if (pg >= 0) atomicOr(sticky_err, 1);
+            atomicExch(&sync[1], 1);
+          }
+          return;
+        }
+        known = pg;
+      }
+      __syncwarp();
+      const int c_lo = t - rows + 1 > 0 ? t - rows + 1 : 0;
+      const int c_hi = t < L.nx - 1 ? t : L.nx - 1;
+      const int ncell = c_hi - c_lo + 1;
+      int d, ix0;
+      if (forward) {
+        d = q * R + t;
+        ix0 = c_lo;
+      } else {
+        d = (L.nx - 1) + (L.ny - 1) - (q * R + t);
+        ix0 = L.nx - 1 - c_hi;
+      }
+      blusgs_group<NC, NS, GRP, true>(L, it.z, it.U, it.ghost, d, ix0, ncell, lane / GRP, lane % GRP);
+      __syncwarp();
+      const int done = t - rows + 2;
+      if (q + 1 < nstrips && done >= 1 && done <= L.nx) {
+        const int rel = forward ? 0 : (ncell - 1) * GRP;
+        if (lane == rel) st_rel(&prog[q], done);
+      }
+    }
+  }
+}
+
+void launch_b_blusgs_strip(const BItem* items, const int2* tickets, int ntickets, int nslots, const int* mask,
+                           int B, int forward, int grid, int* sync, int* sticky_err, cudaStream_t st) {
+  if (ntickets <= 0) return;
+  count_launches(2);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  cudaMemsetAsync(sync, 0, (2 + nslots) * sizeof(int), st);
+  kb_ghost_prologue<3, 4><<<4 * nsm, 128, 0, st>>>(items, mask, B);
+  const int g = grid < ntickets ? grid : ntickets;
+  kb_blusgs_strip<3, 4, 16><<<g > 0 ? g : 1, 32, 0, st>>>(items, tickets, ntickets, mask, forward, sync, sticky_err,
+                                                         1 << 22);
 }
 
 void launch_b_blusgs_sweep(const BItem* items, const int* mask, int B, int nsteps, int forward, int blocks,

@@ -69,6 +69,7 @@ def lib():
         L.swnmg_last_error.argtypes = [vp]
         L.swnmg_last_error.restype = C.c_char_p
         L.swnmg_set_params.argtypes = [vp, C.POINTER(Params)]
+        L.swnmg_set_mesh.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.swnmg_residual.argtypes = [vp, vp, vp, vp, dp]
         L.swnmg_jacobian.argtypes = [vp, vp]
         L.swnmg_get_blocks.argtypes = [vp, C.c_int32, vp]
@@ -114,9 +115,12 @@ class SwnmgError(RuntimeError):
         self.status = status
 
 
-def make_problem(p: W.Problem) -> Problem:
-    if getattr(p, "mesh_x", None) is not None:
-        raise NotImplementedError("the CUDA library solves on uniform Cartesian meshes only; "
+def make_problem(p: W.Problem, allow_mesh: bool = False) -> Problem:
+    """The C struct of a problem.  A curvilinear problem's vertices go to the
+    library separately (swnmg_set_mesh, single problems only): without
+    allow_mesh such a problem is refused."""
+    if getattr(p, "mesh_x", None) is not None and not allow_mesh:
+        raise NotImplementedError("batches solve on uniform Cartesian meshes only; "
                                   "problem %r has a curvilinear mesh" % p.name)
     s = Problem()
     s.dim, s.nx, s.ny = p.dim, p.nx, (p.ny if p.dim == 2 else 1)
@@ -153,7 +157,7 @@ class Solver:
         self.stream = stream or torch.cuda.current_stream()
         self.z = z if z is not None else torch.as_tensor(np.ascontiguousarray(prob.z), dtype=torch.float64,
                                                          device="cuda")
-        self._pp = make_problem(prob)
+        self._pp = make_problem(prob, allow_mesh=True)
         self._pr = make_params(self.params)
         h = C.c_void_p()
         rc = self.L.swnmg_create(C.byref(self._pp), C.byref(self._pr), _ptr(self.z),
@@ -161,6 +165,14 @@ class Solver:
         if rc != OK:
             raise SwnmgError(rc, self.L.swnmg_last_error(None).decode())
         self.h = h
+        if getattr(prob, "mesh_x", None) is not None:   # structured curvilinear mesh
+            mx = np.ascontiguousarray(prob.mesh_x, dtype=np.float64)
+            my = np.ascontiguousarray(prob.mesh_y, dtype=np.float64)
+            if mx.shape != (prob.ny + 1, prob.nx + 1) or my.shape != mx.shape:
+                self.close()
+                raise ValueError("mesh vertices must be (ny + 1, nx + 1) arrays")
+            P = C.POINTER(C.c_double)
+            self._check(self.L.swnmg_set_mesh(self.h, mx.ctypes.data_as(P), my.ctypes.data_as(P)))
 
     def _check(self, rc):
         if rc != OK:

@@ -43,6 +43,7 @@ INIT_NONE = 1      # warm start from the given state
 
 PREC_FP64 = 0
 PREC_MIXED = 1     # FP32 multigrid inner solve, FP64 residual / update / norms
+PREC_MIXED_STEP1 = 2   # PREC_MIXED, and Step 1's coarse-level BLU-SGS in FP32
 
 G = 9.81
 

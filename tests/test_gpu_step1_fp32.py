@@ -1,0 +1,44 @@
+"""SWNMG_PREC_MIXED_STEP1: Step 1's coarse-level BLU-SGS in FP32 (finite-
+difference step 2^-12).  Its iterates differ from the FP64 path, so the bar is
+the method's result: the solve reaches the FP64 oracle's steady state (within
+1e-9 relative, as the mixed mode) in about as many Newton steps, with Step 1
+stopping on every level.  The FP64 oracle run with the same finite-difference
+step in Step 1 takes the same sweep and Newton counts on the 256 x 256 bench
+channel, so the step itself is not what the comparison tests."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.oracle import Oracle
+from paper_1608_06721_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def swnmg():
+    from paper_1608_06721_gb300 import swnmg as S
+    S.lib()
+    return S
+
+
+CASES = [
+    ("channel_128_w", W.channel_2d(nx=128, ny=128, n_levels=4).with_params(gamma=2, eps_p=2.0, coarse_sweeps=0)),
+    ("channel_128x32", W.channel_2d(nx=128, ny=32, n_levels=2)),
+    ("ex36_64x32", W.transcritical_bump_2d(64, 32)),
+    ("ex34_channel_I_72x40", W.constricted_channel("I", 72, 40)),
+    ("ex33_256", W.wetdry_lake_1d(256)),
+]
+
+
+@pytest.mark.parametrize("name,prob", CASES, ids=[c[0] for c in CASES])
+def test_step1_fp32_reaches_the_fp64_steady_state(swnmg, name, prob):
+    Uo, io = Oracle(prob).solve()
+    assert io["status"] == 0
+    S = swnmg.Solver(prob.with_params(precision=W.PREC_MIXED_STEP1))
+    Ug = torch.as_tensor(prob.U0, dtype=torch.float64, device="cuda").contiguous()
+    ig = S.solve(Ug)
+    assert ig["status"] == 0, ig
+    assert abs(ig["n_newton"] - io["n_newton"]) <= 2, (ig["n_newton"], io["n_newton"])
+    assert all(k < prob.params.max_blusgs for k in ig["blusgs_sweeps"][1:])
+    assert np.abs(Ug.cpu().numpy() - Uo).max() <= 1e-9 * np.abs(Uo).max()

@@ -228,10 +228,13 @@ def test_cell_areas_add_up_to_the_channel_area():
     assert abs(Oracle(q).areas().sum() - (3.0 - 0.1 / 2)) <= 2e-5
 
 
-def test_cuda_library_refuses_curvilinear_meshes():
+def test_batches_refuse_curvilinear_meshes():
+    """Single problems take a mesh through swnmg_set_mesh; the batch and
+    no-allocation entry points marshal uniform problems only."""
     from paper_1608_06721_gb300 import swnmg
     with pytest.raises(NotImplementedError):
         swnmg.make_problem(W.constricted_channel("I", 72, 40))
+    assert swnmg.make_problem(W.constricted_channel("I", 72, 40), allow_mesh=True).nx == 72
 
 
 # ---------------------------------------------------------------- Example 3.4
