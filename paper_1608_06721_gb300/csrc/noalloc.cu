@@ -2,18 +2,21 @@
 //
 // swnmg_residual() keeps its per-edge pieces and reduction partials in the
 // context's workspace, which swnmg_create allocates with cudaMalloc.  Some
-// callers cannot allocate: code running inside a host callback (CUDA API
-// calls are not allowed there), code embedded in a runtime that owns every
-// byte of device memory through its own pool, and latency-critical loops
-// that cannot afford cudaMalloc/cudaFree's implicit device-wide
-// synchronisation.  swnmg_residual_noalloc evaluates the same residual with
-// the same kernels, taking its scratch from one fixed array in device global
-// memory instead.
+// callers cannot allocate: code embedded in a runtime that owns every byte
+// of device memory through its own pool, and latency-critical loops that
+// cannot afford cudaMalloc/cudaFree's implicit device-wide synchronisation.
+// swnmg_residual_noalloc evaluates the same residual with the same kernels,
+// taking its scratch from one fixed array in device global memory instead.
+// It enqueues kernels, so (like every CUDA call) it is not for stream or
+// host-function callbacks.
 //
 // That array lives for the whole process on every GPU that loads the
 // library.  Host code cannot use the array's name as a device address (in
 // host code it names a host-side stand-in), so the address is looked up once
-// per device with cudaGetSymbolAddress while that device is current.
+// per device with cudaGetSymbolAddress while that device is current.  With
+// lazy module loading that first lookup is also what loads the module and
+// commits the array, so the first call per device is the warm-up; the cached
+// address does not survive cudaDeviceReset.
 #include <cstdio>
 #include <mutex>
 
@@ -51,7 +54,9 @@ swnmg_status scratch_ptr(double** out) {
       char msg[256];
       snprintf(msg, sizeof msg, "residual_noalloc: cudaGetSymbolAddress failed: %s",
                cudaGetErrorString(e));
-      return noalloc_fail(SWNMG_ERR_CUDA, msg);
+      // the lookup loads the module and commits the array: a shortage of
+      // device memory is reported as such
+      return noalloc_fail(e == cudaErrorMemoryAllocation ? SWNMG_ERR_OOM : SWNMG_ERR_CUDA, msg);
     }
     g_ptr[dev] = static_cast<double*>(p);
   }
