@@ -234,12 +234,26 @@ SWNMG_API swnmg_status swnmg_get_timing(swnmg_ctx* ctx, double* ms_out, int64_t*
  * (all contexts); differences around a region count its launches. */
 SWNMG_API int64_t swnmg_launch_count(void);
 
+/* Failure detection (not in the paper).  Every device-side wait of the
+ * wavefront sweeps (a strip waiting on its predecessor's progress flag, a
+ * warp waiting on its staged operator copy, the BLU-SGS grid barrier) polls
+ * at most `polls` times; then the sweep stops, sets a sticky flag, and the
+ * call returns SWNMG_ERR_TIMEOUT (the context stays usable; the output of
+ * the interrupted sweep is undefined).  polls <= 0 restores the default,
+ * 2^22 polls, seconds of waiting.  The limit is process-wide, read when a
+ * launch is enqueued (a captured CUDA graph keeps the value it was captured
+ * with), and exists so that a test can make a wait run out; warps that gave
+ * up still wait for their own in-flight copies, under a separate bound,
+ * before they exit.  Returns the previous limit. */
+SWNMG_API int32_t swnmg_set_wait_limit(int32_t polls);
+
 /* The residual of swnmg_residual (eq. Res, same kernels, same bits) for
- * callers that cannot allocate device memory -- code running in a host
- * callback, where CUDA calls such as cudaMalloc are not allowed; code inside
- * a runtime that owns all device memory through its own pool; loops that
- * cannot take cudaMalloc/cudaFree's implicit device synchronisation.  The
- * paper has no counterpart: it is an interface convenience only.
+ * callers that cannot allocate device memory: code inside a runtime that
+ * owns all device memory through its own pool, and loops that cannot take
+ * cudaMalloc/cudaFree's implicit device synchronisation.  The paper has no
+ * counterpart: it is an interface convenience only.  The call enqueues
+ * kernels, so like any CUDA call it must not be made from a stream callback
+ * or a cudaLaunchHostFunc function.
  *
  * Needs no context.  Inputs and outputs are the caller's device arrays: z
  * (n), U (ncomp*n), R (ncomp*n), rnorm (n, nullable: ||R_i||_1), l1_dev
@@ -248,12 +262,20 @@ SWNMG_API int64_t swnmg_launch_count(void);
  * waiting.  Scratch comes from one fixed device array of 2^20 doubles
  * (8 MiB) that every GPU loading the library keeps until the process exits;
  * a grid needs 2*ncomp*(edges) + 1024 doubles of it (+ n when rnorm is
- * NULL), i.e. about 256x256 cells in 2D -- larger grids return
- * SWNMG_ERR_ARG with the reason in swnmg_last_error(NULL).  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
- * All calls share the one array, so calls that may overlap on the GPU (other
- * streams, other host threads) race and must be serialised by the caller. */
+ * NULL): up to 294x294 cells in 2D with rnorm, 283x283 without.  Larger
+ * grids return SWNMG_ERR_ARG with the reason in swnmg_last_error(NULL).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current).  With CUDA's lazy module
+ * loading that lookup loads the library's device code and commits the 8 MiB,
+ * which can block or fail (SWNMG_ERR_OOM when memory is short), so "allocates
+ * nothing" holds from the second call on: make one untimed warm-up call per
+ * device, before any stream capture.  The looked-up address is cached per
+ * device for the life of the process and does not survive cudaDeviceReset
+ * (or any reset of the primary context); do not call this function after
+ * one.  All calls share the one array, so calls that may overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller. */
 SWNMG_API swnmg_status swnmg_residual_noalloc(const swnmg_problem* prob, const swnmg_params* prm,
                                               const double* z_dev, const double* U_dev,
                                               double* R_dev, double* rnorm_dev, double* l1_dev,
@@ -272,10 +294,11 @@ SWNMG_API swnmg_status swnmg_residual_noalloc(const swnmg_problem* prob, const s
  *   U_dev     (ncomp*n) the steady state, usually the output of swnmg_solve
  *   g_dev     (ncomp*n) dL/dU
  *   lam_dev   (ncomp*n) out: lambda, cycles started from lambda = 0
- *   dRz_dev   (n) out: lambda^T dR/dz, one value per cell bed
- *   dRq_host  (4 doubles, nullable) out: lambda^T dR/dq of each side's
- *             prescribed discharge (sides W, E, S, N; 0 unless the side is
- *             SWNMG_BC_INFLOW_DISCHARGE)
+ *   gz_dev    (n) out: -lambda^T dR/dz, one value per cell bed: the part of
+ *             dL/dz that flows through U* (add the loss's direct dL/dz)
+ *   gq_host   (4 doubles, nullable) out: -lambda^T dR/dq = dL/dq of each
+ *             side's prescribed discharge (sides W, E, S, N; 0 unless the
+ *             side is SWNMG_BC_INFLOW_DISCHARGE)
  *   max_cycles cycles of Algorithm 0 at most (>= 1)
  *   rtol      > 0: stop once sum_i ||(g - J^T lambda)_i||_1 <= rtol *
  *             sum_i ||g_i||_1 (checked after every cycle);
@@ -288,7 +311,7 @@ SWNMG_API swnmg_status swnmg_residual_noalloc(const swnmg_problem* prob, const s
  * rtol > 0 is not met within max_cycles, SWNMG_ERR_NONFINITE if the linear
  * residual is not finite.  Synchronises the stream. */
 SWNMG_API swnmg_status swnmg_adjoint(swnmg_ctx* ctx, const double* U_dev, const double* g_dev,
-                                     double* lam_dev, double* dRz_dev, double* dRq_host,
+                                     double* lam_dev, double* gz_dev, double* gq_host,
                                      int32_t max_cycles, double rtol, int32_t* cycles_out);
 
 /* ---- batches: many independent 2D problems solved together --------------

@@ -635,7 +635,7 @@ SWNMG_API swnmg_status swnmg_blusgs(swnmg_ctx* c, double* U, int32_t level, int3
   }
   LAUNCH_CHECK(c);
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
-  return SWNMG_OK;
+  return check_sticky(c);
 }
 
 SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) {
@@ -811,9 +811,9 @@ swnmg_status adjoint_alloc(swnmg_ctx* c) {
 }  // namespace
 
 SWNMG_API swnmg_status swnmg_adjoint(swnmg_ctx* c, const double* U, const double* g, double* lam,
-                                     double* dRz, double* dRq_host, int32_t max_cycles, double rtol,
+                                     double* gz, double* gq_host, int32_t max_cycles, double rtol,
                                      int32_t* cycles_out) {
-  if (!c || !U || !g || !lam || !dRz || max_cycles < 1) return fail(c, SWNMG_ERR_ARG, "bad argument");
+  if (!c || !U || !g || !lam || !gz || max_cycles < 1) return fail(c, SWNMG_ERR_ARG, "bad argument");
   if (!(rtol == rtol)) return fail(c, SWNMG_ERR_ARG, "rtol is NaN");
   if (c->curv) return fail(c, SWNMG_ERR_ARG, "the adjoint is built for uniform meshes only");
   if (cycles_out) *cycles_out = 0;
@@ -860,18 +860,18 @@ SWNMG_API swnmg_status swnmg_adjoint(swnmg_ctx* c, const double* U, const double
   if (cycles_out) *cycles_out = k;
   if ((s = check_sticky(c)) != SWNMG_OK) return s;
   launch_from_skew(a0.x, 0, lam, 0, nc, a0.nx, a0.ny, 1.0, c->st);
-  // lambda^T dR/dz and lambda^T dR/dq (central differences of the edge terms)
+  // -lambda^T dR/dz and -lambda^T dR/dq (central differences of the edge terms)
   const double delta = 1e-6;
-  launch_adjoint_z(L, c->lv[0].z, U, lam, delta, c->adj_cz, dRz, c->st);
+  launch_adjoint_z(L, c->lv[0].z, U, lam, delta, c->adj_cz, gz, c->st);
   LAUNCH_CHECK(c);
-  if (dRq_host) {
+  if (gq_host) {
     const int nsides = c->prob.dim == 2 ? 4 : 2;
     for (int side = 0; side < 4; ++side) {
-      dRq_host[side] = 0.0;
+      gq_host[side] = 0.0;
       if (side >= nsides || c->prob.bc[side].kind != SWNMG_BC_INFLOW_DISCHARGE) continue;
       launch_adjoint_q(L, side, c->lv[0].z, U, lam, delta, c->adj_cell, c->st);
       LAUNCH_CHECK(c);
-      if ((s = device_sum(c, c->adj_cell, L.n, &dRq_host[side])) != SWNMG_OK) return s;
+      if ((s = device_sum(c, c->adj_cell, L.n, &gq_host[side])) != SWNMG_OK) return s;
     }
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
@@ -915,5 +915,11 @@ SWNMG_API swnmg_status swnmg_get_timing(swnmg_ctx* c, double* ms_out, int64_t* n
 }
 
 SWNMG_API int64_t swnmg_launch_count(void) { return launches_total(); }
+
+SWNMG_API int32_t swnmg_set_wait_limit(int32_t polls) {
+  const int old = wait_limit();
+  set_wait_limit(polls);
+  return old;
+}
 
 DevLevel swnmg::ctx_dev_level(const swnmg_ctx* c, int l) { return dev_level(c, l); }

@@ -380,7 +380,7 @@ void launch_blusgs32_strip(const DevLevel& L, const double* z, double* U, float*
   const int glen = L.nx > L.ny ? L.nx : L.ny;
   const int gblocks = (4 * glen * (L.nc + 1) + 127) / 128;
   const int grid = nstrips < 16 * nsm ? nstrips : 16 * nsm;
-  const int spin = 1 << 22;
+  const int spin = wait_limit();
   if (L.nc == 3) {
     k_ghost32<3, 4><<<gblocks, 128, 0, st>>>(L, U, gbuf);
     k_blusgs32_strip<3, 4, 16><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);

@@ -124,6 +124,14 @@ void set_static_error(const char* msg);
 
 // process-wide count of kernel launches issued by the library
 void count_launches(long long k);
+// Polls a device-side wait makes before it gives up and sets the sticky
+// error (swnmg_set_wait_limit); read when a launch is enqueued (or captured).
+constexpr int kDefaultWaitLimit = 1 << 22;
+int wait_limit();
+void set_wait_limit(int polls);
+// Bound of the wait for a warp's own in-flight bulk copies before it exits
+// after a failure: independent of wait_limit(), since an issued copy lands.
+constexpr int kDrainLimit = 1 << 24;
 long long launches_total();
 
 // ---- host-side launch wrappers (flux.cu) ---------------------------------

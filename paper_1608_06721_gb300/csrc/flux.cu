@@ -1063,7 +1063,9 @@ __global__ void k_adj_z_edges(DevLevel L, const double* __restrict__ z, const do
   }
 }
 
-__global__ void k_adj_z_cells(DevLevel L, const double* __restrict__ cz, double* __restrict__ dRz, int n_xe,
+// gz[i] = -lambda^T dR/dz_i (the implicit-function part of dL/dz_i); the
+// negation is exact, so gz is bitwise -(lambda^T dR/dz)
+__global__ void k_adj_z_cells(DevLevel L, const double* __restrict__ cz, double* __restrict__ gz, int n_xe,
                               int n_e) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.n) return;
@@ -1071,10 +1073,11 @@ __global__ void k_adj_z_cells(DevLevel L, const double* __restrict__ cz, double*
   cell_edges(L, i, n_xe, eW, eE, eS, eN);
   double a = cz[(long long)n_e + eW] + cz[eE];
   if (L.dim == 2) a = a + cz[(long long)n_e + eS] + cz[eN];
-  dRz[i] = a;
+  gz[i] = -a;
 }
 
-// per boundary cell of `side`: lambda . |e| (G(q + delta) - G(q - delta)) / (2 delta)
+// per boundary cell of `side`: -lambda . |e| (G(q + delta) - G(q - delta)) / (2 delta)
+// (negated, so that the sum over the side is -lambda^T dR/dq)
 template <int NC>
 __global__ void k_adj_q_cells(DevLevel Lp, DevLevel Lm, int side, const double* __restrict__ z,
                               const double* __restrict__ U, const double* __restrict__ lam, double delta,
@@ -1104,7 +1107,7 @@ __global__ void k_adj_q_cells(DevLevel Lp, DevLevel Lm, int side, const double* 
       acc += l[s] * (len * ((gp - gm) * r2d));
     }
   }
-  out[i] = acc;
+  out[i] = -acc;
 }
 
 // U += tau dU with the dry rules of Remark 2.5 (eq. NewtonREG-12)
@@ -1500,7 +1503,7 @@ void launch_blusgs_strip(const DevLevel& L, const double* z, double* U, double* 
   const int gblocks = (gthreads + 127) / 128;
   // at most 16 warps per SM: more strips than that queue on the ticket
   const int grid = nstrips < 16 * nsm ? nstrips : 16 * nsm;
-  const int spin = 1 << 22;
+  const int spin = wait_limit();
   if (L.nc == 3) {
     k_ghost_prologue<3, 4><<<gblocks, 128, 0, st>>>(L, U, gbuf);
     k_blusgs_strip<3, 4, 16><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
@@ -1523,7 +1526,7 @@ void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, double* 
   // one block of 4 warps per SM (co-resident by cooperative launch); a
   // diagonal's cells are dealt to the warps in rounds
   int fw = forward;
-  int spin = 1 << 22;
+  int spin = wait_limit();
   DevLevel Lc = L;
   void* args[] = {(void*)&Lc, (void*)&z, (void*)&U, (void*)&gbuf, (void*)&fw, (void*)&sync, (void*)&sticky_err,
                   (void*)&spin};
@@ -1747,7 +1750,7 @@ void launch_b_blusgs_sweep(const BItem* items, const int* mask, int B, int nstep
                            int* sync, int* sticky_err, cudaStream_t st) {
   count_launches(1);
   cudaMemsetAsync(sync, 0, 2 * sizeof(int), st);
-  int b = B, ns = nsteps, fw = forward, spin = 1 << 22;
+  int b = B, ns = nsteps, fw = forward, spin = wait_limit();
   void* args[] = {(void*)&items, (void*)&mask, (void*)&b, (void*)&ns, (void*)&fw, (void*)&sync,
                   (void*)&sticky_err, (void*)&spin};
   cudaLaunchCooperativeKernel((const void*)kb_blusgs_sweep<3, 4, 16>, dim3(blocks), dim3(128), args, 0, st);

@@ -592,10 +592,12 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
     }
   }
   if (failed) {
-    // stop the other strips, then let this warp's copies land before leaving
+    // stop the other strips, then let this warp's copies land before leaving;
+    // the drain has its own bound: a bulk copy that was issued completes, so
+    // it must not inherit a wait limit shortened for failure tests
     if (lane == 0) st_release(abort_flag, 1);
     for (int st = 0; st < 2; ++st)
-      if (inflight[st]) chunk_wait(&bar[st], parity[st], wait_limit);
+      if (inflight[st]) chunk_wait(&bar[st], parity[st], kDrainLimit);
     return false;
   }
   return true;
@@ -1151,6 +1153,12 @@ static std::atomic<long long> g_launches{0};
 void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
+static std::atomic<int> g_wait_limit{kDefaultWaitLimit};
+int wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+void set_wait_limit(int polls) {
+  g_wait_limit.store(polls > 0 ? polls : kDefaultWaitLimit, std::memory_order_relaxed);
+}
+
 void launch_lu_factor(int nx, int ny, int nc, const void* blk, void* lu, int8_t* piv, int fp32,
                       cudaStream_t st) {
   count_launches(1);
@@ -1210,7 +1218,7 @@ static void sgs_launch(int nx, int ny, const void* blk, const void* lu, const in
     configured = true;
   }
   k_sgs_strip<NC, T, F, S><<<nstrips, 32, smem, st>>>(nx, ny, (const T*)blk, (const T*)lu, piv,
-                                                       (const T*)b, (T*)x, sync, sticky, nstrips, 1 << 22);
+                                                       (const T*)b, (T*)x, sync, sticky, nstrips, wait_limit());
 }
 
 void launch_sgs_sweep(int nc, int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
@@ -1405,7 +1413,7 @@ static void b_sgs_launch(const BItem* items, const int2* tickets, int ntickets, 
   }
   // warps resident at once (each loops over tickets), never more than tickets
   const int grid = ntickets < per_sm * nsm ? ntickets : per_sm * nsm;
-  kb_sgs_strip<3, T, F, S><<<grid, 32, smem, st>>>(items, tickets, ntickets, mask, sync, sticky, 1 << 22);
+  kb_sgs_strip<3, T, F, S><<<grid, 32, smem, st>>>(items, tickets, ntickets, mask, sync, sticky, wait_limit());
 }
 
 size_t b_sgs_smem_bytes(int fp32, int chunk) {

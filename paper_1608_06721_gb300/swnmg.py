@@ -94,6 +94,8 @@ def lib():
         L.swnmg_batch_tune.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.swnmg_batch_set_tuning.argtypes = [vp, C.POINTER(C.c_int32), C.c_int32]
         L.swnmg_level_cells.restype = C.c_int64
+        L.swnmg_set_wait_limit.argtypes = [C.c_int32]
+        L.swnmg_set_wait_limit.restype = C.c_int32
         for f in ("swnmg_default_params", "swnmg_create", "swnmg_destroy", "swnmg_set_params",
                   "swnmg_residual", "swnmg_jacobian", "swnmg_get_blocks", "swnmg_vcycle",
                   "swnmg_sgs_sweep", "swnmg_blusgs", "swnmg_solve", "swnmg_set_timing",
@@ -271,18 +273,19 @@ class Solver:
 
     def adjoint(self, U, g, max_cycles=100, rtol=1e-12, check=True):
         """swnmg_adjoint: lambda with J(U)^T lambda = g by multigrid cycles on the
-        transposed hierarchy, lambda^T dR/dz (n) and lambda^T dR/dq (4 sides).
-        Returns (lam, dRz, dRq, cycles)."""
+        transposed hierarchy, gz = -lambda^T dR/dz (n) and gq = -lambda^T
+        dR/dq (4 sides), the loss gradient's parts through U*.
+        Returns (lam, gz, gq, cycles)."""
         n = self.level_cells(0)
         lam = torch.empty((self.nc, n), dtype=torch.float64, device="cuda")
-        dRz = torch.empty(n, dtype=torch.float64, device="cuda")
-        dRq = (C.c_double * 4)()
+        gz = torch.empty(n, dtype=torch.float64, device="cuda")
+        gq = (C.c_double * 4)()
         cyc = C.c_int32(0)
-        rc = self.L.swnmg_adjoint(self.h, _ptr(U), _ptr(g), _ptr(lam), _ptr(dRz), dRq, max_cycles,
+        rc = self.L.swnmg_adjoint(self.h, _ptr(U), _ptr(g), _ptr(lam), _ptr(gz), gq, max_cycles,
                                   rtol, C.byref(cyc))
         if check or rc != ERR_NOT_CONVERGED:
             self._check(rc)
-        return lam, dRz, np.array(list(dRq)), cyc.value
+        return lam, gz, np.array(list(gq)), cyc.value
 
 
 def _stats_dict(st, n_levels):
@@ -402,9 +405,9 @@ class SteadySWE(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gU):
         (U,) = ctx.saved_tensors
-        _, dRz, dRq, _ = ctx.solver.adjoint(U, gU.contiguous(), ctx.adj[0], ctx.adj[1])
-        gq = torch.as_tensor(-dRq, dtype=ctx.q_meta[1], device=ctx.q_meta[0])
-        return -dRz, gq, None, None, None, None, None
+        _, gz, gq, _ = ctx.solver.adjoint(U, gU.contiguous(), ctx.adj[0], ctx.adj[1])
+        gq = torch.as_tensor(gq, dtype=ctx.q_meta[1], device=ctx.q_meta[0])
+        return gz, gq, None, None, None, None, None
 
 
 def steady_state(z, q, prob: W.Problem, params: W.Params | None = None, U0=None, adj_cycles=400,
@@ -430,6 +433,12 @@ def residual_noalloc(prob: W.Problem, z, U, R, rnorm=None, l1=None, params: W.Pa
                                   _ptr(l1) if l1 is not None else None, C.c_void_p(st.cuda_stream))
     if rc != OK:
         raise SwnmgError(rc, L.swnmg_last_error(None).decode())
+
+
+def set_wait_limit(polls: int) -> int:
+    """swnmg_set_wait_limit: polls of every device-side wait before a sweep
+    gives up with ERR_TIMEOUT (<= 0: the default); returns the old limit."""
+    return int(lib().swnmg_set_wait_limit(int(polls)))
 
 
 def default_params(dim: int) -> dict:

@@ -68,7 +68,9 @@ def test_adjoint_matches_oracle(swnmg, name, prob, seed, ocyc):
     U, g = _inputs(prob, seed)
     lam_o, dRz_o, dRq_o = Oracle(prob).adjoint(U, g, ncycles=ocyc)
     S = swnmg.Solver(prob)
-    lam, dRz, dRq, cyc = S.adjoint(_dev(U), _dev(g), max_cycles=400, rtol=1e-14)
+    lam, gz, gq, cyc = S.adjoint(_dev(U), _dev(g), max_cycles=400, rtol=1e-14)
+    # the library returns the gradient parts -lambda^T dR/dz, -lambda^T dR/dq
+    dRz, dRq = -gz, -gq
     assert 1 <= cyc < 400
     lam, dRz = lam.cpu().numpy(), dRz.cpu().numpy()
     scale = np.abs(lam_o).max()
