@@ -284,6 +284,37 @@ def channel_2d(seed: int = 301, nx: int = 1024, ny: int = 1024, n_bumps: int = 1
     return p
 
 
+def supercritical_channel_2d(nx: int, ny: int, n_levels: int = 2, flux: int = FLUX_HLLC, froude: float = 2.5,
+                             h0: float = 0.6, seed: int = 302) -> Problem:
+    """A supercritical channel with every fixed open-boundary kind of
+    Remark 2.3 that the partial-dry channel lacks: supercritical inflow at
+    x = 0 (depth h0, discharge at the inflow Froude number, no tangential
+    velocity), supercritical outflow at x = 4 and slip walls at y = 0, 1;
+    six low Gaussian bumps (channel_2d's draw scaled by 0.3), initial state
+    the inflow state everywhere."""
+    p = channel_2d(seed=seed, nx=nx, ny=ny, n_bumps=6, n_levels=n_levels, redraw=False)
+    p = p.with_params(flux=flux, llf_wetdry=0)
+    q = h0 * froude * float(np.sqrt(p.g * h0))
+    p.z = 0.3 * p.z
+    p.U0 = np.stack([np.full(p.n, h0), np.full(p.n, q), np.zeros(p.n)])
+    p.bc = [BC(BC_SUPER_INFLOW, h=h0, q=q, ut=0.0), BC(BC_SUPER_OUTFLOW), BC(BC_WALL_SLIP), BC(BC_WALL_SLIP)]
+    p.meta = dict(p.meta, froude=froude)
+    return p
+
+
+def channel_bench(nx: int = 1024, ny: int = 1024, precision: int = PREC_MIXED, n_levels: int | None = None,
+                  seed: int = 301) -> Problem:
+    """The benchmark configuration of the partial-dry channel: channel_2d's
+    input with W-cycles (gamma = 2), an exact solve of the coarsest level,
+    N_mg = 3, eps_p = 2 and tol 1e-10.  The default level count coarsens to
+    8 cells across (N_L = 7 at 1024^2)."""
+    if n_levels is None:
+        n_levels = max(0, min(nx, ny).bit_length() - 4)
+    p = channel_2d(seed=seed, nx=nx, ny=ny, precision=precision)
+    return p.with_params(gamma=2, eps_p=2.0, n_levels=n_levels, n_mg=3, coarse_sweeps=0, tol=1e-10,
+                         max_newton=200)
+
+
 def batch_channels(seed: int = 401, count: int = 64, sizes=(128, 256, 512, 1024), coarsest: int = 8,
                    precision: int = PREC_MIXED) -> list:
     """Batched workload: ``count`` independent channel problems.  A generator

@@ -78,6 +78,12 @@ def _cases():
     p.bc[0] = W.BC(W.BC_AUTO_FROUDE, h=2.0, q=p.bc[0].q)
     p.bc[1] = W.BC(W.BC_AUTO_FROUDE, h=2.0, q=p.bc[0].q)
     out.append(("bump1d_200_auto", p, lambda p: W.random_state(p, 11)))
+    # the fixed open-boundary kinds (Remark 2.3): supercritical inflow and
+    # outflow, slip walls; HLLC and Roe
+    p = W.supercritical_channel_2d(64, 32, n_levels=2)
+    out.append(("super_slip_64x32_hllc", p, lambda p: W.random_state(p, 12)))
+    p = W.supercritical_channel_2d(72, 40, n_levels=3, flux=W.FLUX_ROE)
+    out.append(("super_slip_72x40_roe", p, lambda p: W.random_state(p, 13)))
     return out
 
 
@@ -181,6 +187,8 @@ SOLVES = [
     ("ex36_64x32", W.transcritical_bump_2d(64, 32)),
     ("ex31_256_roe", W.smooth_subcritical_1d(256, flux=W.FLUX_ROE)),
     ("ex36_48x24_roe", W.transcritical_bump_2d(48, 24).with_params(flux=W.FLUX_ROE)),
+    ("super_slip_128x64_hllc", W.supercritical_channel_2d(128, 64, n_levels=3)),
+    ("super_slip_64x32_hll", W.supercritical_channel_2d(64, 32, flux=W.FLUX_HLL)),
 ]
 
 
