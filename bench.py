@@ -41,9 +41,7 @@ LEVELS = 7
 
 def workload(precision, nx=NX, ny=NY):
     from paper_1608_06721_gb300 import workloads as W
-    p = W.channel_2d(seed=301, nx=nx, ny=ny, precision=precision)
-    return p.with_params(gamma=2, eps_p=2.0, n_levels=LEVELS, n_mg=3, coarse_sweeps=0, tol=1e-10,
-                         max_newton=200)
+    return W.channel_bench(nx, ny, precision, n_levels=LEVELS)
 
 
 def config_dict(p, flush):
@@ -493,6 +491,66 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------- profiling cases
+
+def _event_ms(fn):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_profile_case(args):
+    """Small fixed launch sequences for ncu and CUDA-event timing of single
+    kernels (no JSON line).
+
+    sweeps: on the n x n channel (mixed precision, the benchmark's levels
+      for n): residual, Jacobian, one symmetric BLU-SGS sweep twice, a level-0
+      SGS forward and backward half-sweep twice; every kernel of interest
+      launches at least twice, so `-s 1 -c 1` on one kernel name captures a
+      warm launch.
+    cycle: Jacobian then one multigrid cycle of the benchmark configuration,
+      for a launch list of every level's kernels."""
+    import torch
+    from paper_1608_06721_gb300 import swnmg, workloads as W
+    n = args.nx
+    p = W.channel_bench(n, n, W.PREC_MIXED)
+    S = swnmg.Solver(p)
+    U = torch.as_tensor(p.U0, dtype=torch.float64, device="cuda").contiguous()
+    if args.profile_case == "sweeps":
+        for k in range(2):
+            ms = _event_ms(lambda: S.residual(U))
+        print("residual %dx%d: %.3f ms" % (n, n, ms))
+        for k in range(2):
+            ms = _event_ms(lambda: S.jacobian(U))
+        print("jacobian (with hierarchy and LU) %dx%d: %.3f ms" % (n, n, ms))
+        V = U.clone()
+        for k in range(2):
+            ms = _event_ms(lambda: S.blusgs(V, 0, 1))
+        print("blusgs symmetric sweep %dx%d: %.3f ms" % (n, n, ms))
+        S.jacobian(U)
+        R, _, _ = S.residual(U)
+        x = torch.zeros_like(U)
+        for fw in (True, False):
+            for k in range(2):
+                ms = _event_ms(lambda: S.sgs_sweep(0, -R, x, fw))
+            print("sgs half-sweep %s %dx%d: %.3f ms" % ("forward" if fw else "backward", n, n, ms))
+    elif args.profile_case == "cycle":
+        S.jacobian(U)
+        R, _, _ = S.residual(U)
+        x = torch.zeros_like(U)
+        n0 = swnmg.lib().swnmg_launch_count()
+        ms = _event_ms(lambda: S.vcycle(-R, x, 1))
+        print("one cycle (gamma=%d, N_L=%d) %dx%d: %.3f ms, %d launches"
+              % (p.params.gamma, p.params.n_levels, n, n, ms, swnmg.lib().swnmg_launch_count() - n0))
+    else:
+        raise SystemExit("unknown profile case " + args.profile_case)
+    S.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -510,9 +568,13 @@ def main():
     ap.add_argument("--sequential", action="store_true")
     ap.add_argument("--step1-fp32", action="store_true",
                     help="Step 1's coarse-level BLU-SGS in FP32 (precision MIXED_STEP1)")
+    ap.add_argument("--profile-case", choices=["sweeps", "cycle"], default=None,
+                    help="run a small fixed launch sequence for ncu instead of the benchmark")
     args = ap.parse_args()
     globals()["LEVELS"] = args.levels
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
