@@ -89,14 +89,22 @@ typedef struct {
  *   gamma         1: V-cycle, 2: W-cycle (Algorithm 0)
  *   coarse_sweeps 2D coarsest level: this many symmetric SGS sweeps
  *                 (1D coarsest levels are solved exactly)
- *   max_blusgs    cap of BLU-SGS sweeps per level in Step 1 */
+ *   max_blusgs    cap of BLU-SGS sweeps per level in Step 1
+ *   smoother      order of the block SGS smoother: SWNMG_SMOOTH_LEX (0, the
+ *                 paper's lexicographic sweeps, Section 2.3) or
+ *                 SWNMG_SMOOTH_COLOUR (1, a variant that is not in the
+ *                 paper: cells of colour (ix + iy) mod 2, colour 0 then 1
+ *                 forward, 1 then 0 backward; its iterates differ) */
 typedef struct {
   int32_t flux, llf_wetdry;
   double alpha, fd_eps, tau, h_eps, eps_r, eps_p, tol;
   int32_t n_levels, n_mg, nu1, nu2, gamma, coarse_sweeps, max_newton, max_blusgs,
       init_mode, precision;
   double eps_f;   /* Harten's entropy-fix width of the Roe flux (paper: 0.4) */
+  int32_t smoother;
 } swnmg_params;
+
+enum { SWNMG_SMOOTH_LEX = 0, SWNMG_SMOOTH_COLOUR = 1 };
 
 #define SWNMG_HIST 512
 typedef struct {

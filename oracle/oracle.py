@@ -36,7 +36,8 @@ class Cfg(C.Structure):
                 ("gamma", C.c_int), ("coarse_sweeps", C.c_int), ("max_newton", C.c_int),
                 ("max_blusgs", C.c_int), ("init_mode", C.c_int), ("eps_f", C.c_double),
                 ("t_ka", C.c_double), ("t_omb", C.c_double), ("t_src", C.c_void_p),
-                ("mesh_x", C.c_void_p), ("mesh_y", C.c_void_p), ("t_kai", C.c_void_p)]
+                ("mesh_x", C.c_void_p), ("mesh_y", C.c_void_p), ("t_kai", C.c_void_p),
+                ("smoother", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -113,7 +114,7 @@ def make_cfg(prob, **over) -> Cfg:
         c.bc[s].kind, c.bc[s].h, c.bc[s].q, c.bc[s].ut = b.kind, b.h, b.q, b.ut
     for f in ("flux", "llf_wetdry", "alpha", "fd_eps", "tau", "h_eps", "eps_r", "eps_p", "tol",
               "n_levels", "n_mg", "nu1", "nu2", "gamma", "coarse_sweeps", "max_newton",
-              "max_blusgs", "init_mode", "eps_f"):
+              "max_blusgs", "init_mode", "eps_f", "smoother"):
         setattr(c, f, getattr(prm, f))
     return c
 

@@ -68,6 +68,7 @@ typedef struct {
   const double* mesh_x;
   const double* mesh_y;
   const double* t_kai;                /* per-cell |K_i|/dt of a time step on such a mesh */
+  int smoother;                       /* block SGS order: 0 lexicographic (the paper's), 1 two colours */
 } orc_cfg;
 
 #define ORC_HIST 512
@@ -585,6 +586,7 @@ static void lu_solve(int n, const blu* f, const double* b, double* x) {
 static int check_cfg(const orc_cfg* c) {
   if (!c || (c->dim != 1 && c->dim != 2) || c->nx < 1 || (c->dim == 2 && c->ny < 1)) return ST_ARG;
   if (c->n_levels < 0 || c->n_levels > 12) return ST_ARG;
+  if (c->smoother < 0 || c->smoother > 1) return ST_ARG;
   if (c->flux < 0 || c->flux > FLUX_ROE || (c->flux == FLUX_ROE && !(c->eps_f > 0.0))) return ST_ARG;
   int m = 1 << c->n_levels;
   if (c->nx % m) return ST_ARG;
@@ -767,25 +769,43 @@ static void factor_level(const orc_cfg* c, int n, const double* blk, blu* f) {
   for (int i = 0; i < n; ++i) lu_factor(nc, blk + (size_t)i * 5 * bs, &f[i]);
 }
 
-/* one block Gauss-Seidel sweep in lexicographic order (x fastest), forward or
- * backward:  x_i <- D_i^{-1} (b_i - sum_{j != i} A_ij x_j). */
+/* the block Gauss-Seidel update of cell i:
+ *   x_i <- D_i^{-1} (b_i - sum_{j != i} A_ij x_j) */
+static void gs_cell(const orc_cfg* c, const lvl* L, const double* blk, const blu* f,
+                    const double* b, double* x, int i) {
+  int nc = ncomp(c), bs = nc * nc, n = L->n;
+  double r[3], xi[3];
+  for (int s = 0; s < nc; ++s) r[s] = b[s * n + i];
+  for (int side = 0; side < nsides(c); ++side) {
+    int j = nbr(L, i, side);
+    if (j < 0) continue;
+    const double* A = blk + ((size_t)i * 5 + 1 + side) * bs;
+    for (int s = 0; s < nc; ++s)
+      for (int k = 0; k < nc; ++k) r[s] = r[s] - A[s * nc + k] * x[k * n + j];
+  }
+  lu_solve(nc, &f[i], r, xi);
+  for (int s = 0; s < nc; ++s) x[s * n + i] = xi[s];
+}
+
+/* one block Gauss-Seidel sweep, forward or backward.  smoother 0 (the
+ * paper's): lexicographic order, x fastest, or its reverse.  smoother 1 (a
+ * variant, not in the paper): two colours, cell i = (ix, iy) of colour
+ * (ix + iy) mod 2; the forward sweep updates every cell of colour 0, then
+ * every cell of colour 1, the backward sweep colour 1 then colour 0.  Cells
+ * of one colour only couple to the other colour (5-point stencil), so the
+ * order inside a colour does not matter. */
 static void sgs_half(const orc_cfg* c, const lvl* L, const double* blk, const blu* f,
                      const double* b, double* x, int forward) {
-  int nc = ncomp(c), bs = nc * nc, n = L->n;
-  for (int t = 0; t < n; ++t) {
-    int i = forward ? t : n - 1 - t;
-    double r[3], xi[3];
-    for (int s = 0; s < nc; ++s) r[s] = b[s * n + i];
-    for (int side = 0; side < nsides(c); ++side) {
-      int j = nbr(L, i, side);
-      if (j < 0) continue;
-      const double* A = blk + ((size_t)i * 5 + 1 + side) * bs;
-      for (int s = 0; s < nc; ++s)
-        for (int k = 0; k < nc; ++k) r[s] = r[s] - A[s * nc + k] * x[k * n + j];
+  int n = L->n;
+  if (c->smoother == 1) {
+    for (int pass = 0; pass < 2; ++pass) {
+      int colour = forward ? pass : 1 - pass;
+      for (int i = 0; i < n; ++i)
+        if (((i % L->nx) + (i / L->nx)) % 2 == colour) gs_cell(c, L, blk, f, b, x, i);
     }
-    lu_solve(nc, &f[i], r, xi);
-    for (int s = 0; s < nc; ++s) x[s * n + i] = xi[s];
+    return;
   }
+  for (int t = 0; t < n; ++t) gs_cell(c, L, blk, f, b, x, forward ? t : n - 1 - t);
 }
 
 int orc_sgs(const orc_cfg* c, int l, const double* blk, const double* b, double* x, int forward) {

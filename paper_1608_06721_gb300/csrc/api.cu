@@ -112,6 +112,7 @@ DevLevel dev_level(const swnmg_ctx* c, int l) {
 
 swnmg_status check_params(const swnmg_problem* p, const swnmg_params* q) {
   if (q->flux < 0 || q->flux > 3) return SWNMG_ERR_ARG;
+  if (q->smoother != SWNMG_SMOOTH_LEX && q->smoother != SWNMG_SMOOTH_COLOUR) return SWNMG_ERR_ARG;
   if (q->flux == SWNMG_FLUX_ROE && !(q->eps_f > 0)) return SWNMG_ERR_ARG;
   if (p->dim == 1 && q->flux == SWNMG_FLUX_HLLC) return SWNMG_ERR_ARG;
   if (!(q->fd_eps > 0) || !(q->h_eps > 0) || q->alpha < 0) return SWNMG_ERR_ARG;
@@ -190,11 +191,19 @@ swnmg_status level_residual_sum(swnmg_ctx* c, int l, const double* U, double* ou
   return device_sum(c, c->rn, L.n, out);
 }
 
+// one block SGS half-sweep of level l in the order the parameters select
+void sgs_launch(swnmg_ctx* c, const Level& v, int fp32, int forward) {
+  if (c->prm.smoother == SWNMG_SMOOTH_COLOUR)
+    launch_sgs_colour_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward, fp32, c->st);
+  else
+    launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward, fp32, c->sgs_sync, c->sticky,
+                     c->st);
+}
+
 void sgs_half(swnmg_ctx* c, const Hier& H, int l, int forward) {
   Level& v = H.lv[l];
   TimedScope ts(c, l == 0 ? SWNMG_T_SGS_FINE : SWNMG_T_SGS_COARSE, v.n);
-  launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward, H.fp32, c->sgs_sync,
-                   c->sticky, c->st);
+  sgs_launch(c, v, H.fp32, forward);
 }
 
 void blusgs_half(swnmg_ctx* c, int l, double* U, int forward) {
@@ -363,6 +372,7 @@ SWNMG_API swnmg_status swnmg_default_params(int32_t dim, swnmg_params* o) {
   o->init_mode = SWNMG_INIT_CASCADE;
   o->precision = SWNMG_PREC_FP64;
   o->eps_f = 0.4;
+  o->smoother = SWNMG_SMOOTH_LEX;
   return SWNMG_OK;
 }
 
@@ -618,8 +628,7 @@ SWNMG_API swnmg_status swnmg_sgs_sweep(swnmg_ctx* c, int32_t level, const double
   Level& v = c->lv[level];
   launch_to_skew(rhs, 0, v.b, c->fp32, c->nc, v.nx, v.ny, 1.0, c->st);
   launch_to_skew(x, 0, v.x, c->fp32, c->nc, v.nx, v.ny, 1.0, c->st);
-  launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward ? 1 : 0, c->fp32,
-                   c->sgs_sync, c->sticky, c->st);
+  sgs_launch(c, v, c->fp32, forward ? 1 : 0);
   launch_from_skew(v.x, c->fp32, x, 0, c->nc, v.nx, v.ny, 1.0, c->st);
   LAUNCH_CHECK(c);
   return check_sticky(c);

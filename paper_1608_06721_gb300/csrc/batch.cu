@@ -307,6 +307,8 @@ SWNMG_API swnmg_status swnmg_batch_create(const swnmg_problem* probs, const int3
   if (!probs || !n_levels || !prm || !z_dev || !out) return bfail(nullptr, SWNMG_ERR_ARG, "null pointer");
   *out = nullptr;
   if (B < 1 || B > BATCH_MAX) return bfail(nullptr, SWNMG_ERR_ARG, "batch size must be 1..256");
+  if (prm->smoother != SWNMG_SMOOTH_LEX)
+    return bfail(nullptr, SWNMG_ERR_ARG, "batches use the lexicographic block SGS smoother only");
   for (int p = 0; p < B; ++p) {
     if (probs[p].dim != 2) return bfail(nullptr, SWNMG_ERR_ARG, "batched problems must be 2D");
     if (n_levels[p] < 0 || n_levels[p] > 12) return bfail(nullptr, SWNMG_ERR_ARG, "bad n_levels");

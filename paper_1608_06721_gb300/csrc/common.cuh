@@ -200,6 +200,8 @@ void launch_prolong(int dim, int nc, int nxf, int nyf, const void* xc, void* xf,
 void launch_sgs_sweep(int nc, int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
                       const void* b, void* x, int forward, int fp32, int* sync, int* sticky_err,
                       cudaStream_t st);
+void launch_sgs_colour_sweep(int nc, int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
+                             const void* b, void* x, int forward, int fp32, cudaStream_t st);
 void launch_coarse_exact(int nc, int nx, int ny, const void* blk, const void* b, void* x,
                          double* band, int* err, int fp32, cudaStream_t st);
 void launch_coarse_inverse(int nc, int nx, int ny, const void* blk, void* aug, void* X, int* sing,

@@ -635,6 +635,56 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
   }
 }
 
+// ---- block Gauss-Seidel, two-colour variant (SWNMG_SMOOTH_COLOUR) ----------
+// Not the paper's smoother (Section 2.3 sweeps lexicographically): a variant
+// whose iterates differ, reported separately.  Cell (ix, iy) has colour
+// (ix + iy) & 1.  In the strip-skewed layout line d of strip s holds the
+// cells with ix + (iy & 31) = d, of colour (d + 32 s) & 1 = d & 1, so every
+// line is one colour.  One warp per line of the colour being updated: lane k
+// is row k of the strip; its west and east neighbours are lane k of lines
+// d - 1 and d + 1, its south and north neighbours lanes k - 1 and k + 1 of
+// those lines (across a strip edge: the neighbouring strip's edge row).
+// Every neighbour has the other colour, so the lines of one colour are
+// independent; each operator entry, b and x is read and x written as one
+// coalesced line.  The cell update is sgs_cell, the lexicographic
+// smoother's.
+template <int NC, typename T>
+__global__ void __launch_bounds__(256) k_sgs_colour(int nx, int ny, const T* __restrict__ blk,
+                                                    const T* __restrict__ lu, const int8_t* __restrict__ piv,
+                                                    const T* __restrict__ b, T* __restrict__ x, int colour,
+                                                    long long nlines) {
+  const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= nlines) return;
+  constexpr int BS = NC * NC;
+  const int lane = threadIdx.x & 31;
+  const int per = nx + 31;                    // lines per strip
+  const int half = (per - colour + 1) / 2;    // lines d = colour, colour + 2, ... of one strip
+  const int strip = (int)(w / half);
+  const int d = colour + 2 * (int)(w % half);
+  const int ix = d - lane, iy = strip * 32 + lane;
+  if (ix < 0 || ix >= nx || iy >= ny) return;
+  const long long P = skew_slots(nx, ny);
+  const long long slot = ((long long)strip * per + d) * 32 + lane;
+  const bool hW = ix > 0, hE = ix < nx - 1, hS = iy > 0, hN = iy < ny - 1;
+  T xw[NC], xe[NC], xs[NC], xn[NC], bb[NC], res[NC];
+  const long long sW = slot - 32, sE = slot + 32;
+  const long long sS = hS ? skew_pos(ix, iy - 1, nx) : slot, sN = hN ? skew_pos(ix, iy + 1, nx) : slot;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const T* xk = x + (long long)k * P;
+    xw[k] = hW ? xk[sW] : T(0);
+    xe[k] = hE ? xk[sE] : T(0);
+    xs[k] = hS ? xk[sS] : T(0);
+    xn[k] = hN ? xk[sN] : T(0);
+    bb[k] = b[(long long)k * P + slot];
+  }
+  const int es = (int)P;
+  sgs_cell<NC, T>(blk + (long long)BS * P + slot, blk + 2LL * BS * P + slot, blk + 3LL * BS * P + slot,
+                  blk + 4LL * BS * P + slot, es, lu + slot, piv[slot], bb, hW, xw, hE, xe, hS, xs, hN, xn, res);
+#pragma unroll
+  for (int k = 0; k < NC; ++k) x[(long long)k * P + slot] = res[k];
+}
+
 // ---- exact coarse solve: banded Gaussian elimination, partial pivoting -------
 // Unknowns cell-major (i*NC + s); lower bandwidth ml = NC*nx + NC - 1, upper
 // ml (mu) plus ml fill.  One CTA; a pivot <= 1e-14 max|A| leaves its unknown
@@ -1236,6 +1286,22 @@ void launch_sgs_sweep(int nc, int nx, int ny, const void* blk, const void* lu, c
     else { if (forward) SL(2, double, true); else SL(2, double, false); }
   }
 #undef SL
+}
+
+void launch_sgs_colour_sweep(int nc, int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
+                             const void* b, void* x, int forward, int fp32, cudaStream_t st) {
+  const int nstrips = (ny + 31) / 32, per = nx + 31;
+  for (int pass = 0; pass < 2; ++pass) {
+    count_launches(1);
+    const int colour = forward ? pass : 1 - pass;
+    const long long nlines = (long long)nstrips * ((per - colour + 1) / 2);
+    const int grid = (int)((nlines + 7) / 8);
+#define CL(NC, T) k_sgs_colour<NC, T><<<grid, 256, 0, st>>>(nx, ny, (const T*)blk, (const T*)lu, piv, \
+                                                             (const T*)b, (T*)x, colour, nlines)
+    if (nc == 3) { if (fp32) CL(3, float); else CL(3, double); }
+    else { if (fp32) CL(2, float); else CL(2, double); }
+#undef CL
+  }
 }
 
 void launch_coarse_exact(int nc, int nx, int ny, const void* blk, const void* b, void* x,

@@ -41,7 +41,7 @@ class Params(C.Structure):
                 ("n_levels", C.c_int32), ("n_mg", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
                 ("gamma", C.c_int32), ("coarse_sweeps", C.c_int32), ("max_newton", C.c_int32),
                 ("max_blusgs", C.c_int32), ("init_mode", C.c_int32), ("precision", C.c_int32),
-                ("eps_f", C.c_double)]
+                ("eps_f", C.c_double), ("smoother", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -45,6 +45,9 @@ PREC_FP64 = 0
 PREC_MIXED = 1     # FP32 multigrid inner solve, FP64 residual / update / norms
 PREC_MIXED_STEP1 = 2   # PREC_MIXED, and Step 1's coarse-level BLU-SGS in FP32
 
+SMOOTH_LEX = 0     # block SGS in lexicographic order (Section 2.3)
+SMOOTH_COLOUR = 1  # variant: two colours, (ix + iy) even then odd
+
 G = 9.81
 
 
@@ -79,6 +82,7 @@ class Params:
     init_mode: int = INIT_CASCADE
     precision: int = PREC_FP64
     eps_f: float = 0.4          # Harten's entropy-fix width (Roe flux)
+    smoother: int = SMOOTH_LEX  # block SGS order (Section 2.3: lexicographic)
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)

@@ -43,5 +43,5 @@ def test_struct_layouts_match_header():
     from paper_1608_06721_gb300 import swnmg
     assert C.sizeof(swnmg._BC) == 32
     assert C.sizeof(swnmg.Problem) == 3 * 4 + 4 + 5 * 8 + 4 * 32
-    assert C.sizeof(swnmg.Params) == 2 * 4 + 7 * 8 + 10 * 4 + 8
+    assert C.sizeof(swnmg.Params) == 2 * 4 + 7 * 8 + 10 * 4 + 8 + 8   # smoother + padding
     assert C.sizeof(swnmg.Stats) == 3 * 4 + 16 * 4 + 4 + 2 * 8 + 512 * 8 + 2 * 8

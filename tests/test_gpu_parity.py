@@ -282,3 +282,61 @@ def test_small_and_ragged_grids(swnmg, nx, ny):
     x = S.vcycle(_dev(-Ro), _dev(np.zeros_like(Ro)), 1).cpu().numpy()
     xo = o.vcycle(blk, -Ro, np.zeros_like(Ro), 1)
     assert np.abs(x - xo).max() <= 1e-11 * max(np.abs(xo).max(), 1e-300)
+
+
+# ---- the two-colour block SGS smoother (a variant, not the paper's) --------
+
+@pytest.mark.parametrize("name,prob,gen", CASES, ids=IDS)
+def test_colour_sgs_sweeps_and_cycles(swnmg, name, prob, gen):
+    """SWNMG_SMOOTH_COLOUR against the oracle with the same smoother: half-
+    sweeps on the finest and coarsest levels and 2 cycles (V and W) within
+    1e-12 relative."""
+    U = gen(prob)
+    for gamma in (1, 2):
+        p = prob.with_params(smoother=W.SMOOTH_COLOUR, gamma=gamma)
+        S = swnmg.Solver(p)
+        S.jacobian(_dev(U))
+        o = Oracle(p)
+        R, rn, blk = o.jacobian(U)
+        if gamma == 1:
+            H = o.hierarchy(blk)
+            rng = np.random.default_rng(19)
+            for l in (0, len(H) - 1):
+                n = S.level_cells(l)
+                b, x = rng.standard_normal((prob.ncomp, n)), rng.standard_normal((prob.ncomp, n))
+                for fwd in (True, False):
+                    xg = S.sgs_sweep(l, _dev(b), _dev(x), fwd).cpu().numpy()
+                    xo = o.sgs(l, H[l], b, x, forward=fwd)
+                    assert np.abs(xg - xo).max() <= 1e-12 * np.abs(xo).max(), (l, fwd)
+        x = np.zeros_like(R)
+        xg = _dev(x)
+        for k in range(2):
+            x = o.vcycle(blk, -R, x, 1)
+            S.vcycle(_dev(-R), xg, 1)
+            err = np.abs(xg.cpu().numpy() - x).max() / np.abs(x).max()
+            assert err <= 1e-12, (gamma, k, err)
+        S.close()
+
+
+COLOUR_SOLVES = [
+    ("channel_64", W.channel_2d(nx=64, ny=64)),
+    ("ex36_64x32", W.transcritical_bump_2d(64, 32)),
+    ("super_slip_64x32_hll", W.supercritical_channel_2d(64, 32, flux=W.FLUX_HLL)),
+    ("channel_bench_128", W.channel_bench(128, 128, W.PREC_FP64)),
+]
+
+
+@pytest.mark.parametrize("name,prob", COLOUR_SOLVES, ids=[s[0] for s in COLOUR_SOLVES])
+def test_colour_solve_fp64(swnmg, name, prob):
+    """Algorithm 1 with the two-colour smoother: the same Newton and Step 1
+    counts as the oracle run with that smoother, state within 1e-10."""
+    prob = prob.with_params(smoother=W.SMOOTH_COLOUR)
+    Uo, io = Oracle(prob).solve()
+    S = swnmg.Solver(prob)
+    Ug = _dev(prob.U0)
+    ig = S.solve(Ug)
+    assert io["status"] == 0 and ig["status"] == 0, (io["status"], ig["status"])
+    assert ig["n_newton"] == io["n_newton"]
+    assert ig["blusgs_sweeps"] == io["blusgs_sweeps"]
+    assert np.abs(Ug.cpu().numpy() - Uo).max() <= 1e-10 * np.abs(Uo).max()
+    S.close()

@@ -107,6 +107,32 @@ def test_c3_1024_wcycle(swnmg, c3, precision):
     S.close()
 
 
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_MIXED], ids=["fp64", "mixed"])
+def test_c3_1024_colour_sweeps_and_wcycle(swnmg, c3, precision):
+    """The two-colour smoother variant at 1024^2: level-0 half-sweeps and one
+    W-cycle against the oracle with the same smoother (FP64: 1e-12; mixed:
+    printed, bounded by 1e-4)."""
+    p = c3["p"].with_params(precision=precision, smoother=W.SMOOTH_COLOUR)
+    o = c3["o"].reconfigure(smoother=W.SMOOTH_COLOUR)
+    S = swnmg.Solver(p)
+    S.jacobian(_dev(c3["U"]))
+    R = c3["R"]
+    bar = 1e-12 if precision == W.PREC_FP64 else 1e-4
+    x0 = np.random.default_rng(41).standard_normal(R.shape)
+    for fwd in (True, False):
+        xo = o.sgs(0, c3["H"][0], -R, x0, forward=fwd)
+        xg = S.sgs_sweep(0, _dev(-R), _dev(x0), fwd).cpu().numpy()
+        err = np.abs(xg - xo).max() / np.abs(xo).max()
+        print("colour half-sweep %s %s: %.2e" % ("fwd" if fwd else "bwd", "fp64" if bar < 1e-6 else "mixed", err))
+        assert err <= bar, err
+    x = o.vcycle(c3["blk"], -R, np.zeros_like(R), 1)
+    xg = S.vcycle(_dev(-R), _dev(np.zeros_like(R)), 1).cpu().numpy()
+    err = np.abs(xg - x).max() / np.abs(x).max()
+    print("colour W-cycle %s: %.2e" % ("fp64" if bar < 1e-6 else "mixed", err))
+    assert err <= bar, err
+    S.close()
+
+
 @pytest.fixture(scope="module")
 def channel256():
     p = W.channel_bench(256, 256, W.PREC_FP64)

@@ -137,3 +137,54 @@ def test_coarse_solve_1d_is_exact():
     x = o.coarse_solve(2, H[2], b, np.zeros_like(b))
     A = dense.assemble(H[2], *dims[2])
     np.testing.assert_allclose(dense.vec(x), np.linalg.solve(A, dense.vec(b)), rtol=1e-11, atol=1e-13)
+
+
+# ------------------------------------------- two-colour smoother (variant)
+
+def _colour_perm(nx, ny, nc, first):
+    """Unknown permutation that lists the cells of colour `first` ((ix + iy)
+    mod 2), then the other colour, each in cell order."""
+    cells = [i for c in (first, 1 - first) for i in range(nx * ny) if ((i % nx) + (i // nx)) % 2 == c]
+    return np.array([i * nc + s for i in cells for s in range(nc)])
+
+
+def _colour_gs(A, nc, nx, ny, b, x, first):
+    """One block Gauss-Seidel sweep in the colour order, written as forward
+    Gauss-Seidel (D + L)^{-1}(b - U x) on the permuted system."""
+    p = _colour_perm(nx, ny, nc, first)
+    Ap = A[np.ix_(p, p)]
+    D, L, U = dense.split_blocks(Ap, nc)
+    y = np.linalg.solve(D + L, b[p] - U @ x[p])
+    out = np.empty_like(x)
+    out[p] = y
+    return out
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_colour_gauss_seidel_sweeps(dim):
+    """SWNMG_SMOOTH_COLOUR (not the paper's smoother): the forward sweep is
+    block Gauss-Seidel with colour 0 ((ix + iy) even) first, the backward
+    sweep with colour 1 first; inside a colour the cells decouple."""
+    p, ny, o, R, blk = _setup(dim)
+    o = o.reconfigure(smoother=W.SMOOTH_COLOUR)
+    nc = p.ncomp
+    A = dense.assemble(blk, p.nx, ny)
+    rng = np.random.default_rng(2)
+    b, x = rng.standard_normal((nc, p.n)), rng.standard_normal((nc, p.n))
+    for fwd, first in ((True, 0), (False, 1)):
+        xo = o.sgs(0, blk, b, x, forward=fwd)
+        xd = _colour_gs(A, nc, p.nx, ny, dense.vec(b), dense.vec(x), first)
+        np.testing.assert_allclose(dense.vec(xo), xd, rtol=1e-11, atol=1e-12)
+    # it is not the lexicographic sweep
+    assert np.abs(o.sgs(0, blk, b, x, forward=True) - Oracle(p).sgs(0, blk, b, x, forward=True)).max() > 1e-3
+
+
+@pytest.mark.parametrize("dim,gamma", [(1, 1), (2, 1), (2, 2)])
+def test_colour_cycles_converge_to_dense_solution(dim, gamma):
+    """Algorithm 0 with the two-colour smoother still converges to A^{-1} b."""
+    p, ny, o, R, blk = _setup(dim, gamma=gamma, coarse_sweeps=0)
+    o = o.reconfigure(smoother=W.SMOOTH_COLOUR)
+    A = dense.assemble(blk, p.nx, ny)
+    xe = np.linalg.solve(A, dense.vec(-R))
+    x = o.vcycle(blk, -R, np.zeros_like(R), 60)
+    assert np.abs(dense.vec(x) - xe).max() <= 1e-11 * np.abs(xe).max()
