@@ -255,6 +255,16 @@ SWNMG_API int64_t swnmg_launch_count(void);
  * before they exit.  Returns the previous limit. */
 SWNMG_API int32_t swnmg_set_wait_limit(int32_t polls);
 
+/* Measures the FP64 issue rate of the current device (a measurement utility
+ * with no counterpart in the paper; the roofline denominator of the kernels
+ * bound by the FP64 pipe).  op 0: independent chains of fused multiply-adds,
+ * op 1: of additions; eight chains per thread, eight blocks of 256 threads
+ * per SM, best of three timed launches after a warm-up (CUDA events on the
+ * legacy default stream).  *lane_ops_per_s receives the lane operations per
+ * second (an FMA counts once).  Synchronises the device; SWNMG_ERR_ARG for
+ * a bad op or a null pointer. */
+SWNMG_API swnmg_status swnmg_fp64_rate(int32_t op, double* lane_ops_per_s);
+
 /* The residual of swnmg_residual (eq. Res, same kernels, same bits) for
  * callers that cannot allocate device memory: code inside a runtime that
  * owns all device memory through its own pool, and loops that cannot take

@@ -23,6 +23,7 @@ UNITS = {
     "mg.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
+    "probe.cu": [],
     "batch.cu": [],
     "blusgs32.cu": [],
 }

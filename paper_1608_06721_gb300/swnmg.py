@@ -95,6 +95,8 @@ def lib():
         L.swnmg_batch_set_tuning.argtypes = [vp, C.POINTER(C.c_int32), C.c_int32]
         L.swnmg_level_cells.restype = C.c_int64
         L.swnmg_set_wait_limit.argtypes = [C.c_int32]
+        L.swnmg_fp64_rate.argtypes = [C.c_int32, C.POINTER(C.c_double)]
+        L.swnmg_fp64_rate.restype = C.c_int
         L.swnmg_set_wait_limit.restype = C.c_int32
         for f in ("swnmg_default_params", "swnmg_create", "swnmg_destroy", "swnmg_set_params",
                   "swnmg_residual", "swnmg_jacobian", "swnmg_get_blocks", "swnmg_vcycle",
@@ -439,6 +441,16 @@ def set_wait_limit(polls: int) -> int:
     """swnmg_set_wait_limit: polls of every device-side wait before a sweep
     gives up with ERR_TIMEOUT (<= 0: the default); returns the old limit."""
     return int(lib().swnmg_set_wait_limit(int(polls)))
+
+
+def fp64_rate(op: int = 1) -> float:
+    """swnmg_fp64_rate: measured FP64 lane operations per second of the
+    current device (op 0: FMA chains, op 1: additions)."""
+    v = C.c_double(0.0)
+    rc = lib().swnmg_fp64_rate(int(op), C.byref(v))
+    if rc != OK:
+        raise SwnmgError(rc, lib().swnmg_last_error(None).decode())
+    return v.value
 
 
 def default_params(dim: int) -> dict:
