@@ -9,12 +9,17 @@ coarsest level, N_mg = 3), eps_p = 2, tol 1e-10.
 
 One step = one complete swnmg_solve (Algorithm 1 including its Step 1) from
 the same initial state, with inputs resident in HBM.  value = cells x
-multigrid cycles / second over the timed steps; ms_per_step = time to
-sum ||R_i||_1 < 1e-10.  The FP64 path is timed on the same problem and
-reported beside it.  e2e repeats the mixed solve through host buffers
-(pinned H2D of the initial state, D2H of the steady state inside the timed
-region).  Multi-GPU: independent replicas (the lexicographic sweeps do not
-shard), weak scaling.
+multigrid cycles / second over the timed steps (no per-launch
+instrumentation inside them); ms_per_step = time to sum ||R_i||_1 < 1e-10.
+One instrumented solve after the timed steps gives each kernel class's
+device time (CUDA events around its launches) for the roofline entries.
+The FP64 path is timed on the same problem and reported beside it.  e2e
+repeats the mixed solve through host buffers (pinned H2D of the initial
+state, D2H of the steady state inside the timed region), three samples.
+The variants (FP32 Step 1, two-colour smoother) and the like-for-like line
+(the oracle's and the GPU's full solve of the 256^2 channel) are reported
+beside the headline.  Multi-GPU: independent replicas (the lexicographic
+sweeps do not shard), weak scaling.
 
 --impl reference times the CPU FP64 oracle (the reference restatement of the
 method) on a bounded sample of the same workload: one Newton step
@@ -119,45 +124,60 @@ def peaks():
     return 6800.0, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
 
 
-# FP64 unit peak of GB300: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz = 0.63e12
-# FP64 instructions/s (1.26 TFLOP/s counting an FMA as two); the flux
-# kernels are compiled without FMA contraction, so one counted add, mul,
-# div or sqrt is compared against one instruction slot.
-FP64_OPS_PEAK = 152 * 2 * 2.07e9
-
-
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per cell of one
-# launch, from ncu captures of one BLU-SGS and one SGS half-sweep of the
-# 512 x 512 channel; a launch's traffic grows with the cells it processes, so
-# it is scaled to the timed launches by their cell counts.  Both kernels
-# changed after those captures (the Roe flux, the Froude-number boundary and
-# the time-step term entered the BLU-SGS cell update; the SGS cell update
-# became one explicit-FMA function), so `traffic` is null until the next
-# capture, and the captured figure is kept as `traffic_previous_build`.
-TRAFFIC_PER_CELL = {"blusgs": 36.2, "blusgs_coarse": 36.2, "sgs_fine": 217.9, "sgs_coarse": 217.9}
-TRAFFIC_CURRENT = False
+# FP64 lane instructions (dadd + dmul + dfma, predicated on) and DRAM bytes
+# (dram__bytes_read.sum + dram__bytes_write.sum) per cell of one launch of each
+# kernel class, counted by ncu on the 512 x 512 channel (profiles/); a launch's
+# work grows with the cells it processes, so both are scaled to the timed
+# launches by their cell counts.  The FP64 counts include the instruction
+# sequences of the correctly rounded divisions and square roots: they are the
+# work as the GPU executes it, compared against the measured FP64 lane
+# instruction rate (swnmg_fp64_rate).  The SGS classes are HBM-bound kernels
+# whose algorithmic bytes per cell come from the operator layout (below).
+FP64_PER_CELL = {"residual": 181.1, "jacobian": 1380.5, "blusgs": 1485.8, "blusgs_coarse": 1485.8}
+TRAFFIC_PER_CELL = {"residual": 152.2, "jacobian": 782.6, "blusgs": 38.6, "blusgs_coarse": 38.6,
+                    "sgs_fine": 217.6, "sgs_coarse": 217.6}
+# the kernels of these classes are unchanged since the capture above
+TRAFFIC_CURRENT = {"residual", "jacobian", "blusgs", "blusgs_coarse", "sgs_fine", "sgs_coarse"}
 
 
 def algorithmic(cls, p, fp32):
-    """(bound, algorithmic units per cell) of a kernel class: bytes for the
-    block-SGS smoother, FP64 operations for the flux kernels.  One edge
-    evaluation (reconstruction, two reciprocals, two square roots, the flux
-    and the sources) is about 53 FP64 operations; a cell owns about 2.5 edge
-    evaluations in the residual (130), 7 per edge in the FD Jacobian (1035),
-    and a BLU-SGS cell update makes 16 plus a 3x3 elimination (1020).
-    Multiplied by the cells the timed launches processed, as reported by the
-    library."""
+    """(bound, algorithmic units per cell) of a kernel class: bytes of the
+    operator blocks, LU factors, pivot code, b, and x read and written for
+    the block-SGS smoother; counted FP64 lane instructions for the flux
+    kernels."""
     nc = p.ncomp
     w = 4 if fp32 else 8
     if cls in ("sgs_fine", "sgs_coarse"):
         return "hbm", (5 * nc * nc - nc * nc + 9 + 3 + 2 * nc) * w + 1   # blocks, LU, b, x in/out, piv
-    if cls in ("blusgs", "blusgs_coarse"):
-        return "alu", 1020.0
-    if cls == "jacobian":
-        return "alu", 1035.0
-    if cls == "residual":
-        return "alu", 130.0
+    if cls in FP64_PER_CELL:
+        return "alu", FP64_PER_CELL[cls]
     return None, None
+
+
+def roofline_entry(cls, timing, p, fp32, fp64_peak, hbm_peak, hbm_src):
+    """achieved / peak of one kernel class from its CUDA-event totals."""
+    ms, launches, cells = timing[cls]
+    if launches <= 0:
+        return None
+    bound, per_cell = algorithmic(cls, p, fp32)
+    if bound is None:
+        return None
+    avg_ms = ms / launches
+    cells_per_launch = cells / launches
+    units = per_cell * cells_per_launch
+    captured = TRAFFIC_PER_CELL[cls] * cells_per_launch if cls in TRAFFIC_PER_CELL else None
+    traffic = captured if cls in TRAFFIC_CURRENT else None
+    if bound == "hbm":
+        ach = units / (avg_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": cls, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": traffic, "peak_source": hbm_src + ", of measured",
+                "units_per_launch": units, "avg_launch_ms": avg_ms}
+    ach = units / (avg_ms * 1e-3) / 1e12
+    pk = fp64_peak / 1e12
+    return {"bound": "alu", "kernel": cls, "achieved": ach, "peak": pk,
+            "unit": "T FP64 lane instructions/s", "frac": ach / pk, "traffic": traffic,
+            "peak_source": "measured by swnmg_fp64_rate (chains of adds on every SM)",
+            "units_per_launch": units, "avg_launch_ms": avg_ms}
 
 
 # ---------------------------------------------------------------- ranks
@@ -198,7 +218,6 @@ def shard(items, rank, world):
 # ---------------------------------------------------------------- GPU arm
 
 def run_gpu(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
     from paper_1608_06721_gb300 import swnmg, workloads as W
@@ -220,67 +239,58 @@ def run_gpu(args):
     U = torch.empty_like(U0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
-    def one_solve():
-        U.copy_(U0)
-        info = S.solve(U)
+    def one_solve(solver, out):
+        out.copy_(U0)
+        info = solver.solve(out)
         if info["status"] != 0:
             raise RuntimeError("solve did not converge: %s" % info)
         return info
 
+    def timed(solver, out, k):
+        """k solves from U0 (each after an L2 flush), device ms from CUDA
+        events on the solver's stream."""
+        t, infos = 0.0, []
+        for _ in range(k):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(one_solve(solver, out))
+            e1.record(stream)
+            e1.synchronize()
+            t += e0.elapsed_time(e1)
+        return t, infos
+
     for _ in range(args.warmup):
-        one_solve()
+        one_solve(S, U)
     torch.cuda.synchronize()
-    S.set_timing(True)
+    # timed region: no per-launch instrumentation
     n0 = swnmg.lib().swnmg_launch_count()
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
     torch.cuda.synchronize()
-    total_ms, cycles, infos = 0.0, 0, []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        info = one_solve()
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        cycles += info["n_vcycles"]
-        infos.append(info)
+    total_ms, infos = timed(S, U, args.steps)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     launches = swnmg.lib().swnmg_launch_count() - n0
-    timing = S.get_timing()
-    S.set_timing(False)
+    cycles = sum(i["n_vcycles"] for i in infos)
     total_ms = max_over_ranks(total_ms, world, dev)
     value = world * p.n * cycles / (total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
 
-    # roofline of the dominant kernel class (live CUDA events on the solver's stream)
+    # per-kernel-class device time from one instrumented solve of the same
+    # workload after the timed steps (CUDA events around every launch)
+    hbm_peak, hbm_src = peaks()
+    fp64_peak = swnmg.fp64_rate(1)
+    S.set_timing(True)
+    one_solve(S, U)
+    timing = S.get_timing()
+    S.set_timing(False)
     dom = max((k for k in timing if timing[k][1] > 0), key=lambda k: timing[k][0])
-    bound, per_cell = algorithmic(dom, p, True)
-    roof = None
-    if bound is not None:
-        avg_ms = timing[dom][0] / timing[dom][1]
-        units = per_cell * timing[dom][2] / timing[dom][1]    # per launch
-        cells_per_launch = timing[dom][2] / timing[dom][1]
-        captured = TRAFFIC_PER_CELL[dom] * cells_per_launch if dom in TRAFFIC_PER_CELL else None
-        traffic = captured if TRAFFIC_CURRENT else None
-        if bound == "hbm":
-            pk, src = peaks()
-            ach = units / (avg_ms * 1e-3) / 1e9
-            roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk, "unit": "GB/s",
-                    "frac": ach / pk, "traffic": traffic, "traffic_previous_build": captured,
-                    "peak_source": src, "units_per_launch": units, "avg_launch_ms": avg_ms}
-        else:
-            ach = units / (avg_ms * 1e-3) / 1e12
-            pk = FP64_OPS_PEAK / 1e12
-            roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": pk,
-                    "unit": "TFLOP/s (FP64 ops, no FMA)", "frac": ach / pk, "traffic": traffic,
-                    "traffic_previous_build": captured,
-                    "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz",
-                    "units_per_launch": units, "avg_launch_ms": avg_ms}
+    roof = roofline_entry(dom, timing, p, True, fp64_peak, hbm_peak, hbm_src)
+    kernel_roofs = {k: roofline_entry(k, timing, p, True, fp64_peak, hbm_peak, hbm_src)
+                    for k in ("residual", "jacobian", "sgs_fine", "sgs_coarse", "blusgs", "blusgs_coarse")}
     total_dev = sum(v[0] for v in timing.values())
     shares = {k: {"ms": round(v[0], 3), "launches": v[1], "cells": v[2],
                   "share": round(v[0] / total_dev, 4) if total_dev else 0}
@@ -289,33 +299,21 @@ def run_gpu(args):
     # FP64 path on the same problem
     fp64 = None
     if args.fp64_steps > 0 and rank == 0:
-        p64 = workload(W.PREC_FP64, args.nx, args.nx)
-        S64 = swnmg.Solver(p64, stream=stream)
+        S64 = swnmg.Solver(workload(W.PREC_FP64, args.nx, args.nx), stream=stream)
         U64 = torch.empty_like(U0)
-        U64.copy_(U0)
-        S64.solve(U64)   # warm-up
-        t64, c64, n64 = 0.0, 0, 0
-        for _ in range(args.fp64_steps):
-            U64.copy_(U0)
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            i64 = S64.solve(U64)
-            e1.record(stream)
-            e1.synchronize()
-            t64 += e0.elapsed_time(e1)
-            c64 += i64["n_vcycles"]
-            n64 = i64["n_newton"]
+        one_solve(S64, U64)   # warm-up
+        t64, i64 = timed(S64, U64, args.fp64_steps)
+        c64 = sum(i["n_vcycles"] for i in i64)
         diff = float((U64 - U).abs().max() / U64.abs().max())
         fp64 = {"ms_per_step": t64 / args.fp64_steps, "cell_cycles_per_s": p.n * c64 / (t64 * 1e-3),
-                "n_newton": n64, "status": i64["status"], "max_rel_diff_mixed_vs_fp64": diff}
+                "n_newton": i64[-1]["n_newton"], "status": i64[-1]["status"], "max_rel_diff_mixed_vs_fp64": diff}
         S64.close()
 
     # end to end through the public API with host buffers
     hU0 = torch.empty(U0.shape, dtype=torch.float64, pin_memory=True)
     hU0.copy_(U0.cpu())
     hU = torch.empty_like(hU0).pin_memory()
-    e2e_ms, e2e_cycles = 0.0, 0
+    e2e_ms, e2e_cycles, e2e_samples = 0.0, 0, []
     for _ in range(max(1, args.e2e_steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -323,27 +321,109 @@ def run_gpu(args):
         info = S.solve(U)
         hU.copy_(U, non_blocking=True)
         torch.cuda.synchronize()
-        e2e_ms += (time.perf_counter() - t0) * 1e3
+        dt = (time.perf_counter() - t0) * 1e3
+        e2e_samples.append(round(dt, 2))
+        e2e_ms += dt
         e2e_cycles += info["n_vcycles"]
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
     e2e = {"value": world * p.n * e2e_cycles / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": int(hU0.numel() * 8), "d2h_bytes_per_step": int(hU.numel() * 8),
-           "ms_per_step": e2e_ms / max(1, args.e2e_steps)}
+           "ms_per_step": e2e_ms / max(1, args.e2e_steps), "samples_ms": e2e_samples}
+
+    variants = run_variants(args, p, U0, U, stream, timed, one_solve, fp64_peak, hbm_peak, hbm_src) \
+        if rank == 0 and args.variants else None
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (FP32 multigrid, FP64 residual/update)",
-           "data": "synthetic (seeded Gaussian-bump topography)", "config": config_dict(p, "256 MB flush between steps; working set > L2"),
+           "data": "synthetic (seeded Gaussian-bump topography)",
+           "config": config_dict(p, "256 MB flush between steps; working set > L2"),
            "newton_steps": infos[-1]["n_newton"], "cycles_per_solve": infos[-1]["n_vcycles"],
            "step1_blusgs_sweeps": infos[-1]["blusgs_sweeps"], "final_res": infos[-1]["final_res"],
            "fp64": fp64, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-           "roofline": roof, "kernels": shares}
+           "roofline": roof, "kernel_rooflines": kernel_roofs, "fp64_peak_lane_inst_per_s": fp64_peak,
+           "kernels": shares, "kernel_timing": "one instrumented solve after the timed steps",
+           "variants": variants}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_sample(args.nx, args.cpu_sample_steps)
+        if args.like_for_like:
+            out["like_for_like"] = like_for_like(args, stream)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_variants(args, p, U0, U, stream, timed, one_solve, fp64_peak, hbm_peak, hbm_src):
+    """Separately reported variants on the same problem, one solve each
+    after a warm-up: Step 1's coarse-level BLU-SGS in FP32, and the
+    two-colour block SGS smoother (its level-0 half-sweep roofline from one
+    instrumented solve)."""
+    import torch
+    from paper_1608_06721_gb300 import swnmg, workloads as W
+    out = {}
+    Uv = torch.empty_like(U0)
+    S1 = swnmg.Solver(workload(W.PREC_MIXED_STEP1, args.nx, args.nx), stream=stream)
+    one_solve(S1, Uv)
+    t, inf = timed(S1, Uv, 1)
+    out["step1_fp32"] = {"ms_per_step": t, "cell_cycles_per_s": p.n * inf[0]["n_vcycles"] / (t * 1e-3),
+                         "n_newton": inf[0]["n_newton"], "step1_blusgs_sweeps": inf[0]["blusgs_sweeps"],
+                         "max_rel_diff_vs_mixed": float((Uv - U).abs().max() / U.abs().max()),
+                         "precision": "Step 1 coarse-level BLU-SGS in FP32 (FD step 2^-12), else as mixed"}
+    S1.close()
+    pc = workload(W.PREC_MIXED, args.nx, args.nx).with_params(smoother=W.SMOOTH_COLOUR)
+    S2 = swnmg.Solver(pc, stream=stream)
+    one_solve(S2, Uv)
+    t, inf = timed(S2, Uv, 1)
+    S2.set_timing(True)
+    one_solve(S2, Uv)
+    tm = S2.get_timing()
+    S2.set_timing(False)
+    out["colour_smoother"] = {
+        "ms_per_step": t, "cell_cycles_per_s": p.n * inf[0]["n_vcycles"] / (t * 1e-3),
+        "n_newton": inf[0]["n_newton"], "cycles_per_solve": inf[0]["n_vcycles"],
+        "max_rel_diff_vs_mixed": float((Uv - U).abs().max() / U.abs().max()),
+        "sgs_fine_roofline": roofline_entry("sgs_fine", tm, pc, True, fp64_peak, hbm_peak, hbm_src),
+        "sgs_coarse_ms": round(tm["sgs_coarse"][0], 3), "sgs_fine_ms": round(tm["sgs_fine"][0], 3),
+        "smoother": "two colours (ix + iy) mod 2; not the paper's lexicographic order"}
+    out["colour_smoother"]["sgs_fine_roofline"]["traffic"] = None   # not captured by ncu
+    S2.close()
+    return out
+
+
+def like_for_like(args, stream):
+    """The same solve on both sides: the CPU oracle's time to sum ||R_i||_1 <
+    1e-10 on the 256^2 channel (benchmark parameters, one core) beside the
+    GPU's, FP64 and mixed."""
+    import numpy as np
+    import torch
+    from oracle.oracle import Oracle
+    from paper_1608_06721_gb300 import swnmg, workloads as W
+    n = 256
+    p = W.channel_bench(n, n, W.PREC_FP64)
+    t0 = time.perf_counter()
+    Uo, io = Oracle(p).solve()
+    cpu_s = time.perf_counter() - t0
+    out = {"workload": "2D partial-dry channel 256x256 (W-cycle, N_L = 5, exact coarsest, seed 301)",
+           "cpu_oracle_s": cpu_s, "cpu_cores": 1, "cpu_newton": io["n_newton"]}
+    for prec, key in ((W.PREC_FP64, "gpu_fp64_s"), (W.PREC_MIXED, "gpu_mixed_s")):
+        S = swnmg.Solver(p.with_params(precision=prec), stream=stream)
+        U0 = torch.as_tensor(p.U0, dtype=torch.float64, device="cuda").contiguous()
+        U = U0.clone()
+        S.solve(U)   # warm-up
+        U.copy_(U0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = S.solve(U)
+        e1.record(stream)
+        e1.synchronize()
+        out[key] = e0.elapsed_time(e1) * 1e-3
+        out[key.replace("_s", "_newton")] = info["n_newton"]
+        out[key.replace("_s", "_max_rel_diff_vs_oracle")] = float(np.abs(U.cpu().numpy() - Uo).max() / np.abs(Uo).max())
+        S.close()
+    out["speedup_fp64"] = cpu_s / out["gpu_fp64_s"]
+    out["speedup_mixed"] = cpu_s / out["gpu_mixed_s"]
+    return out
 
 
 # ---------------------------------------------------------------- batched workload
@@ -559,7 +639,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nx", type=int, default=NX)
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the FP32 Step 1 and two-colour smoother variant lines")
+    ap.add_argument("--no-like-for-like", dest="like_for_like", action="store_false",
+                    help="skip the oracle-vs-GPU full solve on the 256^2 channel")
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--levels", type=int, default=LEVELS)
