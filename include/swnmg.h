@@ -89,6 +89,11 @@ typedef struct {
  *   gamma         1: V-cycle, 2: W-cycle (Algorithm 0)
  *   coarse_sweeps 2D coarsest level: this many symmetric SGS sweeps
  *                 (1D coarsest levels are solved exactly)
+ *   eps_p         Step 1 stops on level l once sum_i ||R_{i,l}||_1 < eps_p 2^-l;
+ *                 eps_p < 0 selects the paper's rule (its remark on Step 1:
+ *                 about one percent of the initial data's residual), i.e.
+ *                 |eps_p| x sum_i ||R_i||_1 of the initial data on level 0
+ *                 (per problem in a batch)
  *   max_blusgs    cap of BLU-SGS sweeps per level in Step 1
  *   smoother      order of the block SGS smoother: SWNMG_SMOOTH_LEX (0, the
  *                 paper's lexicographic sweeps, Section 2.3) or

@@ -1054,12 +1054,17 @@ int orc_solve(const orc_cfg* c, const double* z0, double* U0, orc_stats* st) {
   memcpy(zl[0], z0, sizeof(double) * L0.n);
   for (int l = 0; l < NL; ++l) orc_average(c, l, 1, zl[l], zl[l + 1]);
 
-  /* Step 1: initial guess by BLU-SGS from the coarsest level up to level 1 */
+  /* Step 1: initial guess by BLU-SGS from the coarsest level up to level 1.
+   * eps_p < 0 selects the paper's rule for it (its remark on Step 1: about
+   * one percent of the residual of the initial data): |eps_p| times
+   * sum_i ||R_i||_1 of the initial data on the finest mesh. */
+  double eps_p = c->eps_p;
+  if (c->init_mode == INIT_CASCADE && NL > 0 && eps_p < 0.0) eps_p = -eps_p * orc_residual_sum(c, 0, zl[0], U0);
   if (c->init_mode == INIT_CASCADE && NL > 0) {
     memcpy(Ul[0], U0, sizeof(double) * (size_t)L0.n * nc);
     for (int l = 0; l < NL; ++l) orc_average(c, l, nc, Ul[l], Ul[l + 1]);
     for (int l = NL; l >= 1; --l) {
-      double thr = c->eps_p / (double)(1 << l);
+      double thr = eps_p / (double)(1 << l);
       double res = orc_residual_sum(c, l, zl[l], Ul[l]);
       int nsw = 0;
       while (res >= thr && nsw < c->max_blusgs && isfinite(res)) {

@@ -659,6 +659,13 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
   // Step 1: BLU-SGS from the coarsest level to level 1, piecewise-constant
   // prolongation of the solution (Algorithm 1)
   if (c->prm.init_mode == SWNMG_INIT_CASCADE && NL > 0) {
+    // eps_p < 0: the paper's rule, |eps_p| x sum_i ||R_i||_1 of the initial data
+    double eps_p = c->prm.eps_p;
+    if (eps_p < 0.0) {
+      double r0;
+      if ((s = level_residual_sum(c, 0, U, &r0)) != SWNMG_OK) return s;
+      eps_p = -eps_p * r0;
+    }
     const double* src = U;
     for (int l = 0; l < NL; ++l) {
       if (c->curv)   // the children weighted by their areas
@@ -669,7 +676,7 @@ SWNMG_API swnmg_status swnmg_solve(swnmg_ctx* c, double* U, swnmg_stats* stats) 
     }
     LAUNCH_CHECK(c);
     for (int l = NL; l >= 1; --l) {
-      const double thr = c->prm.eps_p / (double)(1 << l);
+      const double thr = eps_p / (double)(1 << l);
       double res;
       if ((s = level_residual_sum(c, l, c->lv[l].U, &res)) != SWNMG_OK) return s;
       int nsw = 0;

@@ -651,15 +651,23 @@ SWNMG_API swnmg_status swnmg_batch_solve(swnmg_batch* b, double* const* U, swnmg
   // Step 1: BLU-SGS from each problem's coarsest level to level 1 with
   // piecewise-constant prolongation (Algorithm 1)
   if (b->prm.init_mode == SWNMG_INIT_CASCADE && b->maxNL > 0) {
+    // eps_p < 0: the paper's rule per problem, |eps_p| x sum_i ||R_i||_1 of
+    // that problem's initial data
+    std::vector<double> eps(B, b->prm.eps_p);
+    if (b->prm.eps_p < 0.0) {
+      if ((s = residual_sums(b, 0, M_HAS + 0, res)) != SWNMG_OK) return s;
+      for (int p = 0; p < B; ++p) eps[p] = -b->prm.eps_p * res[p];
+    }
     for (int l = 0; l < b->maxNL; ++l) launch_b_average(bl(b, l + 1, D_CELLS, M_DOWN + l), tab(b, l), b->st);
     BCHECK(b);
     for (int l = b->maxNL; l >= 1; --l) {
-      const double thr = b->prm.eps_p / (double)(1 << l);
+      std::vector<double> thr(B);
+      for (int p = 0; p < B; ++p) thr[p] = eps[p] / (double)(1 << l);
       if ((s = residual_sums(b, l, M_HAS + l, res)) != SWNMG_OK) return s;
       std::vector<int> nsw(B, 0);
       int* casc = hm(b, M_CASC);
       for (int p = 0; p < B; ++p)
-        casc[p] = (l <= b->nl[p]) && res[p] >= thr && 0 < b->prm.max_blusgs && std::isfinite(res[p]);
+        casc[p] = (l <= b->nl[p]) && res[p] >= thr[p] && 0 < b->prm.max_blusgs && std::isfinite(res[p]);
       while (any_mask(b, M_CASC)) {
         if ((s = upload_mask_slot(b, M_CASC)) != SWNMG_OK) return s;
         blusgs(b, l, M_CASC, 1);
@@ -668,7 +676,7 @@ SWNMG_API swnmg_status swnmg_batch_solve(swnmg_batch* b, double* const* U, swnmg
         for (int p = 0; p < B; ++p) nsw[p] += casc[p];
         if ((s = residual_sums(b, l, M_CASC, res)) != SWNMG_OK) return s;
         for (int p = 0; p < B; ++p)
-          casc[p] = casc[p] && res[p] >= thr && nsw[p] < b->prm.max_blusgs && std::isfinite(res[p]);
+          casc[p] = casc[p] && res[p] >= thr[p] && nsw[p] < b->prm.max_blusgs && std::isfinite(res[p]);
       }
       for (int p = 0; p < B; ++p)
         if (l <= b->nl[p] && l < 16) stats[p].blusgs_sweeps[l] = nsw[p];

@@ -44,9 +44,11 @@ __device__ __forceinline__ double harten_q(double x, double ef) {
 // choice for the tangential flux, LLF (eq. LLFflux) with the optional wet/dry
 // speed increase, or Roe with Harten's entropy fix (eq. ROEflux: mean depth,
 // sqrt(h)-weighted velocities, waves u - c, u, u + c).  Both depths zero:
-// zero flux.
-__device__ void num_flux(const DevLevel& L, double hl, double ul, double vl, double hr, double ur,
-                         double vr, double F[3]) {
+// zero flux.  FX is the flux (compile time); num_flux below picks it at run
+// time, so every kernel evaluates the same operations.
+template <int FX>
+__device__ __forceinline__ void num_flux_t(const DevLevel& L, double hl, double ul, double vl, double hr,
+                                           double ur, double vr, double F[3]) {
   if (hl == 0.0 && hr == 0.0) {
     F[0] = 0.0; F[1] = 0.0; F[2] = 0.0;
     return;
@@ -57,7 +59,7 @@ __device__ void num_flux(const DevLevel& L, double hl, double ul, double vl, dou
   const double FL0 = ql, FL1 = ql * ul + hg * (hl * hl), FL2 = ql * vl;
   const double FR0 = qr, FR1 = qr * ur + hg * (hr * hr), FR2 = qr * vr;
   const double dU0 = hr - hl, dU1 = qr - ql, dU2 = hr * vr - hl * vl;   // U+ - U-
-  if (L.flux == FX_ROE) {
+  if constexpr (FX == FX_ROE) {
     const double ef = L.eps_f;
     const double sl = sqrt(hl), sr = sqrt(hr);
     const double rs = 1.0 / (sl + sr);
@@ -77,8 +79,7 @@ __device__ void num_flux(const DevLevel& L, double hl, double ul, double vl, dou
     F[1] = ((FL1 + FR1) - D1) * 0.5;
     F[2] = ((FL2 + FR2) - D2) * 0.5;
     return;
-  }
-  if (L.flux == FX_LLF) {
+  } else if constexpr (FX == FX_LLF) {
     double smax = dmax(fabs(ul) + cl, fabs(ur) + cr);
     // sqrt(g max(h-, h+)) equals max(sqrt(g h-), sqrt(g h+)) bit for bit:
     // scaling by g > 0 and the correctly rounded sqrt are both monotone
@@ -87,24 +88,33 @@ __device__ void num_flux(const DevLevel& L, double hl, double ul, double vl, dou
     F[1] = ((FL1 + FR1) - smax * dU1) * 0.5;
     F[2] = ((FL2 + FR2) - smax * dU2) * 0.5;
     return;
+  } else {
+    // u_* and sqrt(g h_*) = |t|/2 (h_* = t^2 / (4g))
+    const double us = ((ul + ur) * 0.5 + cl) - cr;
+    const double t = (cl + cr) + (ul - ur) * 0.5;
+    const double cs = fabs(t) * 0.5;
+    const double sL = (hl == 0.0) ? ur - 2.0 * cr : dmin(ul - cl, us - cs);
+    const double sR = (hr == 0.0) ? ul + 2.0 * cl : dmax(ur + cr, us + cs);
+    if (sL >= 0.0) { F[0] = FL0; F[1] = FL1; F[2] = FL2; return; }
+    if (sR <= 0.0) { F[0] = FR0; F[1] = FR1; F[2] = FR2; return; }
+    const double rden = 1.0 / (sR - sL), p = sL * sR;
+    F[0] = ((sR * FL0 - sL * FR0) + p * dU0) * rden;
+    F[1] = ((sR * FL1 - sL * FR1) + p * dU1) * rden;
+    F[2] = ((sR * FL2 - sL * FR2) + p * dU2) * rden;
+    if constexpr (FX == FX_HLLC) {
+      const double a = hr * (ur - sR), b = hl * (ul - sL);
+      const double sM = (sL * a - sR * b) / (a - b);
+      F[2] = (sM >= 0.0) ? vl * F[0] : vr * F[0];
+    }
   }
-  // u_* and sqrt(g h_*) = |t|/2 (h_* = t^2 / (4g))
-  const double us = ((ul + ur) * 0.5 + cl) - cr;
-  const double t = (cl + cr) + (ul - ur) * 0.5;
-  const double cs = fabs(t) * 0.5;
-  const double sL = (hl == 0.0) ? ur - 2.0 * cr : dmin(ul - cl, us - cs);
-  const double sR = (hr == 0.0) ? ul + 2.0 * cl : dmax(ur + cr, us + cs);
-  if (sL >= 0.0) { F[0] = FL0; F[1] = FL1; F[2] = FL2; return; }
-  if (sR <= 0.0) { F[0] = FR0; F[1] = FR1; F[2] = FR2; return; }
-  const double rden = 1.0 / (sR - sL), p = sL * sR;
-  F[0] = ((sR * FL0 - sL * FR0) + p * dU0) * rden;
-  F[1] = ((sR * FL1 - sL * FR1) + p * dU1) * rden;
-  F[2] = ((sR * FL2 - sL * FR2) + p * dU2) * rden;
-  if (L.flux == FX_HLLC) {
-    const double a = hr * (ur - sR), b = hl * (ul - sL);
-    const double sM = (sL * a - sR * b) / (a - b);
-    F[2] = (sM >= 0.0) ? vl * F[0] : vr * F[0];
-  }
+}
+
+__device__ void num_flux(const DevLevel& L, double hl, double ul, double vl, double hr, double ur,
+                         double vr, double F[3]) {
+  if (L.flux == FX_ROE) num_flux_t<FX_ROE>(L, hl, ul, vl, hr, ur, vr, F);
+  else if (L.flux == FX_LLF) num_flux_t<FX_LLF>(L, hl, ul, vl, hr, ur, vr, F);
+  else if (L.flux == FX_HLLC) num_flux_t<FX_HLLC>(L, hl, ul, vl, hr, ur, vr, F);
+  else num_flux_t<FX_HLL>(L, hl, ul, vl, hr, ur, vr, F);
 }
 
 // eq. totalFlux with the hydrostatic reconstruction; a is the lower-index
@@ -115,6 +125,18 @@ __device__ __forceinline__ void edge_eval(const DevLevel& L, Prim a, double za, 
   const double tl = (a.h + za) - zs, tr = (b.h + zb) - zs;
   const double hl = (tl > 0.0) ? tl : 0.0, hr = (tr > 0.0) ? tr : 0.0;
   num_flux(L, hl, a.u, a.v, hr, b.u, b.v, out);
+  out[3] = L.half_g * (hl * hl);
+  out[4] = L.half_g * (hr * hr);
+}
+
+// edge_eval with the flux fixed at compile time
+template <int FX>
+__device__ __forceinline__ void edge_eval_t(const DevLevel& L, Prim a, double za, Prim b, double zb,
+                                            double out[5]) {
+  const double zs = dmax(za, zb);
+  const double tl = (a.h + za) - zs, tr = (b.h + zb) - zs;
+  const double hl = (tl > 0.0) ? tl : 0.0, hr = (tr > 0.0) ? tr : 0.0;
+  num_flux_t<FX>(L, hl, a.u, a.v, hr, b.u, b.v, out);
   out[3] = L.half_g * (hl * hl);
   out[4] = L.half_g * (hr * hr);
 }
@@ -288,6 +310,38 @@ __device__ __forceinline__ void eval_edge_states(const DevLevel& L, int axis, co
   edge_G<NC>(o, axis, GL, GR);
 }
 
+// eval_edge_states with the cells' states held by reference and their
+// presence as flags (no pointer to a local array, which would force it into
+// local memory): the same operations
+template <int NC>
+__device__ __forceinline__ void eval_edge_flags(const DevLevel& L, int axis, bool hasL, const double (&cL)[NC],
+                                                double zL, bool hasR, const double (&cR)[NC], double zR,
+                                                double GL[NC], double GR[NC], const Frame* fr) {
+  Prim a, b;
+  double za = zL, zb = zR;
+  if (hasL && hasR) {
+    a = prim_edge<NC>(L, cL, axis, fr);
+    b = prim_edge<NC>(L, cR, axis, fr);
+  } else if (hasR) {
+    b = prim_edge<NC>(L, cR, axis, fr);
+    a = ghost_state(L, 2 * axis, b);
+    za = zR;
+  } else {
+    a = prim_edge<NC>(L, cL, axis, fr);
+    b = ghost_state(L, 2 * axis + 1, a);
+    zb = zL;
+  }
+  double o[5];
+  edge_eval(L, a, za, b, zb, o);
+  if constexpr (NC == 3) {
+    if (fr) {
+      edge_G_frame(o, *fr, GL, GR);
+      return;
+    }
+  }
+  edge_G<NC>(o, axis, GL, GR);
+}
+
 // edge e -> (axis, left cell, right cell, |e|); -1 marks a boundary side
 __device__ __forceinline__ void edge_cells(const DevLevel& L, int e, int n_xe, int& axis, int& iL,
                                            int& iR, double& len) {
@@ -333,7 +387,7 @@ __device__ __forceinline__ void st(void* p, long long idx, double v) {
 template <int NC>
 __device__ __forceinline__ void res_edge(const DevLevel& L, const double* __restrict__ z,
                                          const double* __restrict__ U, double* __restrict__ eb, int n_xe,
-                                         int n_e, int e) {
+                                         int n_e, int e, long long es, int el) {
   int axis, iL, iR;
   double len;
   edge_cells(L, e, n_xe, axis, iL, iR, len);
@@ -345,8 +399,8 @@ __device__ __forceinline__ void res_edge(const DevLevel& L, const double* __rest
   eval_edge_states<NC>(L, axis, iL >= 0 ? cL : nullptr, iL >= 0 ? z[iL] : 0.0,
                        iR >= 0 ? cR : nullptr, iR >= 0 ? z[iR] : 0.0, GL, GR, pf);
   for (int s = 0; s < NC; ++s) {
-    eb[s * (long long)n_e + e] = GL[s];
-    eb[(NC + s) * (long long)n_e + e] = GR[s];
+    eb[s * es + el] = GL[s];
+    eb[(NC + s) * es + el] = GR[s];
   }
 }
 
@@ -354,7 +408,7 @@ template <int NC>
 __global__ void k_res_edges(DevLevel L, const double* __restrict__ z, const double* __restrict__ U,
                             double* __restrict__ eb, int n_xe, int n_e) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n_e) res_edge<NC>(L, z, U, eb, n_xe, n_e, e);
+  if (e < n_e) res_edge<NC>(L, z, U, eb, n_xe, n_e, e, n_e, e);
 }
 
 // cell edges: W (x-edge, cell on the right), E (x-edge, left), S, N
@@ -391,10 +445,14 @@ __device__ __forceinline__ void time_residual(const DevLevel& L, const double* _
   for (int s = 0; s < NC; ++s) r[s] = (L.t_omb * r[s] + tka(L, i) * U[s * n + i]) - L.t_src[s * n + i];
 }
 
+// eb holds the edge pieces at eb[f * es + b], b in the edge numbering of
+// (bW, bE, bS, bN): the global one for the edge buffer, a tile's own for the
+// fused kernels
 template <int NC>
 __device__ __forceinline__ void res_cell(const DevLevel& L, const double* __restrict__ eb,
                                          const double* __restrict__ U, double* __restrict__ R,
-                                         double* __restrict__ rn, int n_xe, int n_e, int i) {
+                                         double* __restrict__ rn, int n_xe, int n_e, int i, long long es,
+                                         int bW, int bE, int bS, int bN) {
   int eW, eE, eS, eN;
   cell_edges(L, i, n_xe, eW, eE, eS, eN);
   const double lW = elen(L, eW, 0), lE = elen(L, eE, 0);
@@ -402,11 +460,11 @@ __device__ __forceinline__ void res_cell(const DevLevel& L, const double* __rest
   double r[NC];
   for (int s = 0; s < NC; ++s) {
     double a = 0.0;
-    a = a + lW * eb[(NC + s) * (long long)n_e + eW];
-    a = a + lE * eb[s * (long long)n_e + eE];
+    a = a + lW * eb[(NC + s) * es + bW];
+    a = a + lE * eb[s * es + bE];
     if (L.dim == 2) {
-      a = a + lS * eb[(NC + s) * (long long)n_e + eS];
-      a = a + lN * eb[s * (long long)n_e + eN];
+      a = a + lS * eb[(NC + s) * es + bS];
+      a = a + lN * eb[s * es + bN];
     }
     r[s] = a;
   }
@@ -423,7 +481,11 @@ template <int NC>
 __global__ void k_res_cells(DevLevel L, const double* __restrict__ eb, const double* __restrict__ U,
                             double* __restrict__ R, double* __restrict__ rn, int n_xe, int n_e) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < L.n) res_cell<NC>(L, eb, U, R, rn, n_xe, n_e, i);
+  if (i < L.n) {
+    int eW, eE, eS, eN;
+    cell_edges(L, i, n_xe, eW, eE, eS, eN);
+    res_cell<NC>(L, eb, U, R, rn, n_xe, n_e, i, n_e, eW, eE, eS, eN);
+  }
 }
 
 // ---- finite-difference Jacobian ---------------------------------------------
@@ -435,25 +497,27 @@ __global__ void k_res_cells(DevLevel L, const double* __restrict__ eb, const dou
 template <int NC, typename T>
 __device__ __forceinline__ void jac_edge(const DevLevel& L, const double* __restrict__ z,
                                          const double* __restrict__ U, double* __restrict__ eb,
-                                         void* __restrict__ blk, int n_xe, int n_e, int e) {
+                                         void* __restrict__ blk, int n_xe, int n_e, int e, long long es,
+                                         int el) {
   int axis, iL, iR;
   double len;
   edge_cells(L, e, n_xe, axis, iL, iR, len);
-  const long long ne = n_e, P = skew_slots(L.nx, L.ny);
+  const long long P = skew_slots(L.nx, L.ny);
   const long long sL = iL >= 0 ? skew_pos(iL % L.nx, iL / L.nx, L.nx) : 0;
   const long long sR = iR >= 0 ? skew_pos(iR % L.nx, iR / L.nx, L.nx) : 0;
   double cL[NC], cR[NC], GLb[NC], GRb[NC], GL[NC], GR[NC];
-  if (iL >= 0) load_c<NC>(U, L.n, iL, cL);
-  if (iR >= 0) load_c<NC>(U, L.n, iR, cR);
-  const double zL = iL >= 0 ? z[iL] : 0.0, zR = iR >= 0 ? z[iR] : 0.0;
-  const double* pL = iL >= 0 ? cL : nullptr;
-  const double* pR = iR >= 0 ? cR : nullptr;
+  const bool hL = iL >= 0, hR = iR >= 0;
+  for (int s = 0; s < NC; ++s) {
+    cL[s] = hL ? U[s * (long long)L.n + iL] : 0.0;
+    cR[s] = hR ? U[s * (long long)L.n + iR] : 0.0;
+  }
+  const double zL = hL ? z[iL] : 0.0, zR = hR ? z[iR] : 0.0;
   Frame fr;
   const Frame* pf = frame_of<NC>(L, e, axis, fr);
-  eval_edge_states<NC>(L, axis, pL, zL, pR, zR, GLb, GRb, pf);
+  eval_edge_flags<NC>(L, axis, hL, cL, zL, hR, cR, zR, GLb, GRb, pf);
   for (int s = 0; s < NC; ++s) {
-    eb[s * ne + e] = GLb[s];
-    eb[(NC + s) * ne + e] = GRb[s];
+    eb[s * es + el] = GLb[s];
+    eb[(NC + s) * es + el] = GRb[s];
   }
   const int f_dLL = 2 * NC, f_dRR = 2 * NC + NC * NC;
   const int bR = axis == 0 ? 1 : 3;   // block of the right cell pointing left (W / S)
@@ -462,17 +526,16 @@ __device__ __forceinline__ void jac_edge(const DevLevel& L, const double* __rest
   for (int k = 0; k < NC; ++k) {
     if (iL >= 0) {
       double c[NC];
-      for (int s = 0; s < NC; ++s) c[s] = cL[s];
-      c[k] = c[k] + L.eps;
-      eval_edge_states<NC>(L, axis, c, zL, pR, zR, GL, GR, pf);
+      for (int s = 0; s < NC; ++s) c[s] = (s == k) ? cL[s] + L.eps : cL[s];
+      eval_edge_flags<NC>(L, axis, true, c, zL, hR, cR, zR, GL, GR, pf);
       for (int s = 0; s < NC; ++s) {
-        eb[(f_dLL + s * NC + k) * ne + e] = len * ((GL[s] - GLb[s]) * L.reps);
+        eb[(f_dLL + s * NC + k) * es + el] = len * ((GL[s] - GLb[s]) * L.reps);
         if (iR >= 0) st<T>(blk, ((long long)(bR * NC * NC + s * NC + k)) * P + sR,
                            time_scale(L, len * ((GR[s] - GRb[s]) * L.reps)));
       }
     } else {
       for (int s = 0; s < NC; ++s) {
-        eb[(f_dLL + s * NC + k) * ne + e] = 0.0;
+        eb[(f_dLL + s * NC + k) * es + el] = 0.0;
         st<T>(blk, ((long long)(bR * NC * NC + s * NC + k)) * P + sR, 0.0);
       }
     }
@@ -481,17 +544,16 @@ __device__ __forceinline__ void jac_edge(const DevLevel& L, const double* __rest
   for (int k = 0; k < NC; ++k) {
     if (iR >= 0) {
       double c[NC];
-      for (int s = 0; s < NC; ++s) c[s] = cR[s];
-      c[k] = c[k] + L.eps;
-      eval_edge_states<NC>(L, axis, pL, zL, c, zR, GL, GR, pf);
+      for (int s = 0; s < NC; ++s) c[s] = (s == k) ? cR[s] + L.eps : cR[s];
+      eval_edge_flags<NC>(L, axis, hL, cL, zL, true, c, zR, GL, GR, pf);
       for (int s = 0; s < NC; ++s) {
-        eb[(f_dRR + s * NC + k) * ne + e] = len * ((GR[s] - GRb[s]) * L.reps);
+        eb[(f_dRR + s * NC + k) * es + el] = len * ((GR[s] - GRb[s]) * L.reps);
         if (iL >= 0) st<T>(blk, ((long long)(bL * NC * NC + s * NC + k)) * P + sL,
                            time_scale(L, len * ((GL[s] - GLb[s]) * L.reps)));
       }
     } else {
       for (int s = 0; s < NC; ++s) {
-        eb[(f_dRR + s * NC + k) * ne + e] = 0.0;
+        eb[(f_dRR + s * NC + k) * es + el] = 0.0;
         st<T>(blk, ((long long)(bL * NC * NC + s * NC + k)) * P + sL, 0.0);
       }
     }
@@ -502,7 +564,7 @@ template <int NC, typename T>
 __global__ void k_jac_edges(DevLevel L, const double* __restrict__ z, const double* __restrict__ U,
                             double* __restrict__ eb, void* __restrict__ blk, int n_xe, int n_e) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n_e) jac_edge<NC, T>(L, z, U, eb, blk, n_xe, n_e, e);
+  if (e < n_e) jac_edge<NC, T>(L, z, U, eb, blk, n_xe, n_e, e, n_e, e);
 }
 
 // Diagonal block D_i = sum_{W,E,S,N} dG + alpha ||R_i||_1 I (eq. NewtonREG),
@@ -511,21 +573,21 @@ template <int NC, typename T>
 __device__ __forceinline__ void jac_cell(const DevLevel& L, const double* __restrict__ eb,
                                          const double* __restrict__ U, double* __restrict__ R,
                                          double* __restrict__ rn, void* __restrict__ blk, int n_xe, int n_e,
-                                         int i) {
+                                         int i, long long es, int bW, int bE, int bS, int bN) {
   int eW, eE, eS, eN;
   cell_edges(L, i, n_xe, eW, eE, eS, eN);
-  const long long ne = n_e, n = L.n, P = skew_slots(L.nx, L.ny);
+  const long long n = L.n, P = skew_slots(L.nx, L.ny);
   const long long si = skew_pos(i % L.nx, i / L.nx, L.nx);
   const double lW = elen(L, eW, 0), lE = elen(L, eE, 0);
   const double lS = L.dim == 2 ? elen(L, eS, 1) : 0.0, lN = L.dim == 2 ? elen(L, eN, 1) : 0.0;
   double r[NC];
   for (int s = 0; s < NC; ++s) {
     double a = 0.0;
-    a = a + lW * eb[(NC + s) * ne + eW];
-    a = a + lE * eb[s * ne + eE];
+    a = a + lW * eb[(NC + s) * es + bW];
+    a = a + lE * eb[s * es + bE];
     if (L.dim == 2) {
-      a = a + lS * eb[(NC + s) * ne + eS];
-      a = a + lN * eb[s * ne + eN];
+      a = a + lS * eb[(NC + s) * es + bS];
+      a = a + lN * eb[s * es + bN];
     }
     r[s] = a;
   }
@@ -541,11 +603,11 @@ __device__ __forceinline__ void jac_cell(const DevLevel& L, const double* __rest
     for (int k = 0; k < NC; ++k) {
       const int f = s * NC + k;
       double d = 0.0;
-      d = d + eb[(f_dRR + f) * ne + eW];
-      d = d + eb[(f_dLL + f) * ne + eE];
+      d = d + eb[(f_dRR + f) * es + bW];
+      d = d + eb[(f_dLL + f) * es + bE];
       if (L.dim == 2) {
-        d = d + eb[(f_dRR + f) * ne + eS];
-        d = d + eb[(f_dLL + f) * ne + eN];
+        d = d + eb[(f_dRR + f) * es + bS];
+        d = d + eb[(f_dLL + f) * es + bN];
       }
       if (tm) {
         d = L.t_omb * d;
@@ -561,7 +623,83 @@ __global__ void k_jac_cells(DevLevel L, const double* __restrict__ eb, const dou
                             double* __restrict__ R, double* __restrict__ rn, void* __restrict__ blk, int n_xe,
                             int n_e) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < L.n) jac_cell<NC, T>(L, eb, U, R, rn, blk, n_xe, n_e, i);
+  if (i < L.n) {
+    int eW, eE, eS, eN;
+    cell_edges(L, i, n_xe, eW, eE, eS, eN);
+    jac_cell<NC, T>(L, eb, U, R, rn, blk, n_xe, n_e, i, n_e, eW, eE, eS, eN);
+  }
+}
+
+// ---- fused residual and Jacobian: one CTA per tile of TX x TY cells (2D) ---
+// The tile's edges (its cells' own and the ones on its border, which the
+// neighbouring tile evaluates as well) are evaluated into shared memory by
+// res_edge / jac_edge, then every cell sums its sides from there by
+// res_cell / jac_cell: the same operations in the same order as the two-pass
+// kernels above, without the per-edge pieces going through HBM.  Tile edge
+// numbering: the x-edges, TX + 1 per tile row, then the y-edges, TX per
+// edge row.  A CTA has NT >= TX * TY threads, so that the tile's edges take
+// two rounds (552 edges on 288 threads for 32 x 8 cells) instead of two and
+// a small third.  The Jacobian's off-diagonal blocks go straight to the level's
+// block arrays; a border edge's blocks are written by both tiles with the
+// same bits.
+template <int TX, int TY>
+__device__ __forceinline__ bool tile_edge(const DevLevel& L, int n_xe, int x0, int y0, int le, int& e) {
+  constexpr int NXE = (TX + 1) * TY;
+  if (le < NXE) {
+    const int gx = x0 + le % (TX + 1), gy = y0 + le / (TX + 1);
+    if (gx > L.nx || gy >= L.ny) return false;
+    e = gx + (L.nx + 1) * gy;
+    return true;
+  }
+  const int l2 = le - NXE;
+  const int gx = x0 + l2 % TX, gy = y0 + l2 / TX;
+  if (gx >= L.nx || gy > L.ny) return false;
+  e = n_xe + gx + L.nx * gy;
+  return true;
+}
+
+template <int TX, int TY>
+constexpr int tile_edges() { return (TX + 1) * TY + TX * (TY + 1); }
+
+template <int NC, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_res_tile(DevLevel L, const double* __restrict__ z,
+                                                      const double* __restrict__ U, double* __restrict__ R,
+                                                      double* __restrict__ rn, int n_xe, int n_e) {
+  constexpr int NXE = (TX + 1) * TY, NE = tile_edges<TX, TY>();
+  __shared__ double eb[2 * NC * NE];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  for (int le = threadIdx.x; le < NE; le += NT) {
+    int e;
+    if (tile_edge<TX, TY>(L, n_xe, x0, y0, le, e)) res_edge<NC>(L, z, U, eb, n_xe, n_e, e, NE, le);
+  }
+  __syncthreads();
+  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+  const int gx = x0 + lx, gy = y0 + ly;
+  if (ly < TY && gx < L.nx && gy < L.ny) {
+    const int bW = lx + (TX + 1) * ly, bS = NXE + lx + TX * ly;
+    res_cell<NC>(L, eb, U, R, rn, n_xe, n_e, gx + L.nx * gy, NE, bW, bW + 1, bS, bS + TX);
+  }
+}
+
+template <int NC, typename T, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_jac_tile(DevLevel L, const double* __restrict__ z,
+                                                      const double* __restrict__ U, double* __restrict__ R,
+                                                      double* __restrict__ rn, void* __restrict__ blk, int n_xe,
+                                                      int n_e) {
+  constexpr int NXE = (TX + 1) * TY, NE = tile_edges<TX, TY>();
+  extern __shared__ double ebj[];   // (2 NC + 2 NC^2) fields x NE edges
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  for (int le = threadIdx.x; le < NE; le += NT) {
+    int e;
+    if (tile_edge<TX, TY>(L, n_xe, x0, y0, le, e)) jac_edge<NC, T>(L, z, U, ebj, blk, n_xe, n_e, e, NE, le);
+  }
+  __syncthreads();
+  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+  const int gx = x0 + lx, gy = y0 + ly;
+  if (ly < TY && gx < L.nx && gy < L.ny) {
+    const int bW = lx + (TX + 1) * ly, bS = NXE + lx + TX * ly;
+    jac_cell<NC, T>(L, ebj, U, R, rn, blk, n_xe, n_e, gx + L.nx * gy, NE, bW, bW + 1, bS, bS + TX);
+  }
 }
 
 // ---- block solve with the same elimination as the reference definition -----
@@ -1021,6 +1159,200 @@ __global__ void __launch_bounds__(32) k_blusgs_strip(DevLevel L, const double* _
   }
 }
 
+// ---- BLU-SGS, strip-pipelined, 2D uniform mesh, flux fixed at compile time --
+// The schedule of k_blusgs_strip (one warp per strip of R = 2 rows, 16 lanes
+// per cell: side sd in W, E, S, N order times perturbation p = 0..3; strips
+// claimed by ticket; bounded waits on the previous strip's published
+// progress) and the same operations in the same order, so the sweeps are
+// bit-identical.  What changes is how the operands reach the lanes:
+//   * the two neighbours that are new in this sweep (the previous column and
+//     the previous row) come in registers: the previous column is the group's
+//     own last result, the previous row the result of the group below it in
+//     the warp, by shuffle; only the strip's first row loads its previous-row
+//     neighbour from global memory, after the progress wait;
+//   * the cell's own state and the two neighbours that are still old (the
+//     next column and row), the beds and the boundary ghosts do not change
+//     before the cell's update, so they are loaded one step ahead;
+//   * every lane computes its reciprocals itself (the same values a shared
+//     lane would broadcast), the side sums go through shared memory, and the
+//     perturbed component is chosen by selection, not by indexing.
+template <int FX>
+__global__ void __launch_bounds__(32) k_blusgs_lean(DevLevel L, const double* __restrict__ z, double* U,
+                                                    const double* __restrict__ gbuf, int forward, int* sync,
+                                                    int* sticky_err, int spin_limit) {
+  constexpr int NC = 3, NP = 4, GRP = 16, R = 2;
+  __shared__ double sv[R][GRP][NC];
+  __shared__ double ss[R][GRP];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / GRP, g = lane % GRP;
+  const int sd = g / NP, p = g % NP;
+  const int axis = sd >> 1, upper = sd & 1;
+  // the side's role in this sweep: 0 previous column, 1 next column,
+  // 2 previous row (new values), 3 next row (old values)
+  const int role = forward ? sd : (sd ^ 1);
+  const long long n = L.n;
+  const int nstrips = (L.ny + R - 1) / R;
+  const int glen = L.nx > L.ny ? L.nx : L.ny;
+  const double len = axis == 0 ? L.ex : L.ey;
+  const int src0 = lane - p;                 // the side's p = 0 lane
+  int* prog = sync + 2;
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(&sync[0], 1);
+    q = __shfl_sync(full, q, 0);
+    if (q >= nstrips) return;
+    const int rows = (L.ny - q * R < R) ? L.ny - q * R : R;
+    const int nsteps = L.nx + rows - 1;
+    const int rr = q * R + grp;              // this group's row, counted in sweep order
+    const bool row_ok = grp < rows;
+    const int iy = forward ? rr : L.ny - 1 - rr;
+    const bool has_py = rr > 0, has_ny = rr < L.ny - 1;
+    // operands of the group's next cell, loaded one step ahead
+    double ci[NC], cj[NC], zi = 0.0, zj = 0.0;
+    Prim gh{0.0, 0.0, 0.0};
+    auto fetch = [&](int c) {
+      const int ix = forward ? c : L.nx - 1 - c;
+      const int i = ix + L.nx * iy;
+      for (int k = 0; k < NC; ++k) ci[k] = __ldcg(&U[k * n + i]);
+      zi = z[i];
+      const bool has = role == 0 ? c > 0 : role == 1 ? c < L.nx - 1 : role == 2 ? has_py : has_ny;
+      int j = i;
+      if (sd == 0) j = i - 1;
+      else if (sd == 1) j = i + 1;
+      else if (sd == 2) j = i - L.nx;
+      else j = i + L.nx;
+      if (has) {
+        zj = z[j];
+        if (role == 1 || role == 3)
+          for (int k = 0; k < NC; ++k) cj[k] = __ldcg(&U[k * n + j]);
+      } else {                               // precomputed by ghost_prologue
+        const long long t3 = ((long long)(sd * glen + (sd < 2 ? iy : ix)) * NP + p) * 3;
+        gh.h = __ldcg(&gbuf[t3]);
+        gh.u = __ldcg(&gbuf[t3 + 1]);
+        gh.v = __ldcg(&gbuf[t3 + 2]);
+      }
+    };
+    if (row_ok && grp == 0) fetch(0);
+    double prevx[NC] = {0.0, 0.0, 0.0};      // the group's last result (new)
+    int known = 0;
+    for (int t = 0; t < nsteps; ++t) {
+      if (q > 0 && t < L.nx && known < t + 1) {   // the previous strip's last row at column t
+        int pg = 0, it = 0;
+        do {
+          if (lane == 0) {
+            pg = ld_acq(&prog[q - 1]);
+            if (pg < t + 1 && ld_acq(&sync[1])) pg = -1;
+          }
+          pg = __shfl_sync(full, pg, 0);
+          if (pg >= t + 1 || pg < 0) break;
+          __nanosleep(32);
+        } while (++it < spin_limit);
+        if (pg < t + 1) {
+          if (lane == 0) {
+            if (pg >= 0) atomicOr(sticky_err, 1);
+            atomicExch(&sync[1], 1);
+          }
+          return;
+        }
+        known = pg;
+      }
+      __syncwarp();   // lane 0's acquire before the other lanes' loads of that row
+      const int c = t - grp;
+      const bool act = row_ok && c >= 0 && c < L.nx;
+      const int ix = forward ? c : L.nx - 1 - c;
+      const int i = ix + L.nx * iy;
+      // the previous row's new values: the group below, or the previous strip
+      double py[NC];
+      for (int k = 0; k < NC; ++k) py[k] = __shfl_up_sync(full, prevx[k], GRP);
+      double G[NC] = {0.0, 0.0, 0.0};
+      if (act) {
+        const bool has = role == 0 ? c > 0 : role == 1 ? c < L.nx - 1 : role == 2 ? has_py : has_ny;
+        double cn[NC];
+        for (int k = 0; k < NC; ++k) cn[k] = role == 0 ? prevx[k] : cj[k];
+        if (role == 2 && has) {
+          if (grp > 0) {
+            for (int k = 0; k < NC; ++k) cn[k] = py[k];
+          } else {
+            const int j = forward ? i - L.nx : i + L.nx;
+            for (int k = 0; k < NC; ++k) cn[k] = __ldcg(&U[k * n + j]);
+          }
+        }
+        // this lane's perturbation of the cell (component p - 1 by eps)
+        double cp[NC];
+        for (int k = 0; k < NC; ++k) cp[k] = (k == p - 1) ? ci[k] + L.eps : ci[k];
+        Prim me;
+        me.h = cp[0];
+        const double qa = axis == 0 ? cp[1] : cp[2], qb = axis == 0 ? cp[2] : cp[1];
+        if (cp[0] >= L.h_eps) {
+          const double r = 1.0 / cp[0];
+          me.u = qa * r;
+          me.v = qb * r;
+        } else {
+          me.u = 0.0;
+          me.v = 0.0;
+        }
+        const Prim other = has ? to_prim(cn[0], axis == 0 ? cn[1] : cn[2], axis == 0 ? cn[2] : cn[1], L.h_eps) : gh;
+        const double zo = has ? zj : zi;
+        const Prim a = upper ? me : other, b = upper ? other : me;
+        const double za = upper ? zi : zo, zb = upper ? zo : zi;
+        double o[5], GL[NC], GR[NC];
+        edge_eval_t<FX>(L, a, za, b, zb, o);
+        edge_G<NC>(o, axis, GL, GR);
+        for (int k = 0; k < NC; ++k) G[k] = upper ? GL[k] : GR[k];
+      }
+      // p = 0 lanes hold |e| G, p = k+1 lanes column k of |e| dG/dU_i
+      for (int k = 0; k < NC; ++k) {
+        const double gb = __shfl_sync(full, G[k], src0);
+        sv[grp][g][k] = (p == 0) ? len * G[k] : len * ((G[k] - gb) * L.reps);
+      }
+      __syncwarp();
+      if (g < NC * NP) {   // entry (component g / NP, perturbation g % NP): sides in W, E, S, N order
+        const int es = g / NP, ep = g % NP;
+        double acc = 0.0;
+        for (int qs = 0; qs < 4; ++qs) acc = acc + sv[grp][qs * NP + ep][es];
+        ss[grp][g] = acc;
+      }
+      __syncwarp();
+      double un[NC] = {0.0, 0.0, 0.0};
+      if (act && g == 0) {
+        double Rs[NC], D[NC * NC];
+        for (int k = 0; k < NC; ++k) {
+          Rs[k] = ss[grp][k * NP];
+          for (int pp = 1; pp < NP; ++pp) D[k * NC + (pp - 1)] = ss[grp][k * NP + pp];
+        }
+        if (L.t_ka > 0.0) {   // time step (Remark 2.6): the step's residual and diagonal block
+          const double ka = tka(L, i);
+          for (int k = 0; k < NC; ++k) Rs[k] = (L.t_omb * Rs[k] + ka * ci[k]) - L.t_src[k * n + i];
+          for (int e = 0; e < NC * NC; ++e) D[e] = L.t_omb * D[e];
+          for (int k = 0; k < NC; ++k) D[k * NC + k] = D[k * NC + k] + ka;
+        }
+        double m = fabs(Rs[0]) + fabs(Rs[1]);
+        m = m + fabs(Rs[2]);
+        const double am = L.alpha * m;
+        for (int k = 0; k < NC; ++k) D[k * NC + k] = D[k * NC + k] + am;
+        double x[NC];
+        small_solve<NC>(D, Rs, x);
+        if (ci[0] < L.h_eps)   // dry at the start: momentum stays zero (Remark 2.5)
+          for (int k = 1; k < NC; ++k) x[k] = 0.0;
+        for (int k = 0; k < NC; ++k) un[k] = ci[k] - x[k];
+        if (un[0] < L.h_eps)
+          for (int k = 0; k < NC; ++k) un[k] = 0.0;
+        for (int k = 0; k < NC; ++k) U[k * n + i] = un[k];
+      }
+      for (int k = 0; k < NC; ++k) {
+        const double v = __shfl_sync(full, un[k], grp * GRP);
+        if (act) prevx[k] = v;
+      }
+      // operands of the next cell (its own state is still old: nobody else writes it)
+      if (row_ok && c + 1 >= 0 && c + 1 < L.nx) fetch(c + 1);
+      const int done = t - rows + 2;                  // columns completed by the last row
+      if (q + 1 < nstrips && done >= 1 && done <= L.nx && lane == (rows - 1) * GRP)
+        st_rel(&prog[q], done);   // orders this lane's store of the last row's cell
+    }
+  }
+}
+
 // ---- adjoint: lambda^T dR/dz and lambda^T dR/dq --------------------------------
 // Central differences (step delta) of the edge terms with respect to the bed of
 // either cell, contracted with lambda of both cells: cz[e] for the left cell's
@@ -1302,7 +1634,7 @@ __global__ void __launch_bounds__(128) kb_res_edges(BLaunch bl) {
   BATCH_PROLOGUE(bl)
   if (idx >= it->n_e) return;
   const DevLevel L = it->L;
-  res_edge<NC>(L, it->z, it->U, it->eb, it->n_xe, it->n_e, idx);
+  res_edge<NC>(L, it->z, it->U, it->eb, it->n_xe, it->n_e, idx, it->n_e, idx);
 }
 
 template <int NC>
@@ -1310,7 +1642,9 @@ __global__ void __launch_bounds__(128) kb_res_cells(BLaunch bl) {
   BATCH_PROLOGUE(bl)
   const DevLevel L = it->L;
   if (idx >= L.n) return;
-  res_cell<NC>(L, it->eb, it->U, it->R, it->rn, it->n_xe, it->n_e, idx);
+  int eW, eE, eS, eN;
+  cell_edges(L, idx, it->n_xe, eW, eE, eS, eN);
+  res_cell<NC>(L, it->eb, it->U, it->R, it->rn, it->n_xe, it->n_e, idx, it->n_e, eW, eE, eS, eN);
 }
 
 template <int NC, typename T>
@@ -1318,7 +1652,7 @@ __global__ void __launch_bounds__(128) kb_jac_edges(BLaunch bl) {
   BATCH_PROLOGUE(bl)
   if (idx >= it->n_e) return;
   const DevLevel L = it->L;
-  jac_edge<NC, T>(L, it->z, it->U, it->eb, it->blk, it->n_xe, it->n_e, idx);
+  jac_edge<NC, T>(L, it->z, it->U, it->eb, it->blk, it->n_xe, it->n_e, idx, it->n_e, idx);
 }
 
 template <int NC, typename T>
@@ -1326,7 +1660,9 @@ __global__ void __launch_bounds__(128) kb_jac_cells(BLaunch bl) {
   BATCH_PROLOGUE(bl)
   const DevLevel L = it->L;
   if (idx >= L.n) return;
-  jac_cell<NC, T>(L, it->eb, it->U, it->R, it->rn, it->blk, it->n_xe, it->n_e, idx);
+  int eW, eE, eS, eN;
+  cell_edges(L, idx, it->n_xe, eW, eE, eS, eN);
+  jac_cell<NC, T>(L, it->eb, it->U, it->R, it->rn, it->blk, it->n_xe, it->n_e, idx, it->n_e, eW, eE, eS, eN);
 }
 
 template <typename T>
@@ -1446,14 +1782,19 @@ static void edge_counts(const DevLevel& L, int& n_xe, int& n_e) {
   n_e = n_xe + (L.dim == 2 ? L.nx * (L.ny + 1) : 0);
 }
 
+// tile shapes of the fused 2D residual and Jacobian
+constexpr int RT_X = 32, RT_Y = 8, RT_T = 288;
+constexpr int JT_X = 32, JT_Y = 8, JT_T = 288;
+
 void launch_residual(const DevLevel& L, const double* z, const double* U, double* R, double* rn,
                      double* eb, cudaStream_t st) {
   count_launches(2);
   int n_xe, n_e;
   edge_counts(L, n_xe, n_e);
-  if (L.nc == 3) {
-    k_res_edges<3><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, n_xe, n_e);
-    k_res_cells<3><<<nblk(L.n, 256), 256, 0, st>>>(L, eb, U, R, rn, n_xe, n_e);
+  if (L.nc == 3) {   // 2D: fused tiles, the edge pieces stay in shared memory (eb unused)
+    count_launches(-1);
+    const dim3 grid((L.nx + RT_X - 1) / RT_X, (L.ny + RT_Y - 1) / RT_Y);
+    k_res_tile<3, RT_X, RT_Y, RT_T><<<grid, RT_T, 0, st>>>(L, z, U, R, rn, n_xe, n_e);
   } else {
     k_res_edges<2><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, n_xe, n_e);
     k_res_cells<2><<<nblk(L.n, 256), 256, 0, st>>>(L, eb, U, R, rn, n_xe, n_e);
@@ -1465,14 +1806,18 @@ void launch_jacobian(const DevLevel& L, const double* z, const double* U, double
   count_launches(2);
   int n_xe, n_e;
   edge_counts(L, n_xe, n_e);
-  if (L.nc == 3) {
-    if (fp32) {
-      k_jac_edges<3, float><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, blk, n_xe, n_e);
-      k_jac_cells<3, float><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, U, R, rn, blk, n_xe, n_e);
-    } else {
-      k_jac_edges<3, double><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, blk, n_xe, n_e);
-      k_jac_cells<3, double><<<nblk(L.n, 128), 128, 0, st>>>(L, eb, U, R, rn, blk, n_xe, n_e);
+  if (L.nc == 3) {   // 2D: fused tiles, the edge pieces stay in shared memory (eb unused)
+    count_launches(-1);
+    const dim3 grid((L.nx + JT_X - 1) / JT_X, (L.ny + JT_Y - 1) / JT_Y);
+    constexpr size_t smem = (size_t)(2 * 3 + 2 * 9) * tile_edges<JT_X, JT_Y>() * sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_jac_tile<3, float, JT_X, JT_Y, JT_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_jac_tile<3, double, JT_X, JT_Y, JT_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr_set = true;
     }
+    if (fp32) k_jac_tile<3, float, JT_X, JT_Y, JT_T><<<grid, JT_T, smem, st>>>(L, z, U, R, rn, blk, n_xe, n_e);
+    else k_jac_tile<3, double, JT_X, JT_Y, JT_T><<<grid, JT_T, smem, st>>>(L, z, U, R, rn, blk, n_xe, n_e);
   } else {
     if (fp32) {
       k_jac_edges<2, float><<<nblk(n_e, 128), 128, 0, st>>>(L, z, U, eb, blk, n_xe, n_e);
@@ -1504,7 +1849,13 @@ void launch_blusgs_strip(const DevLevel& L, const double* z, double* U, double* 
   // at most 16 warps per SM: more strips than that queue on the ticket
   const int grid = nstrips < 16 * nsm ? nstrips : 16 * nsm;
   const int spin = wait_limit();
-  if (L.nc == 3) {
+  if (L.nc == 3 && L.geo == nullptr) {   // 2D uniform mesh: the lean kernel, flux fixed at compile time
+    k_ghost_prologue<3, 4><<<gblocks, 128, 0, st>>>(L, U, gbuf);
+    if (L.flux == FX_LLF) k_blusgs_lean<FX_LLF><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
+    else if (L.flux == FX_HLLC) k_blusgs_lean<FX_HLLC><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
+    else if (L.flux == FX_ROE) k_blusgs_lean<FX_ROE><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
+    else k_blusgs_lean<FX_HLL><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
+  } else if (L.nc == 3) {
     k_ghost_prologue<3, 4><<<gblocks, 128, 0, st>>>(L, U, gbuf);
     k_blusgs_strip<3, 4, 16><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
   } else {

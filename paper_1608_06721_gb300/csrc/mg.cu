@@ -378,9 +378,13 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
   constexpr int NE = EX + NC;
   constexpr size_t STAGE = sgs_stage_bytes<NC, T, S>();
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  T* vals[2] = {reinterpret_cast<T*>(smem + 128), reinterpret_cast<T*>(smem + 128 + STAGE)};
-  int8_t* pvs[2] = {reinterpret_cast<int8_t*>(smem + 128 + (size_t)NE * S * 32 * sizeof(T)),
-                    reinterpret_cast<int8_t*>(smem + 128 + STAGE + (size_t)NE * S * 32 * sizeof(T))};
+  // staging buffer st at smem + 128 + st * STAGE: values, then the pivot codes.
+  // Addresses are formed by arithmetic on the shared array (not picked from an
+  // array of pointers), so every operand read stays a shared-memory load.
+  auto vals = [&](int st) { return reinterpret_cast<T*>(smem + 128 + (size_t)st * STAGE); };
+  auto pvs = [&](int st) {
+    return reinterpret_cast<int8_t*>(smem + 128 + (size_t)st * STAGE + (size_t)NE * S * 32 * sizeof(T));
+  };
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
   const long long P = skew_slots(nx, ny);
@@ -414,16 +418,16 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
     fence_proxy_async();
     mbar_expect_tx(&bar[st], vb * EX + xbytes * NC + (unsigned)(cnt * 32));
     for (int e = 0; e < NOFF; ++e)
-      bulk_g2s(vals[st] + (size_t)e * S * 32, blk + (long long)(BS + e) * P + off, vb, &bar[st]);
+      bulk_g2s(vals(st) + (size_t)e * S * 32, blk + (long long)(BS + e) * P + off, vb, &bar[st]);
     for (int e = 0; e < LU_E; ++e)
-      bulk_g2s(vals[st] + (size_t)(NOFF + e) * S * 32, lu + (long long)e * P + off, vb, &bar[st]);
+      bulk_g2s(vals(st) + (size_t)(NOFF + e) * S * 32, lu + (long long)e * P + off, vb, &bar[st]);
     for (int k = 0; k < NC; ++k)
-      bulk_g2s(vals[st] + (size_t)(EB + k) * S * 32, b + (long long)k * P + off, vb, &bar[st]);
+      bulk_g2s(vals(st) + (size_t)(EB + k) * S * 32, b + (long long)k * P + off, vb, &bar[st]);
     if (xbytes)
       for (int k = 0; k < NC; ++k)
-        bulk_g2s(vals[st] + (size_t)(EX + k) * S * 32 + (size_t)(xa - xlo) * 32,
+        bulk_g2s(vals(st) + (size_t)(EX + k) * S * 32 + (size_t)(xa - xlo) * 32,
                  x + (long long)k * P + (line_base + xa) * 32, xbytes, &bar[st]);
-    bulk_g2s(pvs[st], piv + off, (unsigned)(cnt * 32), &bar[st]);
+    bulk_g2s(pvs(st), piv + off, (unsigned)(cnt * 32), &bar[st]);
   };
   bool inflight[2] = {false, false};
   if (lane == 0) {
@@ -486,8 +490,8 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
     }
     parity[st] ^= 1u;
     inflight[st] = false;
-    const T* V = vals[st];
-    const int8_t* PV = pvs[st];
+    const T* V = vals(st);
+    const int8_t* PV = pvs(st);
     const int s0 = j * S, cnt = min(S, nsteps - s0);
     const long long dbase = line_base + (FWD ? s0 : nsteps_full - s0 - cnt);
     for (int s = s0; s < s0 + cnt; ++s) {

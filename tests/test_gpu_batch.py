@@ -135,3 +135,16 @@ def test_batched_channel_workload_subset(swnmg):
     infos = bt.solve(Us)
     for p in range(len(probs)):
         _same(infos[p], ref[p][1], Us[p].cpu().numpy(), ref[p][0])
+
+
+def test_batch_eps_p_rule_per_problem(swnmg):
+    """eps_p < 0 (the paper's rule) gives every problem of a batch its own
+    Step 1 thresholds from its own initial residual: each problem still ends
+    exactly as its single solve."""
+    probs = [p.with_params(eps_p=-0.01) for p in _mixed_batch(W.PREC_MIXED)]
+    ref = [_single(swnmg, p) for p in probs]
+    bt = swnmg.BatchSolver(probs)
+    Us = bt.states()
+    infos = bt.solve(Us)
+    for p in range(len(probs)):
+        _same(infos[p], ref[p][1], Us[p].cpu().numpy(), ref[p][0])

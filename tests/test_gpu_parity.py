@@ -189,6 +189,8 @@ SOLVES = [
     ("ex36_48x24_roe", W.transcritical_bump_2d(48, 24).with_params(flux=W.FLUX_ROE)),
     ("super_slip_128x64_hllc", W.supercritical_channel_2d(128, 64, n_levels=3)),
     ("super_slip_64x32_hll", W.supercritical_channel_2d(64, 32, flux=W.FLUX_HLL)),
+    # the paper's rule for eps_p (1 % of the initial data's residual)
+    ("channel_bench_128_rule", W.channel_bench(128, 128, W.PREC_FP64).with_params(eps_p=-0.01)),
 ]
 
 

@@ -177,6 +177,8 @@ def _step1(o, p):
     until sum_i ||R_{i,l}||_1 < eps_p 2^{-l}, injection to level l - 1, for
     l = N_L ... 1.  Returns the level-0 initial guess and the sweep counts."""
     NL, eps_p, cap = o.cfg.n_levels, o.cfg.eps_p, o.cfg.max_blusgs
+    if eps_p < 0:   # the paper's rule: a fraction of the initial data's residual
+        eps_p = -eps_p * o.residual_sum(p.U0)
     sizes = [(p.nx >> l, (p.ny >> l) if p.dim == 2 else 1) for l in range(NL + 1)]
     zs, Us = [np.asarray(p.z, dtype=float)], [np.asarray(p.U0, dtype=float)]
     for l in range(NL):
@@ -203,8 +205,10 @@ def _coarse_problem(p, l, z_l):
 @pytest.mark.parametrize("make", [lambda: W.smooth_subcritical_1d(64),
                                   lambda: W.wetdry_lake_1d(64),
                                   lambda: W.hill_wetdry_2d(32, 16, n_levels=2),
-                                  lambda: W.channel_2d(nx=32, ny=16, n_levels=2)],
-                         ids=["ex31", "ex33", "ex37_2d", "channel_2d"])
+                                  lambda: W.channel_2d(nx=32, ny=16, n_levels=2),
+                                  lambda: W.channel_2d(nx=32, ny=16, n_levels=2).with_params(eps_p=-0.01),
+                                  lambda: W.smooth_subcritical_1d(64).with_params(eps_p=-0.01)],
+                         ids=["ex31", "ex33", "ex37_2d", "channel_2d", "channel_2d_rule", "ex31_rule"])
 def test_step1_cascade_matches_restatement(make):
     """The oracle's Step 1 (orc_solve with no Newton step) equals the
     restated cascade: the same BLU-SGS sweep count on every level and the
