@@ -710,12 +710,20 @@ __global__ void __launch_bounds__(NT) k_jac_tile(DevLevel L, const double* __res
 // elimination's, operation by operation.
 template <int NC>
 __device__ __forceinline__ void small_solve(double m[NC * NC], const double b[NC], double x[NC]) {
-  double amax = 0.0;
+  // max |entry|, NaN entries counting as 0 (as in a running "if (a > amax)
+  // amax = a" from 0).  The bit patterns of non-negative doubles order like
+  // their values, so the maximum is taken on the integer pipe: |x| is x's
+  // pattern without the sign bit, and a NaN (pattern above infinity's) is
+  // replaced by 0.  The result is the same double, without a chain of FP64
+  // comparisons on the cell update's critical path.
+  unsigned long long amax_bits = 0ull;
 #pragma unroll
   for (int e = 0; e < NC * NC; ++e) {
-    const double a = fabs(m[e]);
-    if (a > amax) amax = a;
+    unsigned long long u = (unsigned long long)__double_as_longlong(m[e]) & 0x7fffffffffffffffull;
+    u = (u > 0x7ff0000000000000ull) ? 0ull : u;
+    amax_bits = (u > amax_bits) ? u : amax_bits;
   }
+  const double amax = __longlong_as_double((long long)amax_bits);
   const double tiny = 1e-14 * amax;
   int perm[NC];
   bool sing[NC];
@@ -723,13 +731,18 @@ __device__ __forceinline__ void small_solve(double m[NC * NC], const double b[NC
   for (int r = 0; r < NC; ++r) { perm[r] = r; sing[r] = false; }
 #pragma unroll
   for (int col = 0; col < NC; ++col) {
+    // the pivot row: "if (|a| > best)" over the rows below, compared on the
+    // magnitudes' bit patterns (a NaN on either side compares false, as in
+    // FP64); best is the chosen entry's magnitude, the same double
     int p = col;
-    double best = fabs(m[col * NC + col]);
+    unsigned long long kb = (unsigned long long)__double_as_longlong(m[col * NC + col]) & 0x7fffffffffffffffull;
 #pragma unroll
     for (int r = col + 1; r < NC; ++r) {
-      const double a = fabs(m[r * NC + col]);
-      if (a > best) { best = a; p = r; }
+      const unsigned long long ka =
+          (unsigned long long)__double_as_longlong(m[r * NC + col]) & 0x7fffffffffffffffull;
+      if (ka <= 0x7ff0000000000000ull && kb <= 0x7ff0000000000000ull && ka > kb) { kb = ka; p = r; }
     }
+    const double best = __longlong_as_double((long long)kb);
 #pragma unroll
     for (int r = col + 1; r < NC; ++r)
       if (r == p) {
@@ -1172,7 +1185,9 @@ __global__ void __launch_bounds__(32) k_blusgs_strip(DevLevel L, const double* _
 //     neighbour from global memory, after the progress wait;
 //   * the cell's own state and the two neighbours that are still old (the
 //     next column and row), the beds and the boundary ghosts do not change
-//     before the cell's update, so they are loaded one step ahead;
+//     before the cell's update, so they are loaded one step ahead, at the
+//     start of the previous step (double-buffered), where the load latency
+//     hides behind that step's flux and elimination;
 //   * every lane computes its reciprocals itself (the same values a shared
 //     lane would broadcast), the side sums go through shared memory, and the
 //     perturbed component is chosen by selection, not by indexing.
@@ -1208,14 +1223,18 @@ __global__ void __launch_bounds__(32) k_blusgs_lean(DevLevel L, const double* __
     const bool row_ok = grp < rows;
     const int iy = forward ? rr : L.ny - 1 - rr;
     const bool has_py = rr > 0, has_ny = rr < L.ny - 1;
-    // operands of the group's next cell, loaded one step ahead
+    // operands of the group's cell (ci ...) and of its next one (n*), the
+    // latter loaded during the current step
     double ci[NC], cj[NC], zi = 0.0, zj = 0.0;
     Prim gh{0.0, 0.0, 0.0};
+    double nci[NC], ncj[NC], nzi = 0.0, nzj = 0.0;
+    Prim ngh{0.0, 0.0, 0.0};
+    for (int k = 0; k < NC; ++k) { ci[k] = cj[k] = nci[k] = ncj[k] = 0.0; }
     auto fetch = [&](int c) {
       const int ix = forward ? c : L.nx - 1 - c;
       const int i = ix + L.nx * iy;
-      for (int k = 0; k < NC; ++k) ci[k] = __ldcg(&U[k * n + i]);
-      zi = z[i];
+      for (int k = 0; k < NC; ++k) nci[k] = __ldcg(&U[k * n + i]);
+      nzi = z[i];
       const bool has = role == 0 ? c > 0 : role == 1 ? c < L.nx - 1 : role == 2 ? has_py : has_ny;
       int j = i;
       if (sd == 0) j = i - 1;
@@ -1223,17 +1242,26 @@ __global__ void __launch_bounds__(32) k_blusgs_lean(DevLevel L, const double* __
       else if (sd == 2) j = i - L.nx;
       else j = i + L.nx;
       if (has) {
-        zj = z[j];
+        nzj = z[j];
         if (role == 1 || role == 3)
-          for (int k = 0; k < NC; ++k) cj[k] = __ldcg(&U[k * n + j]);
+          for (int k = 0; k < NC; ++k) ncj[k] = __ldcg(&U[k * n + j]);
       } else {                               // precomputed by ghost_prologue
         const long long t3 = ((long long)(sd * glen + (sd < 2 ? iy : ix)) * NP + p) * 3;
-        gh.h = __ldcg(&gbuf[t3]);
-        gh.u = __ldcg(&gbuf[t3 + 1]);
-        gh.v = __ldcg(&gbuf[t3 + 2]);
+        ngh.h = __ldcg(&gbuf[t3]);
+        ngh.u = __ldcg(&gbuf[t3 + 1]);
+        ngh.v = __ldcg(&gbuf[t3 + 2]);
       }
     };
-    if (row_ok && grp == 0) fetch(0);
+    auto advance = [&]() {   // the next cell's operands become the current ones
+      for (int k = 0; k < NC; ++k) { ci[k] = nci[k]; cj[k] = ncj[k]; }
+      zi = nzi;
+      zj = nzj;
+      gh = ngh;
+    };
+    if (row_ok && grp == 0) {
+      fetch(0);
+      advance();
+    }
     double prevx[NC] = {0.0, 0.0, 0.0};      // the group's last result (new)
     int known = 0;
     for (int t = 0; t < nsteps; ++t) {
@@ -1262,6 +1290,10 @@ __global__ void __launch_bounds__(32) k_blusgs_lean(DevLevel L, const double* __
       const bool act = row_ok && c >= 0 && c < L.nx;
       const int ix = forward ? c : L.nx - 1 - c;
       const int i = ix + L.nx * iy;
+      // operands of the next cell (its own state is still old: nobody else
+      // writes it before this group's next step)
+      const bool next_ok = row_ok && c + 1 >= 0 && c + 1 < L.nx;
+      if (next_ok) fetch(c + 1);
       // the previous row's new values: the group below, or the previous strip
       double py[NC];
       for (int k = 0; k < NC; ++k) py[k] = __shfl_up_sync(full, prevx[k], GRP);
@@ -1344,8 +1376,7 @@ __global__ void __launch_bounds__(32) k_blusgs_lean(DevLevel L, const double* __
         const double v = __shfl_sync(full, un[k], grp * GRP);
         if (act) prevx[k] = v;
       }
-      // operands of the next cell (its own state is still old: nobody else writes it)
-      if (row_ok && c + 1 >= 0 && c + 1 < L.nx) fetch(c + 1);
+      if (next_ok) advance();
       const int done = t - rows + 2;                  // columns completed by the last row
       if (q + 1 < nstrips && done >= 1 && done <= L.nx && lane == (rows - 1) * GRP)
         st_rel(&prog[q], done);   // orders this lane's store of the last row's cell

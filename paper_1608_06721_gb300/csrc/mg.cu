@@ -298,7 +298,7 @@ __global__ void k_prolong(int dim, int nc, int nxf, int nyf, const T* __restrict
 // word and the abort flag, waits (bounded) for its own copies in flight, and
 // returns; the other strips see the abort flag and return as well.
 // sync layout: [0] ticket, [1] abort, [2 .. 2+nstrips) progress.
-constexpr int SGS_PUBLISH = 4;
+constexpr int SGS_PUBLISH = 8;
 constexpr int SGS_PREFETCH = 4;   // columns of b / old x values loaded ahead
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
