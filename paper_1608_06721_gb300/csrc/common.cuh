@@ -58,7 +58,8 @@ struct DevLevel {
 // x2 = y2 inv22; x1 = (y1 - u12 x2) inv11; x0 = (y0 - u01 x1 - u02 x2) inv00.
 // Entries: 0 l10, 1 l20, 2 l21, 3 u01, 4 u02, 5 u12, 6 inv00, 7 inv11, 8 inv22
 // (inv = 0 marks a singular unknown whose correction is zero).
-// piv = p0 + 3 p1 + 9 p2 with P b = (b[p0], b[p1], b[p2]).
+// piv = p0 | p1 << 2 | p2 << 4 (2-bit fields, decoded with shifts) with
+// P b = (b[p0], b[p1], b[p2]).
 constexpr int LU_E = 9;
 
 inline int blk_entries(int nc) { return 5 * nc * nc; }

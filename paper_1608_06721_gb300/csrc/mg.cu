@@ -63,12 +63,12 @@ __device__ __forceinline__ void lu_factor_slot(int nx, int ny, const T* __restri
     lu[0 * P + i] = m[1][0]; lu[1 * P + i] = m[2 % NC][0]; lu[2 * P + i] = m[2 % NC][1];
     lu[3 * P + i] = m[0][1]; lu[4 * P + i] = m[0][2 % NC]; lu[5 * P + i] = m[1][2 % NC];
     lu[6 * P + i] = inv[0]; lu[7 * P + i] = inv[1]; lu[8 * P + i] = inv[2];
-    piv[i] = (int8_t)(perm[0] + 3 * perm[1] + 9 * perm[2]);
+    piv[i] = (int8_t)(perm[0] | (perm[1] << 2) | (perm[2] << 4));
   } else {
     lu[0 * P + i] = m[1][0]; lu[1 * P + i] = T(0); lu[2 * P + i] = T(0);
     lu[3 * P + i] = m[0][1]; lu[4 * P + i] = T(0); lu[5 * P + i] = T(0);
     lu[6 * P + i] = inv[0]; lu[7 * P + i] = inv[1]; lu[8 * P + i] = T(0);
-    piv[i] = (int8_t)(perm[0] + 3 * perm[1]);
+    piv[i] = (int8_t)(perm[0] | (perm[1] << 2));
   }
 }
 
@@ -93,7 +93,7 @@ template <typename T> __device__ __forceinline__ T pick3(const T* r, int p) {
 template <int NC, typename T>
 __device__ __forceinline__ void lu_apply_v(const T* __restrict__ L, int ls, int8_t pv, const T r[NC],
                                            T x[NC]) {
-  const int p0 = pv % 3, p1 = (pv / 3) % 3, p2 = pv / 9;
+  const int p0 = pv & 3, p1 = (pv >> 2) & 3, p2 = (pv >> 4) & 3;
   if (NC == 3) {
     const T y0 = pick3(r, p0);
     const T y1 = tfma(-L[0 * ls], y0, pick3(r, p1));
@@ -351,7 +351,9 @@ __host__ __device__ constexpr size_t sgs_stage_bytes() {
 }
 
 template <int NC, typename T, int S>
-size_t sgs_smem_bytes() { return 128 + 2 * sgs_stage_bytes<NC, T, S>(); }
+size_t sgs_smem_bytes() {   // barriers, two staging buffers, two groups of the previous strip's row
+  return 128 + 2 * sgs_stage_bytes<NC, T, S>() + 2 * SGS_PUBLISH * NC * sizeof(T);
+}
 
 // bounded wait of every lane for one chunk; warp-uniform result, false when
 // the bound expired for some lane
@@ -462,23 +464,23 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
     for (int k = 0; k < NC; ++k) rn[t][k] = T(0);
     if (nedge && rowok && hasN && t - lagk >= 0 && t - lagk < nx) load_north(t - lagk, rn[t]);
   }
-  // the previous strip's last row for the lag-0 lane: the current group of
-  // SGS_PUBLISH columns (sc) and, once published, the next one (sn)
-  T sc[SGS_PUBLISH][NC], sn[SGS_PUBLISH][NC];
-#pragma unroll
-  for (int t = 0; t < SGS_PUBLISH; ++t)
-#pragma unroll
-    for (int k = 0; k < NC; ++k) { sc[t][k] = T(0); sn[t][k] = T(0); }
+  // the previous strip's last row for the lag-0 lane, SGS_PUBLISH columns at
+  // a time: the current group and, once published, the next one, in two
+  // shared-memory buffers after the staging ring.  That lane alone writes
+  // and reads them, and a column's values are picked by index (not by a
+  // chain of selections).
+  T* sgrp = reinterpret_cast<T*>(smem + 128 + 2 * STAGE);
+  int gcur = 0;
   bool have_next = false;
   const int poller = FWD ? 0 : 31;   // the lag-0 lane
-  auto load_group = [&](int c0, T g[SGS_PUBLISH][NC]) {
+  auto load_group = [&](int c0, int buf) {
 #pragma unroll
     for (int t = 0; t < SGS_PUBLISH; ++t)
       if (c0 + t < nx) {
         const int pxt = FWD ? c0 + t : nx - 1 - (c0 + t);
         const long long jj = skew_pos(pxt, yS, nx);
 #pragma unroll
-        for (int k = 0; k < NC; ++k) g[t][k] = __ldcg(&x[k * P + jj]);
+        for (int k = 0; k < NC; ++k) sgrp[(buf * SGS_PUBLISH + t) * NC + k] = __ldcg(&x[k * P + jj]);
       }
   };
   for (int j = 0; j < nchunks && !failed; ++j) {
@@ -505,10 +507,7 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
       if (q > 0 && s < nx && (s & (SGS_PUBLISH - 1)) == 0) {
         // group start of the lag-0 lane (column s): its south values
         if (have_next) {
-#pragma unroll
-          for (int t = 0; t < SGS_PUBLISH; ++t)
-#pragma unroll
-            for (int k = 0; k < NC; ++k) sc[t][k] = sn[t][k];
+          gcur ^= 1;
           have_next = false;
         } else {
           const int need = min(s + SGS_PUBLISH, nx);
@@ -530,7 +529,7 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
             }
             known = pg;
           }
-          if (lane == poller && hasS) load_group(s, sc);
+          if (lane == poller && hasS) load_group(s, gcur);
         }
         // the next group too, if the previous strip has already published it
         const int need2 = min(s + 2 * SGS_PUBLISH, nx);
@@ -542,7 +541,7 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
             if (pg > known) known = pg;
           }
           if (known >= need2) {
-            if (lane == poller && hasS) load_group(s + SGS_PUBLISH, sn);
+            if (lane == poller && hasS) load_group(s + SGS_PUBLISH, gcur ^ 1);
             have_next = true;
           }
         }
@@ -550,10 +549,7 @@ __device__ __forceinline__ bool sgs_strip_run(int nx, int ny, const T* __restric
       if (act) {
         if (lagk == 0 && hasS) {   // south value from the previous strip
 #pragma unroll
-          for (int t = 0; t < SGS_PUBLISH; ++t)
-            if ((c & (SGS_PUBLISH - 1)) == t)
-#pragma unroll
-              for (int k = 0; k < NC; ++k) xS[k] = sc[t][k];
+          for (int k = 0; k < NC; ++k) xS[k] = sgrp[(gcur * SGS_PUBLISH + (c & (SGS_PUBLISH - 1))) * NC + k];
         }
         const T* Vl = V + line * 32 + lane;
         const int ES = S * 32;   // stride between entries in the stage
