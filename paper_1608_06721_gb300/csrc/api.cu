@@ -196,8 +196,8 @@ void sgs_launch(swnmg_ctx* c, const Level& v, int fp32, int forward) {
   if (c->prm.smoother == SWNMG_SMOOTH_COLOUR)
     launch_sgs_colour_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward, fp32, c->st);
   else
-    launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward, fp32, c->sgs_sync, c->sticky,
-                     c->st);
+    launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward, fp32, c->sgs_sync, c->sgs_edge,
+                     ++c->sgs_epoch, c->sticky, c->st);
 }
 
 void sgs_half(swnmg_ctx* c, const Hier& H, int l, int forward) {
@@ -336,6 +336,7 @@ void free_ctx(swnmg_ctx* c) {
   if (c->csing) cudaFree(c->csing);
   if (c->derr) cudaFree(c->derr);
   if (c->sgs_sync) cudaFree(c->sgs_sync);
+  if (c->sgs_edge) cudaFree(c->sgs_edge);
   if (c->blu_sync) cudaFree(c->blu_sync);
   if (c->sticky) cudaFree(c->sticky);
   if (c->ghost) cudaFree(c->ghost);
@@ -455,6 +456,12 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
     ALLOC(c->red, 1032 * sizeof(double));
     ALLOC(c->derr, sizeof(int));
     ALLOC(c->sgs_sync, sizeof(int) * (2 + (v0.ny + 31) / 32 + 8));
+    ALLOC(c->sgs_edge, sizeof(unsigned long long) * (size_t)((v0.ny + 31) / 32) * v0.nx * c->nc * 2);
+    if (cudaMemset(c->sgs_edge, 0, sizeof(unsigned long long) * (size_t)((v0.ny + 31) / 32) * v0.nx * c->nc * 2) !=
+        cudaSuccess) {
+      rc = fail(c, SWNMG_ERR_CUDA, "memset of the SGS hand-off words");
+      goto fail_out;
+    }
     ALLOC(c->blu_sync, sizeof(int) * (2 + (v0.ny + 1) / 2 + 8));   // 2-row strips
     ALLOC(c->sticky, sizeof(int));
     ALLOC(c->ghost, sizeof(double) * 4 * (size_t)std::max(v0.nx, v0.ny) * (c->nc + 1) * 3);

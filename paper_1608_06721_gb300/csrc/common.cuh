@@ -198,9 +198,12 @@ void launch_restrict(int dim, int nc, int nxf, int nyf, const void* blk, const v
                      const void* x, void* bcoarse, int fp32, cudaStream_t st);
 void launch_prolong(int dim, int nc, int nxf, int nyf, const void* xc, void* xf, int fp32,
                     cudaStream_t st);
+// edge: tagged last-row words of the strips, (ny/32 rounded up) * nx * nc * 2
+// entries at least, for the warp-specialised kernel (NULL: the one-warp strip
+// kernel); epoch: differs from every earlier launch's on the same edge buffer
 void launch_sgs_sweep(int nc, int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
-                      const void* b, void* x, int forward, int fp32, int* sync, int* sticky_err,
-                      cudaStream_t st);
+                      const void* b, void* x, int forward, int fp32, int* sync, unsigned long long* edge,
+                      unsigned epoch, int* sticky_err, cudaStream_t st);
 void launch_sgs_colour_sweep(int nc, int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
                              const void* b, void* x, int forward, int fp32, cudaStream_t st);
 void launch_coarse_exact(int nc, int nx, int ny, const void* blk, const void* b, void* x,

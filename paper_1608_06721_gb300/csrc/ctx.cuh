@@ -58,6 +58,10 @@ struct swnmg_ctx {
   double* mesh = nullptr;
   double* kai = nullptr;
   int* sgs_sync = nullptr;  // ticket / abort / per-strip progress of the wavefront sweeps
+  // tagged last-row words of the SGS strips (level-0 strips x nx x nc x 2) and
+  // the epoch of the last SGS launch (every launch takes the next one)
+  unsigned long long* sgs_edge = nullptr;
+  unsigned sgs_epoch = 0;
   int* blu_sync = nullptr;  // ticket / abort / per-strip progress of the BLU-SGS strip sweep
   int* sticky = nullptr;    // set by a device wait that ran out of its bound
   double* hbuf = nullptr;   // pinned host scalars

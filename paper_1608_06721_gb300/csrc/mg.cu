@@ -635,6 +635,445 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
   }
 }
 
+// ---- block SGS half-sweep, warp-specialised strip kernel -------------------
+// The sweep, the cell order and the cell arithmetic (sgs_cell) of k_sgs_strip,
+// with everything that is not on the sweep's dependency chain taken off the
+// warp that updates the cells.  One CTA of two warps per strip in flight:
+//   warp 0 (compute) updates the strip's 32 rows, one skewed line per step,
+//     reading its operands from shared memory only;
+//   warp 1 (loader) stages the operator chunks into the two shared buffers
+//     (cp.async.bulk, mbarrier completion; the compute warp hands a buffer
+//     back through a second mbarrier), loads the old values of the row beyond
+//     the strip's last row (the next strip's first row in sweep order) into a
+//     shared ring, and moves the previous strip's new last-row values into a
+//     second ring.
+// Hand-off between strips without fences: the strip's last lane writes every
+// new value of its row as 64-bit words, each holding 32 bits of the value and
+// the launch's epoch (a counter that differs between launches).  The next
+// strip's loader polls these words and takes a column once all of its words
+// carry the current epoch; a word is written and read in one access, so a
+// value never arrives without its tag.  On a GB300 a release store costs about
+// a microsecond, several cell updates of this kernel.
+// Every wait is bounded.  On expiry the kernel sets the sticky error word and
+// the abort word, lets its own bulk copies in flight land (bounded), and
+// returns; the other CTAs see the abort word and return as well.
+// sync: [0] ticket, [1] abort.  edge: (strip q, column c, word w) at
+// (q * nx + c) * WPC + w, WPC = NC * sizeof(T) / 4.
+constexpr int SGS_RING = 32;   // columns held by each shared ring
+
+__device__ __forceinline__ int lds_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts_release(int* p, int v) {
+  asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_tagged(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_tagged(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// 32-bit pieces of a value: one for float, two (low, high) for double
+template <typename T> struct Words;
+template <> struct Words<float> {
+  static constexpr int N = 1;
+  __device__ static unsigned get(float v, int) { return __float_as_uint(v); }
+};
+template <> struct Words<double> {
+  static constexpr int N = 2;
+  __device__ static unsigned get(double v, int h) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return h ? (unsigned)(u >> 32) : (unsigned)u;
+  }
+};
+
+__host__ __device__ constexpr int pow2_floor(int v) { return v >= 32 ? 32 : v >= 16 ? 16 : v >= 8 ? 8 : v >= 4 ? 4 : v >= 2 ? 2 : 1; }
+
+template <int NC, typename T>
+struct SgsWs {
+  static constexpr int WPC = NC * Words<T>::N;         // tagged words per column
+  static constexpr int GS = pow2_floor(32 / WPC);      // previous-strip columns polled at once
+  static constexpr int GN = pow2_floor(32 / NC);       // north columns loaded at once
+  // control block (the first 128 bytes): full[2], empty[2] mbarriers in
+  // bytes 0-31, then these int slots (indices into the block as int[32])
+  static constexpr int Q = 8, SOUTH = 9, NORTH = 10, LEAD = 11, TRAIL = 12, FAIL = 13, ISSUED = 14;
+  static_assert(Q * 4 >= 32 && ISSUED * 4 + 4 <= 128, "control slots must sit between the barriers and byte 128");
+  static_assert(GS * WPC <= 32 && GN * NC <= 32 && 2 * GS <= SGS_RING && 2 * GN <= SGS_RING, "ring groups");
+};
+
+template <int NC, typename T, int S>
+size_t sgs_ws_smem_bytes() {   // control block, two staging buffers, two rings
+  return 128 + 2 * sgs_stage_bytes<NC, T, S>() + 2 * (size_t)SGS_RING * NC * sizeof(T);
+}
+
+// warp 0 of k_sgs_ws: the strip's cell updates, operands from shared memory.
+// waited counts the chunks whose staging completed.  Returns false when a wait
+// ran out (sticky error and abort word set here) or the loader failed.
+template <int NC, typename T, bool FWD, int S>
+__device__ __forceinline__ bool sgs_ws_compute(int nx, int ny, T* x, unsigned long long* edge, unsigned epoch,
+                                               int* abort_flag, int* sticky_err, int q, int nstrips,
+                                               int spin_limit, unsigned char* smem, unsigned& parity_f,
+                                               int& waited) {
+  using W = SgsWs<NC, T>;
+  constexpr int BS = NC * NC;
+  constexpr int NOFF = 4 * BS;
+  constexpr int EB = NOFF + LU_E;
+  constexpr int EX = EB + NC;
+  constexpr int NE = EX + NC;
+  constexpr size_t STAGE = sgs_stage_bytes<NC, T, S>();
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);   // full[0..1], empty[2..3]
+  int* ctl = reinterpret_cast<int*>(smem);
+  auto vals = [&](int st) { return reinterpret_cast<const T*>(smem + 128 + (size_t)st * STAGE); };
+  auto pvs = [&](int st) {
+    return reinterpret_cast<const int8_t*>(smem + 128 + (size_t)st * STAGE + (size_t)NE * S * 32 * sizeof(T));
+  };
+  const T* ring_s = reinterpret_cast<const T*>(smem + 128 + 2 * STAGE);
+  const T* ring_n = ring_s + SGS_RING * NC;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const long long P = skew_slots(nx, ny);
+  const int oW = (FWD ? 0 : 1) * BS, oE = (FWD ? 1 : 0) * BS, oS = (FWD ? 2 : 3) * BS,
+            oN = (FWD ? 3 : 2) * BS;
+  const int lagk = FWD ? lane : 31 - lane;
+  const int nsteps_full = nx + 31;
+  const int ps = FWD ? q : nstrips - 1 - q;
+  const long long line_base = (long long)ps * (nx + 31);
+  const int rows = min(32, ny - ps * 32);
+  const int nsteps = FWD ? nx + rows - 1 : nsteps_full;
+  const int nchunks = (nsteps + S - 1) / S;
+  const int y = ps * 32 + lane;
+  const bool rowok = y < ny;
+  const bool hasS = FWD ? (y > 0) : (y < ny - 1);
+  const bool hasN = FWD ? (y < ny - 1) : (y > 0);
+  const int lead = FWD ? 0 : 31, trail = FWD ? 31 : 0;   // the lanes of lag 0 and lag 31
+  const bool need_s = q > 0 && __shfl_sync(FULL, (int)(rowok && hasS), lead) != 0;
+  const bool need_n = __shfl_sync(FULL, (int)(rowok && hasN), trail) != 0;
+  const bool publish = q + 1 < nstrips;
+  int known_s = need_s ? 0 : nx;   // previous-strip columns known to be in the south ring
+  int known_n = need_n ? 0 : nx;   // columns known to be in the north ring
+  T xprev[NC], res[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) { xprev[k] = T(0); res[k] = T(0); }
+  bool failed = false, timeout = false;
+  for (int j = 0; j < nchunks && !failed; ++j) {
+    const int st = j & 1;
+    {   // the chunk's staging, watching the loader's fail word
+      bool ok = false;
+      for (int it = 0;; ++it) {
+        ok = __all_sync(FULL, mbar_try_wait(&bar[st], (parity_f >> st) & 1u)) != 0;
+        if (ok) break;
+        int f = 0;
+        if (lane == 0) f = lds_acquire(&ctl[W::FAIL]);
+        if (__shfl_sync(FULL, f, 0)) break;
+        if (it + 1 >= spin_limit) { timeout = true; break; }
+      }
+      if (!ok) { failed = true; break; }
+    }
+    parity_f ^= 1u << st;
+    ++waited;
+    const T* V = vals(st);
+    const int8_t* PV = pvs(st);
+    const int s0 = j * S, cnt = min(S, nsteps - s0);
+    const long long dbase = line_base + (FWD ? s0 : nsteps_full - s0 - cnt);
+    for (int s = s0; s < s0 + cnt; ++s) {
+      const int line = FWD ? s - s0 : cnt - 1 - (s - s0);
+      const int c = s - lagk;
+      const bool act = rowok && c >= 0 && c < nx;
+      T xS[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k)
+        xS[k] = FWD ? __shfl_up_sync(FULL, res[k], 1) : __shfl_down_sync(FULL, res[k], 1);
+      if (s < nx && s >= known_s) {   // the lead lane's south value of column s
+        int h = 0;
+        for (int it = 0;; ++it) {
+          if (lane == lead) {
+            h = lds_acquire(&ctl[W::SOUTH]);
+            if (h <= s && lds_acquire(&ctl[W::FAIL])) h = -1;
+          }
+          h = __shfl_sync(FULL, h, lead);
+          if (h > s || h < 0) break;
+          if (it + 1 >= spin_limit) { timeout = true; break; }
+        }
+        if (h <= s) { failed = true; break; }
+        known_s = h;
+      }
+      const int cn = s - 31;   // the trail lane's column
+      if (cn >= 0 && cn < nx && cn >= known_n) {
+        int h = 0;
+        for (int it = 0;; ++it) {
+          if (lane == trail) {
+            h = lds_acquire(&ctl[W::NORTH]);
+            if (h <= cn && lds_acquire(&ctl[W::FAIL])) h = -1;
+          }
+          h = __shfl_sync(FULL, h, trail);
+          if (h > cn || h < 0) break;
+          if (it + 1 >= spin_limit) { timeout = true; break; }
+        }
+        if (h <= cn) { failed = true; break; }
+        known_n = h;
+      }
+      if (act) {
+        const int rs = (c & (SGS_RING - 1)) * NC;
+        if (lagk == 0 && hasS) {
+#pragma unroll
+          for (int k = 0; k < NC; ++k) xS[k] = ring_s[rs + k];
+        }
+        const T* Vl = V + line * 32 + lane;
+        const int ES = S * 32;   // stride between entries in the stage
+        T xe[NC], xn[NC], bb[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          xe[k] = Vl[(EX + k) * ES];
+          xn[k] = lagk == 31 ? (hasN ? ring_n[rs + k] : T(0)) : Vl[(EX + k) * ES + (FWD ? 1 : -1)];
+          bb[k] = Vl[(EB + k) * ES];
+        }
+        sgs_cell<NC, T>(Vl + oW * ES, Vl + oE * ES, Vl + oS * ES, Vl + oN * ES, ES, Vl + (size_t)NOFF * ES,
+                        PV[line * 32 + lane], bb, c > 0, xprev, c < nx - 1, xe, hasS, xS, hasN, xn, res);
+        const long long slot = (dbase + line) * 32 + lane;   // coalesced: one line per step
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          x[k * P + slot] = res[k];
+          xprev[k] = res[k];
+        }
+        if (lagk == 31 && publish) {   // the new last-row value for the next strip, tagged
+          unsigned long long* e = edge + ((long long)q * nx + c) * W::WPC;
+#pragma unroll
+          for (int k = 0; k < NC; ++k)
+#pragma unroll
+            for (int h = 0; h < Words<T>::N; ++h)
+              st_tagged(e + k * Words<T>::N + h, ((unsigned long long)epoch << 32) | Words<T>::get(res[k], h));
+        }
+      }
+      // ring slots the lead and trail lanes are done with
+      if (lagk == 0 && s < nx && ((s + 1) % W::GS == 0 || s == nx - 1)) sts_release(&ctl[W::LEAD], s + 1);
+      if (lagk == 31 && cn >= 0 && cn < nx && ((cn + 1) % W::GN == 0 || cn == nx - 1))
+        sts_release(&ctl[W::TRAIL], cn + 1);
+    }
+    __syncwarp();
+    if (failed) break;
+    if (lane == 0) mbar_arrive(&bar[2 + st]);   // the buffer goes back to the loader
+  }
+  if (failed && lane == 0) {
+    if (timeout) atomicOr(sticky_err, 1);
+    sts_release(&ctl[W::FAIL], 1);
+    st_release(abort_flag, 1);
+  }
+  return !failed;
+}
+
+// warp 1 of k_sgs_ws: operator chunks, the north ring, the south ring.  One
+// pass of its loop looks at each task once and never blocks on any of them.
+// Returns false when its wait ran out (sticky error and abort word set here)
+// or the compute warp or another CTA failed.
+template <int NC, typename T, bool FWD, int S>
+__device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restrict__ blk,
+                                              const T* __restrict__ lu, const int8_t* __restrict__ piv,
+                                              const T* __restrict__ b, const T* x,
+                                              const unsigned long long* edge, unsigned epoch, int* abort_flag,
+                                              int* sticky_err, int q, int nstrips, int spin_limit,
+                                              unsigned char* smem, unsigned& parity_e, unsigned& used) {
+  using W = SgsWs<NC, T>;
+  constexpr int BS = NC * NC;
+  constexpr int NOFF = 4 * BS;
+  constexpr int EB = NOFF + LU_E;
+  constexpr int EX = EB + NC;
+  constexpr int NE = EX + NC;
+  constexpr size_t STAGE = sgs_stage_bytes<NC, T, S>();
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  int* ctl = reinterpret_cast<int*>(smem);
+  auto vals = [&](int st) { return reinterpret_cast<T*>(smem + 128 + (size_t)st * STAGE); };
+  auto pvs = [&](int st) {
+    return reinterpret_cast<int8_t*>(smem + 128 + (size_t)st * STAGE + (size_t)NE * S * 32 * sizeof(T));
+  };
+  T* ring_n = reinterpret_cast<T*>(smem + 128 + 2 * STAGE) + SGS_RING * NC;
+  unsigned* ring_s32 = reinterpret_cast<unsigned*>(smem + 128 + 2 * STAGE);
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const long long P = skew_slots(nx, ny);
+  const int nsteps_full = nx + 31;
+  const int ps = FWD ? q : nstrips - 1 - q;
+  const long long line_base = (long long)ps * (nx + 31);
+  const int rows = min(32, ny - ps * 32);
+  const int nsteps = FWD ? nx + rows - 1 : nsteps_full;
+  const int nchunks = (nsteps + S - 1) / S;
+  // chunk j (S lines) of the operator, LU factors, b and the old x lines one
+  // step ahead, as in k_sgs_strip
+  auto issue = [&](int j, int st) {
+    const int s0 = j * S, cnt = min(S, nsteps - s0);
+    const int dlo = FWD ? s0 : nsteps_full - s0 - cnt;
+    const long long off = (line_base + dlo) * 32;
+    const unsigned vb = (unsigned)(cnt * 32 * sizeof(T));
+    const int xlo = dlo + (FWD ? 1 : -1);
+    const int xa = max(xlo, 0), xb = min(xlo + cnt, nsteps_full);
+    const unsigned xbytes = xb > xa ? (unsigned)((xb - xa) * 32 * sizeof(T)) : 0u;
+    fence_proxy_async();
+    mbar_expect_tx(&bar[st], vb * EX + xbytes * NC + (unsigned)(cnt * 32));
+    for (int e = 0; e < NOFF; ++e)
+      bulk_g2s(vals(st) + (size_t)e * S * 32, blk + (long long)(BS + e) * P + off, vb, &bar[st]);
+    for (int e = 0; e < LU_E; ++e)
+      bulk_g2s(vals(st) + (size_t)(NOFF + e) * S * 32, lu + (long long)e * P + off, vb, &bar[st]);
+    for (int k = 0; k < NC; ++k)
+      bulk_g2s(vals(st) + (size_t)(EB + k) * S * 32, b + (long long)k * P + off, vb, &bar[st]);
+    if (xbytes)
+      for (int k = 0; k < NC; ++k)
+        bulk_g2s(vals(st) + (size_t)(EX + k) * S * 32 + (size_t)(xa - xlo) * 32,
+                 x + (long long)k * P + (line_base + xa) * 32, xbytes, &bar[st]);
+    bulk_g2s(pvs(st), piv + off, (unsigned)(cnt * 32), &bar[st]);
+  };
+  // the lead lane (lag 0) takes its south values from the previous strip, the
+  // trail lane (lag 31) its north values from the row beyond the strip
+  const int ylead = ps * 32 + (FWD ? 0 : 31), ytrail = ps * 32 + (FWD ? 31 : 0);
+  const bool need_s = q > 0 && ylead < ny && (FWD ? ylead > 0 : ylead < ny - 1);
+  const bool need_n = ytrail < ny && (FWD ? ytrail < ny - 1 : ytrail > 0);
+  const int yN = FWD ? ytrail + 1 : ytrail - 1;
+  int next = 0, s_loaded = need_s ? 0 : nx, n_loaded = need_n ? 0 : nx;
+  bool failed = false, timeout = false;
+  for (int idle = 0;;) {
+    bool prog = false;
+    if (next < nchunks) {   // the next chunk, once its buffer is free
+      const int st = next & 1;
+      bool free_buf = true;
+      if ((used >> st) & 1u) {
+        int ok = 0;
+        if (lane == 0) ok = mbar_try_wait(&bar[2 + st], (parity_e >> st) & 1u) ? 1 : 0;
+        free_buf = __shfl_sync(FULL, ok, 0) != 0;
+      }
+      if (free_buf) {
+        if ((used >> st) & 1u) parity_e ^= 1u << st;
+        used |= 1u << st;
+        if (lane == 0) issue(next, st);
+        ++next;
+        prog = true;
+      }
+    }
+    if (n_loaded < nx) {   // old values beyond the strip's last row, GN columns at a time
+      const int tdone = lds_acquire(&ctl[W::TRAIL]);
+      if (__all_sync(FULL, n_loaded + W::GN <= tdone + SGS_RING)) {
+        if (lane < W::GN * NC) {
+          const int t = lane / NC, k = lane % NC, c = n_loaded + t;
+          if (c < nx) {
+            const int px = FWD ? c : nx - 1 - c;
+            ring_n[(c & (SGS_RING - 1)) * NC + k] = __ldcg(&x[k * P + skew_pos(px, yN, nx)]);
+          }
+        }
+        __syncwarp();
+        n_loaded = min(n_loaded + W::GN, nx);
+        if (lane == 0) sts_release(&ctl[W::NORTH], n_loaded);
+        prog = true;
+      }
+    }
+    if (s_loaded < nx) {   // the previous strip's new last row, up to GS columns at a time
+      const int ldone = lds_acquire(&ctl[W::LEAD]);
+      if (__all_sync(FULL, s_loaded + W::GS <= ldone + SGS_RING)) {
+        const int t = lane / W::WPC, w = lane % W::WPC, c = s_loaded + t;
+        const bool mine = lane < W::GS * W::WPC && c < nx;
+        unsigned long long word = 0ull;
+        bool ok = true;
+        if (mine) {
+          word = ld_tagged(edge + ((long long)(q - 1) * nx + c) * W::WPC + w);
+          ok = (unsigned)(word >> 32) == epoch;
+        }
+        const unsigned stale = __ballot_sync(FULL, mine && !ok);
+        int nv = stale ? (__ffs(stale) - 1) / W::WPC : W::GS;   // columns before the first stale word
+        nv = min(nv, nx - s_loaded);
+        if (nv > 0) {
+          if (mine && t < nv) ring_s32[(c & (SGS_RING - 1)) * W::WPC + w] = (unsigned)word;
+          __syncwarp();
+          s_loaded += nv;
+          if (lane == 0) sts_release(&ctl[W::SOUTH], s_loaded);
+          prog = true;
+        }
+      }
+    }
+    if (next >= nchunks && n_loaded >= nx && s_loaded >= nx) break;
+    if (prog) {
+      idle = 0;
+      continue;
+    }
+    int stop = 0;
+    if (lane == 0) stop = (lds_acquire(&ctl[W::FAIL]) || ld_acquire(abort_flag)) ? 1 : 0;
+    if (__shfl_sync(FULL, stop, 0)) {
+      failed = true;
+      break;
+    }
+    if (++idle >= spin_limit) {
+      failed = timeout = true;
+      break;
+    }
+    __nanosleep(20);
+  }
+  if (lane == 0) {
+    ctl[W::ISSUED] = next;
+    if (failed) {
+      if (timeout) atomicOr(sticky_err, 1);
+      sts_release(&ctl[W::FAIL], 1);
+      st_release(abort_flag, 1);
+    }
+  }
+  return !failed;
+}
+
+template <int NC, typename T, bool FWD, int S>
+__global__ void __launch_bounds__(64, 1) k_sgs_ws(int nx, int ny, const T* __restrict__ blk,
+                                                  const T* __restrict__ lu, const int8_t* __restrict__ piv,
+                                                  const T* __restrict__ b, T* x, int* sync,
+                                                  unsigned long long* edge, unsigned epoch, int* sticky_err,
+                                                  int nstrips, int spin_limit) {
+  using W = SgsWs<NC, T>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  int* ctl = reinterpret_cast<int*>(smem);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) mbar_init(&bar[k]);
+    ctl[W::FAIL] = 0;
+    fence_proxy_async();
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  unsigned parity_f = 0u, parity_e = 0u, used = 0u;   // bit st: stage st
+  for (;;) {
+    if (threadIdx.x == 0) {
+      ctl[W::Q] = atomicAdd(&sync[0], 1);
+      ctl[W::SOUTH] = 0;
+      ctl[W::NORTH] = 0;
+      ctl[W::LEAD] = 0;
+      ctl[W::TRAIL] = 0;
+      ctl[W::ISSUED] = 0;
+    }
+    __syncthreads();
+    const int q = ctl[W::Q];
+    if (q >= nstrips) return;
+    int waited = 0;
+    if (warp == 0)
+      sgs_ws_compute<NC, T, FWD, S>(nx, ny, x, edge, epoch, sync + 1, sticky_err, q, nstrips, spin_limit, smem,
+                                    parity_f, waited);
+    else
+      sgs_ws_loader<NC, T, FWD, S>(nx, ny, blk, lu, piv, b, x, edge, epoch, sync + 1, sticky_err, q, nstrips,
+                                   spin_limit, smem, parity_e, used);
+    __syncthreads();
+    if (ctl[W::FAIL]) {
+      // the bulk copies in flight land before the CTA's shared memory goes
+      // away; the drain has its own bound (an issued copy completes)
+      if (warp == 0) {
+        const int issued = ctl[W::ISSUED];
+        for (int j = waited; j < issued; ++j) {
+          chunk_wait(&bar[j & 1], (parity_f >> (j & 1)) & 1u, kDrainLimit);
+          parity_f ^= 1u << (j & 1);
+        }
+      }
+      return;
+    }
+  }
+}
+
 // ---- block Gauss-Seidel, two-colour variant (SWNMG_SMOOTH_COLOUR) ----------
 // Not the paper's smoother (Section 2.3 sweeps lexicographically): a variant
 // whose iterates differ, reported separately.  Cell (ix, iy) has colour
@@ -1271,12 +1710,40 @@ static void sgs_launch(int nx, int ny, const void* blk, const void* lu, const in
                                                        (const T*)b, (T*)x, sync, sticky, nstrips, wait_limit());
 }
 
+template <int NC, typename T, bool F>
+static void sgs_ws_launch(int nx, int ny, const void* blk, const void* lu, const int8_t* piv, const void* b,
+                          void* x, int* sync, unsigned long long* edge, unsigned epoch, int* sticky,
+                          cudaStream_t st) {
+  constexpr int S = SgsChunk<T>::S;
+  const int nstrips = (ny + 31) / 32;
+  const size_t smem = sgs_ws_smem_bytes<NC, T, S>();
+  static bool configured = false;   // per template instance
+  if (!configured) {
+    cudaFuncSetAttribute(k_sgs_ws<NC, T, F, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
+  }
+  k_sgs_ws<NC, T, F, S><<<nstrips, 64, smem, st>>>(nx, ny, (const T*)blk, (const T*)lu, piv, (const T*)b,
+                                                    (T*)x, sync, edge, epoch, sticky, nstrips, wait_limit());
+}
+
 void launch_sgs_sweep(int nc, int nx, int ny, const void* blk, const void* lu, const int8_t* piv,
-                      const void* b, void* x, int forward, int fp32, int* sync, int* sticky_err,
-                      cudaStream_t st) {
+                      const void* b, void* x, int forward, int fp32, int* sync, unsigned long long* edge,
+                      unsigned epoch, int* sticky_err, cudaStream_t st) {
   count_launches(1);
   const int nstrips = (ny + 31) / 32;
   cudaMemsetAsync(sync, 0, sizeof(int) * (2 + nstrips), st);
+  if (edge) {   // the warp-specialised kernel
+#define WL(NC, T, F) sgs_ws_launch<NC, T, F>(nx, ny, blk, lu, piv, b, x, sync, edge, epoch, sticky_err, st)
+    if (nc == 3) {
+      if (fp32) { if (forward) WL(3, float, true); else WL(3, float, false); }
+      else { if (forward) WL(3, double, true); else WL(3, double, false); }
+    } else {
+      if (fp32) { if (forward) WL(2, float, true); else WL(2, float, false); }
+      else { if (forward) WL(2, double, true); else WL(2, double, false); }
+    }
+#undef WL
+    return;
+  }
 #define SL(NC, T, F) sgs_launch<NC, T, F>(nx, ny, blk, lu, piv, b, x, sync, sticky_err, st)
   if (nc == 3) {
     if (fp32) { if (forward) SL(3, float, true); else SL(3, float, false); }
