@@ -144,6 +144,44 @@ __device__ __forceinline__ void sgs_cell(const T* AW, const T* AE, const T* AS, 
   lu_apply_v<NC, T>(lu, es, pv, r, res);
 }
 
+// sgs_cell in two parts, with its operations in its order: the old east and
+// north terms (known a step ahead), then the new west and south terms and the
+// LU solve on operands held in registers (blocks row-major, entry s NC + k).
+// A neighbour that does not exist contributes through a zero sum, as in
+// sgs_cell, so the two parts together give sgs_cell's bits.
+template <int NC, typename T>
+__device__ __forceinline__ void sgs_cell_old(const T* AE, const T* AN, int es, const T bb[NC], bool hE,
+                                             const T xe[NC], bool hN, const T xn[NC], T a[NC]) {
+#pragma unroll
+  for (int s2 = 0; s2 < NC; ++s2) {
+    T v = bb[s2], ve = bb[s2];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) ve = tfma(-AE[(s2 * NC + k) * es], xe[k], ve);
+    v = hE ? ve : v;
+    T vn = v;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) vn = tfma(-AN[(s2 * NC + k) * es], xn[k], vn);
+    a[s2] = hN ? vn : v;
+  }
+}
+
+template <int NC, typename T>
+__device__ __forceinline__ void sgs_cell_new(const T aw[NC * NC], const T as[NC * NC], const T lu[LU_E],
+                                             int8_t pv, const T a[NC], bool hW, const T xw[NC], bool hS,
+                                             const T xs[NC], T res[NC]) {
+  T r[NC];
+#pragma unroll
+  for (int s2 = 0; s2 < NC; ++s2) {
+    T w = T(0), so = T(0);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) w = tfma(aw[s2 * NC + k], xw[k], w);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) so = tfma(as[s2 * NC + k], xs[k], so);
+    r[s2] = (a[s2] - (hW ? w : T(0))) - (hS ? so : T(0));
+  }
+  lu_apply_v<NC, T>(lu, 1, pv, r, res);
+}
+
 // ---- Galerkin coarse operator: A_{IJ,l+1} = sum_{i in I} sum_{j in J} A_ij ---
 // children 00, 10, 01, 11; diagonal = children's diagonals plus the 8
 // couplings between children; W/E/S/N = the two couplings crossing that side.
@@ -638,15 +676,18 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
 // ---- block SGS half-sweep, warp-specialised strip kernel -------------------
 // The sweep, the cell order and the cell arithmetic (sgs_cell) of k_sgs_strip,
 // with everything that is not on the sweep's dependency chain taken off the
-// warp that updates the cells.  One CTA of two warps per strip in flight:
+// warp that updates the cells.  One CTA of three warps per strip in flight:
 //   warp 0 (compute) updates the strip's 32 rows, one skewed line per step,
 //     reading its operands from shared memory only;
-//   warp 1 (loader) stages the operator chunks into the two shared buffers
+//   warp 1 moves the previous strip's new last-row values into a shared ring;
+//   warp 2 stages the operator chunks into the two shared buffers
 //     (cp.async.bulk, mbarrier completion; the compute warp hands a buffer
-//     back through a second mbarrier), loads the old values of the row beyond
-//     the strip's last row (the next strip's first row in sweep order) into a
-//     shared ring, and moves the previous strip's new last-row values into a
-//     second ring.
+//     back through a second mbarrier) and loads the old values of the row
+//     beyond the strip's last row (the next strip's first row in sweep order)
+//     into a second ring.  Ring words carry the strip and column they hold, so the
+//     compute warp needs no fence to read them (a fence would wait for its
+//     own stores in flight); it reports the columns it is done with through
+//     plain counters that only pace the loader.
 // Hand-off between strips without fences: the strip's last lane writes every
 // new value of its row as 64-bit words, each holding 32 bits of the value and
 // the launch's epoch (a counter that differs between launches).  The next
@@ -661,13 +702,53 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
 // (q * nx + c) * WPC + w, WPC = NC * sizeof(T) / 4.
 constexpr int SGS_RING = 32;   // columns held by each shared ring
 
-__device__ __forceinline__ int lds_acquire(const int* p) {
+// plain (volatile) shared-memory words: the progress counters between the two
+// warps only pace the rings; the data in the rings carries its own tag
+__device__ __forceinline__ int lds_vol(const int* p) {
   int v;
-  asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+  asm volatile("ld.volatile.shared.s32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
   return v;
 }
-__device__ __forceinline__ void sts_release(int* p, int v) {
-  asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+__device__ __forceinline__ void sts_vol(int* p, int v) {
+  asm volatile("st.volatile.shared.s32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long lds64_vol(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v) : "r"(smem_addr(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts64_vol(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.volatile.shared.u64 [%0], %1;" ::"r"(smem_addr(p)), "l"(v) : "memory");
+}
+// predicated forms: the lane-specific accesses of a warp step without a branch
+__device__ __forceinline__ unsigned long long lds64_vol_if(const unsigned long long* p, bool c) {
+  unsigned long long v = 0ull;
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q ld.volatile.shared.u64 %0, [%1];\n}"
+               : "+l"(v)
+               : "r"(smem_addr(p)), "r"((unsigned)c)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts_vol_if(int* p, int v, bool c) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q st.volatile.shared.s32 [%0], %1;\n}" ::"r"(smem_addr(p)),
+               "r"(v), "r"((unsigned)c)
+               : "memory");
+}
+__device__ __forceinline__ void st_tagged_if(unsigned long long* p, unsigned long long v, bool c) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q st.relaxed.gpu.global.u64 [%0], %1;\n}" ::"l"(p), "l"(v),
+               "r"((unsigned)c)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_if(uint64_t* bar, bool c) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n @q mbarrier.arrive.shared::cta.b64 _, [%0];\n}" ::"r"(
+                   smem_addr(bar)),
+               "r"((unsigned)c)
+               : "memory");
+}
+__device__ __forceinline__ int ldg_vol(const int* p) {
+  int v;
+  asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 __device__ __forceinline__ void st_tagged(unsigned long long* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -686,12 +767,16 @@ template <typename T> struct Words;
 template <> struct Words<float> {
   static constexpr int N = 1;
   __device__ static unsigned get(float v, int) { return __float_as_uint(v); }
+  __device__ static float make(const unsigned* w) { return __uint_as_float(w[0]); }
 };
 template <> struct Words<double> {
   static constexpr int N = 2;
   __device__ static unsigned get(double v, int h) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(v);
     return h ? (unsigned)(u >> 32) : (unsigned)u;
+  }
+  __device__ static double make(const unsigned* w) {
+    return __longlong_as_double((long long)(((unsigned long long)w[1] << 32) | w[0]));
   }
 };
 
@@ -704,19 +789,24 @@ struct SgsWs {
   static constexpr int GN = pow2_floor(32 / NC);       // north columns loaded at once
   // control block (the first 128 bytes): full[2], empty[2] mbarriers in
   // bytes 0-31, then these int slots (indices into the block as int[32])
-  static constexpr int Q = 8, SOUTH = 9, NORTH = 10, LEAD = 11, TRAIL = 12, FAIL = 13, ISSUED = 14;
+  static constexpr int Q = 8, LEAD = 9, TRAIL = 10, FAIL = 11, ISSUED = 12;
   static_assert(Q * 4 >= 32 && ISSUED * 4 + 4 <= 128, "control slots must sit between the barriers and byte 128");
   static_assert(GS * WPC <= 32 && GN * NC <= 32 && 2 * GS <= SGS_RING && 2 * GN <= SGS_RING, "ring groups");
 };
 
+// The rings hold 64-bit words: 32 bits of a value and, above them, the tag
+// q * nx + c of the strip q and column c it belongs to (all ones: empty).
 template <int NC, typename T, int S>
 size_t sgs_ws_smem_bytes() {   // control block, two staging buffers, two rings
-  return 128 + 2 * sgs_stage_bytes<NC, T, S>() + 2 * (size_t)SGS_RING * NC * sizeof(T);
+  return 128 + 2 * sgs_stage_bytes<NC, T, S>() + 2 * (size_t)SGS_RING * SgsWs<NC, T>::WPC * 8;
 }
 
-// warp 0 of k_sgs_ws: the strip's cell updates, operands from shared memory.
-// waited counts the chunks whose staging completed.  Returns false when a wait
-// ran out (sticky error and abort word set here) or the loader failed.
+// warp 0 of k_sgs_ws: the strip's cell updates, software-pipelined: while a
+// step runs its dependent chain (the new west and south terms, the LU solve),
+// the same instruction stream loads the next step's operands from shared
+// memory into registers and forms its old east / north part.  waited counts
+// the chunks whose staging completed.  Returns false when a wait ran out
+// (sticky error and abort word set here) or another warp failed.
 template <int NC, typename T, bool FWD, int S>
 __device__ __forceinline__ bool sgs_ws_compute(int nx, int ny, T* x, unsigned long long* edge, unsigned epoch,
                                                int* abort_flag, int* sticky_err, int q, int nstrips,
@@ -728,6 +818,7 @@ __device__ __forceinline__ bool sgs_ws_compute(int nx, int ny, T* x, unsigned lo
   constexpr int EB = NOFF + LU_E;
   constexpr int EX = EB + NC;
   constexpr int NE = EX + NC;
+  constexpr int ES = S * 32;   // stride between entries in a stage
   constexpr size_t STAGE = sgs_stage_bytes<NC, T, S>();
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);   // full[0..1], empty[2..3]
   int* ctl = reinterpret_cast<int*>(smem);
@@ -735,11 +826,12 @@ __device__ __forceinline__ bool sgs_ws_compute(int nx, int ny, T* x, unsigned lo
   auto pvs = [&](int st) {
     return reinterpret_cast<const int8_t*>(smem + 128 + (size_t)st * STAGE + (size_t)NE * S * 32 * sizeof(T));
   };
-  const T* ring_s = reinterpret_cast<const T*>(smem + 128 + 2 * STAGE);
-  const T* ring_n = ring_s + SGS_RING * NC;
+  const unsigned long long* ring_s = reinterpret_cast<const unsigned long long*>(smem + 128 + 2 * STAGE);
+  const unsigned long long* ring_n = ring_s + SGS_RING * W::WPC;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const long long P = skew_slots(nx, ny);
+  const unsigned tag0 = (unsigned)q * (unsigned)nx;   // ring tag of column c: tag0 + c
   const int oW = (FWD ? 0 : 1) * BS, oE = (FWD ? 1 : 0) * BS, oS = (FWD ? 2 : 3) * BS,
             oN = (FWD ? 3 : 2) * BS;
   const int lagk = FWD ? lane : 31 - lane;
@@ -748,7 +840,6 @@ __device__ __forceinline__ bool sgs_ws_compute(int nx, int ny, T* x, unsigned lo
   const long long line_base = (long long)ps * (nx + 31);
   const int rows = min(32, ny - ps * 32);
   const int nsteps = FWD ? nx + rows - 1 : nsteps_full;
-  const int nchunks = (nsteps + S - 1) / S;
   const int y = ps * 32 + lane;
   const bool rowok = y < ny;
   const bool hasS = FWD ? (y > 0) : (y < ny - 1);
@@ -757,129 +848,174 @@ __device__ __forceinline__ bool sgs_ws_compute(int nx, int ny, T* x, unsigned lo
   const bool need_s = q > 0 && __shfl_sync(FULL, (int)(rowok && hasS), lead) != 0;
   const bool need_n = __shfl_sync(FULL, (int)(rowok && hasN), trail) != 0;
   const bool publish = q + 1 < nstrips;
-  int known_s = need_s ? 0 : nx;   // previous-strip columns known to be in the south ring
-  int known_n = need_n ? 0 : nx;   // columns known to be in the north ring
+  bool timeout = false;
+  int bad = 0;   // this lane's ring wait: 1 another warp failed, 2 ran out
+  // bounded wait for chunk j's staging (warp-uniform)
+  auto wait_chunk = [&](int j) -> bool {
+    const int st = j & 1;
+    for (int it = 0;; ++it) {
+      if (__all_sync(FULL, mbar_try_wait(&bar[st], (parity_f >> st) & 1u))) {
+        parity_f ^= 1u << st;
+        ++waited;
+        return true;
+      }
+      int f = 0;
+      if (lane == 0) f = lds_vol(&ctl[W::FAIL]);
+      if (__shfl_sync(FULL, f, 0)) return false;
+      if (it + 1 >= spin_limit) {
+        timeout = true;
+        return false;
+      }
+    }
+  };
+  // the lane's ring words of column cr (want: the lane reads a ring this
+  // step), once their tag names this strip and column; the wait, when some
+  // lane's words are not there yet, is warp-uniform
+  auto ring_get = [&](const unsigned long long* ring, int cr, bool want, T v[NC]) {
+    const unsigned long long* r = ring + (cr & (SGS_RING - 1)) * W::WPC;
+    const unsigned tg = tag0 + (unsigned)cr;
+    unsigned bits[W::WPC];
+    bool ok = true;
+#pragma unroll
+    for (int w = 0; w < W::WPC; ++w) {
+      const unsigned long long v64 = lds64_vol_if(r + w, want);
+      bits[w] = (unsigned)v64;
+      ok = ok && (unsigned)(v64 >> 32) == tg;
+    }
+    ok = ok || !want;
+    if (__any_sync(FULL, !ok)) {
+      for (int it = 1; !ok && !bad; ++it) {
+        ok = true;
+#pragma unroll
+        for (int w = 0; w < W::WPC; ++w) {
+          const unsigned long long v64 = lds64_vol(r + w);
+          bits[w] = (unsigned)v64;
+          ok = ok && (unsigned)(v64 >> 32) == tg;
+        }
+        if (!ok && (it & 63) == 63 && lds_vol(&ctl[W::FAIL])) bad = 1;
+        else if (!ok && it + 1 >= spin_limit) bad = 2;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) v[k] = want ? Words<T>::make(bits + k * Words<T>::N) : T(0);
+  };
+  // step s's operands: W and S blocks, LU factors and pivot code, the old
+  // east / north part, and the lane's ring value (lead: south, trail: north)
+  T cAW[BS], cAS[BS], cLU[LU_E], ca[NC], crv[NC];
+  T nAW[BS], nAS[BS], nLU[LU_E], na[NC], nrv[NC];
+  int8_t cpv = 0, npv = 0;
+  auto load_step = [&](int s, T AWo[BS], T ASo[BS], T LUo[LU_E], int8_t& pvo, T ao[NC], T rvo[NC]) {
+    const int j = s / S, s0 = j * S, cnt = min(S, nsteps - s0);
+    const int line = FWD ? s - s0 : cnt - 1 - (s - s0);
+    const T* Vl = vals(j & 1) + line * 32 + lane;
+#pragma unroll
+    for (int e = 0; e < BS; ++e) {
+      AWo[e] = Vl[(oW + e) * ES];
+      ASo[e] = Vl[(oS + e) * ES];
+    }
+#pragma unroll
+    for (int e = 0; e < LU_E; ++e) LUo[e] = Vl[(NOFF + e) * ES];
+    pvo = pvs(j & 1)[line * 32 + lane];
+    const int cn = s - 31;
+    const bool rl = lagk == 0 && need_s && s < nx;
+    const bool rt = lagk == 31 && need_n && cn >= 0 && cn < nx;
+    ring_get(lagk == 0 ? ring_s : ring_n, lagk == 0 ? s : cn, rl || rt, rvo);
+    T xe[NC], xn[NC], bb[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      xe[k] = Vl[(EX + k) * ES];
+      xn[k] = lagk == 31 ? rvo[k] : Vl[(EX + k) * ES + (FWD ? 1 : -1)];
+      bb[k] = Vl[(EB + k) * ES];
+    }
+    sgs_cell_old<NC, T>(Vl + oE * ES, Vl + oN * ES, ES, bb, s - lagk < nx - 1, xe, hasN, xn, ao);
+  };
+  bool failed = !wait_chunk(0);
+  if (!failed) load_step(0, cAW, cAS, cLU, cpv, ca, crv);
   T xprev[NC], res[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) { xprev[k] = T(0); res[k] = T(0); }
-  bool failed = false, timeout = false;
-  for (int j = 0; j < nchunks && !failed; ++j) {
-    const int st = j & 1;
-    {   // the chunk's staging, watching the loader's fail word
-      bool ok = false;
-      for (int it = 0;; ++it) {
-        ok = __all_sync(FULL, mbar_try_wait(&bar[st], (parity_f >> st) & 1u)) != 0;
-        if (ok) break;
-        int f = 0;
-        if (lane == 0) f = lds_acquire(&ctl[W::FAIL]);
-        if (__shfl_sync(FULL, f, 0)) break;
-        if (it + 1 >= spin_limit) { timeout = true; break; }
-      }
-      if (!ok) { failed = true; break; }
+  for (int s = 0; s < nsteps && !failed; ++s) {
+    const int c = s - lagk;
+    const bool act = rowok && c >= 0 && c < nx;
+    // step s: the new west (own last result) and south (lane below, or the
+    // previous strip through the ring for the lead lane) terms, the LU solve
+    T xS[NC], rnew[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      xS[k] = FWD ? __shfl_up_sync(FULL, res[k], 1) : __shfl_down_sync(FULL, res[k], 1);
+      if (lagk == 0) xS[k] = crv[k];
     }
-    parity_f ^= 1u << st;
-    ++waited;
-    const T* V = vals(st);
-    const int8_t* PV = pvs(st);
-    const int s0 = j * S, cnt = min(S, nsteps - s0);
-    const long long dbase = line_base + (FWD ? s0 : nsteps_full - s0 - cnt);
-    for (int s = s0; s < s0 + cnt; ++s) {
-      const int line = FWD ? s - s0 : cnt - 1 - (s - s0);
-      const int c = s - lagk;
-      const bool act = rowok && c >= 0 && c < nx;
-      T xS[NC];
+    sgs_cell_new<NC, T>(cAW, cAS, cLU, cpv, ca, c > 0, xprev, hasS, xS, rnew);
+    // step s + 1's operands, independent of this step's result
+    const int s1 = s + 1;
+    if (s1 < nsteps) {
+      if (s1 % S == 0) {   // a new chunk: the finished buffer goes back to the loader
+        __syncwarp();
+        mbar_arrive_if(&bar[2 + ((s1 / S - 1) & 1)], lane == 0);
+        if (__any_sync(FULL, bad != 0) || !wait_chunk(s1 / S)) failed = true;
+      }
+      if (!failed) load_step(s1, nAW, nAS, nLU, npv, na, nrv);
+    }
+    {
+      const long long slot = (line_base + (FWD ? s : nsteps_full - 1 - s)) * 32 + lane;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        if (act) x[k * P + slot] = rnew[k];
+        xprev[k] = act ? rnew[k] : xprev[k];
+      }
+      // the new last-row value for the next strip, tagged
+      const bool pub = lagk == 31 && publish && act;
+      unsigned long long* e = edge + ((long long)q * nx + (pub ? c : 0)) * W::WPC;
 #pragma unroll
       for (int k = 0; k < NC; ++k)
-        xS[k] = FWD ? __shfl_up_sync(FULL, res[k], 1) : __shfl_down_sync(FULL, res[k], 1);
-      if (s < nx && s >= known_s) {   // the lead lane's south value of column s
-        int h = 0;
-        for (int it = 0;; ++it) {
-          if (lane == lead) {
-            h = lds_acquire(&ctl[W::SOUTH]);
-            if (h <= s && lds_acquire(&ctl[W::FAIL])) h = -1;
-          }
-          h = __shfl_sync(FULL, h, lead);
-          if (h > s || h < 0) break;
-          if (it + 1 >= spin_limit) { timeout = true; break; }
-        }
-        if (h <= s) { failed = true; break; }
-        known_s = h;
-      }
-      const int cn = s - 31;   // the trail lane's column
-      if (cn >= 0 && cn < nx && cn >= known_n) {
-        int h = 0;
-        for (int it = 0;; ++it) {
-          if (lane == trail) {
-            h = lds_acquire(&ctl[W::NORTH]);
-            if (h <= cn && lds_acquire(&ctl[W::FAIL])) h = -1;
-          }
-          h = __shfl_sync(FULL, h, trail);
-          if (h > cn || h < 0) break;
-          if (it + 1 >= spin_limit) { timeout = true; break; }
-        }
-        if (h <= cn) { failed = true; break; }
-        known_n = h;
-      }
-      if (act) {
-        const int rs = (c & (SGS_RING - 1)) * NC;
-        if (lagk == 0 && hasS) {
 #pragma unroll
-          for (int k = 0; k < NC; ++k) xS[k] = ring_s[rs + k];
-        }
-        const T* Vl = V + line * 32 + lane;
-        const int ES = S * 32;   // stride between entries in the stage
-        T xe[NC], xn[NC], bb[NC];
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-          xe[k] = Vl[(EX + k) * ES];
-          xn[k] = lagk == 31 ? (hasN ? ring_n[rs + k] : T(0)) : Vl[(EX + k) * ES + (FWD ? 1 : -1)];
-          bb[k] = Vl[(EB + k) * ES];
-        }
-        sgs_cell<NC, T>(Vl + oW * ES, Vl + oE * ES, Vl + oS * ES, Vl + oN * ES, ES, Vl + (size_t)NOFF * ES,
-                        PV[line * 32 + lane], bb, c > 0, xprev, c < nx - 1, xe, hasS, xS, hasN, xn, res);
-        const long long slot = (dbase + line) * 32 + lane;   // coalesced: one line per step
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-          x[k * P + slot] = res[k];
-          xprev[k] = res[k];
-        }
-        if (lagk == 31 && publish) {   // the new last-row value for the next strip, tagged
-          unsigned long long* e = edge + ((long long)q * nx + c) * W::WPC;
-#pragma unroll
-          for (int k = 0; k < NC; ++k)
-#pragma unroll
-            for (int h = 0; h < Words<T>::N; ++h)
-              st_tagged(e + k * Words<T>::N + h, ((unsigned long long)epoch << 32) | Words<T>::get(res[k], h));
-        }
-      }
-      // ring slots the lead and trail lanes are done with
-      if (lagk == 0 && s < nx && ((s + 1) % W::GS == 0 || s == nx - 1)) sts_release(&ctl[W::LEAD], s + 1);
-      if (lagk == 31 && cn >= 0 && cn < nx && ((cn + 1) % W::GN == 0 || cn == nx - 1))
-        sts_release(&ctl[W::TRAIL], cn + 1);
+        for (int h = 0; h < Words<T>::N; ++h)
+          st_tagged_if(e + k * Words<T>::N + h, ((unsigned long long)epoch << 32) | Words<T>::get(rnew[k], h), pub);
     }
-    __syncwarp();
-    if (failed) break;
-    if (lane == 0) mbar_arrive(&bar[2 + st]);   // the buffer goes back to the loader
+#pragma unroll
+    for (int k = 0; k < NC; ++k) res[k] = rnew[k];
+    // ring slots the lead and trail lanes are done with (pace the loader)
+    const int cn = s - 31;
+    sts_vol_if(&ctl[W::LEAD], s + 1, lagk == 0 && s < nx && (((s + 1) & (W::GS - 1)) == 0 || s == nx - 1));
+    sts_vol_if(&ctl[W::TRAIL], cn + 1,
+               lagk == 31 && cn >= 0 && cn < nx && (((cn + 1) & (W::GN - 1)) == 0 || cn == nx - 1));
+#pragma unroll
+    for (int e = 0; e < BS; ++e) { cAW[e] = nAW[e]; cAS[e] = nAS[e]; }
+#pragma unroll
+    for (int e = 0; e < LU_E; ++e) cLU[e] = nLU[e];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) { ca[k] = na[k]; crv[k] = nrv[k]; }
+    cpv = npv;
   }
-  if (failed && lane == 0) {
-    if (timeout) atomicOr(sticky_err, 1);
-    sts_release(&ctl[W::FAIL], 1);
+  if (!failed && __any_sync(FULL, bad != 0)) failed = true;
+  if (!failed) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&bar[2 + ((nsteps - 1) / S & 1)]);   // the last buffer goes back
+  } else if (lane == 0) {
+    if (timeout || bad == 2) atomicOr(sticky_err, 1);
+    sts_vol(&ctl[W::FAIL], 1);
     st_release(abort_flag, 1);
+  }
+  if (failed) {
+    const int b2 = __any_sync(FULL, bad == 2);
+    if (lane == 0 && b2) atomicOr(sticky_err, 1);
   }
   return !failed;
 }
 
-// warp 1 of k_sgs_ws: operator chunks, the north ring, the south ring.  One
-// pass of its loop looks at each task once and never blocks on any of them.
+// warps 1 and 2 of k_sgs_ws: role 1 the south ring (polling the previous
+// strip's tagged words), role 2 the operator chunks and the north ring.  One
+// pass of the loop looks at each of the role's tasks once and blocks on none.
 // Returns false when its wait ran out (sticky error and abort word set here)
-// or the compute warp or another CTA failed.
+// or another warp or CTA failed.
 template <int NC, typename T, bool FWD, int S>
 __device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restrict__ blk,
                                               const T* __restrict__ lu, const int8_t* __restrict__ piv,
                                               const T* __restrict__ b, const T* x,
                                               const unsigned long long* edge, unsigned epoch, int* abort_flag,
                                               int* sticky_err, int q, int nstrips, int spin_limit,
-                                              unsigned char* smem, unsigned& parity_e, unsigned& used) {
+                                              unsigned char* smem, unsigned& parity_e, unsigned& used,
+                                              int role) {
   using W = SgsWs<NC, T>;
   constexpr int BS = NC * NC;
   constexpr int NOFF = 4 * BS;
@@ -893,10 +1029,11 @@ __device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restric
   auto pvs = [&](int st) {
     return reinterpret_cast<int8_t*>(smem + 128 + (size_t)st * STAGE + (size_t)NE * S * 32 * sizeof(T));
   };
-  T* ring_n = reinterpret_cast<T*>(smem + 128 + 2 * STAGE) + SGS_RING * NC;
-  unsigned* ring_s32 = reinterpret_cast<unsigned*>(smem + 128 + 2 * STAGE);
+  unsigned long long* ring_s = reinterpret_cast<unsigned long long*>(smem + 128 + 2 * STAGE);
+  unsigned long long* ring_n = ring_s + SGS_RING * W::WPC;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const unsigned tag0 = (unsigned)q * (unsigned)nx;   // ring tag of column c: tag0 + c
   const long long P = skew_slots(nx, ny);
   const int nsteps_full = nx + 31;
   const int ps = FWD ? q : nstrips - 1 - q;
@@ -906,6 +1043,7 @@ __device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restric
   const int nchunks = (nsteps + S - 1) / S;
   // chunk j (S lines) of the operator, LU factors, b and the old x lines one
   // step ahead, as in k_sgs_strip
+  // (copies spread over the warp's lanes: one bulk copy per lane at a time)
   auto issue = [&](int j, int st) {
     const int s0 = j * S, cnt = min(S, nsteps - s0);
     const int dlo = FWD ? s0 : nsteps_full - s0 - cnt;
@@ -914,19 +1052,25 @@ __device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restric
     const int xlo = dlo + (FWD ? 1 : -1);
     const int xa = max(xlo, 0), xb = min(xlo + cnt, nsteps_full);
     const unsigned xbytes = xb > xa ? (unsigned)((xb - xa) * 32 * sizeof(T)) : 0u;
-    fence_proxy_async();
-    mbar_expect_tx(&bar[st], vb * EX + xbytes * NC + (unsigned)(cnt * 32));
-    for (int e = 0; e < NOFF; ++e)
-      bulk_g2s(vals(st) + (size_t)e * S * 32, blk + (long long)(BS + e) * P + off, vb, &bar[st]);
-    for (int e = 0; e < LU_E; ++e)
-      bulk_g2s(vals(st) + (size_t)(NOFF + e) * S * 32, lu + (long long)e * P + off, vb, &bar[st]);
-    for (int k = 0; k < NC; ++k)
-      bulk_g2s(vals(st) + (size_t)(EB + k) * S * 32, b + (long long)k * P + off, vb, &bar[st]);
-    if (xbytes)
-      for (int k = 0; k < NC; ++k)
-        bulk_g2s(vals(st) + (size_t)(EX + k) * S * 32 + (size_t)(xa - xlo) * 32,
-                 x + (long long)k * P + (line_base + xa) * 32, xbytes, &bar[st]);
-    bulk_g2s(pvs(st), piv + off, (unsigned)(cnt * 32), &bar[st]);
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(&bar[st], vb * EX + xbytes * NC + (unsigned)(cnt * 32));
+    }
+    __syncwarp();
+    const int ncopy = EX + (xbytes ? NC : 0) + 1;   // operator, LU, b, old x, pivot codes
+    for (int e = lane; e < ncopy; e += 32) {
+      if (e < NOFF)
+        bulk_g2s(vals(st) + (size_t)e * S * 32, blk + (long long)(BS + e) * P + off, vb, &bar[st]);
+      else if (e < NOFF + LU_E)
+        bulk_g2s(vals(st) + (size_t)e * S * 32, lu + (long long)(e - NOFF) * P + off, vb, &bar[st]);
+      else if (e < EX)
+        bulk_g2s(vals(st) + (size_t)e * S * 32, b + (long long)(e - EB) * P + off, vb, &bar[st]);
+      else if (e < ncopy - 1)
+        bulk_g2s(vals(st) + (size_t)e * S * 32 + (size_t)(xa - xlo) * 32,
+                 x + (long long)(e - EX) * P + (line_base + xa) * 32, xbytes, &bar[st]);
+      else
+        bulk_g2s(pvs(st), piv + off, (unsigned)(cnt * 32), &bar[st]);
+    }
   };
   // the lead lane (lag 0) takes its south values from the previous strip, the
   // trail lane (lag 31) its north values from the row beyond the strip
@@ -934,45 +1078,17 @@ __device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restric
   const bool need_s = q > 0 && ylead < ny && (FWD ? ylead > 0 : ylead < ny - 1);
   const bool need_n = ytrail < ny && (FWD ? ytrail < ny - 1 : ytrail > 0);
   const int yN = FWD ? ytrail + 1 : ytrail - 1;
-  int next = 0, s_loaded = need_s ? 0 : nx, n_loaded = need_n ? 0 : nx;
+  int next = role == 2 ? 0 : nchunks;
+  int s_loaded = role == 1 && need_s ? 0 : nx;
+  int n_loaded = role == 2 && need_n ? 0 : nx;
   bool failed = false, timeout = false;
   for (int idle = 0;;) {
     bool prog = false;
-    if (next < nchunks) {   // the next chunk, once its buffer is free
-      const int st = next & 1;
-      bool free_buf = true;
-      if ((used >> st) & 1u) {
-        int ok = 0;
-        if (lane == 0) ok = mbar_try_wait(&bar[2 + st], (parity_e >> st) & 1u) ? 1 : 0;
-        free_buf = __shfl_sync(FULL, ok, 0) != 0;
-      }
-      if (free_buf) {
-        if ((used >> st) & 1u) parity_e ^= 1u << st;
-        used |= 1u << st;
-        if (lane == 0) issue(next, st);
-        ++next;
-        prog = true;
-      }
-    }
-    if (n_loaded < nx) {   // old values beyond the strip's last row, GN columns at a time
-      const int tdone = lds_acquire(&ctl[W::TRAIL]);
-      if (__all_sync(FULL, n_loaded + W::GN <= tdone + SGS_RING)) {
-        if (lane < W::GN * NC) {
-          const int t = lane / NC, k = lane % NC, c = n_loaded + t;
-          if (c < nx) {
-            const int px = FWD ? c : nx - 1 - c;
-            ring_n[(c & (SGS_RING - 1)) * NC + k] = __ldcg(&x[k * P + skew_pos(px, yN, nx)]);
-          }
-        }
-        __syncwarp();
-        n_loaded = min(n_loaded + W::GN, nx);
-        if (lane == 0) sts_release(&ctl[W::NORTH], n_loaded);
-        prog = true;
-      }
-    }
     if (s_loaded < nx) {   // the previous strip's new last row, up to GS columns at a time
-      const int ldone = lds_acquire(&ctl[W::LEAD]);
-      if (__all_sync(FULL, s_loaded + W::GS <= ldone + SGS_RING)) {
+      int ldone = 0;
+      if (lane == 0) ldone = lds_vol(&ctl[W::LEAD]);
+      ldone = __shfl_sync(FULL, ldone, 0);
+      if (s_loaded + W::GS <= ldone + SGS_RING) {
         const int t = lane / W::WPC, w = lane % W::WPC, c = s_loaded + t;
         const bool mine = lane < W::GS * W::WPC && c < nx;
         unsigned long long word = 0ull;
@@ -985,12 +1101,48 @@ __device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restric
         int nv = stale ? (__ffs(stale) - 1) / W::WPC : W::GS;   // columns before the first stale word
         nv = min(nv, nx - s_loaded);
         if (nv > 0) {
-          if (mine && t < nv) ring_s32[(c & (SGS_RING - 1)) * W::WPC + w] = (unsigned)word;
-          __syncwarp();
+          if (mine && t < nv)
+            sts64_vol(ring_s + (c & (SGS_RING - 1)) * W::WPC + w,
+                      ((unsigned long long)(tag0 + (unsigned)c) << 32) | (unsigned)word);
           s_loaded += nv;
-          if (lane == 0) sts_release(&ctl[W::SOUTH], s_loaded);
           prog = true;
         }
+      }
+    }
+    if (next < nchunks) {   // the next chunk, once its buffer is free
+      const int st = next & 1;
+      bool free_buf = true;
+      if ((used >> st) & 1u) {
+        int ok = 0;
+        if (lane == 0) ok = mbar_try_wait(&bar[2 + st], (parity_e >> st) & 1u) ? 1 : 0;
+        free_buf = __shfl_sync(FULL, ok, 0) != 0;
+      }
+      if (free_buf) {
+        if ((used >> st) & 1u) parity_e ^= 1u << st;
+        used |= 1u << st;
+        issue(next, st);
+        ++next;
+        prog = true;
+      }
+    }
+    if (n_loaded < nx) {   // old values beyond the strip's last row, GN columns at a time
+      int tdone = 0;
+      if (lane == 0) tdone = lds_vol(&ctl[W::TRAIL]);
+      tdone = __shfl_sync(FULL, tdone, 0);
+      if (n_loaded + W::GN <= tdone + SGS_RING) {
+        if (lane < W::GN * NC) {
+          const int t = lane / NC, k = lane % NC, c = n_loaded + t;
+          if (c < nx) {
+            const int px = FWD ? c : nx - 1 - c;
+            const T v = __ldcg(&x[k * P + skew_pos(px, yN, nx)]);
+            const unsigned long long tg = (unsigned long long)(tag0 + (unsigned)c) << 32;
+#pragma unroll
+            for (int h = 0; h < Words<T>::N; ++h)
+              sts64_vol(ring_n + (c & (SGS_RING - 1)) * W::WPC + k * Words<T>::N + h, tg | Words<T>::get(v, h));
+          }
+        }
+        n_loaded = min(n_loaded + W::GN, nx);
+        prog = true;
       }
     }
     if (next >= nchunks && n_loaded >= nx && s_loaded >= nx) break;
@@ -999,7 +1151,7 @@ __device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restric
       continue;
     }
     int stop = 0;
-    if (lane == 0) stop = (lds_acquire(&ctl[W::FAIL]) || ld_acquire(abort_flag)) ? 1 : 0;
+    if (lane == 0) stop = (lds_vol(&ctl[W::FAIL]) || ldg_vol(abort_flag)) ? 1 : 0;
     if (__shfl_sync(FULL, stop, 0)) {
       failed = true;
       break;
@@ -1011,10 +1163,10 @@ __device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restric
     __nanosleep(20);
   }
   if (lane == 0) {
-    ctl[W::ISSUED] = next;
+    if (role == 2) ctl[W::ISSUED] = next;
     if (failed) {
       if (timeout) atomicOr(sticky_err, 1);
-      sts_release(&ctl[W::FAIL], 1);
+      sts_vol(&ctl[W::FAIL], 1);
       st_release(abort_flag, 1);
     }
   }
@@ -1022,7 +1174,7 @@ __device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restric
 }
 
 template <int NC, typename T, bool FWD, int S>
-__global__ void __launch_bounds__(64, 1) k_sgs_ws(int nx, int ny, const T* __restrict__ blk,
+__global__ void __launch_bounds__(96, 1) k_sgs_ws(int nx, int ny, const T* __restrict__ blk,
                                                   const T* __restrict__ lu, const int8_t* __restrict__ piv,
                                                   const T* __restrict__ b, T* x, int* sync,
                                                   unsigned long long* edge, unsigned epoch, int* sticky_err,
@@ -1036,14 +1188,16 @@ __global__ void __launch_bounds__(64, 1) k_sgs_ws(int nx, int ny, const T* __res
     ctl[W::FAIL] = 0;
     fence_proxy_async();
   }
+  {   // empty ring words: a tag no column has
+    unsigned long long* ring = reinterpret_cast<unsigned long long*>(smem + 128 + 2 * sgs_stage_bytes<NC, T, S>());
+    for (int i = threadIdx.x; i < 2 * SGS_RING * W::WPC; i += blockDim.x) ring[i] = ~0ull;
+  }
   __syncthreads();
   const int warp = threadIdx.x >> 5;
   unsigned parity_f = 0u, parity_e = 0u, used = 0u;   // bit st: stage st
   for (;;) {
     if (threadIdx.x == 0) {
       ctl[W::Q] = atomicAdd(&sync[0], 1);
-      ctl[W::SOUTH] = 0;
-      ctl[W::NORTH] = 0;
       ctl[W::LEAD] = 0;
       ctl[W::TRAIL] = 0;
       ctl[W::ISSUED] = 0;
@@ -1057,7 +1211,7 @@ __global__ void __launch_bounds__(64, 1) k_sgs_ws(int nx, int ny, const T* __res
                                     parity_f, waited);
     else
       sgs_ws_loader<NC, T, FWD, S>(nx, ny, blk, lu, piv, b, x, edge, epoch, sync + 1, sticky_err, q, nstrips,
-                                   spin_limit, smem, parity_e, used);
+                                   spin_limit, smem, parity_e, used, warp);
     __syncthreads();
     if (ctl[W::FAIL]) {
       // the bulk copies in flight land before the CTA's shared memory goes
@@ -1722,7 +1876,7 @@ static void sgs_ws_launch(int nx, int ny, const void* blk, const void* lu, const
     cudaFuncSetAttribute(k_sgs_ws<NC, T, F, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
   }
-  k_sgs_ws<NC, T, F, S><<<nstrips, 64, smem, st>>>(nx, ny, (const T*)blk, (const T*)lu, piv, (const T*)b,
+  k_sgs_ws<NC, T, F, S><<<nstrips, 96, smem, st>>>(nx, ny, (const T*)blk, (const T*)lu, piv, (const T*)b,
                                                     (T*)x, sync, edge, epoch, sticky, nstrips, wait_limit());
 }
 
