@@ -682,12 +682,13 @@ __global__ void __launch_bounds__(32, 1) k_sgs_strip(int nx, int ny, const T* __
 //   warp 1 moves the previous strip's new last-row values into a shared ring;
 //   warp 2 stages the operator chunks into the two shared buffers
 //     (cp.async.bulk, mbarrier completion; the compute warp hands a buffer
-//     back through a second mbarrier) and loads the old values of the row
-//     beyond the strip's last row (the next strip's first row in sweep order)
-//     into a second ring.  Ring words carry the strip and column they hold, so the
-//     compute warp needs no fence to read them (a fence would wait for its
-//     own stores in flight); it reports the columns it is done with through
-//     plain counters that only pace the loader.
+//     back through a second mbarrier) and, once a chunk has landed, forms the
+//     old east / north part of every step of it (a third mbarrier), so that
+//     a step of warp 0 is only the new west / south terms and the LU solve.
+// Ring words carry the strip and column they hold, so the compute warp needs
+// no fence to read them (a fence would wait for its own stores in flight);
+// it reports the columns it is done with through a plain counter that only
+// paces warp 1.
 // Hand-off between strips without fences: the strip's last lane writes every
 // new value of its row as 64-bit words, each holding 32 bits of the value and
 // the launch's epoch (a counter that differs between launches).  The next
@@ -786,79 +787,79 @@ template <int NC, typename T>
 struct SgsWs {
   static constexpr int WPC = NC * Words<T>::N;         // tagged words per column
   static constexpr int GS = pow2_floor(32 / WPC);      // previous-strip columns polled at once
-  static constexpr int GN = pow2_floor(32 / NC);       // north columns loaded at once
-  // control block (the first 128 bytes): full[2], empty[2] mbarriers in
-  // bytes 0-31, then these int slots (indices into the block as int[32])
-  static constexpr int Q = 8, LEAD = 9, TRAIL = 10, FAIL = 11, ISSUED = 12;
-  static_assert(Q * 4 >= 32 && ISSUED * 4 + 4 <= 128, "control slots must sit between the barriers and byte 128");
-  static_assert(GS * WPC <= 32 && GN * NC <= 32 && 2 * GS <= SGS_RING && 2 * GN <= SGS_RING, "ring groups");
+  // control block (the first 128 bytes): mbarriers full[2] (a chunk's bulk
+  // copies landed), empty[2] (the compute warp is done with a buffer),
+  // afull[2] (the chunk's old east / north parts are written) in bytes 0-47,
+  // then these int slots (indices into the block as int[32])
+  static constexpr int Q = 12, LEAD = 13, FAIL = 14, ISSUED = 15;
+  static_assert(Q * 4 >= 48 && ISSUED * 4 + 4 <= 128, "control slots must sit between the barriers and byte 128");
+  static_assert(GS * WPC <= 32 && 2 * GS <= SGS_RING, "ring groups");
 };
 
-// The rings hold 64-bit words: 32 bits of a value and, above them, the tag
-// q * nx + c of the strip q and column c it belongs to (all ones: empty).
+// Shared memory of k_sgs_ws: control block, two staging buffers, two buffers
+// of the old east / north parts (S lines x NC x 32 lanes), the north values of
+// a chunk (S x NC), the south ring.  The ring holds 64-bit words: 32 bits of a
+// value and, above them, the tag q * nx + c of the strip q and column c it
+// belongs to (all ones: empty).
 template <int NC, typename T, int S>
-size_t sgs_ws_smem_bytes() {   // control block, two staging buffers, two rings
-  return 128 + 2 * sgs_stage_bytes<NC, T, S>() + 2 * (size_t)SGS_RING * SgsWs<NC, T>::WPC * 8;
-}
+struct SgsWsLayout {
+  static constexpr size_t STAGE = sgs_stage_bytes<NC, T, S>();
+  static constexpr size_t ABUF = (size_t)S * NC * 32 * sizeof(T);
+  static constexpr size_t OFF_A = 128 + 2 * STAGE;
+  static constexpr size_t OFF_N = OFF_A + 2 * ABUF;
+  static constexpr size_t OFF_R = OFF_N + ((S * NC * sizeof(T) + 15) / 16) * 16;
+  static constexpr size_t BYTES = OFF_R + (size_t)SGS_RING * SgsWs<NC, T>::WPC * 8;
+};
 
-// warp 0 of k_sgs_ws: the strip's cell updates, software-pipelined: while a
-// step runs its dependent chain (the new west and south terms, the LU solve),
-// the same instruction stream loads the next step's operands from shared
-// memory into registers and forms its old east / north part.  waited counts
-// the chunks whose staging completed.  Returns false when a wait ran out
-// (sticky error and abort word set here) or another warp failed.
+template <int NC, typename T, int S>
+size_t sgs_ws_smem_bytes() { return SgsWsLayout<NC, T, S>::BYTES; }
+
+// warp 0 of k_sgs_ws: the strip's cell updates.  Per step it reads the new
+// west (its own last result) and south (the lane below; for the lane of lag
+// 0 the previous strip, through the south ring) values, the W and S blocks,
+// the LU factors and the old east / north part that warp 2 formed for the
+// chunk, and finishes the cell (sgs_cell_new).  waited counts the chunks
+// whose staging completed.  Returns false when a wait ran out (sticky error
+// and abort word set here) or another warp failed.
 template <int NC, typename T, bool FWD, int S>
 __device__ __forceinline__ bool sgs_ws_compute(int nx, int ny, T* x, unsigned long long* edge, unsigned epoch,
                                                int* abort_flag, int* sticky_err, int q, int nstrips,
                                                int spin_limit, unsigned char* smem, unsigned& parity_f,
-                                               int& waited) {
+                                               unsigned& parity_a, int& waited) {
   using W = SgsWs<NC, T>;
+  using LY = SgsWsLayout<NC, T, S>;
   constexpr int BS = NC * NC;
   constexpr int NOFF = 4 * BS;
-  constexpr int EB = NOFF + LU_E;
-  constexpr int EX = EB + NC;
+  constexpr int EX = NOFF + LU_E + NC;
   constexpr int NE = EX + NC;
   constexpr int ES = S * 32;   // stride between entries in a stage
-  constexpr size_t STAGE = sgs_stage_bytes<NC, T, S>();
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);   // full[0..1], empty[2..3]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);   // full[0..1], empty[2..3], afull[4..5]
   int* ctl = reinterpret_cast<int*>(smem);
-  auto vals = [&](int st) { return reinterpret_cast<const T*>(smem + 128 + (size_t)st * STAGE); };
-  auto pvs = [&](int st) {
-    return reinterpret_cast<const int8_t*>(smem + 128 + (size_t)st * STAGE + (size_t)NE * S * 32 * sizeof(T));
-  };
-  const unsigned long long* ring_s = reinterpret_cast<const unsigned long long*>(smem + 128 + 2 * STAGE);
-  const unsigned long long* ring_n = ring_s + SGS_RING * W::WPC;
+  const unsigned long long* ring_s = reinterpret_cast<const unsigned long long*>(smem + LY::OFF_R);
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const long long P = skew_slots(nx, ny);
   const unsigned tag0 = (unsigned)q * (unsigned)nx;   // ring tag of column c: tag0 + c
-  const int oW = (FWD ? 0 : 1) * BS, oE = (FWD ? 1 : 0) * BS, oS = (FWD ? 2 : 3) * BS,
-            oN = (FWD ? 3 : 2) * BS;
+  const int oW = (FWD ? 0 : 1) * BS, oS = (FWD ? 2 : 3) * BS;
   const int lagk = FWD ? lane : 31 - lane;
   const int nsteps_full = nx + 31;
   const int ps = FWD ? q : nstrips - 1 - q;
   const long long line_base = (long long)ps * (nx + 31);
   const int rows = min(32, ny - ps * 32);
   const int nsteps = FWD ? nx + rows - 1 : nsteps_full;
+  const int nchunks = (nsteps + S - 1) / S;
   const int y = ps * 32 + lane;
   const bool rowok = y < ny;
   const bool hasS = FWD ? (y > 0) : (y < ny - 1);
-  const bool hasN = FWD ? (y < ny - 1) : (y > 0);
-  const int lead = FWD ? 0 : 31, trail = FWD ? 31 : 0;   // the lanes of lag 0 and lag 31
+  const int lead = FWD ? 0 : 31;   // the lane of lag 0
   const bool need_s = q > 0 && __shfl_sync(FULL, (int)(rowok && hasS), lead) != 0;
-  const bool need_n = __shfl_sync(FULL, (int)(rowok && hasN), trail) != 0;
   const bool publish = q + 1 < nstrips;
-  bool timeout = false;
+  bool timeout = false, failed = false;
   int bad = 0;   // this lane's ring wait: 1 another warp failed, 2 ran out
-  // bounded wait for chunk j's staging (warp-uniform)
-  auto wait_chunk = [&](int j) -> bool {
-    const int st = j & 1;
+  // bounded wait for a barrier phase (warp-uniform), watching the fail word
+  auto wait_bar = [&](uint64_t* b, unsigned par) -> bool {
     for (int it = 0;; ++it) {
-      if (__all_sync(FULL, mbar_try_wait(&bar[st], (parity_f >> st) & 1u))) {
-        parity_f ^= 1u << st;
-        ++waited;
-        return true;
-      }
+      if (__all_sync(FULL, mbar_try_wait(b, par))) return true;
       int f = 0;
       if (lane == 0) f = lds_vol(&ctl[W::FAIL]);
       if (__shfl_sync(FULL, f, 0)) return false;
@@ -868,182 +869,157 @@ __device__ __forceinline__ bool sgs_ws_compute(int nx, int ny, T* x, unsigned lo
       }
     }
   };
-  // the lane's ring words of column cr (want: the lane reads a ring this
-  // step), once their tag names this strip and column; the wait, when some
-  // lane's words are not there yet, is warp-uniform
-  auto ring_get = [&](const unsigned long long* ring, int cr, bool want, T v[NC]) {
-    const unsigned long long* r = ring + (cr & (SGS_RING - 1)) * W::WPC;
-    const unsigned tg = tag0 + (unsigned)cr;
-    unsigned bits[W::WPC];
-    bool ok = true;
-#pragma unroll
-    for (int w = 0; w < W::WPC; ++w) {
-      const unsigned long long v64 = lds64_vol_if(r + w, want);
-      bits[w] = (unsigned)v64;
-      ok = ok && (unsigned)(v64 >> 32) == tg;
-    }
-    ok = ok || !want;
-    if (__any_sync(FULL, !ok)) {
-      for (int it = 1; !ok && !bad; ++it) {
-        ok = true;
-#pragma unroll
-        for (int w = 0; w < W::WPC; ++w) {
-          const unsigned long long v64 = lds64_vol(r + w);
-          bits[w] = (unsigned)v64;
-          ok = ok && (unsigned)(v64 >> 32) == tg;
-        }
-        if (!ok && (it & 63) == 63 && lds_vol(&ctl[W::FAIL])) bad = 1;
-        else if (!ok && it + 1 >= spin_limit) bad = 2;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < NC; ++k) v[k] = want ? Words<T>::make(bits + k * Words<T>::N) : T(0);
-  };
-  // step s's operands: W and S blocks, LU factors and pivot code, the old
-  // east / north part, and the lane's ring value (lead: south, trail: north)
-  T cAW[BS], cAS[BS], cLU[LU_E], ca[NC], crv[NC];
-  T nAW[BS], nAS[BS], nLU[LU_E], na[NC], nrv[NC];
-  int8_t cpv = 0, npv = 0;
-  auto load_step = [&](int s, T AWo[BS], T ASo[BS], T LUo[LU_E], int8_t& pvo, T ao[NC], T rvo[NC]) {
-    const int j = s / S, s0 = j * S, cnt = min(S, nsteps - s0);
-    const int line = FWD ? s - s0 : cnt - 1 - (s - s0);
-    const T* Vl = vals(j & 1) + line * 32 + lane;
-#pragma unroll
-    for (int e = 0; e < BS; ++e) {
-      AWo[e] = Vl[(oW + e) * ES];
-      ASo[e] = Vl[(oS + e) * ES];
-    }
-#pragma unroll
-    for (int e = 0; e < LU_E; ++e) LUo[e] = Vl[(NOFF + e) * ES];
-    pvo = pvs(j & 1)[line * 32 + lane];
-    const int cn = s - 31;
-    const bool rl = lagk == 0 && need_s && s < nx;
-    const bool rt = lagk == 31 && need_n && cn >= 0 && cn < nx;
-    ring_get(lagk == 0 ? ring_s : ring_n, lagk == 0 ? s : cn, rl || rt, rvo);
-    T xe[NC], xn[NC], bb[NC];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      xe[k] = Vl[(EX + k) * ES];
-      xn[k] = lagk == 31 ? rvo[k] : Vl[(EX + k) * ES + (FWD ? 1 : -1)];
-      bb[k] = Vl[(EB + k) * ES];
-    }
-    sgs_cell_old<NC, T>(Vl + oE * ES, Vl + oN * ES, ES, bb, s - lagk < nx - 1, xe, hasN, xn, ao);
-  };
-  bool failed = !wait_chunk(0);
-  if (!failed) load_step(0, cAW, cAS, cLU, cpv, ca, crv);
   T xprev[NC], res[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) { xprev[k] = T(0); res[k] = T(0); }
-  for (int s = 0; s < nsteps && !failed; ++s) {
-    const int c = s - lagk;
-    const bool act = rowok && c >= 0 && c < nx;
-    // step s: the new west (own last result) and south (lane below, or the
-    // previous strip through the ring for the lead lane) terms, the LU solve
-    T xS[NC], rnew[NC];
+  for (int j = 0; j < nchunks; ++j) {
+    const int st = j & 1;
+    if (!wait_bar(&bar[st], (parity_f >> st) & 1u)) { failed = true; break; }
+    parity_f ^= 1u << st;
+    ++waited;
+    if (!wait_bar(&bar[4 + st], (parity_a >> st) & 1u)) { failed = true; break; }
+    parity_a ^= 1u << st;
+    const T* V = reinterpret_cast<const T*>(smem + 128 + (size_t)st * LY::STAGE) + lane;
+    const int8_t* PV = reinterpret_cast<const int8_t*>(smem + 128 + (size_t)st * LY::STAGE +
+                                                       (size_t)NE * S * 32 * sizeof(T)) + lane;
+    const T* A = reinterpret_cast<const T*>(smem + LY::OFF_A + (size_t)st * LY::ABUF) + lane;
+    const int s0 = j * S, cnt = min(S, nsteps - s0);
+#pragma unroll 2
+    for (int i = 0; i < cnt; ++i) {
+      const int s = s0 + i;
+      const int line = FWD ? i : cnt - 1 - i;
+      const T* Vl = V + line * 32;
+      const int c = s - lagk;
+      const bool act = rowok && (unsigned)c < (unsigned)nx;
+      T aw[BS], as[BS], lu[LU_E], a[NC];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      xS[k] = FWD ? __shfl_up_sync(FULL, res[k], 1) : __shfl_down_sync(FULL, res[k], 1);
-      if (lagk == 0) xS[k] = crv[k];
-    }
-    sgs_cell_new<NC, T>(cAW, cAS, cLU, cpv, ca, c > 0, xprev, hasS, xS, rnew);
-    // step s + 1's operands, independent of this step's result
-    const int s1 = s + 1;
-    if (s1 < nsteps) {
-      if (s1 % S == 0) {   // a new chunk: the finished buffer goes back to the loader
-        __syncwarp();
-        mbar_arrive_if(&bar[2 + ((s1 / S - 1) & 1)], lane == 0);
-        if (__any_sync(FULL, bad != 0) || !wait_chunk(s1 / S)) failed = true;
+      for (int e = 0; e < BS; ++e) {
+        aw[e] = Vl[(oW + e) * ES];
+        as[e] = Vl[(oS + e) * ES];
       }
-      if (!failed) load_step(s1, nAW, nAS, nLU, npv, na, nrv);
-    }
-    {
+#pragma unroll
+      for (int e = 0; e < LU_E; ++e) lu[e] = Vl[(NOFF + e) * ES];
+      const int8_t pv = PV[line * 32];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) a[k] = A[(line * NC + k) * 32];
+      // the lead lane's south value of column s, once its ring words carry
+      // this strip's and column's tag (the wait is warp-uniform)
+      const bool want = lagk == 0 && need_s && s < nx;
+      T rv[NC];
+      {
+        const unsigned long long* r = ring_s + (s & (SGS_RING - 1)) * W::WPC;
+        const unsigned tg = tag0 + (unsigned)s;
+        unsigned bits[W::WPC];
+        bool ok = true;
+#pragma unroll
+        for (int w = 0; w < W::WPC; ++w) {
+          const unsigned long long v64 = lds64_vol_if(r + w, want);
+          bits[w] = (unsigned)v64;
+          ok = ok && (unsigned)(v64 >> 32) == tg;
+        }
+        ok = ok || !want;
+        if (__any_sync(FULL, !ok)) {
+          for (int it = 1; !ok && !bad; ++it) {
+            ok = true;
+#pragma unroll
+            for (int w = 0; w < W::WPC; ++w) {
+              const unsigned long long v64 = lds64_vol(r + w);
+              bits[w] = (unsigned)v64;
+              ok = ok && (unsigned)(v64 >> 32) == tg;
+            }
+            if (!ok && (it & 63) == 63 && lds_vol(&ctl[W::FAIL])) bad = 1;
+            else if (!ok && it + 1 >= spin_limit) bad = 2;
+          }
+          if (__any_sync(FULL, bad != 0)) { failed = true; break; }
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k) rv[k] = Words<T>::make(bits + k * Words<T>::N);
+      }
+      T xS[NC], rnew[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        xS[k] = FWD ? __shfl_up_sync(FULL, res[k], 1) : __shfl_down_sync(FULL, res[k], 1);
+        if (lagk == 0) xS[k] = rv[k];
+      }
+      sgs_cell_new<NC, T>(aw, as, lu, pv, a, c > 0, xprev, hasS, xS, rnew);
       const long long slot = (line_base + (FWD ? s : nsteps_full - 1 - s)) * 32 + lane;
+      const bool pub = lagk == 31 && publish && act;
+      unsigned long long* e = edge + ((long long)q * nx + (pub ? c : 0)) * W::WPC;
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         if (act) x[k * P + slot] = rnew[k];
         xprev[k] = act ? rnew[k] : xprev[k];
-      }
-      // the new last-row value for the next strip, tagged
-      const bool pub = lagk == 31 && publish && act;
-      unsigned long long* e = edge + ((long long)q * nx + (pub ? c : 0)) * W::WPC;
+        res[k] = rnew[k];
 #pragma unroll
-      for (int k = 0; k < NC; ++k)
-#pragma unroll
-        for (int h = 0; h < Words<T>::N; ++h)
+        for (int h = 0; h < Words<T>::N; ++h)   // the new last-row value for the next strip, tagged
           st_tagged_if(e + k * Words<T>::N + h, ((unsigned long long)epoch << 32) | Words<T>::get(rnew[k], h), pub);
+      }
+      // south ring slots the lead lane is done with (pace the poller)
+      sts_vol_if(&ctl[W::LEAD], s + 1, lagk == 0 && s < nx && (((s + 1) & (W::GS - 1)) == 0 || s == nx - 1));
     }
-#pragma unroll
-    for (int k = 0; k < NC; ++k) res[k] = rnew[k];
-    // ring slots the lead and trail lanes are done with (pace the loader)
-    const int cn = s - 31;
-    sts_vol_if(&ctl[W::LEAD], s + 1, lagk == 0 && s < nx && (((s + 1) & (W::GS - 1)) == 0 || s == nx - 1));
-    sts_vol_if(&ctl[W::TRAIL], cn + 1,
-               lagk == 31 && cn >= 0 && cn < nx && (((cn + 1) & (W::GN - 1)) == 0 || cn == nx - 1));
-#pragma unroll
-    for (int e = 0; e < BS; ++e) { cAW[e] = nAW[e]; cAS[e] = nAS[e]; }
-#pragma unroll
-    for (int e = 0; e < LU_E; ++e) cLU[e] = nLU[e];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) { ca[k] = na[k]; crv[k] = nrv[k]; }
-    cpv = npv;
-  }
-  if (!failed && __any_sync(FULL, bad != 0)) failed = true;
-  if (!failed) {
+    if (failed) break;
     __syncwarp();
-    if (lane == 0) mbar_arrive(&bar[2 + ((nsteps - 1) / S & 1)]);   // the last buffer goes back
-  } else if (lane == 0) {
-    if (timeout || bad == 2) atomicOr(sticky_err, 1);
+    mbar_arrive_if(&bar[2 + st], lane == 0);   // the buffer goes back to warp 2
+  }
+  if (failed && lane == 0) {
+    if (timeout) atomicOr(sticky_err, 1);
     sts_vol(&ctl[W::FAIL], 1);
     st_release(abort_flag, 1);
   }
-  if (failed) {
-    const int b2 = __any_sync(FULL, bad == 2);
-    if (lane == 0 && b2) atomicOr(sticky_err, 1);
-  }
+  if (failed && __any_sync(FULL, bad == 2) && lane == 0) atomicOr(sticky_err, 1);
   return !failed;
 }
 
-// warps 1 and 2 of k_sgs_ws: role 1 the south ring (polling the previous
-// strip's tagged words), role 2 the operator chunks and the north ring.  One
-// pass of the loop looks at each of the role's tasks once and blocks on none.
+// warps 1 and 2 of k_sgs_ws.  Role 1 fills the south ring from the previous
+// strip's tagged words.  Role 2 stages the operator chunks and, once a chunk
+// has landed, forms its old east / north part for every line and lane
+// (sgs_cell_old, the north values of the strip's last lane loaded from the
+// next strip's first row, which that strip cannot have updated yet: it waits
+// for this strip's last row, which needs these values first).  One pass of
+// the loop looks at each of the role's tasks once and blocks on none.
 // Returns false when its wait ran out (sticky error and abort word set here)
 // or another warp or CTA failed.
 template <int NC, typename T, bool FWD, int S>
-__device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restrict__ blk,
+__device__ __forceinline__ bool sgs_ws_helper(int nx, int ny, const T* __restrict__ blk,
                                               const T* __restrict__ lu, const int8_t* __restrict__ piv,
                                               const T* __restrict__ b, const T* x,
                                               const unsigned long long* edge, unsigned epoch, int* abort_flag,
                                               int* sticky_err, int q, int nstrips, int spin_limit,
-                                              unsigned char* smem, unsigned& parity_e, unsigned& used,
-                                              int role) {
+                                              unsigned char* smem, unsigned& parity_e, unsigned& parity_f2,
+                                              unsigned& used, int role) {
   using W = SgsWs<NC, T>;
+  using LY = SgsWsLayout<NC, T, S>;
   constexpr int BS = NC * NC;
   constexpr int NOFF = 4 * BS;
   constexpr int EB = NOFF + LU_E;
   constexpr int EX = EB + NC;
   constexpr int NE = EX + NC;
-  constexpr size_t STAGE = sgs_stage_bytes<NC, T, S>();
+  constexpr int ES = S * 32;
+  constexpr size_t STAGE = LY::STAGE;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   int* ctl = reinterpret_cast<int*>(smem);
   auto vals = [&](int st) { return reinterpret_cast<T*>(smem + 128 + (size_t)st * STAGE); };
   auto pvs = [&](int st) {
     return reinterpret_cast<int8_t*>(smem + 128 + (size_t)st * STAGE + (size_t)NE * S * 32 * sizeof(T));
   };
-  unsigned long long* ring_s = reinterpret_cast<unsigned long long*>(smem + 128 + 2 * STAGE);
-  unsigned long long* ring_n = ring_s + SGS_RING * W::WPC;
+  unsigned long long* ring_s = reinterpret_cast<unsigned long long*>(smem + LY::OFF_R);
+  T* nbuf = reinterpret_cast<T*>(smem + LY::OFF_N);
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const unsigned tag0 = (unsigned)q * (unsigned)nx;   // ring tag of column c: tag0 + c
   const long long P = skew_slots(nx, ny);
+  const unsigned tag0 = (unsigned)q * (unsigned)nx;
+  const int oE = (FWD ? 1 : 0) * BS, oN = (FWD ? 3 : 2) * BS;
+  const int lagk = FWD ? lane : 31 - lane;
   const int nsteps_full = nx + 31;
   const int ps = FWD ? q : nstrips - 1 - q;
   const long long line_base = (long long)ps * (nx + 31);
   const int rows = min(32, ny - ps * 32);
   const int nsteps = FWD ? nx + rows - 1 : nsteps_full;
   const int nchunks = (nsteps + S - 1) / S;
+  const int y = ps * 32 + lane;
+  const bool hasN = FWD ? (y < ny - 1) : (y > 0);
   // chunk j (S lines) of the operator, LU factors, b and the old x lines one
-  // step ahead, as in k_sgs_strip
-  // (copies spread over the warp's lanes: one bulk copy per lane at a time)
+  // step ahead, copies spread over the warp's lanes
   auto issue = [&](int j, int st) {
     const int s0 = j * S, cnt = min(S, nsteps - s0);
     const int dlo = FWD ? s0 : nsteps_full - s0 - cnt;
@@ -1072,15 +1048,46 @@ __device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restric
         bulk_g2s(pvs(st), piv + off, (unsigned)(cnt * 32), &bar[st]);
     }
   };
-  // the lead lane (lag 0) takes its south values from the previous strip, the
-  // trail lane (lag 31) its north values from the row beyond the strip
-  const int ylead = ps * 32 + (FWD ? 0 : 31), ytrail = ps * 32 + (FWD ? 31 : 0);
+  // the old east / north part of every step of chunk j into its buffer
+  auto old_part = [&](int j) {
+    const int st = j & 1;
+    const int s0 = j * S, cnt = min(S, nsteps - s0);
+    // north values of the last lane's columns s - 31, s in the chunk
+    const int ytrail = ps * 32 + (FWD ? 31 : 0);
+    const bool need_n = ytrail < ny && (FWD ? ytrail < ny - 1 : ytrail > 0);
+    const int yN = FWD ? ytrail + 1 : ytrail - 1;
+    for (int idx = lane; idx < cnt * NC; idx += 32) {
+      const int t = idx / NC, k = idx - t * NC, c = s0 + t - 31;
+      T v = T(0);
+      if (need_n && c >= 0 && c < nx) v = __ldcg(&x[k * P + skew_pos(FWD ? c : nx - 1 - c, yN, nx)]);
+      nbuf[idx] = v;
+    }
+    __syncwarp();
+    const T* V = vals(st) + lane;
+    T* A = reinterpret_cast<T*>(smem + LY::OFF_A + (size_t)st * LY::ABUF) + lane;
+    for (int line = 0; line < cnt; ++line) {
+      const int i = FWD ? line : cnt - 1 - line;   // the chunk step of this line
+      const int c = s0 + i - lagk;
+      const T* Vl = V + line * 32;
+      T xe[NC], xn[NC], bb[NC], a[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        xe[k] = Vl[(EX + k) * ES];
+        xn[k] = lagk == 31 ? nbuf[i * NC + k] : Vl[(EX + k) * ES + (FWD ? 1 : -1)];
+        bb[k] = Vl[(EB + k) * ES];
+      }
+      sgs_cell_old<NC, T>(Vl + oE * ES, Vl + oN * ES, ES, bb, c < nx - 1, xe, hasN, xn, a);
+#pragma unroll
+      for (int k = 0; k < NC; ++k) A[(line * NC + k) * 32] = a[k];
+    }
+    __syncwarp();
+    mbar_arrive_if(&bar[4 + st], lane == 0);
+  };
+  const int ylead = ps * 32 + (FWD ? 0 : 31);
   const bool need_s = q > 0 && ylead < ny && (FWD ? ylead > 0 : ylead < ny - 1);
-  const bool need_n = ytrail < ny && (FWD ? ytrail < ny - 1 : ytrail > 0);
-  const int yN = FWD ? ytrail + 1 : ytrail - 1;
-  int next = role == 2 ? 0 : nchunks;
+  int next = role == 2 ? 0 : nchunks;      // chunks issued
+  int next_a = role == 2 ? 0 : nchunks;    // chunks whose old part is written
   int s_loaded = role == 1 && need_s ? 0 : nx;
-  int n_loaded = role == 2 && need_n ? 0 : nx;
   bool failed = false, timeout = false;
   for (int idle = 0;;) {
     bool prog = false;
@@ -1109,6 +1116,16 @@ __device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restric
         }
       }
     }
+    if (next_a < next) {   // a landed chunk's old part
+      int ok = 0;
+      if (lane == 0) ok = mbar_try_wait(&bar[next_a & 1], (parity_f2 >> (next_a & 1)) & 1u) ? 1 : 0;
+      if (__shfl_sync(FULL, ok, 0)) {
+        parity_f2 ^= 1u << (next_a & 1);
+        old_part(next_a);
+        ++next_a;
+        prog = true;
+      }
+    }
     if (next < nchunks) {   // the next chunk, once its buffer is free
       const int st = next & 1;
       bool free_buf = true;
@@ -1125,27 +1142,7 @@ __device__ __forceinline__ bool sgs_ws_loader(int nx, int ny, const T* __restric
         prog = true;
       }
     }
-    if (n_loaded < nx) {   // old values beyond the strip's last row, GN columns at a time
-      int tdone = 0;
-      if (lane == 0) tdone = lds_vol(&ctl[W::TRAIL]);
-      tdone = __shfl_sync(FULL, tdone, 0);
-      if (n_loaded + W::GN <= tdone + SGS_RING) {
-        if (lane < W::GN * NC) {
-          const int t = lane / NC, k = lane % NC, c = n_loaded + t;
-          if (c < nx) {
-            const int px = FWD ? c : nx - 1 - c;
-            const T v = __ldcg(&x[k * P + skew_pos(px, yN, nx)]);
-            const unsigned long long tg = (unsigned long long)(tag0 + (unsigned)c) << 32;
-#pragma unroll
-            for (int h = 0; h < Words<T>::N; ++h)
-              sts64_vol(ring_n + (c & (SGS_RING - 1)) * W::WPC + k * Words<T>::N + h, tg | Words<T>::get(v, h));
-          }
-        }
-        n_loaded = min(n_loaded + W::GN, nx);
-        prog = true;
-      }
-    }
-    if (next >= nchunks && n_loaded >= nx && s_loaded >= nx) break;
+    if (next >= nchunks && next_a >= nchunks && s_loaded >= nx) break;
     if (prog) {
       idle = 0;
       continue;
@@ -1180,26 +1177,28 @@ __global__ void __launch_bounds__(96, 1) k_sgs_ws(int nx, int ny, const T* __res
                                                   unsigned long long* edge, unsigned epoch, int* sticky_err,
                                                   int nstrips, int spin_limit) {
   using W = SgsWs<NC, T>;
+  using LY = SgsWsLayout<NC, T, S>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   int* ctl = reinterpret_cast<int*>(smem);
   if (threadIdx.x == 0) {
-    for (int k = 0; k < 4; ++k) mbar_init(&bar[k]);
+    for (int k = 0; k < 6; ++k) mbar_init(&bar[k]);
     ctl[W::FAIL] = 0;
     fence_proxy_async();
   }
   {   // empty ring words: a tag no column has
-    unsigned long long* ring = reinterpret_cast<unsigned long long*>(smem + 128 + 2 * sgs_stage_bytes<NC, T, S>());
-    for (int i = threadIdx.x; i < 2 * SGS_RING * W::WPC; i += blockDim.x) ring[i] = ~0ull;
+    unsigned long long* ring = reinterpret_cast<unsigned long long*>(smem + LY::OFF_R);
+    for (int i = threadIdx.x; i < SGS_RING * W::WPC; i += blockDim.x) ring[i] = ~0ull;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5;
-  unsigned parity_f = 0u, parity_e = 0u, used = 0u;   // bit st: stage st
+  // per stage st (bit st): phase parities of full (warps 0 and 2 each keep
+  // their own), afull, empty; buffers used once
+  unsigned parity_f = 0u, parity_a = 0u, parity_e = 0u, used = 0u;
   for (;;) {
     if (threadIdx.x == 0) {
       ctl[W::Q] = atomicAdd(&sync[0], 1);
       ctl[W::LEAD] = 0;
-      ctl[W::TRAIL] = 0;
       ctl[W::ISSUED] = 0;
     }
     __syncthreads();
@@ -1208,10 +1207,10 @@ __global__ void __launch_bounds__(96, 1) k_sgs_ws(int nx, int ny, const T* __res
     int waited = 0;
     if (warp == 0)
       sgs_ws_compute<NC, T, FWD, S>(nx, ny, x, edge, epoch, sync + 1, sticky_err, q, nstrips, spin_limit, smem,
-                                    parity_f, waited);
+                                    parity_f, parity_a, waited);
     else
-      sgs_ws_loader<NC, T, FWD, S>(nx, ny, blk, lu, piv, b, x, edge, epoch, sync + 1, sticky_err, q, nstrips,
-                                   spin_limit, smem, parity_e, used, warp);
+      sgs_ws_helper<NC, T, FWD, S>(nx, ny, blk, lu, piv, b, x, edge, epoch, sync + 1, sticky_err, q, nstrips,
+                                   spin_limit, smem, parity_e, parity_f, used, warp);
     __syncthreads();
     if (ctl[W::FAIL]) {
       // the bulk copies in flight land before the CTA's shared memory goes
