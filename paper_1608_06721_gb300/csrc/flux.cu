@@ -17,12 +17,43 @@ struct Prim { double h, u, v; };   // edge frame: u along +axis, v tangential
 __device__ __forceinline__ double dmin(double a, double b) { return (a < b) ? a : b; }
 __device__ __forceinline__ double dmax(double a, double b) { return (a > b) ? a : b; }
 
+// Comparisons of doubles on the integer pipe, with the results of the FP64
+// comparisons they replace (NaN operands and signed zeros included).  A GB300
+// SM issues one FP64 instruction per warp every 64 cycles, so on the cell
+// update's dependent chain every FP64 comparison costs as much as a multiply.
+// The bit patterns of doubles with a clear sign bit order like their values;
+// patterns above infinity's are NaNs.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+constexpr long long kInfBits = 0x7ff0000000000000LL;
+// x > 0.0
+__device__ __forceinline__ bool gt_zero(double x) {
+  const long long u = dbits(x);
+  return u > 0 && u <= kInfBits;
+}
+// x >= c for a positive c (not NaN)
+__device__ __forceinline__ bool ge_pos(double x, double c) {
+  const long long u = dbits(x);
+  return u >= dbits(c) && u <= kInfBits;
+}
+// x < c for a positive c (not NaN)
+__device__ __forceinline__ bool lt_pos(double x, double c) {
+  const long long u = dbits(x);
+  return u < dbits(c) && (u & 0x7fffffffffffffffLL) <= kInfBits;
+}
+// x == 0.0 (either zero)
+__device__ __forceinline__ bool is_zero(double x) { return (dbits(x) << 1) == 0; }
+// (a > b) ? a : b for a and b that are NaN or at least +0 (never -0)
+__device__ __forceinline__ double dmax_nonneg(double a, double b) {
+  const long long ua = dbits(a), ub = dbits(b);
+  return (ua > ub && ua <= kInfBits && ub <= kInfBits && ub >= 0) ? a : b;
+}
+
 // cell velocities from the conserved state: 1/h once, zero below h_eps
 // (a cell with h < h_eps is treated as dry, Remark 2.5)
 __device__ __forceinline__ Prim to_prim(double h, double qa, double qb, double h_eps) {
   Prim p;
   p.h = h;
-  if (h >= h_eps) {
+  if (ge_pos(h, h_eps)) {
     double r = 1.0 / h;
     p.u = qa * r;
     p.v = qb * r;
@@ -49,7 +80,7 @@ __device__ __forceinline__ double harten_q(double x, double ef) {
 template <int FX>
 __device__ __forceinline__ void num_flux_t(const DevLevel& L, double hl, double ul, double vl, double hr,
                                            double ur, double vr, double F[3]) {
-  if (hl == 0.0 && hr == 0.0) {
+  if (is_zero(hl) && is_zero(hr)) {
     F[0] = 0.0; F[1] = 0.0; F[2] = 0.0;
     return;
   }
@@ -80,10 +111,10 @@ __device__ __forceinline__ void num_flux_t(const DevLevel& L, double hl, double 
     F[2] = ((FL2 + FR2) - D2) * 0.5;
     return;
   } else if constexpr (FX == FX_LLF) {
-    double smax = dmax(fabs(ul) + cl, fabs(ur) + cr);
+    double smax = dmax_nonneg(fabs(ul) + cl, fabs(ur) + cr);
     // sqrt(g max(h-, h+)) equals max(sqrt(g h-), sqrt(g h+)) bit for bit:
     // scaling by g > 0 and the correctly rounded sqrt are both monotone
-    if (L.llf_wetdry) smax = smax + L.eps_r * dmax(cl, cr);
+    if (L.llf_wetdry) smax = smax + L.eps_r * dmax_nonneg(cl, cr);
     F[0] = ((FL0 + FR0) - smax * dU0) * 0.5;
     F[1] = ((FL1 + FR1) - smax * dU1) * 0.5;
     F[2] = ((FL2 + FR2) - smax * dU2) * 0.5;
@@ -93,8 +124,8 @@ __device__ __forceinline__ void num_flux_t(const DevLevel& L, double hl, double 
     const double us = ((ul + ur) * 0.5 + cl) - cr;
     const double t = (cl + cr) + (ul - ur) * 0.5;
     const double cs = fabs(t) * 0.5;
-    const double sL = (hl == 0.0) ? ur - 2.0 * cr : dmin(ul - cl, us - cs);
-    const double sR = (hr == 0.0) ? ul + 2.0 * cl : dmax(ur + cr, us + cs);
+    const double sL = is_zero(hl) ? ur - 2.0 * cr : dmin(ul - cl, us - cs);
+    const double sR = is_zero(hr) ? ul + 2.0 * cl : dmax(ur + cr, us + cs);
     if (sL >= 0.0) { F[0] = FL0; F[1] = FL1; F[2] = FL2; return; }
     if (sR <= 0.0) { F[0] = FR0; F[1] = FR1; F[2] = FR2; return; }
     const double rden = 1.0 / (sR - sL), p = sL * sR;
@@ -123,7 +154,7 @@ __device__ __forceinline__ void edge_eval(const DevLevel& L, Prim a, double za, 
                                           double out[5]) {
   const double zs = dmax(za, zb);
   const double tl = (a.h + za) - zs, tr = (b.h + zb) - zs;
-  const double hl = (tl > 0.0) ? tl : 0.0, hr = (tr > 0.0) ? tr : 0.0;
+  const double hl = gt_zero(tl) ? tl : 0.0, hr = gt_zero(tr) ? tr : 0.0;
   num_flux(L, hl, a.u, a.v, hr, b.u, b.v, out);
   out[3] = L.half_g * (hl * hl);
   out[4] = L.half_g * (hr * hr);
@@ -135,7 +166,7 @@ __device__ __forceinline__ void edge_eval_t(const DevLevel& L, Prim a, double za
                                             double out[5]) {
   const double zs = dmax(za, zb);
   const double tl = (a.h + za) - zs, tr = (b.h + zb) - zs;
-  const double hl = (tl > 0.0) ? tl : 0.0, hr = (tr > 0.0) ? tr : 0.0;
+  const double hl = gt_zero(tl) ? tl : 0.0, hr = gt_zero(tr) ? tr : 0.0;
   num_flux_t<FX>(L, hl, a.u, a.v, hr, b.u, b.v, out);
   out[3] = L.half_g * (hl * hl);
   out[4] = L.half_g * (hr * hr);
@@ -733,7 +764,7 @@ __device__ __forceinline__ void small_solve(double m[NC * NC], const double b[NC
   for (int col = 0; col < NC; ++col) {
     // the pivot row: "if (|a| > best)" over the rows below, compared on the
     // magnitudes' bit patterns (a NaN on either side compares false, as in
-    // FP64); best is the chosen entry's magnitude, the same double
+    // FP64); kb ends as the pattern of the chosen entry's magnitude
     int p = col;
     unsigned long long kb = (unsigned long long)__double_as_longlong(m[col * NC + col]) & 0x7fffffffffffffffull;
 #pragma unroll
@@ -742,7 +773,6 @@ __device__ __forceinline__ void small_solve(double m[NC * NC], const double b[NC
           (unsigned long long)__double_as_longlong(m[r * NC + col]) & 0x7fffffffffffffffull;
       if (ka <= 0x7ff0000000000000ull && kb <= 0x7ff0000000000000ull && ka > kb) { kb = ka; p = r; }
     }
-    const double best = __longlong_as_double((long long)kb);
 #pragma unroll
     for (int r = col + 1; r < NC; ++r)
       if (r == p) {
@@ -754,7 +784,7 @@ __device__ __forceinline__ void small_solve(double m[NC * NC], const double b[NC
         }
         const int t = perm[col]; perm[col] = perm[r]; perm[r] = t;
       }
-    if (!(best > tiny)) {
+    if (!(kb > (unsigned long long)dbits(tiny) && kb <= (unsigned long long)kInfBits)) {   // !(best > tiny), tiny >= +0
       sing[col] = true;
 #pragma unroll
       for (int r = col + 1; r < NC; ++r) m[r * NC + col] = 0.0;
@@ -815,7 +845,7 @@ __device__ __forceinline__ Prim pert_prim(const DevLevel& L, const double c[NC],
     if (fr) {   // curvilinear: global velocities, then the edge frame
       Prim gl;
       gl.h = c[0];
-      if (c[0] >= L.h_eps) {
+      if (ge_pos(c[0], L.h_eps)) {
         const double r = (p == 1) ? 1.0 / c[0] : rinv;
         gl.u = c[1] * r;
         gl.v = c[2] * r;
@@ -830,7 +860,7 @@ __device__ __forceinline__ Prim pert_prim(const DevLevel& L, const double c[NC],
   me.h = c[0];
   const double qa = (NC == 2) ? c[1] : (axis == 0 ? c[1] : c[NC - 1]);
   const double qb = (NC == 2) ? 0.0 : (axis == 0 ? c[NC - 1] : c[1]);
-  if (c[0] >= L.h_eps) {
+  if (ge_pos(c[0], L.h_eps)) {
     const double r = (p == 1) ? 1.0 / c[0] : rinv;
     me.u = qa * r;
     me.v = qb * r;
@@ -873,7 +903,7 @@ __device__ __forceinline__ void ghost_prologue(const DevLevel& L, const double* 
     const int i = ix + L.nx * iy;
     double c[NC];
     for (int s = 0; s < NC; ++s) c[s] = __ldcg(&U[s * n + i]);
-    const double rinv = c[0] >= L.h_eps ? 1.0 / c[0] : 0.0;
+    const double rinv = ge_pos(c[0], L.h_eps) ? 1.0 / c[0] : 0.0;
     if (p > 0) c[p - 1] = c[p - 1] + L.eps;
     Frame fr;
     const Frame* pf = frame_of<NC>(L, side_edge(L, ix, iy, sd), sd >> 1, fr);
@@ -920,7 +950,7 @@ __device__ __forceinline__ void blusgs_group(const DevLevel& L, const double* __
   double rinv = 0.0;
   Prim nb{0.0, 0.0, 0.0};
   if (act && p == 0) {
-    if (ci[0] >= L.h_eps) rinv = 1.0 / ci[0];
+    if (ge_pos(ci[0], L.h_eps)) rinv = 1.0 / ci[0];
     if (j >= 0) {
       double cj[NC];
       for (int s = 0; s < NC; ++s) cj[s] = ldU<L2>(&U[s * n + j]);
@@ -1010,11 +1040,11 @@ __device__ __forceinline__ void blusgs_group(const DevLevel& L, const double* __
   for (int s = 0; s < NC; ++s) D[s * NC + s] = D[s * NC + s] + am;
   double x[NC];
   small_solve<NC>(D, Rs, x);
-  if (ci[0] < L.h_eps)   // dry at the start: momentum stays zero (Remark 2.5)
+  if (lt_pos(ci[0], L.h_eps))   // dry at the start: momentum stays zero (Remark 2.5)
     for (int s = 1; s < NC; ++s) x[s] = 0.0;
   double un[NC];
   for (int s = 0; s < NC; ++s) un[s] = ci[s] - x[s];
-  if (un[0] < L.h_eps)
+  if (lt_pos(un[0], L.h_eps))
     for (int s = 0; s < NC; ++s) un[s] = 0.0;
   for (int s = 0; s < NC; ++s) U[s * n + i] = un[s];
 }
@@ -1316,7 +1346,7 @@ __global__ void __launch_bounds__(32) k_blusgs_lean(DevLevel L, const double* __
         Prim me;
         me.h = cp[0];
         const double qa = axis == 0 ? cp[1] : cp[2], qb = axis == 0 ? cp[2] : cp[1];
-        if (cp[0] >= L.h_eps) {
+        if (ge_pos(cp[0], L.h_eps)) {
           const double r = 1.0 / cp[0];
           me.u = qa * r;
           me.v = qb * r;
@@ -1365,10 +1395,10 @@ __global__ void __launch_bounds__(32) k_blusgs_lean(DevLevel L, const double* __
         for (int k = 0; k < NC; ++k) D[k * NC + k] = D[k * NC + k] + am;
         double x[NC];
         small_solve<NC>(D, Rs, x);
-        if (ci[0] < L.h_eps)   // dry at the start: momentum stays zero (Remark 2.5)
+        if (lt_pos(ci[0], L.h_eps))   // dry at the start: momentum stays zero (Remark 2.5)
           for (int k = 1; k < NC; ++k) x[k] = 0.0;
         for (int k = 0; k < NC; ++k) un[k] = ci[k] - x[k];
-        if (un[0] < L.h_eps)
+        if (lt_pos(un[0], L.h_eps))
           for (int k = 0; k < NC; ++k) un[k] = 0.0;
         for (int k = 0; k < NC; ++k) U[k * n + i] = un[k];
       }
