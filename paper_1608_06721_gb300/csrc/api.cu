@@ -213,7 +213,8 @@ void blusgs_half(swnmg_ctx* c, int l, double* U, int forward) {
     launch_blusgs32_strip(L, c->lv[l].z, U, reinterpret_cast<float*>(c->ghost), forward, c->blu_sync, c->sticky,
                           c->st);
   else
-    launch_blusgs_strip(L, c->lv[l].z, U, c->ghost, forward, c->blu_sync, c->sticky, c->st);
+    launch_blusgs_strip(L, c->lv[l].z, U, c->ghost, forward, c->blu_sync, c->blu_edge, ++c->blu_epoch, c->sticky,
+                        c->st);
 }
 
 // Algorithm 0 on level l of hierarchy H (lv[l].b, lv[l].x)
@@ -338,6 +339,7 @@ void free_ctx(swnmg_ctx* c) {
   if (c->sgs_sync) cudaFree(c->sgs_sync);
   if (c->sgs_edge) cudaFree(c->sgs_edge);
   if (c->blu_sync) cudaFree(c->blu_sync);
+  if (c->blu_edge) cudaFree(c->blu_edge);
   if (c->sticky) cudaFree(c->sticky);
   if (c->ghost) cudaFree(c->ghost);
   if (c->t_src) cudaFree(c->t_src);
@@ -463,6 +465,12 @@ SWNMG_API swnmg_status swnmg_create(const swnmg_problem* p, const swnmg_params* 
       goto fail_out;
     }
     ALLOC(c->blu_sync, sizeof(int) * (2 + (v0.ny + 1) / 2 + 8));   // 2-row strips
+    ALLOC(c->blu_edge, sizeof(unsigned long long) * (size_t)((v0.ny + 1) / 2) * v0.nx * 6);
+    if (cudaMemset(c->blu_edge, 0, sizeof(unsigned long long) * (size_t)((v0.ny + 1) / 2) * v0.nx * 6) !=
+        cudaSuccess) {
+      rc = fail(c, SWNMG_ERR_CUDA, "memset of the BLU-SGS hand-off words");
+      goto fail_out;
+    }
     ALLOC(c->sticky, sizeof(int));
     ALLOC(c->ghost, sizeof(double) * 4 * (size_t)std::max(v0.nx, v0.ny) * (c->nc + 1) * 3);
   }

@@ -144,8 +144,11 @@ void launch_jacobian(const DevLevel& L, const double* z, const double* U, double
 // FP32 BLU-SGS half-sweep (blusgs32.cu): Step 1 under SWNMG_PREC_MIXED_STEP1
 void launch_blusgs32_strip(const DevLevel& L, const double* z, double* U, float* gbuf, int forward, int* sync,
                            int* sticky_err, cudaStream_t st);
+// edge: tagged last-row words of the 2-row strips, (ny/2 rounded up) * nx * 6
+// entries at least, for the two-warp LLF kernel (NULL: the one-warp kernels);
+// epoch: differs from every earlier launch's on the same edge buffer
 void launch_blusgs_strip(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
-                         int* sticky_err, cudaStream_t st);
+                         unsigned long long* edge, unsigned epoch, int* sticky_err, cudaStream_t st);
 void launch_blusgs_sweep(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
                          int* sticky_err, cudaStream_t st);
 // dU strip-skewed (a level-0 multigrid iterate)

@@ -63,6 +63,10 @@ struct swnmg_ctx {
   unsigned long long* sgs_edge = nullptr;
   unsigned sgs_epoch = 0;
   int* blu_sync = nullptr;  // ticket / abort / per-strip progress of the BLU-SGS strip sweep
+  // tagged last-row words of the BLU-SGS strips (level-0 strips x nx x 6) and
+  // the epoch of the last launch that used them
+  unsigned long long* blu_edge = nullptr;
+  unsigned blu_epoch = 0;
   int* sticky = nullptr;    // set by a device wait that ran out of its bound
   double* hbuf = nullptr;   // pinned host scalars
   bool coarse_exact = false;

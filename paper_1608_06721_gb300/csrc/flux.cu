@@ -1414,6 +1414,382 @@ __global__ void __launch_bounds__(32) k_blusgs_lean(DevLevel L, const double* __
   }
 }
 
+// ---- BLU-SGS with the edge flux split between two warps (LLF, 2D uniform) ---
+// The LLF flux of eq. LLFflux between hydrostatically reconstructed states
+// splits into what each side contributes on its own (reconstructed depth,
+// celerity, momentum, the flux of that side, the wave-speed bound, the source
+// term) and their combination.  Half and llf_combine are those two parts of
+// edge_eval_t<FX_LLF> with its operations in its order, so together they give
+// its bits.
+struct Half {
+  double h, c, q, f1, f2, hv, s, src;   // h*, sqrt(g h*), h* u, q u + g/2 h*^2, q v, h* v, |u| + c, g/2 h*^2
+};
+
+// one side of the edge: state p on bed zp, zs = max of the two beds
+__device__ __forceinline__ Half llf_half(const DevLevel& L, const Prim& p, double zp, double zs) {
+  Half o;
+  const double t = (p.h + zp) - zs;
+  o.h = gt_zero(t) ? t : 0.0;
+  o.c = sqrt(L.g * o.h);
+  o.q = o.h * p.u;
+  o.src = L.half_g * (o.h * o.h);
+  o.f1 = o.q * p.u + o.src;
+  o.f2 = o.q * p.v;
+  o.hv = o.h * p.v;
+  o.s = fabs(p.u) + o.c;
+  return o;
+}
+
+// the flux from the two sides (l: the lower-index cell's side) and the cell's
+// G on the side `upper` (as edge_G)
+template <int NC>
+__device__ __forceinline__ void llf_combine(const DevLevel& L, const Half& l, const Half& r, int axis, bool upper,
+                                            double G[NC]) {
+  double o[5];
+  if (is_zero(l.h) && is_zero(r.h)) {
+    o[0] = 0.0; o[1] = 0.0; o[2] = 0.0;
+  } else {
+    const double dU0 = r.h - l.h, dU1 = r.q - l.q, dU2 = r.hv - l.hv;
+    double smax = dmax_nonneg(l.s, r.s);
+    if (L.llf_wetdry) smax = smax + L.eps_r * dmax_nonneg(l.c, r.c);
+    o[0] = ((l.q + r.q) - smax * dU0) * 0.5;
+    o[1] = ((l.f1 + r.f1) - smax * dU1) * 0.5;
+    o[2] = ((l.f2 + r.f2) - smax * dU2) * 0.5;
+  }
+  o[3] = l.src;
+  o[4] = r.src;
+  double GL[NC], GR[NC];
+  edge_G<NC>(o, axis, GL, GR);
+#pragma unroll
+  for (int k = 0; k < NC; ++k) G[k] = upper ? GL[k] : GR[k];
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bl_mbar_init(uint64_t* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool bl_mbar_try_wait(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok)
+               : "r"(smem_u32(b)), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bl_mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ int bl_ld_vol(const int* p) {
+  int v;
+  asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_tagged_g(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_tagged_g(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void bl_sts_vol(int* p, int v) {
+  asm volatile("st.volatile.shared.s32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ int bl_lds_vol(const int* p) {
+  int v;
+  asm volatile("ld.volatile.shared.s32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+
+// BLU-SGS half-sweep (Algorithm 1, Steps 1 and 2.1) on a 2D uniform mesh with
+// the LLF flux: the cell order, the operations and so the bits of
+// k_blusgs_lean, with the step's work divided between two warps.  One CTA per
+// strip of two rows in flight, 16 lanes per cell (side sd in W, E, S, N order
+// times perturbation p):
+//   warp 1 (helper), up to two steps ahead, loads the next cells' old
+//     operands and forms every edge term that does not involve a value new in
+//     this sweep: the whole G of the sides whose neighbour is old or a
+//     boundary ghost, and the cell's own half of the other sides; then it
+//     waits for the previous strip's new last-row value the first row needs
+//     and passes it on;
+//   warp 0 (critical) finishes the sides with a new neighbour (the own last
+//     result, the row below, or the passed-on value: its half of the flux and
+//     the combination), sums the sides, solves the 3x3 system and updates the
+//     cell.  On a GB300 a warp issues one FP64 instruction per 64 cycles, so
+//     the critical warp's FP64 instruction count sets the step time.
+// Hand-offs inside the CTA go through two buffers and mbarriers (bounded
+// waits); between strips the last row's new values travel as tagged 64-bit
+// words (32 bits of a value and the launch's epoch), as in the SGS kernel.
+// sync: [0] ticket, [1] abort.  edge: (strip q, column c, word w) at
+// (q * nx + c) * 6 + 2 k + h (component k, half h).
+__global__ void __launch_bounds__(64, 1) k_blusgs_ws(DevLevel L, const double* __restrict__ z, double* U,
+                                                     const double* __restrict__ gbuf, int forward, int* sync,
+                                                     unsigned long long* edge, unsigned epoch, int* sticky_err,
+                                                     int spin_limit) {
+  constexpr int NC = 3, NP = 4, GRP = 16, R = 2, NF = 16;
+  // per buffer, field, lane: kinds 0 (the critical warp supplies the new
+  // neighbour) and 2 (field 10-12: the previous strip's value): fields 0-7
+  // the cell's half, 8 max bed, 9 neighbour bed; kind 3: fields 0-2 G.
+  // Fields 13-15: the cell's old state.
+  __shared__ double rec[2][NF][32];
+  __shared__ int kind[2][32];
+  __shared__ double sv[R][GRP][NC];
+  __shared__ double ss[R][GRP];
+  __shared__ __align__(8) uint64_t bar[4];   // full[0..1] helper -> critical, empty[2..3] back
+  __shared__ int ctl[2];                      // [0] strip, [1] fail
+  const unsigned full = 0xffffffffu;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / GRP, g = lane % GRP;
+  const int sd = g / NP, p = g % NP;
+  const int axis = sd >> 1, upper = sd & 1;
+  const int role = forward ? sd : (sd ^ 1);   // 0 previous column, 1 next column, 2 previous row, 3 next row
+  const bool newside = (role & 1) == 0;       // neighbour updated earlier in this sweep
+  const long long n = L.n;
+  const int nstrips = (L.ny + R - 1) / R;
+  const int glen = L.nx > L.ny ? L.nx : L.ny;
+  const double len = axis == 0 ? L.ex : L.ey;
+  const int src0 = lane - p;                  // the side's p = 0 lane
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) bl_mbar_init(&bar[k]);
+    ctl[1] = 0;
+  }
+  __syncthreads();
+  unsigned pf = 0u, pe = 0u, used = 0u;   // per buffer (bit b): full parity, empty parity, written once
+  for (;;) {
+    if (threadIdx.x == 0) ctl[0] = atomicAdd(&sync[0], 1);
+    __syncthreads();
+    const int q = ctl[0];
+    if (q >= nstrips) return;
+    const int rows = (L.ny - q * R < R) ? L.ny - q * R : R;
+    const int nsteps = L.nx + rows - 1;
+    const int rr = q * R + grp;
+    const bool row_ok = grp < rows;
+    const int iy = forward ? rr : L.ny - 1 - rr;
+    const bool has_py = rr > 0, has_ny = rr < L.ny - 1;
+    bool failed = false, timeout = false;
+    if (warp == 1) {
+      // ---- helper: records of steps 0 .. nsteps-1 ----
+      const bool south = q > 0 && has_py;   // the first row's previous-row neighbour is in strip q - 1
+      for (int t = 0; t < nsteps && !failed; ++t) {
+        const int b = t & 1;
+        if ((used >> b) & 1u) {   // the critical warp is done with step t - 2
+          for (int it = 0;; ++it) {
+            int ok = 0;
+            if (lane == 0) ok = bl_mbar_try_wait(&bar[2 + b], (pe >> b) & 1u) ? 1 : 0;
+            if (__shfl_sync(full, ok, 0)) break;
+            int f = 0;
+            if (lane == 0) f = bl_lds_vol(&ctl[1]);
+            if (__shfl_sync(full, f, 0)) { failed = true; break; }
+            if (it + 1 >= spin_limit) { failed = timeout = true; break; }
+          }
+          if (failed) break;
+          pe ^= 1u << b;
+        }
+        used |= 1u << b;
+        const int c = t - grp;
+        const bool act = row_ok && c >= 0 && c < L.nx;
+        int kd = 3;
+        if (act) {
+          const int ix = forward ? c : L.nx - 1 - c;
+          const int i = ix + L.nx * iy;
+          double ci[NC];
+          for (int k = 0; k < NC; ++k) ci[k] = __ldcg(&U[k * n + i]);
+          const double zi = z[i];
+          const bool has = role == 0 ? c > 0 : role == 1 ? c < L.nx - 1 : role == 2 ? has_py : has_ny;
+          const int j = sd == 0 ? i - 1 : sd == 1 ? i + 1 : sd == 2 ? i - L.nx : i + L.nx;
+          const double zo = has ? z[j] : zi;
+          // this lane's perturbation of the cell (component p - 1 by eps)
+          double cp[NC];
+          for (int k = 0; k < NC; ++k) cp[k] = (k == p - 1) ? ci[k] + L.eps : ci[k];
+          Prim me;
+          me.h = cp[0];
+          const double qa = axis == 0 ? cp[1] : cp[2], qb = axis == 0 ? cp[2] : cp[1];
+          if (ge_pos(cp[0], L.h_eps)) {
+            const double r = 1.0 / cp[0];
+            me.u = qa * r;
+            me.v = qb * r;
+          } else {
+            me.u = 0.0;
+            me.v = 0.0;
+          }
+          const double za = upper ? zi : zo, zb = upper ? zo : zi;
+          const double zs = dmax(za, zb);
+          const Half mh = llf_half(L, me, zi, zs);
+          if (!has || !newside) {   // an old neighbour or a boundary ghost: the whole G here
+            Prim other;
+            if (has) {
+              double cj[NC];
+              for (int k = 0; k < NC; ++k) cj[k] = __ldcg(&U[k * n + j]);
+              other = to_prim(cj[0], axis == 0 ? cj[1] : cj[2], axis == 0 ? cj[2] : cj[1], L.h_eps);
+            } else {   // precomputed by ghost_prologue
+              const long long t3 = ((long long)(sd * glen + (sd < 2 ? iy : ix)) * NP + p) * 3;
+              other.h = __ldcg(&gbuf[t3]);
+              other.u = __ldcg(&gbuf[t3 + 1]);
+              other.v = __ldcg(&gbuf[t3 + 2]);
+            }
+            const Half oh = llf_half(L, other, zo, zs);
+            double G[NC];
+            llf_combine<NC>(L, upper ? mh : oh, upper ? oh : mh, axis, upper, G);
+            for (int k = 0; k < NC; ++k) rec[b][k][lane] = G[k];
+          } else {
+            kd = (role == 2 && grp == 0) ? 2 : 0;
+            rec[b][0][lane] = mh.h;
+            rec[b][1][lane] = mh.c;
+            rec[b][2][lane] = mh.q;
+            rec[b][3][lane] = mh.f1;
+            rec[b][4][lane] = mh.f2;
+            rec[b][5][lane] = mh.hv;
+            rec[b][6][lane] = mh.s;
+            rec[b][7][lane] = mh.src;
+            rec[b][8][lane] = zs;
+            rec[b][9][lane] = zo;
+          }
+          for (int k = 0; k < NC; ++k) rec[b][13 + k][lane] = ci[k];
+        }
+        kind[b][lane] = kd;
+        // the previous strip's new value of column c for the first row, once
+        // all six words carry this launch's epoch
+        if (south && t < L.nx) {
+          double sval[NC];
+          for (int it = 0;; ++it) {
+            unsigned long long w = 0ull;
+            if (lane < 6) w = ld_tagged_g(edge + ((long long)(q - 1) * L.nx + t) * 6 + lane);
+            const bool ok = lane >= 6 || (unsigned)(w >> 32) == epoch;
+            const unsigned lo = __shfl_sync(full, (unsigned)w, 0), hi0 = __shfl_sync(full, (unsigned)w, 1);
+            const unsigned lo1 = __shfl_sync(full, (unsigned)w, 2), hi1 = __shfl_sync(full, (unsigned)w, 3);
+            const unsigned lo2 = __shfl_sync(full, (unsigned)w, 4), hi2 = __shfl_sync(full, (unsigned)w, 5);
+            if (__all_sync(full, ok)) {
+              sval[0] = __longlong_as_double((long long)(((unsigned long long)hi0 << 32) | lo));
+              sval[1] = __longlong_as_double((long long)(((unsigned long long)hi1 << 32) | lo1));
+              sval[2] = __longlong_as_double((long long)(((unsigned long long)hi2 << 32) | lo2));
+              break;
+            }
+            if ((it & 63) == 63) {
+              int f = 0;
+              if (lane == 0) f = bl_lds_vol(&ctl[1]) || bl_ld_vol(sync + 1);
+              if (__shfl_sync(full, f, 0)) { failed = true; break; }
+            }
+            if (it + 1 >= spin_limit) { failed = timeout = true; break; }
+          }
+          if (failed) break;
+          if (kd == 2)
+            for (int k = 0; k < NC; ++k) rec[b][10 + k][lane] = sval[k];
+        }
+        __syncwarp();
+        if (lane == 0) bl_mbar_arrive(&bar[b]);
+      }
+    } else {
+      // ---- critical: the cell updates of steps 0 .. nsteps-1 ----
+      double prevx[NC] = {0.0, 0.0, 0.0};   // the group's last result (new)
+      for (int t = 0; t < nsteps; ++t) {
+        const int b = t & 1;
+        for (int it = 0;; ++it) {   // step t's record
+          if (__all_sync(full, bl_mbar_try_wait(&bar[b], (pf >> b) & 1u))) break;
+          int f = 0;
+          if (lane == 0) f = bl_lds_vol(&ctl[1]);
+          if (__shfl_sync(full, f, 0)) { failed = true; break; }
+          if (it + 1 >= spin_limit) { failed = timeout = true; break; }
+        }
+        if (failed) break;
+        pf ^= 1u << b;
+        const int c = t - grp;
+        const bool act = row_ok && c >= 0 && c < L.nx;
+        const int kd = kind[b][lane];
+        double f8[8], zs = 0.0, zo = 0.0, sn[NC], ci[NC];
+        for (int e = 0; e < 8; ++e) f8[e] = rec[b][e][lane];
+        if (kd != 3) {
+          zs = rec[b][8][lane];
+          zo = rec[b][9][lane];
+        }
+        for (int k = 0; k < NC; ++k) {
+          sn[k] = kd == 2 ? rec[b][10 + k][lane] : 0.0;
+          ci[k] = rec[b][13 + k][lane];
+        }
+        __syncwarp();
+        if (lane == 0) bl_mbar_arrive(&bar[2 + b]);   // the record goes back to the helper
+        // the previous row's new values: the group below
+        double py[NC];
+        for (int k = 0; k < NC; ++k) py[k] = __shfl_up_sync(full, prevx[k], GRP);
+        double G[NC] = {0.0, 0.0, 0.0};
+        if (act) {
+          if (kd == 3) {
+            for (int k = 0; k < NC; ++k) G[k] = f8[k];
+          } else {   // a new neighbour: its half and the combination
+            double cn[NC];
+            for (int k = 0; k < NC; ++k) cn[k] = kd == 2 ? sn[k] : (role == 0 ? prevx[k] : py[k]);
+            const Prim other = to_prim(cn[0], axis == 0 ? cn[1] : cn[2], axis == 0 ? cn[2] : cn[1], L.h_eps);
+            const Half oh = llf_half(L, other, zo, zs);
+            Half mh;
+            mh.h = f8[0]; mh.c = f8[1]; mh.q = f8[2]; mh.f1 = f8[3];
+            mh.f2 = f8[4]; mh.hv = f8[5]; mh.s = f8[6]; mh.src = f8[7];
+            llf_combine<NC>(L, upper ? mh : oh, upper ? oh : mh, axis, upper, G);
+          }
+        }
+        // p = 0 lanes hold |e| G, p = k+1 lanes column k of |e| dG/dU_i
+        for (int k = 0; k < NC; ++k) {
+          const double gb = __shfl_sync(full, G[k], src0);
+          sv[grp][g][k] = (p == 0) ? len * G[k] : len * ((G[k] - gb) * L.reps);
+        }
+        __syncwarp();
+        if (g < NC * NP) {   // entry (component g / NP, perturbation g % NP): sides in W, E, S, N order
+          const int es = g / NP, ep = g % NP;
+          double acc = 0.0;
+          for (int qs = 0; qs < 4; ++qs) acc = acc + sv[grp][qs * NP + ep][es];
+          ss[grp][g] = acc;
+        }
+        __syncwarp();
+        double un[NC] = {0.0, 0.0, 0.0};
+        if (act && g == 0) {
+          const int ix = forward ? c : L.nx - 1 - c;
+          const int i = ix + L.nx * iy;
+          double Rs[NC], D[NC * NC];
+          for (int k = 0; k < NC; ++k) {
+            Rs[k] = ss[grp][k * NP];
+            for (int pp = 1; pp < NP; ++pp) D[k * NC + (pp - 1)] = ss[grp][k * NP + pp];
+          }
+          if (L.t_ka > 0.0) {   // time step (Remark 2.6): the step's residual and diagonal block
+            const double ka = tka(L, i);
+            for (int k = 0; k < NC; ++k) Rs[k] = (L.t_omb * Rs[k] + ka * ci[k]) - L.t_src[k * n + i];
+            for (int e = 0; e < NC * NC; ++e) D[e] = L.t_omb * D[e];
+            for (int k = 0; k < NC; ++k) D[k * NC + k] = D[k * NC + k] + ka;
+          }
+          double m = fabs(Rs[0]) + fabs(Rs[1]);
+          m = m + fabs(Rs[2]);
+          const double am = L.alpha * m;
+          for (int k = 0; k < NC; ++k) D[k * NC + k] = D[k * NC + k] + am;
+          double x[NC];
+          small_solve<NC>(D, Rs, x);
+          if (lt_pos(ci[0], L.h_eps))   // dry at the start: momentum stays zero (Remark 2.5)
+            for (int k = 1; k < NC; ++k) x[k] = 0.0;
+          for (int k = 0; k < NC; ++k) un[k] = ci[k] - x[k];
+          if (lt_pos(un[0], L.h_eps))
+            for (int k = 0; k < NC; ++k) un[k] = 0.0;
+          for (int k = 0; k < NC; ++k) U[k * n + i] = un[k];
+          if (grp == rows - 1 && q + 1 < nstrips) {   // the last row's new value for the next strip, tagged
+            unsigned long long* e = edge + ((long long)q * L.nx + c) * 6;
+            for (int k = 0; k < NC; ++k) {
+              const unsigned long long u = (unsigned long long)__double_as_longlong(un[k]);
+              st_tagged_g(e + 2 * k, ((unsigned long long)epoch << 32) | (u & 0xffffffffull));
+              st_tagged_g(e + 2 * k + 1, ((unsigned long long)epoch << 32) | (u >> 32));
+            }
+          }
+        }
+        for (int k = 0; k < NC; ++k) {
+          const double v = __shfl_sync(full, un[k], grp * GRP);
+          if (act) prevx[k] = v;
+        }
+      }
+    }
+    if (failed && lane == 0) {
+      if (timeout) atomicOr(sticky_err, 1);
+      bl_sts_vol(&ctl[1], 1);
+      st_rel(sync + 1, 1);
+    }
+    __syncthreads();
+    if (ctl[1]) return;
+  }
+}
+
 // ---- adjoint: lambda^T dR/dz and lambda^T dR/dq --------------------------------
 // Central differences (step delta) of the edge terms with respect to the bed of
 // either cell, contracted with lambda of both cells: cz[e] for the left cell's
@@ -1893,7 +2269,7 @@ void launch_jacobian(const DevLevel& L, const double* z, const double* U, double
 // strip-pipelined half-sweep: ghosts, then one warp per strip in flight;
 // sync holds 2 + ceil(ny / R) ints, R = 2 (2D) or 4 (1D) rows per strip
 void launch_blusgs_strip(const DevLevel& L, const double* z, double* U, double* gbuf, int forward, int* sync,
-                         int* sticky_err, cudaStream_t st) {
+                         unsigned long long* edge, unsigned epoch, int* sticky_err, cudaStream_t st) {
   count_launches(2);
   static int nsm = 0;
   if (nsm == 0) {
@@ -1912,7 +2288,9 @@ void launch_blusgs_strip(const DevLevel& L, const double* z, double* U, double* 
   const int spin = wait_limit();
   if (L.nc == 3 && L.geo == nullptr) {   // 2D uniform mesh: the lean kernel, flux fixed at compile time
     k_ghost_prologue<3, 4><<<gblocks, 128, 0, st>>>(L, U, gbuf);
-    if (L.flux == FX_LLF) k_blusgs_lean<FX_LLF><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
+    if (L.flux == FX_LLF && edge)   // the two-warp kernel
+      k_blusgs_ws<<<grid, 64, 0, st>>>(L, z, U, gbuf, forward, sync, edge, epoch, sticky_err, spin);
+    else if (L.flux == FX_LLF) k_blusgs_lean<FX_LLF><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
     else if (L.flux == FX_HLLC) k_blusgs_lean<FX_HLLC><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
     else if (L.flux == FX_ROE) k_blusgs_lean<FX_ROE><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
     else k_blusgs_lean<FX_HLL><<<grid, 32, 0, st>>>(L, z, U, gbuf, forward, sync, sticky_err, spin);
