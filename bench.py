@@ -135,15 +135,18 @@ def peaks():
 # divisions and square roots: the method's work as the GPU executes it,
 # compared against the measured FP64 lane instruction rate (swnmg_fp64_rate).
 # The fused tile kernels evaluate a tile's border edges twice (+8 %) and the
-# lean BLU-SGS lanes compute their own reciprocals (+6 %); that extra work is
-# not counted.  The SGS classes are HBM-bound kernels whose algorithmic bytes
-# per cell come from the operator layout (below).
+# two-warp BLU-SGS kernel forms the cell's half of a new-side edge term in one
+# warp and the combination in the other; that extra work is not counted.
+# The SGS classes are HBM-bound kernels whose algorithmic bytes per cell come
+# from the operator layout (below).
 # TRAFFIC_PER_CELL: dram__bytes_read.sum + dram__bytes_write.sum of the
-# current kernels (k_res_tile, k_jac_tile, k_blusgs_lean, k_sgs_strip); at
+# current kernels (k_res_tile, k_jac_tile, k_blusgs_ws, k_sgs_ws); at
 # 512 x 512 their outputs stay in the 126 MB L2, so the writes are not seen.
+# The BLU-SGS figure includes the tagged words the strips hand on (48 bytes
+# per column of a two-row strip, written and read back).
 FP64_PER_CELL = {"residual": 181.1, "jacobian": 1380.5, "blusgs": 1485.8, "blusgs_coarse": 1485.8}
-TRAFFIC_PER_CELL = {"residual": 32.3, "jacobian": 74.6, "blusgs": 37.9, "blusgs_coarse": 37.9,
-                    "sgs_fine": 217.7, "sgs_coarse": 217.7}
+TRAFFIC_PER_CELL = {"residual": 32.3, "jacobian": 76.3, "blusgs": 61.0, "blusgs_coarse": 61.0,
+                    "sgs_fine": 218.5, "sgs_coarse": 218.5}
 # the kernels of these classes are unchanged since the captures above
 TRAFFIC_CURRENT = {"residual", "jacobian", "blusgs", "blusgs_coarse", "sgs_fine", "sgs_coarse"}
 
