@@ -751,16 +751,10 @@ __device__ __forceinline__ int ldg_vol(const int* p) {
   asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_tagged(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 __device__ __forceinline__ unsigned long long ld_tagged(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // 32-bit pieces of a value: one for float, two (low, high) for double
@@ -1430,16 +1424,30 @@ __device__ __forceinline__ void coarse_inverse_cta(int nx, int ny, const T* __re
   __syncthreads();
   const T tiny = T(1e-14) * s_amax[0];
   for (int c = 0; c < m; ++c) {
-    if (threadIdx.x == 0) {
-      int p = c;
-      T best = tabs(aug[(long long)c * w + c]);
-      for (int r = c + 1; r < m; ++r) {
+    if (threadIdx.x < 32) {
+      // the pivot row of the scan "if (|a| > best)" from row c down, by the
+      // first warp: each lane scans every 32nd row, then the largest value
+      // wins, the lower row on ties (the first one the scan meets); NaN
+      // entries never win, and a NaN in row c keeps the scan there
+      const int ln = (int)threadIdx.x;
+      T best = T(-1);
+      int p = m;
+      for (int r = c + ln; r < m; r += 32) {
         const T v = tabs(aug[(long long)r * w + c]);
         if (v > best) { best = v; p = r; }
       }
-      s_p = p;
-      s_sing = !(best > tiny);
-      if (s_sing) sing[c] = 1;
+      for (int off = 16; off > 0; off >>= 1) {
+        const T ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int op = __shfl_down_sync(0xffffffffu, p, off);
+        if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
+      }
+      if (ln == 0) {
+        const T d = tabs(aug[(long long)c * w + c]);
+        if (d != d) { best = d; p = c; }
+        s_p = p;
+        s_sing = !(best > tiny);
+        if (s_sing) sing[c] = 1;
+      }
     }
     __syncthreads();
     const int p = s_p;
@@ -1456,10 +1464,13 @@ __device__ __forceinline__ void coarse_inverse_cta(int nx, int ny, const T* __re
       const T piv = aug[(long long)c * w + c];
       for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) aug[(long long)r * w + c] /= piv;
       __syncthreads();
-      const int rows = m - c - 1, cols = w - c - 1;
-      for (long long e = threadIdx.x; e < (long long)rows * cols; e += blockDim.x) {
-        const int r = c + 1 + (int)(e / cols), k = c + 1 + (int)(e % cols);
-        aug[(long long)r * w + k] -= aug[(long long)r * w + c] * aug[(long long)c * w + k];
+      // a warp per row, its lanes along the row (no index division)
+      const int nwarps = (int)(blockDim.x >> 5), wid = (int)(threadIdx.x >> 5), ln = (int)(threadIdx.x & 31);
+      const T* prow = aug + (long long)c * w;
+      for (int r = c + 1 + wid; r < m; r += nwarps) {
+        T* row = aug + (long long)r * w;
+        const T l = row[c];
+        for (int k = c + 1 + ln; k < w; k += 32) row[k] -= l * prow[k];
       }
     }
     __syncthreads();
