@@ -297,6 +297,40 @@ __global__ void k_restrict(int dim, int nxf, int nyf, const T* __restrict__ blk,
   if (I < (nxf / 2) * (dim == 2 ? nyf / 2 : 1)) restrict_cell<NC, T>(dim, nxf, nyf, blk, b, x, bc, I);
 }
 
+// restrict_cell in 2D with a lane per child: lane 4 I + q forms child q's
+// residual, lane 4 I sums the four in child order (the same operations)
+template <int NC, typename T>
+__global__ void k_restrict4(int nxf, int nyf, const T* __restrict__ blk, const T* __restrict__ b,
+                            const T* __restrict__ x, T* __restrict__ bc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nxc = nxf / 2, nyc = nyf / 2;
+  const int I = t >> 2, q = t & 3;
+  const bool ok = I < nxc * nyc;
+  T r[NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) r[s] = T(0);
+  if (ok) {
+    const int Ix = I % nxc, Iy = I / nxc;
+    const int ch = 2 * Ix + nxf * 2 * Iy + (q & 1) + (q >> 1) * nxf;   // children 00, 10, 01, 11
+    lin_resid<NC, T>(2, nxf, nyf, blk, b, x, ch, r);
+  }
+  T acc[NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    const T r1 = __shfl_down_sync(0xffffffffu, r[s], 1), r2 = __shfl_down_sync(0xffffffffu, r[s], 2),
+            r3 = __shfl_down_sync(0xffffffffu, r[s], 3);
+    acc[s] = r[s];
+    acc[s] = acc[s] + r1;
+    acc[s] = acc[s] + r2;
+    acc[s] = acc[s] + r3;
+  }
+  if (ok && q == 0) {
+    const long long Pc = skew_slots(nxc, nyc), sc = skew_pos(I % nxc, I / nxc, nxc);
+#pragma unroll
+    for (int s = 0; s < NC; ++s) bc[(long long)s * Pc + sc] = acc[s];
+  }
+}
+
 // x_j += x_I for every child j of I  (eq. correction, piecewise constant)
 template <typename T>
 __device__ __forceinline__ void prolong_cell(int dim, int nc, int nxf, int nyf, const T* __restrict__ xc,
@@ -1844,6 +1878,16 @@ void launch_restrict(int dim, int nc, int nxf, int nyf, const void* blk, const v
   count_launches(1);
   const int ncc = (nxf / 2) * (dim == 2 ? nyf / 2 : 1);
   const int g = nblk(ncc, 128);
+  if (dim == 2) {   // a lane per child
+    const int g4 = nblk(4LL * ncc, 128);
+    if (nc == 3) {
+      if (fp32) k_restrict4<3, float><<<g4, 128, 0, st>>>(nxf, nyf, (const float*)blk, (const float*)b,
+                                                          (const float*)x, (float*)bcoarse);
+      else k_restrict4<3, double><<<g4, 128, 0, st>>>(nxf, nyf, (const double*)blk, (const double*)b,
+                                                      (const double*)x, (double*)bcoarse);
+      return;
+    }
+  }
 #define RL(NC, T) k_restrict<NC, T><<<g, 128, 0, st>>>(dim, nxf, nyf, (const T*)blk, (const T*)b, \
                                                         (const T*)x, (T*)bcoarse)
   if (nc == 3) { if (fp32) RL(3, float); else RL(3, double); }
