@@ -1028,7 +1028,7 @@ __device__ __forceinline__ void blusgs_group(const DevLevel& L, const double* __
       else D[s * NC + (pp - 1)] = t;
     }
   if (!cell_ok || g != 0) return;
-  if (L.t_ka > 0.0) {   // time step (Remark 2.6): the step's residual and diagonal block
+  if (gt_zero(L.t_ka)) {   // time step (Remark 2.6): the step's residual and diagonal block
     const double ka = tka(L, i);
     for (int s = 0; s < NC; ++s) Rs[s] = (L.t_omb * Rs[s] + ka * ci[s]) - L.t_src[s * n + i];
     for (int e = 0; e < NC * NC; ++e) D[e] = L.t_omb * D[e];
@@ -1366,7 +1366,7 @@ __global__ void __launch_bounds__(32) k_blusgs_lean(DevLevel L, const double* __
       // p = 0 lanes hold |e| G, p = k+1 lanes column k of |e| dG/dU_i
       for (int k = 0; k < NC; ++k) {
         const double gb = __shfl_sync(full, G[k], src0);
-        sv[grp][g][k] = (p == 0) ? len * G[k] : len * ((G[k] - gb) * L.reps);
+        sv[grp][g][k] = len * ((p == 0) ? G[k] : (G[k] - gb) * L.reps);   // |e| G, or |e| (G - G_0) / eps
       }
       __syncwarp();
       if (g < NC * NP) {   // entry (component g / NP, perturbation g % NP): sides in W, E, S, N order
@@ -1383,7 +1383,7 @@ __global__ void __launch_bounds__(32) k_blusgs_lean(DevLevel L, const double* __
           Rs[k] = ss[grp][k * NP];
           for (int pp = 1; pp < NP; ++pp) D[k * NC + (pp - 1)] = ss[grp][k * NP + pp];
         }
-        if (L.t_ka > 0.0) {   // time step (Remark 2.6): the step's residual and diagonal block
+        if (gt_zero(L.t_ka)) {   // time step (Remark 2.6): the step's residual and diagonal block
           const double ka = tka(L, i);
           for (int k = 0; k < NC; ++k) Rs[k] = (L.t_omb * Rs[k] + ka * ci[k]) - L.t_src[k * n + i];
           for (int e = 0; e < NC * NC; ++e) D[e] = L.t_omb * D[e];
@@ -1728,7 +1728,7 @@ __global__ void __launch_bounds__(64, 1) k_blusgs_ws(DevLevel L, const double* _
         // p = 0 lanes hold |e| G, p = k+1 lanes column k of |e| dG/dU_i
         for (int k = 0; k < NC; ++k) {
           const double gb = __shfl_sync(full, G[k], src0);
-          sv[grp][g][k] = (p == 0) ? len * G[k] : len * ((G[k] - gb) * L.reps);
+          sv[grp][g][k] = len * ((p == 0) ? G[k] : (G[k] - gb) * L.reps);   // |e| G, or |e| (G - G_0) / eps
         }
         __syncwarp();
         if (g < NC * NP) {   // entry (component g / NP, perturbation g % NP): sides in W, E, S, N order
@@ -1747,7 +1747,7 @@ __global__ void __launch_bounds__(64, 1) k_blusgs_ws(DevLevel L, const double* _
             Rs[k] = ss[grp][k * NP];
             for (int pp = 1; pp < NP; ++pp) D[k * NC + (pp - 1)] = ss[grp][k * NP + pp];
           }
-          if (L.t_ka > 0.0) {   // time step (Remark 2.6): the step's residual and diagonal block
+          if (gt_zero(L.t_ka)) {   // time step (Remark 2.6): the step's residual and diagonal block
             const double ka = tka(L, i);
             for (int k = 0; k < NC; ++k) Rs[k] = (L.t_omb * Rs[k] + ka * ci[k]) - L.t_src[k * n + i];
             for (int e = 0; e < NC * NC; ++e) D[e] = L.t_omb * D[e];

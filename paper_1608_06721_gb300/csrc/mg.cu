@@ -1516,6 +1516,7 @@ __device__ __forceinline__ void coarse_inverse_cta(int nx, int ny, const T* __re
       if (sing[r]) v = T(0);
       else {
         T acc = aug[(long long)r * w + m + jcol];
+#pragma unroll 8
         for (int k = r + 1; k < m; ++k) acc -= aug[(long long)r * w + k] * X[(long long)jcol * m + k];
         v = acc / aug[(long long)r * w + r];
       }
@@ -1547,7 +1548,8 @@ __device__ __forceinline__ void coarse_apply_block(int nx, int ny, const T* __re
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= m) return;
   T acc = T(0);
-  for (int jcol = 0; jcol < m; ++jcol) acc += X[(long long)jcol * m + u] * sb[jcol];
+#pragma unroll 16
+  for (int jcol = 0; jcol < m; ++jcol) acc += X[(long long)jcol * m + u] * sb[jcol];   // in column order
   const int cell = u / NC;
   x[(long long)(u % NC) * P + skew_pos(cell % nx, cell / nx, nx)] = acc;
 }
