@@ -191,13 +191,20 @@ swnmg_status level_residual_sum(swnmg_ctx* c, int l, const double* U, double* ou
   return device_sum(c, c->rn, L.n, out);
 }
 
+// the epoch of the next launch that hands values between strips through tagged
+// words: never 0, the tag of the zero-filled words before the first launch
+unsigned next_epoch(unsigned& e) {
+  if (++e == 0u) e = 1u;
+  return e;
+}
+
 // one block SGS half-sweep of level l in the order the parameters select
 void sgs_launch(swnmg_ctx* c, const Level& v, int fp32, int forward) {
   if (c->prm.smoother == SWNMG_SMOOTH_COLOUR)
     launch_sgs_colour_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward, fp32, c->st);
   else
     launch_sgs_sweep(c->nc, v.nx, v.ny, v.blk, v.lu, v.piv, v.b, v.x, forward, fp32, c->sgs_sync, c->sgs_edge,
-                     ++c->sgs_epoch, c->sticky, c->st);
+                     next_epoch(c->sgs_epoch), c->sticky, c->st);
 }
 
 void sgs_half(swnmg_ctx* c, const Hier& H, int l, int forward) {
@@ -213,8 +220,8 @@ void blusgs_half(swnmg_ctx* c, int l, double* U, int forward) {
     launch_blusgs32_strip(L, c->lv[l].z, U, reinterpret_cast<float*>(c->ghost), forward, c->blu_sync, c->sticky,
                           c->st);
   else
-    launch_blusgs_strip(L, c->lv[l].z, U, c->ghost, forward, c->blu_sync, c->blu_edge, ++c->blu_epoch, c->sticky,
-                        c->st);
+    launch_blusgs_strip(L, c->lv[l].z, U, c->ghost, forward, c->blu_sync, c->blu_edge, next_epoch(c->blu_epoch),
+                        c->sticky, c->st);
 }
 
 // Algorithm 0 on level l of hierarchy H (lv[l].b, lv[l].x)
